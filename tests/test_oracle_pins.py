@@ -1,0 +1,453 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it pins and the mistake it would catch.  None of
+them re-runs the oracle's own formula as the expected value: expectations come
+from the paper's printed numbers (tests/golden/paper_values.json), from closed
+forms checked against an independent ODE integration (scipy), from invariants,
+limits and continuity, from the heat equation the moving source must satisfy,
+or from convergence under dt-halving.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from workloads import Grid, HeatSource, NEVER
+
+P = orc.params()
+
+
+# ----------------------------------------------------------------- constants
+def test_defaults_are_the_paper_tables(golden):
+    """Tables 1-3, T_reg (Sec. 2.2), the App. A exit threshold."""
+    t2, t3 = golden["table2_micro"], golden["table3_diffusion"]
+    for k in ("T_as_start", "T_as_end", "T_am_start", "T_inf", "k_alpha_eq", "k_am_eq", "T_s", "T_l"):
+        assert orc.DEFAULTS[k] == t2[k], k
+    for k in ("c_as", "c_b", "k1", "k2", "k3", "f"):
+        assert orc.DEFAULTS[k] == t3[k], k
+    assert orc.DEFAULTS["T_reg"] == golden["T_reg"]["value"]
+    assert orc.DEFAULTS["init_exit"] == golden["init_exit"]["value"]
+
+
+# ------------------------------------------------------------- equilibria
+def test_equilibria_sum_at_T_inf(golden):
+    """Sec. 2.2 prints that X_alpha^eq + X_am,0^eq = 1.8 at T = T_inf (catches a
+    wrong branch, sign or constant in either equilibrium)."""
+    s = orc.xalpha_eq(293.0) + orc.xam0_eq(293.0)
+    assert abs(s - golden["equilibria_sum_at_T_inf"]["value"]) < 1e-3
+
+
+def test_xalpha_eq_shape():
+    """eq:equilibrium_phase_as: 0.9 below T_as,end, 0 above T_as,start,
+    continuous at T_as,start, monotone, and within 5e-4 of 0.9 at T_as,end
+    (the Table 2 constants make the branches meet; a swapped constant or
+    sign breaks this)."""
+    T = np.linspace(200, 2000, 3601)
+    x = orc.xalpha_eq(T)
+    assert np.all((x >= 0) & (x <= 0.9))
+    assert np.all(np.diff(x) <= 1e-15)
+    assert orc.xalpha_eq(1273.0 - 1e-9) < 1e-10 and orc.xalpha_eq(1273.5) == 0.0
+    assert orc.xalpha_eq(934.999) == 0.9
+    assert abs(orc.xalpha_eq(935.0) - 0.9) < 5e-4
+    # Koistinen-Marburger law: ln(1 - X) linear in T with slope k_alpha_eq (Table 2)
+    Tm = np.linspace(950, 1250, 7)
+    slope = np.diff(np.log(1 - orc.xalpha_eq(Tm))) / np.diff(Tm)
+    assert np.allclose(slope, P[orc.PARAM_NAMES.index("k_alpha_eq")], rtol=1e-9)
+
+
+def test_xam0_eq_shape():
+    """eq:equilibrium_phase_am0 (reading A1): 0 above T_am,start, continuous
+    there, monotone, ~0.9 at T_inf, capped at 0.9 (A2)."""
+    T = np.linspace(200, 1500, 2601)
+    x = orc.xam0_eq(T)
+    assert np.all((x >= 0) & (x <= 0.9))
+    assert np.all(np.diff(x) <= 1e-15)
+    assert orc.xam0_eq(848.0) == 0.0 and orc.xam0_eq(847.9999) < 1e-5
+    assert orc.xam0_eq(900.0) == 0.0 and orc.xam0_eq(1200.0) == 0.0  # A1: not only above T_as,start
+    assert abs(orc.xam0_eq(293.5) - 0.9) < 2e-3
+    Tm = np.linspace(400, 800, 5)
+    slope = np.diff(np.log(1 - orc.xam0_eq(Tm))) / np.diff(Tm)
+    assert np.allclose(slope, P[orc.PARAM_NAMES.index("k_am_eq")], rtol=1e-9)
+
+
+def test_xam_eq_respects_alpha_bound(golden):
+    """eq:equilibrium_phase_am: X_as + X_am^eq <= 0.9 for every T and X_as."""
+    for T in np.linspace(250, 900, 27):
+        for xas in np.linspace(0, 0.9, 19):
+            assert xas + orc.xam_eq(T, xas) <= golden["alpha_max"]["value"] + 1e-12
+
+
+def test_rate_constant_sigmoid():
+    """k_as(T) = k1 / (1 + exp(-k3 (T - k2))): midpoint k1/2 at k2, limits 0 and k1,
+    slope k1 k3 / 4 at k2."""
+    assert abs(orc.k_alpha_s(850.0) - 0.294 / 2) < 1e-15
+    assert orc.k_alpha_s(5000.0) == pytest.approx(0.294, rel=1e-12)
+    assert orc.k_alpha_s(100.0) < 1e-10
+    h = 1e-3
+    slope = (orc.k_alpha_s(850 + h) - orc.k_alpha_s(850 - h)) / (2 * h)
+    assert slope == pytest.approx(0.294 * 0.0337 / 4, rel=1e-6)
+
+
+# -------------------------------------------------- generalised logistic ODE
+def closed_form(t, D, k, c, X0=0.0):
+    """X(t) of dX/dt = k X^((c-1)/c) (D - X)^((c+1)/c), i.e. of
+    dxi/dt = D k xi^((c-1)/c) (1-xi)^((c+1)/c) with xi = X / D:
+    (xi/(1-xi))^(1/c) grows linearly at rate D k / c."""
+    u0 = 0.0 if X0 == 0 else (X0 / D / (1 - X0 / D)) ** (1 / c)
+    y = (u0 + D * k * t / c) ** c
+    return D * y / (1 + y)
+
+
+@pytest.mark.parametrize("c,X0", [(2.51, 0.05), (11.0, 1e-3), (11.0, 0.2)])
+def test_closed_form_solves_the_ode(c, X0):
+    """The closed form used by the pins below solves the ODE (independent
+    integration with scipy's adaptive Runge-Kutta)."""
+    from scipy.integrate import solve_ivp
+    D, k = 0.6, 0.8
+    # the paper's rate form: dX/dt = k X^((c-1)/c) (D - X)^((c+1)/c)
+    f = lambda t, y: [k * max(y[0], 0) ** ((c - 1) / c) * max(D - y[0], 0) ** ((c + 1) / c)]
+    ts = np.array([1.0, 5.0, 20.0])
+    sol = solve_ivp(f, (0, ts[-1]), [X0], t_eval=ts, rtol=1e-11, atol=1e-14, method="DOP853")
+    assert np.allclose(sol.y[0], [closed_form(t, D, k, c, X0) for t in ts], rtol=1e-7, atol=1e-12)
+
+
+def test_logistic_step_is_exact():
+    """eq:analytical_solution_beta is exact for constant k: stepping it with any
+    dt lands on the closed form (App. A)."""
+    D, k, c = 0.5087, 1.117, 11.0
+    for dt in (1e-5, 0.37, 2.0):
+        X, t = 0.0, 0.0
+        for _ in range(20):
+            X = orc.logistic_step(X, D, k, c, dt)
+            t += dt
+        assert X == pytest.approx(closed_form(t, D, k, c), rel=1e-9, abs=1e-300)
+
+
+# ------------------------------------------------------ P1: beta -> alpha_s
+def test_p1_isothermal_beta_to_alpha_s_converges_first_order():
+    """eq:beta_to_alpha_s at 900 K from pure beta (X_am stays 0, X_alpha^eq = 0.9):
+    the explicit scheme with the A6 first step converges to the closed form
+    with error ratio ~2 per dt halving (Sec. 3.1, explicit Euler)."""
+    T = 900.0
+    D, k, c = 0.9, orc.k_alpha_s(T), 2.51
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        s = orc.State.uniform(1, 0.0, 0.0)
+        n = int(round(20.0 / dt))
+        orc.run_temps(s, np.full(n + 1, T), dt)
+        errs.append(abs(s.xas[0] - closed_form(20.0, D, k, c)))
+    assert s.xam[0] == 0.0
+    assert errs[2] < 2e-3
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.6 < r1 < 2.5 and 1.6 < r2 < 2.5, errs
+
+
+def test_p1_analytic_steps_exact_with_init_ba_steps():
+    """Reading A6 with INIT_BA_STEPS and an exit threshold never met: every
+    step is the closed form, exact for any dt at constant T."""
+    p = orc.params(init_ba_steps=1, init_exit=1e300)
+    s = orc.State.uniform(1, 0.0, 0.0)
+    orc.run_temps(s, np.full(11, 900.0), 1.0, p)
+    assert s.xas[0] == pytest.approx(closed_form(10.0, 0.9, orc.k_alpha_s(900.0), 2.51), rel=1e-9)
+
+
+# ----------------------------------------------- P2: App. A alpha_s -> beta
+@pytest.mark.parametrize("floor", [0.0, 1e-3])
+def test_p2_appendix_a_case(golden, floor):
+    """App. A: T = 1200 K from (0.9, 0, 0.1).  The first step equals the closed
+    form at t = dt (values below 1e-16 survive, ~3.6e-70); the run converges
+    to the closed form with the beta rate k_beta = f k_as and equilibrium
+    D = X_beta^eq - 0.1.  Checked for the literal exit rule (floor 0) and
+    reading A5's floor."""
+    case = golden["appendix_a_case"]
+    T = case["T"]
+    p = orc.params(init_exit_floor=floor)
+    D = (1 - orc.xalpha_eq(T)) - case["X_beta0"]
+    kb = 3.8 * orc.k_alpha_s(T)
+    s = orc.State.uniform(1, case["X_as0"], 0.0)
+    orc.run_temps(s, np.array([T, T]), 1e-5, p)
+    assert s.mode[0] == orc.MODE_AS_TO_B and s.xas[0] == 0.9
+    assert s.xt[0] == pytest.approx(closed_form(1e-5, D, kb, 11.0), rel=1e-9)
+    assert 1e-71 < s.xt[0] < 1e-69
+    errs = []
+    for dt in (4e-3, 2e-3, 1e-3):
+        s = orc.State.uniform(1, 0.9, 0.0)
+        n = int(round(30.0 / dt))
+        orc.run_temps(s, np.full(n + 1, T), dt, p)
+        xb = 1 - s.xas[0] - s.xam[0]
+        errs.append(abs((xb - 0.1) - closed_form(30.0, D, kb, 11.0)))
+    assert s.mode[0] == orc.MODE_NONE
+    assert errs[2] < 1e-3
+    assert 1.6 < errs[0] / errs[1] < 2.6 and 1.6 < errs[1] / errs[2] < 2.6, errs
+
+
+def test_p2_exit_rule_literal_vs_floor_agree():
+    """Reading A5's floor only moves the switch from the closed form to Euler:
+    the two runs differ by Euler's truncation error, which falls with dt and is
+    far inside the 1e-4 budget at the workloads' dt."""
+    diffs = []
+    for dt in (1e-3, 2.5e-4):
+        out = []
+        for floor in (0.0, 1e-3):
+            s = orc.State.uniform(1, 0.9, 0.0)
+            orc.run_temps(s, np.full(int(round(20.0 / dt)) + 1, 1150.0), dt,
+                          orc.params(init_exit_floor=floor))
+            out.append(s.xas[0])
+        diffs.append(abs(out[0] - out[1]))
+    assert diffs[1] < 0.35 * diffs[0] and diffs[1] < 1e-5, diffs
+
+
+# --------------------------------------------------- alpha_m -> alpha_s (r2)
+def test_alpha_m_to_alpha_s_closed_form():
+    """eq:alpha_m_to_alpha_s alone (900 K: X_alpha = X_alpha^eq = 0.9 so r1 = r3 = 0,
+    no martensite formation or dissolution): X_as/0.9 follows the same
+    generalised logistic with D = 0.9, k = k_as."""
+    T, dt = 900.0, 2e-3
+    k = orc.k_alpha_s(T)
+    s = orc.State.make([0.3], [0.6])
+    n = int(round(15.0 / dt))
+    orc.run_temps(s, np.full(n + 1, T), dt)
+    assert s.xas[0] + s.xam[0] == pytest.approx(0.9, abs=1e-12)
+    assert s.xas[0] == pytest.approx(closed_form(15.0, 0.9, k, 2.51, X0=0.3), abs=2e-4)
+
+
+# --------------------------------------------------------- P3 equilibria
+@pytest.mark.parametrize("T", [1000.0, 1100.0])
+def test_p3_long_holds_reach_equilibrium_from_both_sides(T):
+    """Long isothermal holds in (T_as,end, T_as,start) converge to the
+    Koistinen-Marburger equilibrium from pure beta (r1) and from 0.9 (r3 via
+    App. A); X_am stays 0 above T_am,start."""
+    xeq = 1 - math.exp(-0.0068 * (1273 - T))
+    for x0 in (0.0, 0.9):
+        s = orc.State.uniform(1, x0, 0.0)
+        orc.run_temps(s, np.full(40001, T), 0.01)
+        assert s.xam[0] == 0.0
+        assert abs(s.xas[0] - xeq) < 3e-3, (x0, s.xas[0], xeq)
+
+
+def test_p3_high_temperature_and_melt(golden):
+    """Above T_as,start + T_reg only beta remains (Sec. 2.2 regularisation);
+    in the mushy zone X_beta = 1 - (T - T_s)/(T_l - T_s); above T_l all liquid."""
+    for T, xb_expect, xl_expect in ((1400.0, 1.0, 0.0), (1903.0, 0.5, 0.5), (2000.0, 0.0, 1.0)):
+        s = orc.State.make([0.5], [0.3])
+        orc.run_temps(s, np.array([T, T]), 1e-5)
+        _, _, xb, xl = orc.fractions(s, T)
+        assert s.xas[0] == 0.0 and s.xam[0] == 0.0
+        assert xb[0] == pytest.approx(xb_expect, abs=1e-12)
+        assert xl[0] == pytest.approx(xl_expect, abs=1e-12)
+
+
+def test_room_temperature_state_is_stationary(golden):
+    """(0.9, 0, 0.1) below T_as,end is an equilibrium (Sec. 4.2: beta reaches
+    its 10 % equilibrium; Sec. 4.3: 90 % alpha_s)."""
+    s = orc.State.uniform(1, 0.9, 0.0)
+    orc.run_temps(s, np.full(1001, 353.0), 0.1)
+    _, _, xb, _ = orc.fractions(s, 353.0)
+    assert s.xas[0] == 0.9 and s.xam[0] == 0.0
+    assert xb[0] == pytest.approx(golden["beta_room_temperature"]["value"], abs=1e-14)
+
+
+# ---------------------------------------------------------- P4 / P5 martensite
+@pytest.mark.parametrize("T1", [353.0, 600.0, 800.0])
+def test_p4_quench_forms_pseudo_equilibrium_martensite(T1):
+    """eq:inst_martensite_formation: an instant drop from the beta range below
+    T_am,start gives X_am = X_am,0^eq(T1) (X_as = 0)."""
+    s = orc.State.make([0.0], [0.0])
+    orc.run_temps(s, np.array([1400.0, T1]), 1e-5)
+    assert s.xas[0] == 0.0
+    assert s.xam[0] == pytest.approx(1 - math.exp(-0.00415 * (848 - T1)), rel=1e-12)
+
+
+def test_p5_martensite_only_on_fast_cooling():
+    """Sec. 2.2: high cooling rates give martensite, low rates stable alpha_s."""
+    def cool(rate, dt):
+        n = int(round((1400 - 353) / rate / dt))
+        T = np.linspace(1400.0, 353.0, n + 1)
+        s = orc.State.make([0.0], [0.0])
+        orc.run_temps(s, T, dt)
+        return s.xas[0], s.xam[0]
+    xas, xam = cool(1e5, 1e-5)
+    assert xas < 1e-3 and xam == pytest.approx(1 - math.exp(-0.00415 * 495), abs=2e-3)
+    xas, xam = cool(0.1, 0.5)
+    assert xas > 0.89 and xam < 1e-2
+
+
+def test_martensite_readings_agree_on_monotone_cooling():
+    """Reading A3: formation-only and the literal equality agree when T only falls."""
+    T = np.linspace(1500.0, 300.0, 5001)
+    a, b = orc.State.make([0.0], [0.0]), orc.State.make([0.0], [0.0])
+    orc.run_temps(a, T, 1e-4)
+    orc.run_temps(b, T, 1e-4, orc.params(martensite_literal=1))
+    assert a.xam[0] == pytest.approx(b.xam[0], abs=1e-12)
+    assert a.xas[0] == pytest.approx(b.xas[0], abs=1e-12)
+
+
+def test_martensite_does_not_revert_on_mild_reheating():
+    """Reading A3 default: reheating below T_as,end keeps martensite (dissolution
+    needs X_alpha > X_alpha^eq = 0.9, eq:inst_martensite_dissolution)."""
+    s = orc.State.make([0.0], [0.0])
+    orc.run_temps(s, np.array([1400.0, 400.0, 700.0, 700.0]), 1e-5)
+    assert s.xam[0] == pytest.approx(1 - math.exp(-0.00415 * 448), abs=1e-6)
+
+
+# ------------------------------------------------------------ g function
+def test_correction_clamp_and_rescale():
+    """eq:explicit_correction text: negative fractions become 0; X_alpha > 0.9 is
+    scaled back to 0.9 keeping X_as / X_am."""
+    xas, xam = orc.correct(900.0, -0.1, 0.3)
+    assert xas == 0.0 and xam == 0.3
+    xas, xam = orc.correct(900.0, 0.6, 0.4)
+    assert xas + xam == pytest.approx(0.9, abs=1e-15) and xas / xam == pytest.approx(1.5, rel=1e-13)
+
+
+def test_correction_regularisation_linear():
+    """Sec. 2.2 regularisation (reading A4): the cap falls linearly from 0.9 at
+    T_as,start to 0 at T_as,start + T_reg and stays 0 above."""
+    caps = [orc.correct(T, 0.9, 0.0)[0] for T in (1273.0, 1298.0, 1323.0, 1348.0, 1373.0, 1500.0)]
+    assert caps == pytest.approx([0.9, 0.675, 0.45, 0.225, 0.0, 0.0], abs=1e-12)
+
+
+def test_correction_dissolution():
+    """eq:inst_martensite_dissolution: if X_alpha > X_alpha^eq then
+    X_am = max(X_alpha^eq - X_as, 0)."""
+    T = 1100.0
+    xeq = orc.xalpha_eq(T)
+    xas, xam = orc.correct(T, 0.2, 0.6)
+    assert xas == 0.2 and xam == pytest.approx(xeq - 0.2, abs=1e-14)
+    xas, xam = orc.correct(T, 0.8, 0.05)
+    assert xas == 0.8 and xam == 0.0
+
+
+# ---------------------------------------------------------- P6 invariants
+def test_p6_invariants_random_histories():
+    """Phase continuity (eq:phase_continuity_*): every fraction in [0, 1],
+    X_alpha <= 0.9, the four fractions sum to 1, along random temperature
+    walks through every branch."""
+    rng = np.random.default_rng(7)
+    n, steps = 400, 300
+    T = np.empty((steps + 1, n))
+    T[0] = rng.uniform(250, 2600, n)
+    for s in range(steps):
+        T[s + 1] = np.clip(T[s] + rng.normal(0, 60, n), 250, 2600)
+    st = orc.State.make(rng.uniform(0, 0.45, n), rng.uniform(0, 0.45, n))
+    for s in range(steps):
+        orc.run_temps(st, T[s:s + 2], 1e-3)
+        xas, xam, xb, xl = orc.fractions(st, T[s + 1])
+        for a in (xas, xam, xb, xl):
+            assert np.all(a >= -1e-14) and np.all(a <= 1 + 1e-14)
+        assert np.all(xas + xam <= 0.9 + 1e-14)
+        assert np.allclose(xas + xam + xb + xl, 1.0, atol=1e-12)
+
+
+# ---------------------------------------------------------- moving source
+def _one_track(P=200.0, v=1.0):
+    tracks = np.array([[0.0, 0.0, 1.0, 0.0, v, P, 0.0, 0]])
+    return HeatSource(tracks, np.array([[0.0, 0.0, NEVER, NEVER]]), T_max=1e9)
+
+
+def test_source_satisfies_heat_equation():
+    """The synthetic driver must be a solution of dT/dt = alpha lap(T) away from
+    the source (checked by finite differences in space and time)."""
+    src = _one_track()
+    t = 2e-3
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        x = 2e-3 + rng.uniform(-4e-4, 1e-4)
+        y = rng.uniform(-2e-4, 2e-4)
+        z = -rng.uniform(5e-5, 3e-4)
+        h, dt = 3e-7, 2e-8  # well below the 2 alpha / v = 6 um decay length
+        T = lambda a, b, c, tt: orc.temperature(src, a, b, c, tt)[0][0]
+        lap = sum(T(x + e[0], y + e[1], z + e[2], t) for e in
+                  ((h, 0, 0), (-h, 0, 0), (0, h, 0), (0, -h, 0), (0, 0, h), (0, 0, -h)))
+        lap = (lap - 6 * T(x, y, z, t)) / h ** 2
+        dTdt = (T(x, y, z, t + dt) - T(x, y, z, t - dt)) / (2 * dt)
+        assert dTdt == pytest.approx(3e-6 * lap, rel=5e-4, abs=1e-3)
+
+
+def test_source_energy_balance_and_adiabatic_surface():
+    """Conducted heat through a tiny hemisphere around the source equals the
+    absorbed power A P (fixes the 2 pi k R normalisation of a half-space), and
+    the surface z = 0 carries no flux away from the source."""
+    src = _one_track(P=200.0)
+    t = 1e-3
+    sx = 1e-3
+    r = 1e-8
+    k = 7.0
+    nth, nph = 120, 240
+    th = (np.arange(nth) + 0.5) * (0.5 * math.pi / nth)   # polar angle from -z
+    ph = (np.arange(nph) + 0.5) * (2 * math.pi / nph)
+    flux = 0.0
+    dr = 1e-11
+    for a in th:
+        ca, sa = math.cos(a), math.sin(a)
+        dirs = np.stack([sa * np.cos(ph), sa * np.sin(ph), -ca * np.ones(nph)])
+        p1 = np.array([[sx], [0], [0]]) + r * dirs
+        p2 = np.array([[sx], [0], [0]]) + (r + dr) * dirs
+        T1 = orc.temperature(src, *p1, t)[0]
+        T2 = orc.temperature(src, *p2, t)[0]
+        dTdr = (T2 - T1) / dr
+        flux += np.sum(-k * dTdr) * r * r * sa * (0.5 * math.pi / nth) * (2 * math.pi / nph)
+    assert flux == pytest.approx(0.35 * 200.0, rel=2e-3)
+    h = 1e-7
+    for x in (5e-4, 8e-4, 1.2e-3):
+        Tm = orc.temperature(src, x, 1e-4, -h, t)[0][0]
+        Tp = orc.temperature(src, x, 1e-4, h, t)[0][0]
+        assert abs(Tp - Tm) < 1e-9 * Tm
+
+
+def test_source_superposition_cap_and_layers():
+    """Sources add linearly (below the cap); distance 0 gives T_max (reading A7);
+    points above the current layer surface are inactive; the interlayer
+    factor brings the field back to T0."""
+    tr = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0, 0],
+                   [0.0, 1e-4, 1.0, 0.0, 0.9, 150.0, 1e-3, 0]])
+    L = np.array([[0.0, 0.0, NEVER, NEVER]])
+    both = HeatSource(tr, L)
+    a, b = HeatSource(tr[:1], L), HeatSource(tr[1:], L)
+    x, y, z = np.array([3e-3, 2e-3]), np.array([5e-4, 2e-4]), np.array([-1e-4, -3e-4])
+    t = 4e-3
+    Tab = orc.temperature(both, x, y, z, t)[0]
+    Ta, Tb = orc.temperature(a, x, y, z, t)[0], orc.temperature(b, x, y, z, t)[0]
+    assert np.allclose(Tab - 353.0, (Ta - 353.0) + (Tb - 353.0), rtol=1e-12)
+    T0, _ = orc.temperature(a, 1e-3, 0.0, 0.0, 1e-3)
+    assert T0[0] == 4130.0
+    # layers: surface at -3e-5 during layer 0, at 0 during layer 1
+    tr2 = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0, 0],
+                    [0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.02, 1]])
+    L2 = np.array([[-3e-5, 0.0, 0.005, 0.01], [0.0, 0.01, 0.03, 0.04]])
+    src = HeatSource(tr2, L2)
+    _, act = orc.temperature(src, [1e-3, 1e-3], [0, 0], [-1e-5, -3e-5], 1e-3)
+    assert list(act) == [0, 1]
+    T_end, _ = orc.temperature(src, 1e-3, 0.0, -3e-5, 0.00999999)
+    assert T_end[0] == pytest.approx(353.0, abs=0.05)
+    T_mid, _ = orc.temperature(src, 1e-3, 0.0, -3e-5, 0.0075)
+    T_scan, _ = orc.temperature(src, 1e-3, 0.0, -3e-5, 0.0050)
+    assert (T_mid[0] - 353) == pytest.approx(0.5 * (orc.temperature(
+        HeatSource(tr2[:1], np.array([[-3e-5, 0, NEVER, NEVER]])), 1e-3, 0, -3e-5, 0.0075)[0][0] - 353), rel=1e-9)
+    assert T_scan[0] > T_mid[0]
+    _, act = orc.temperature(src, [1e-3], [0], [-1e-5], 0.015)
+    assert list(act) == [1]
+    # before the specimen's start offset nothing is hot
+    off = HeatSource(tr[:1], L, t_offset=0.5)
+    assert orc.temperature(off, 1e-4, 0, 0, 0.3)[0][0] == 353.0
+
+
+# ------------------------------------------------------------- dt halving
+def test_dt_halving_on_a_moving_source_run():
+    """Sec. 3.1: the explicit scheme converges at first order on a real heating
+    / melting / quench history (a line of points under one moving source)."""
+    src = HeatSource(np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0, 0]]),
+                     np.array([[0.0, 0.0, NEVER, NEVER]]))
+    g = Grid((2e-4, 0.0, 0.0), (2.7e-5, 1.3e-5, -1e-5), (6, 2, 3))
+    x, y, z = g.coords()
+    t_end = 6e-3
+    res = {}
+    for dt in (8e-6, 4e-6, 2e-6, 1e-6, 2.5e-7):
+        s = orc.State.uniform(g.n, 0.9, 0.0)
+        orc.run_track(s, src, x, y, z, 0, int(round(t_end / dt)), dt)
+        res[dt] = np.concatenate([s.xas, s.xam])
+    ref = res[2.5e-7]
+    e = [np.max(np.abs(res[d] - ref)) for d in (8e-6, 4e-6, 2e-6, 1e-6)]
+    assert e[-1] < 1e-4
+    assert all(e[i + 1] < 0.75 * e[i] for i in range(3)), e
