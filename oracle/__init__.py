@@ -80,7 +80,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # MS_ORACLE_LIB loads a deliberately broken copy of the oracle
+            # (tests/test_oracle_mutations.py checks that the pins catch it)
+            lib = ctypes.CDLL(os.environ.get("MS_ORACLE_LIB") or build())
             d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
             P = ctypes.c_void_p
             for name in ("orc_liquid_fraction", "orc_xalpha_eq", "orc_xam0_eq", "orc_k_alpha_s"):

@@ -1,0 +1,62 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of oracle/ms_oracle.c (a dropped term,
+a wrong sign, index or exponent, a transposed operand), compiles it on the
+CPU and runs tests/test_oracle_pins.py against it; the pins must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ms_oracle.c")
+
+MUTANTS = {
+    "xalpha_eq_sign": ("exp(-p[P_K_ALPHA_EQ] * (p[P_T_AS_START] - T))",
+                       "exp(p[P_K_ALPHA_EQ] * (p[P_T_AS_START] - T))"),
+    "xam0_eq_constant": ("exp(-p[P_K_AM_EQ] * (p[P_T_AM_START] - T))",
+                         "exp(-p[P_K_ALPHA_EQ] * (p[P_T_AM_START] - T))"),
+    "xam_eq_factor": ("(XMAX - xas) / XMAX", "(XMAX + xas) / XMAX"),
+    "k_beta_drops_f": ("double k = k_alpha_s(p, T), kb = p[P_F] * k;",
+                       "double k = k_alpha_s(p, T), kb = k;"),
+    "r3_exponents_swapped": ("powpos(XMAX - xa, (cb - 1.0) / cb) * powpos(xa - xeq, (cb + 1.0) / cb)",
+                             "powpos(XMAX - xa, (cb + 1.0) / cb) * powpos(xa - xeq, (cb - 1.0) / cb)"),
+    "r1_exponents_swapped": ("k * powpos(xas, (ca - 1.0) / ca) * powpos(xeq - xa, (ca + 1.0) / ca)",
+                             "k * powpos(xas, (ca + 1.0) / ca) * powpos(xeq - xa, (ca - 1.0) / ca)"),
+    "r2_dropped": ("*das = r1 + r2 - r3;", "*das = r1 - r3;"),
+    "rescale_inverted": ("double s = XMAX / xa;", "double s = xa / XMAX;"),
+    "regularisation_sign": ("(p[P_T_AS_START] + p[P_T_REG] - T) / p[P_T_REG]",
+                            "(T - p[P_T_AS_START]) / p[P_T_REG]"),
+    "dissolution_dropped": ("    xam = v > 0.0 ? v : 0.0;\n", "    (void)v;\n"),
+    "rates_at_T1": ("rates(p, T0, xas, xam, &das, &dam);", "rates(p, T1, xas, xam, &das, &dam);"),
+    "logistic_power": ("pow(xi / (1.0 - xi), 1.0 / c)", "pow(xi / (1.0 - xi), c)"),
+    "appendix_shift_dropped": ("double D = (1.0 - xeq0) - 0.1;", "double D = 1.0 - xeq0;"),
+    "beta_rate_in_init": ("xt = logistic_step(xt, D, kb, p[P_C_B], dt);",
+                          "xt = logistic_step(xt, D, k, p[P_C_B], dt);"),
+    "liquid_fraction_flipped": ("return (T - p[P_T_S]) / (p[P_T_L] - p[P_T_S]);",
+                                "return (p[P_T_L] - T) / (p[P_T_L] - p[P_T_S]);"),
+    "source_full_space": ("(2.0 * M_PI * spec[S_K] * R)", "(4.0 * M_PI * spec[S_K] * R)"),
+    "source_xi_sign": ("exp(-tr[TR_V] * (R + xi)", "exp(-tr[TR_V] * (R - xi)"),
+    "source_depth_dropped": ("dx * dx + dy * dy + dz * dz", "dx * dx + dy * dy"),
+    "interlayer_dropped": ("double T = spec[S_T0] + scale * sum;", "double T = spec[S_T0] + sum;"),
+    "clamp_dropped": ("  if (xas < 0.0) xas = 0.0;\n", ""),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fopenmp",
+                    "-shared", "-fPIC", str(mut), "-o", str(lib), "-lm"], check=True)
+    env = dict(os.environ, MS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"

@@ -212,6 +212,20 @@ def test_alpha_m_to_alpha_s_closed_form():
     assert s.xas[0] == pytest.approx(closed_form(15.0, 0.9, k, 2.51, X0=0.3), abs=2e-4)
 
 
+def test_explicit_rates_use_T_n():
+    """eq:explicit_integration evaluates the diffusive rates at T^n: when the
+    correction g is the identity at both candidate T^{n+1}, the step result
+    must not depend on T^{n+1}."""
+    for T0, xas, xam in ((1000.0, 0.3, 0.0), (1100.0, 0.2, 0.1), (900.0, 0.4, 0.3)):
+        out = []
+        for T1 in (880.0, 905.0, 930.0):
+            s = orc.State.make([xas], [xam])
+            orc.run_temps(s, np.array([T0, T1]), 0.5)
+            out.append((s.xas[0], s.xam[0]))
+        assert out[0] == out[1] == out[2], (T0, out)
+        assert out[0][0] != xas
+
+
 # --------------------------------------------------------- P3 equilibria
 @pytest.mark.parametrize("T", [1000.0, 1100.0])
 def test_p3_long_holds_reach_equilibrium_from_both_sides(T):
@@ -229,7 +243,7 @@ def test_p3_long_holds_reach_equilibrium_from_both_sides(T):
 def test_p3_high_temperature_and_melt(golden):
     """Above T_as,start + T_reg only beta remains (Sec. 2.2 regularisation);
     in the mushy zone X_beta = 1 - (T - T_s)/(T_l - T_s); above T_l all liquid."""
-    for T, xb_expect, xl_expect in ((1400.0, 1.0, 0.0), (1903.0, 0.5, 0.5), (2000.0, 0.0, 1.0)):
+    for T, xb_expect, xl_expect in ((1400.0, 1.0, 0.0), (1888.0, 0.8, 0.2), (2000.0, 0.0, 1.0)):
         s = orc.State.make([0.5], [0.3])
         orc.run_temps(s, np.array([T, T]), 1e-5)
         _, _, xb, xl = orc.fractions(s, T)
