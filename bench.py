@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the phase-model hot path on GB300.
+
+One bench step = one full ``ms_run_track`` pass of the workload from the
+room-temperature state (default: the 256 x 256 x 64 block, 4.19M points,
+20 serpentine tracks, 20000 steps of 1e-5 s = 8.4e10 point-updates).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload block_256|line_4096|batch_64] [--precision f32|f64acc]
+
+Prints one JSON line (rank 0).  ``value`` is point-updates/s of the whole job
+timed with CUDA events on the library's stream (inputs resident in HBM, L2
+flushed between steps); ``e2e`` is the same metric through the C ABI with
+pinned host buffers (state upload, run, download of the four fractions);
+``roofline`` is the hot kernel's achieved SFU rate against the SFU peak;
+``cpu_baseline`` is the FP64 oracle on a bounded sample of the same workload
+on the host cores.  ``--impl reference`` times the oracle alone (rank 0).
+Under torchrun (N > 1) every rank advances its own block (weak scaling; no
+data exchange), and the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase point-updates/s and % roofline: FP32 plain vs FP64 vs surrogate-hybrid at stated max|dX|"
+UNIT = "point-updates/s"
+SM_COUNT = 152
+SFU_PER_SM_CLK = 16          # MUFU (ex2/lg2/rsqrt/rcp) results per SM per clock
+SM_MAX_MHZ = 2070.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_track_block_256.json")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="block_256")
+    ap.add_argument("--precision", choices=("f32", "f64acc"), default="f32")
+    ap.add_argument("--steps-per-launch", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def make_workload(name, rank=0):
+    import workloads as wl
+    if name == "block_256":
+        return wl.block_256(seed=wl.SEED_BASE + 2 + 1000 * rank)
+    if name == "line_4096":
+        return wl.line_4096()
+    if name == "batch_64":
+        return wl.batch_64(seed=wl.SEED_BASE + 3 + 1000 * rank)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w):
+    cfg = {"workload": w.name, "points": w.n_points, "time_steps": w.n_steps, "dt_s": w.dt,
+           "specimens": len(w.specimens),
+           "tracks": int(sum(len(s.source.tracks) for s in w.specimens)),
+           "T_thr_K": w.T_thr, "point_updates_per_step": w.point_updates}
+    if len(w.specimens) == 1:
+        cfg["grid"] = "x".join(str(d) for d in w.specimens[0].grid.dims)
+    return cfg
+
+
+# ------------------------------------------------------------ clocks sampler
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples under load: the upper half of the clock distribution is not
+        # needed; take all samples of the timed region
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------- algorithmic work
+def algorithmic_sfu_per_run(w):
+    """SFU operations one pass requires by the method's formulas (a lower
+    bound): per point and step, 2 per started moving source (1/R and the
+    exponential) at the new time level plus 2 for k_as(T^n) (exponential and
+    division).  Counting started sources needs only the track start times."""
+    import numpy as np
+    total = 0
+    for s in w.specimens:
+        tr = s.source.tracks
+        ly = s.source.layers
+        t = (np.arange(1, w.n_steps + 1) * w.dt) - s.source.t_offset
+        layer_of = np.zeros(t.size, dtype=np.int64)
+        for j in range(len(ly)):
+            layer_of[t >= ly[j, 1]] = j
+        n_src = np.zeros(t.size, dtype=np.int64)
+        for r in tr:
+            n_src += ((layer_of == int(r[7])) & (t >= r[6])).astype(np.int64)
+        total += int(s.grid.n) * int(np.sum(2 * n_src + 2))
+    return total
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ms_device.cuh", "ms_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2402_17580_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the hot kernel from the committed ncu summary,
+    only if the kernel source is unchanged since the capture."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            s = json.load(f)
+    except (OSError, ValueError):
+        return None, None
+    if s.get("kernel_source_hash") != kernel_source_hash():
+        return None, s.get("kernel_source_hash")
+    return s.get("dram_bytes_per_launch_full"), s.get("kernel_source_hash")
+
+
+# ------------------------------------------------------------ oracle sample
+def oracle_sample(w, seconds, seed=12345):
+    """Run the FP64 oracle on a seeded sample of the workload's points, sized
+    for about `seconds` of CPU time; returns (point-updates/s, sample indices,
+    oracle fractions, threads, description)."""
+    import numpy as np
+
+    import oracle as orc
+    offs = np.cumsum([0] + [s.grid.n for s in w.specimens])
+    rng = np.random.default_rng(seed)
+
+    def run(idx):
+        spec_of = np.searchsorted(offs, idx, side="right") - 1
+        out = np.empty((4, idx.size))
+        t0 = time.perf_counter()
+        for s in np.unique(spec_of):
+            sel = np.nonzero(spec_of == s)[0]
+            sp = w.specimens[s]
+            x, y, z = sp.grid.coords(idx[sel] - offs[s])
+            st = orc.State.uniform(sel.size, 0.9, 0.0)
+            T_last = orc.run_track(st, sp.source, x, y, z, 0, w.n_steps, w.dt)
+            out[:, sel] = np.stack(orc.fractions(st, T_last))
+        return time.perf_counter() - t0, out
+
+    threads = orc.num_threads()
+    n_probe = max(threads * 2, 16)
+    idx = np.sort(rng.choice(w.n_points, n_probe, replace=False))
+    dt_probe, _ = run(idx)
+    n = int(min(max(n_probe, n_probe * seconds / max(dt_probe, 1e-3)), 16384, w.n_points))
+    idx = np.sort(rng.choice(w.n_points, n, replace=False))
+    el, out = run(idx)
+    rate = n * w.n_steps / el
+    desc = (f"{n} seeded points of {w.name} x all {w.n_steps} steps, FP64 oracle, "
+            f"{threads} OpenMP threads, {el:.1f} s")
+    return rate, idx, out, threads, desc, el
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", 0))
+    import paper_2402_17580_gb300 as ms
+    ms.load()
+
+    w = make_workload(args.workload, rank)
+    prec = ms.MS_F64ACC if args.precision == "f64acc" else ms.MS_F32
+    over = dict(T_thr=w.T_thr, precision=prec, flags=ms._binding.MS_FLAG_TIME_KERNELS)
+    if args.steps_per_launch:
+        over["steps_per_launch"] = args.steps_per_launch
+    ctx = ms.Context(w.n_points, **over)
+    ctx.set_points([s.grid for s in w.specimens])
+    srcs = [s.source for s in w.specimens]
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def one_pass():
+        ctx.fill_state(w.init_xas, w.init_xam)
+        ctx.run_track(srcs, w.n_steps, w.dt)
+
+    for _ in range(args.warmup):
+        one_pass()
+    ctx.synchronize()
+    ctx.reset_stats()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    wall0 = time.perf_counter()
+    step_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()              # L2 flush, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_pass()
+            e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    st = ctx.stats()
+
+    t_mean = sum(step_ms) / len(step_ms)
+    t_max = t_mean
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_mean], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = w.point_updates * world / (t_max * 1e-3)
+
+    # roofline of the hot kernel (k_track): SFU-bound (state is L2-resident)
+    alg_ops = algorithmic_sfu_per_run(w)
+    launches_per_pass = st.hot_kernel_launches / args.steps
+    kernel_ms_per_pass = st.hot_kernel_ms / args.steps
+    ops_per_launch = alg_ops / launches_per_pass
+    ms_per_launch = kernel_ms_per_pass / launches_per_pass
+    achieved = ops_per_launch / (ms_per_launch * 1e-3) / 1e9
+    peak = SM_COUNT * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    traffic_full, prof_hash = ncu_traffic()
+    state_bytes = 2 * w.n_points * (3 * 4 if prec == ms.MS_F32 else 2 * 8 + 4)
+    roofline = {
+        "bound": "alu", "kernel": "k_track", "achieved": round(achieved, 1), "peak": round(peak, 1),
+        "unit": "Gop/s (SFU)", "frac": round(achieved / peak, 4),
+        "traffic": traffic_full,
+        "algorithmic_ops_per_launch": int(ops_per_launch),
+        "ms_per_launch": round(ms_per_launch, 4), "launches_per_step": launches_per_pass,
+        "kernel_share_of_step": round(kernel_ms_per_pass / t_mean, 4),
+        "peak_basis": f"{SM_COUNT} SMs x {SFU_PER_SM_CLK} SFU/clk x {SM_MAX_MHZ:.0f} MHz max clock",
+        "frac_at_observed_clock": (round(achieved / (SM_COUNT * SFU_PER_SM_CLK * clocks["sm_mhz"] * 1e-3), 4)
+                                   if clocks.get("sm_mhz") else None),
+        "hbm_view": {"state_bytes_per_launch": state_bytes,
+                     "GB_per_s": round(state_bytes / (ms_per_launch * 1e-3) / 1e9, 1),
+                     "note": "fractions are L2-resident across the S steps of a launch"},
+    }
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == ms.MS_F32 else "f32+f64acc",
+        "data": "synthetic (seeded Rosenthal-driven tracks, no dataset)",
+        "config": dict(workload_config(w), parallelism=f"{world} independent blocks",
+                       steps_per_launch=int(ctx.params.steps_per_launch),
+                       l2="L2 flushed (512 MiB write) between bench steps; the 50 MB state is "
+                          "L2-resident inside a pass by design"),
+        "wall_ms_per_step": wall / args.steps * 1e3,
+        "clocks": clocks, "gpu_launches": int(st.launches), "roofline": roofline,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e_pass(ctx, w, srcs, args, ms, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g = ctx.fractions()   # state after the last full pass
+        rate, idx, ofr, threads, desc, el = oracle_sample(w, args.cpu_seconds)
+        gs = np.stack(g)[:, idx]
+        out["max_abs_dX"] = float(np.max(np.abs(gs - ofr)))
+        out["max_abs_dX_basis"] = f"{idx.size} seeded sample points vs the FP64 oracle"
+        out["sum_err"] = float(np.max(np.abs(np.stack(g).sum(axis=0) - 1.0)))
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": desc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_pass(ctx, w, srcs, args, ms, torch):
+    """Same metric through the public API with pinned host buffers: upload the
+    initial state, run, download the four fractions, every step."""
+    import numpy as np
+    n = w.n_points
+    pin = lambda: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    xas0, xam0 = pin(), pin()
+    xas0[:] = w.init_xas
+    xam0[:] = w.init_xam
+    outs = [pin() for _ in range(4)]
+    ctx.set_stream(None)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ctx.set_state(xas0, xam0)
+        ctx.run_track(srcs, w.n_steps, w.dt)
+        ctx.fractions_into(outs)
+        t = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(t)
+    mean = sum(times) / len(times)
+    return {"value": w.point_updates / mean, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8,
+            "d2h_bytes_per_step": 4 * n * 8, "ms_per_step": mean * 1e3,
+            "path": "ms_set_state + ms_run_track + ms_get_fractions, pinned host buffers"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0)
+    per_step = max(2.0, min(20.0, 100.0 / max(1, args.steps + args.warmup)))
+    rates, desc, threads = [], None, None
+    for k in range(args.warmup + args.steps):
+        rate, idx, _, threads, desc, el = oracle_sample(w, per_step, seed=777 + k)
+        if k >= args.warmup:
+            rates.append(rate)
+    value = sum(rates) / len(rates)
+    pu = w.point_updates
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": pu / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference", "config": dict(workload_config(w), parallelism="host cores"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": "the FP64 CPU oracle timed on a bounded seeded sample of the workload "
+                "(every step of the pass, a subset of the points); ms_per_step is "
+                "extrapolated to the full point count",
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if world > 1:
+        # one GPU per rank, seen as device 0 by torch and by the library
+        vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+        os.environ["CUDA_VISIBLE_DEVICES"] = vis[local] if len(vis) > local else str(local)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,276 @@
+/*
+ * ms.h -- C ABI of the GB300 (sm_103a) Ti-6Al-4V microstructure point solver.
+ *
+ * The library advances the phenomenological phase model of Proell et al.,
+ * arXiv 2402.17580 (beta, stable alpha_s, martensitic alpha_m) at every point
+ * of a part, one explicit time step at a time:
+ *
+ *   m = (X_as, X_am)                                  Sec. 3.1 (state vector)
+ *   m~ = m^n + dt * m_diff(T^n, m^n)                  Sec. 3.1, eq:explicit_integration
+ *   m^{n+1} = g(T^{n+1}, m~)                          Sec. 3.1, eq:explicit_correction
+ *   X_beta = X_sol(T) - X_as - X_am, X_sol = 1 - g(T) Sec. 3.1, eq:time_integration_beta_postprocess
+ *
+ * with the rates of Sec. 2.2 (eq:beta_to_alpha_s, eq:alpha_m_to_alpha_s,
+ * eq:alpha_s_to_beta), the instantaneous martensite terms
+ * (eq:inst_martensite_formation, eq:inst_martensite_dissolution), the alpha_s
+ * regularisation and the analytical initiation of Appendix A
+ * (eq:analytical_solution_beta).  Points are independent (Sec. 3: no
+ * communication), so the library is a data-parallel point solver.
+ *
+ * Conventions for every entry point:
+ *  - return value: MS_OK (0) or a negative MS_ERR_* code; no exceptions cross
+ *    the ABI; ms_strerror() gives a message, ms_last_error() the detail of the
+ *    last failure on the calling thread.
+ *  - host arrays are owned by the caller and are only read / written during
+ *    the call (the library copies).  Device pointers (flag MS_PTR_DEVICE) are
+ *    borrowed for the call only and never freed by the library.
+ *  - a context owns all device memory it allocates and its CUDA stream (or
+ *    uses the stream given to ms_set_stream, which it never destroys).
+ *  - calls on one context must not overlap (one host thread at a time);
+ *    different contexts are independent.
+ *  - points are in natural order: specimen by specimen, and inside a
+ *    specimen's grid i (x) fastest, then j (y), then k (z).
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define MS_OK                   0
+#define MS_ERR_INVALID_ARG     -1  /* bad pointer, size, dt, fraction or parameter      */
+#define MS_ERR_OOM             -2  /* device or host allocation failed                   */
+#define MS_ERR_CUDA            -3  /* a CUDA runtime call failed (see ms_last_error)     */
+#define MS_ERR_DEVICE_TIMEOUT  -4  /* a bounded device wait gave up                      */
+#define MS_ERR_NONFINITE       -5  /* a fraction became NaN or infinite on the device    */
+#define MS_ERR_STATE           -6  /* call out of order (e.g. run_track without points)  */
+#define MS_ERR_UNSUPPORTED     -7  /* option not available in this build or context     */
+
+/* precision of the stored fractions (the arithmetic of the rates is FP32) */
+#define MS_F32      0  /* fractions stored and accumulated in FP32                       */
+#define MS_F64ACC   1  /* fractions stored and accumulated in FP64                       */
+#define MS_KAHAN    2  /* FP32 fractions with a compensation term (two floats each)      */
+
+/* flags for ms_step */
+#define MS_PTR_DEVICE  1  /* T_prev / T_new are device pointers (else host pointers)    */
+
+/* bits of ms_params.flags */
+#define MS_FLAG_TIME_KERNELS 1  /* time every hot-kernel launch with CUDA events on the
+                                   context stream (read back by ms_stats)            */
+
+/* ---------------------------------------------------------------- params */
+/* Model constants and options.  ms_params_default() fills the paper's values:
+ * Table 1/2 (T_s, T_l, T_as_start, T_as_end, T_am_start, T_inf, k_alpha_eq,
+ * k_am_eq), Table 3 (c_as, c_b, k1, k2, k3, f), T_reg = 100 K (Sec. 2.2) and
+ * the App. A exit threshold 1e-15.  Readings where the paper is ambiguous:
+ *   martensite_literal  0: X_am <- max(X_am, X_am^eq) below T_am,start (default),
+ *                       1: X_am <- X_am^eq (eq:inst_martensite_formation literally)
+ *   init_ba_steps       0: one analytical beta -> alpha_s step when X_as == 0,
+ *                       1: keep the analytical step until the App. A exit rule
+ *   init_exit_floor     App. A initiation of alpha_s -> beta ends when
+ *                       X~_beta * dt > init_exit AND X~_beta >= init_exit_floor
+ *                       (default 1e-3: FP32 cannot resolve smaller X~_beta
+ *                       against 0.9; 0 restores the literal rule)
+ *   T_thr               active-set threshold [K]: a 128-point tile may skip a
+ *                       step only if it stays below T_thr and its martensite
+ *                       is saturated (<= 0 disables all skipping)           */
+typedef struct ms_params {
+  double T_s, T_l;                /* solidus, liquidus [K]                       */
+  double T_as_start, T_as_end;    /* beta -> alpha_s range [K]                   */
+  double T_am_start, T_inf;       /* martensite start, ambient [K]               */
+  double k_alpha_eq, k_am_eq;     /* equilibrium constants [1/K]                 */
+  double c_as, c_b;               /* logistic exponents                          */
+  double k1, k2, k3, f;           /* rate constant k_as(T) = k1/(1+exp(-k3(T-k2))), k_b = f k_as */
+  double T_reg;                   /* regularisation width [K]                    */
+  double init_exit;               /* App. A exit threshold on X~ * dt            */
+  double init_exit_floor;         /* reading A5 floor on X~                       */
+  double T_thr;                   /* active-set threshold [K]                    */
+  int32_t martensite_literal;     /* reading A3                                  */
+  int32_t init_ba_steps;          /* reading A6                                  */
+  int32_t precision;              /* MS_F32 | MS_F64ACC | MS_KAHAN               */
+  int32_t steps_per_launch;       /* S: steps per state load in ms_run_track (1..512) */
+  int32_t rebuild_steps;          /* active-set rebuild period (multiple of S; 0 = S) */
+  int32_t block_threads;          /* CTA size, multiple of 32 (0 = library choice) */
+  int32_t flags;                  /* reserved, 0                                  */
+  int32_t reserved0;
+  double reserved[4];
+} ms_params;
+
+/* ------------------------------------------------------------ geometry */
+/* A regular grid of points: x = origin[0] + i*spacing[0], y likewise with j,
+ * z likewise with k (spacing may be negative, e.g. z going down). */
+typedef struct ms_grid {
+  double origin[3];
+  double spacing[3];
+  int32_t dims[3];                /* nx, ny, nz (each >= 1)                     */
+  int32_t reserved;
+} ms_grid;
+
+/* ----------------------------------------------------- moving heat source */
+/* The synthetic temperature driver evaluated on the device: every track of the
+ * current layer that has started contributes a moving point source on a
+ * half-space (thick-plate Rosenthal solution)
+ *     dT = A P / (2 pi k R) * exp(-v (R + xi) / (2 alpha)),
+ * R = |x - x_s|, xi = (x - x_s) . u (positive ahead of the source), with the
+ * source at x_s = (x0, y0) + u v (t - t_start) on the layer surface and still
+ * moving after its track ends.  T = min(T0 + s(t) * sum dT, T_max), where
+ * s(t) = 1 during the layer's scan and falls linearly to 0 at the layer's
+ * t_end (interlayer cool-down).  T_max = T_v + 1000 K (Sec. 2.1).  R = 0 gives
+ * T_max.  Points above the current layer surface (z > z_surface + z_tol) are
+ * not advanced.  Specimen-local time is t - t_offset. */
+typedef struct ms_track {
+  double x0, y0;                  /* start point on the layer surface [m]        */
+  double ux, uy;                  /* unit direction                              */
+  double v;                       /* speed [m/s]                                 */
+  double P;                       /* power [W]                                   */
+  double t_start;                 /* specimen-local start time [s]               */
+  int32_t layer;                  /* index into the layer table                  */
+  int32_t reserved;
+} ms_track;
+
+typedef struct ms_layer {
+  double z_surface;               /* surface height during this layer [m]        */
+  double t_begin;                 /* layer becomes current at this local time [s]*/
+  double t_scan_end;              /* scan ends, cool-down scaling starts [s]      */
+  double t_end;                   /* scaling reaches 0 [s]                        */
+} ms_layer;
+
+typedef struct ms_heat_source {
+  double A;                       /* absorptivity                                */
+  double k;                       /* conductivity [W/(m K)]                      */
+  double alpha;                   /* diffusivity [m^2/s]                         */
+  double T0;                      /* preheat / ambient [K]                       */
+  double T_max;                   /* temperature cap [K]                         */
+  double t_offset;                /* specimen start offset [s]                   */
+  double z_tol;                   /* activity tolerance above the surface [m]    */
+  int32_t n_tracks, n_layers;
+  const ms_track* tracks;         /* tracks of one layer sorted by t_start       */
+  const ms_layer* layers;
+} ms_heat_source;
+
+/* ------------------------------------------------------------- counters */
+typedef struct ms_stats_t {
+  int64_t steps;                  /* time levels advanced so far                 */
+  int64_t point_updates;          /* points x steps advanced (dense count)       */
+  int64_t tile_steps_total;       /* 128-point tiles x steps offered             */
+  int64_t tile_steps_active;      /* ... of which were not skipped by the active set */
+  int64_t launches;               /* kernel launches issued by the library       */
+  double  last_run_ms;            /* device time of the last ms_run_track / ms_step */
+  double  hot_kernel_ms;          /* summed device time of timed hot-kernel launches
+                                     (MS_FLAG_TIME_KERNELS), since the last reset   */
+  int64_t hot_kernel_launches;    /* number of launches in hot_kernel_ms          */
+  int32_t device_error;           /* sticky device error word (0 = none)         */
+  int32_t reserved;
+} ms_stats_t;
+
+typedef struct ms_ctx ms_ctx;
+
+/* ---------------------------------------------------------------- calls */
+
+/* Library version string (static storage). */
+const char* ms_version(void);
+
+/* Message for a status code (static storage). */
+const char* ms_strerror(int code);
+
+/* Detail of the last failing call on this thread (thread-local storage). */
+const char* ms_last_error(void);
+
+/* sizeof of the public structs, for bindings to check their layouts:
+ * which = 0 ms_params, 1 ms_grid, 2 ms_track, 3 ms_layer, 4 ms_heat_source,
+ * 5 ms_stats_t.  Returns 0 for an unknown index. */
+size_t ms_struct_size(int which);
+
+/* Fill *p with the paper's constants and the default readings / options.
+ * Errors: MS_ERR_INVALID_ARG if p is NULL. */
+int ms_params_default(ms_params* p);
+
+/* Create a context for n_points points on the current CUDA device and
+ * allocate their state (all points start at the room-temperature
+ * equilibrium X_as = 0.9, X_am = 0, App. A).  The parameters are copied.
+ * Errors: INVALID_ARG (NULL, n_points <= 0, bad parameter), OOM, CUDA. */
+int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out);
+
+/* Release all device memory and the owned stream.  NULL is ignored. */
+void ms_destroy(ms_ctx* ctx);
+
+/* Make the context launch on an existing CUDA stream (cudaStream_t passed as
+ * void*; NULL = the context's own stream).  The stream is borrowed. */
+int ms_set_stream(ms_ctx* ctx, void* cuda_stream);
+
+/* Geometry for ms_run_track: n_specimens regular grids whose point counts add
+ * up to the context's n_points (natural order, specimen after specimen).
+ * Copied.  Errors: INVALID_ARG (count mismatch, bad dims), OOM, CUDA. */
+int ms_set_points(ms_ctx* ctx, const ms_grid* grids, int32_t n_specimens);
+
+/* Set the state of every point from host arrays of n_points doubles.
+ * aux may be NULL (no initiation in progress) or give per point the App. A
+ * variable: X~_beta > 0 of an active alpha_s -> beta initiation, -1 for an
+ * active (init_ba_steps) beta -> alpha_s initiation, 0 for none.
+ * Validates 0 <= X_as, 0 <= X_am, X_as + X_am <= 0.9 (+1e-6).
+ * Resets the step counter to 0.  Errors: INVALID_ARG, NONFINITE, CUDA. */
+int ms_set_state(ms_ctx* ctx, const double* x_as, const double* x_am, const double* aux);
+
+/* Set every point to the same state (X_as = x_as, X_am = x_am, no initiation
+ * in progress) with a device fill, no host copy, and reset the step counter.
+ * Asynchronous.  Errors: INVALID_ARG (fractions outside [0, 0.9]), CUDA. */
+int ms_fill_state(ms_ctx* ctx, double x_as, double x_am);
+
+/* Reset the counters of ms_stats (not the state).  Synchronises the stream. */
+int ms_reset_stats(ms_ctx* ctx);
+
+/* One explicit step of every point with given temperatures T_prev = T^n and
+ * T_new = T^{n+1} (n_points floats each, Algorithm 1 / Algorithm 2; rates at
+ * T^n, correction at T^{n+1}).  flags & MS_PTR_DEVICE: device pointers,
+ * borrowed for the call (and T_new until the next ms_step or
+ * ms_get_fractions, which reads it for X_beta and X_liq); else host pointers
+ * (copied).  dt > 0 [s].  Asynchronous on the context stream for device
+ * pointers.  Errors: INVALID_ARG, STATE (context has several specimens),
+ * CUDA. */
+int ms_step(ms_ctx* ctx, const float* T_prev, const float* T_new, double dt, int32_t flags);
+
+/* Advance every point n_steps explicit steps of size dt under the moving
+ * sources, src[s] being the heat source of specimen s (as many as given to
+ * ms_set_points).  Temperatures are evaluated on the device at every time
+ * level t_n = n * dt (n counts the steps since ms_set_state), so only the
+ * phase state touches memory.  Asynchronous on the context stream.
+ * Errors: INVALID_ARG (dt <= 0, n_steps < 0, bad source), STATE (no points),
+ * OOM, CUDA. */
+int ms_run_track(ms_ctx* ctx, const ms_heat_source* src, int64_t n_steps, double dt);
+
+/* Copy the four fractions of every point to host arrays of n_points doubles:
+ * X_as, X_am, X_beta = 1 - g(T) - X_as - X_am, X_liq = g(T) with T the
+ * temperature of the last level (x_beta and x_liq may be NULL).  Synchronises
+ * the stream and reports a sticky device error.  Errors: INVALID_ARG, STATE
+ * (no temperature known yet for X_beta / X_liq), NONFINITE, CUDA. */
+int ms_get_fractions(ms_ctx* ctx, double* x_as, double* x_am, double* x_beta, double* x_liq);
+
+/* App. A variable of every point in the encoding of ms_set_state (n_points
+ * doubles).  Errors: INVALID_ARG, CUDA. */
+int ms_get_aux(ms_ctx* ctx, double* aux);
+
+/* Checkpoint: serialise the full device state (fractions, App. A variables,
+ * step counter, dt) into blob.  With blob == NULL only *bytes is set to the
+ * required size.  Errors: INVALID_ARG (buffer too small), CUDA. */
+int ms_get_state(ms_ctx* ctx, void* blob, size_t* bytes);
+
+/* Restore a checkpoint made by ms_get_state on a context with the same
+ * n_points and precision.  Errors: INVALID_ARG (size / header mismatch), CUDA. */
+int ms_set_state_blob(ms_ctx* ctx, const void* blob, size_t bytes);
+
+/* Counters and the sticky device error word (synchronises the stream). */
+int ms_stats(ms_ctx* ctx, ms_stats_t* out);
+
+/* Wait for all work on the context stream; reports a sticky device error. */
+int ms_synchronize(ms_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MS_H */

@@ -1,0 +1,14 @@
+"""GB300 (sm_103a) point solver for the Ti-6Al-4V phase model of
+Proell et al., arXiv 2402.17580.
+
+The compute path is the CUDA library ``_build/libms_gb300.so`` behind the C ABI
+of ``include/ms.h``; this package only builds it and marshals arguments
+(see ``_binding``).  PyTorch is not needed; where a caller uses it, it only
+provides device memory and streams.
+"""
+from ._binding import (MS_F32, MS_F64ACC, MS_KAHAN, MS_PTR_DEVICE, Context, MSError,
+                       default_params, library_path, load)
+from .build import build
+
+__all__ = ["Context", "MSError", "default_params", "load", "build", "library_path",
+           "MS_F32", "MS_F64ACC", "MS_KAHAN", "MS_PTR_DEVICE"]

@@ -1,0 +1,276 @@
+"""ctypes binding of libms_gb300.so (the C ABI in include/ms.h).
+
+Argument marshalling only: every step of the phase model runs in the CUDA
+kernels behind the C ABI.  There is no CPU fallback; a missing library or a
+failing call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MS_OK = 0
+ERRORS = {
+    -1: "MS_ERR_INVALID_ARG", -2: "MS_ERR_OOM", -3: "MS_ERR_CUDA", -4: "MS_ERR_DEVICE_TIMEOUT",
+    -5: "MS_ERR_NONFINITE", -6: "MS_ERR_STATE", -7: "MS_ERR_UNSUPPORTED",
+}
+MS_F32, MS_F64ACC, MS_KAHAN = 0, 1, 2
+MS_PTR_DEVICE = 1
+MS_FLAG_TIME_KERNELS = 1
+
+d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, d) for n in (
+        "T_s", "T_l", "T_as_start", "T_as_end", "T_am_start", "T_inf", "k_alpha_eq", "k_am_eq",
+        "c_as", "c_b", "k1", "k2", "k3", "f", "T_reg", "init_exit", "init_exit_floor", "T_thr")] + [
+        (n, i32) for n in ("martensite_literal", "init_ba_steps", "precision", "steps_per_launch",
+                           "rebuild_steps", "block_threads", "flags", "reserved0")] + [
+        ("reserved", d * 4)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("origin", d * 3), ("spacing", d * 3), ("dims", i32 * 3), ("reserved", i32)]
+
+
+class Track(ctypes.Structure):
+    _fields_ = [(n, d) for n in ("x0", "y0", "ux", "uy", "v", "P", "t_start")] + [
+        ("layer", i32), ("reserved", i32)]
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [(n, d) for n in ("z_surface", "t_begin", "t_scan_end", "t_end")]
+
+
+class HeatSource(ctypes.Structure):
+    _fields_ = [(n, d) for n in ("A", "k", "alpha", "T0", "T_max", "t_offset", "z_tol")] + [
+        ("n_tracks", i32), ("n_layers", i32), ("tracks", ctypes.POINTER(Track)),
+        ("layers", ctypes.POINTER(Layer))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, i64) for n in ("steps", "point_updates", "tile_steps_total",
+                                   "tile_steps_active", "launches")] + [
+        ("last_run_ms", d), ("hot_kernel_ms", d), ("hot_kernel_launches", i64),
+        ("device_error", i32), ("reserved", i32)]
+
+
+STRUCTS = (Params, Grid, Track, Layer, HeatSource, Stats)
+
+_lib = None
+
+
+class MSError(RuntimeError):
+    def __init__(self, code, where, detail):
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({detail})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libms_gb300.so (building it first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.ms_version.restype = ctypes.c_char_p
+    lib.ms_strerror.restype = ctypes.c_char_p
+    lib.ms_strerror.argtypes = [ctypes.c_int]
+    lib.ms_last_error.restype = ctypes.c_char_p
+    lib.ms_struct_size.restype = ctypes.c_size_t
+    lib.ms_struct_size.argtypes = [ctypes.c_int]
+    lib.ms_params_default.argtypes = [ctypes.POINTER(Params)]
+    lib.ms_create.argtypes = [ctypes.POINTER(Params), i64, ctypes.POINTER(P)]
+    lib.ms_destroy.argtypes = [P]
+    lib.ms_destroy.restype = None
+    lib.ms_set_stream.argtypes = [P, P]
+    lib.ms_set_points.argtypes = [P, ctypes.POINTER(Grid), i32]
+    lib.ms_set_state.argtypes = [P, P, P, P]
+    lib.ms_step.argtypes = [P, P, P, d, i32]
+    lib.ms_run_track.argtypes = [P, ctypes.POINTER(HeatSource), i64, d]
+    lib.ms_get_fractions.argtypes = [P, P, P, P, P]
+    lib.ms_get_aux.argtypes = [P, P]
+    lib.ms_get_state.argtypes = [P, P, ctypes.POINTER(ctypes.c_size_t)]
+    lib.ms_set_state_blob.argtypes = [P, P, ctypes.c_size_t]
+    lib.ms_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.ms_fill_state.argtypes = [P, d, d]
+    lib.ms_reset_stats.argtypes = [P]
+    lib.ms_synchronize.argtypes = [P]
+    for i, s in enumerate(STRUCTS):
+        if lib.ms_struct_size(i) != ctypes.sizeof(s):
+            raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
+                               f"vs ctypes {ctypes.sizeof(s)}")
+    _lib = lib
+    return lib
+
+
+def _check(rc, where):
+    if rc != MS_OK:
+        raise MSError(rc, where, load().ms_last_error().decode())
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    _check(load().ms_params_default(ctypes.byref(p)), "ms_params_default")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def make_heat_source(src) -> tuple:
+    """ms_heat_source for an object with the fields of workloads.HeatSource;
+    returns (struct, keep-alive arrays)."""
+    tr = np.asarray(src.tracks, dtype=np.float64).reshape(-1, 8)
+    ly = np.asarray(src.layers, dtype=np.float64).reshape(-1, 4)
+    tracks = (Track * max(1, len(tr)))()
+    for i, r in enumerate(tr):
+        tracks[i] = Track(r[0], r[1], r[2], r[3], r[4], r[5], r[6], int(r[7]), 0)
+    layers = (Layer * len(ly))()
+    for i, r in enumerate(ly):
+        layers[i] = Layer(*r)
+    h = HeatSource(src.A, src.k, src.alpha, src.T0, src.T_max, src.t_offset, src.z_tol,
+                   len(tr), len(ly), ctypes.cast(tracks, ctypes.POINTER(Track)),
+                   ctypes.cast(layers, ctypes.POINTER(Layer)))
+    return h, (tracks, layers)
+
+
+class Context:
+    """One ms_ctx: n_points points on the current CUDA device."""
+
+    def __init__(self, n_points: int, params: Params | None = None, **overrides):
+        self._lib = load()
+        p = params if params is not None else default_params(**overrides)
+        if params is not None:
+            for k, v in overrides.items():
+                setattr(p, k, v)
+        self.params = p
+        self.n = int(n_points)
+        self._h = ctypes.c_void_p()
+        _check(self._lib.ms_create(ctypes.byref(p), self.n, ctypes.byref(self._h)), "ms_create")
+        self._keep = None
+
+    def close(self):
+        if self._h:
+            self._lib.ms_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream_handle: int | None):
+        _check(self._lib.ms_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)), "ms_set_stream")
+
+    def set_points(self, grids):
+        arr = (Grid * len(grids))()
+        for i, g in enumerate(grids):
+            arr[i] = Grid((d * 3)(*g.origin), (d * 3)(*g.spacing), (i32 * 3)(*g.dims), 0)
+        _check(self._lib.ms_set_points(self._h, arr, len(grids)), "ms_set_points")
+
+    def set_state(self, xas, xam, aux=None):
+        xas, xam = _f64(xas, self.n), _f64(xam, self.n)
+        a = None if aux is None else _f64(aux, self.n)
+        _check(self._lib.ms_set_state(self._h, _ptr(xas), _ptr(xam), None if a is None else _ptr(a)),
+               "ms_set_state")
+
+    def fill_state(self, xas=0.9, xam=0.0):
+        """Uniform state on the device (no host copy); resets the step counter."""
+        _check(self._lib.ms_fill_state(self._h, float(xas), float(xam)), "ms_fill_state")
+
+    def reset_stats(self):
+        _check(self._lib.ms_reset_stats(self._h), "ms_reset_stats")
+
+    def step(self, T_prev, T_new, dt):
+        """One explicit step with host temperature arrays (float32)."""
+        t0 = np.ascontiguousarray(T_prev, dtype=np.float32)
+        t1 = np.ascontiguousarray(T_new, dtype=np.float32)
+        assert t0.size == self.n and t1.size == self.n
+        _check(self._lib.ms_step(self._h, _ptr(t0), _ptr(t1), float(dt), 0), "ms_step")
+
+    def step_device(self, T_prev_ptr: int, T_new_ptr: int, dt):
+        """One explicit step with device temperature arrays (raw pointers)."""
+        _check(self._lib.ms_step(self._h, ctypes.c_void_p(T_prev_ptr), ctypes.c_void_p(T_new_ptr),
+                                 float(dt), MS_PTR_DEVICE), "ms_step")
+
+    def run_track(self, sources, n_steps, dt):
+        hs = [make_heat_source(s) for s in sources]
+        arr = (HeatSource * len(hs))(*[h for h, _ in hs])
+        self._keep = (arr, hs)
+        _check(self._lib.ms_run_track(self._h, arr, int(n_steps), float(dt)), "ms_run_track")
+
+    def fractions(self, with_beta=True):
+        out = [np.empty(self.n) for _ in range(4)]
+        _check(self._lib.ms_get_fractions(self._h, _ptr(out[0]), _ptr(out[1]),
+                                          _ptr(out[2]) if with_beta else None,
+                                          _ptr(out[3]) if with_beta else None), "ms_get_fractions")
+        return tuple(out) if with_beta else (out[0], out[1])
+
+    def fractions_into(self, outs):
+        """Write X_as, X_am, X_beta, X_liq into four caller arrays (float64,
+        n_points each, e.g. pinned host memory)."""
+        assert len(outs) == 4 and all(o.dtype == np.float64 and o.size == self.n and
+                                      o.flags["C_CONTIGUOUS"] for o in outs)
+        _check(self._lib.ms_get_fractions(self._h, *[_ptr(o) for o in outs]), "ms_get_fractions")
+
+    def aux(self):
+        out = np.empty(self.n)
+        _check(self._lib.ms_get_aux(self._h, _ptr(out)), "ms_get_aux")
+        return out
+
+    def checkpoint(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        _check(self._lib.ms_get_state(self._h, None, ctypes.byref(n)), "ms_get_state")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.ms_get_state(self._h, buf, ctypes.byref(n)), "ms_get_state")
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.ms_set_state_blob(self._h, buf, len(blob)), "ms_set_state_blob")
+
+    def stats(self) -> Stats:
+        s = Stats()
+        _check(self._lib.ms_stats(self._h, ctypes.byref(s)), "ms_stats")
+        return s
+
+    def synchronize(self):
+        _check(self._lib.ms_synchronize(self._h), "ms_synchronize")

@@ -1,0 +1,829 @@
+// C ABI of the microstructure point solver (declared in include/ms.h).
+//
+// The context owns the padded SoA state on the device (X_as, X_am in the
+// fraction type, the App. A variable as float), the specimen table, the track
+// and layer tables of the moving sources, a per-launch source table and a
+// staging buffer for host <-> device copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ms_internal.h"
+
+using ms::LayerDev;
+using ms::SpecDev;
+using ms::SrcEntry;
+using ms::SrcLevel;
+using ms::TrackDev;
+using ms::TILE;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define MS_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+constexpr uint64_t kBlobMagic = 0x4d53434b50543031ull;  // "MSCKPT01"
+
+struct BlobHeader {
+  uint64_t magic;
+  int64_t n_points;
+  int64_t n_pad;
+  int32_t precision;
+  int32_t reserved;
+  int64_t step_n;
+  int64_t n_base;
+  double t_base;
+  double dt;
+};
+
+}  // namespace
+
+struct ms_ctx {
+  ms_params prm{};
+  ms::ModelConst mc{};
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t n_points = 0;
+  size_t fbytes = 4;  // bytes of the fraction type
+
+  // layout
+  std::vector<SpecDev> specs_h;
+  SpecDev* specs_d = nullptr;
+  int32_t* tile_spec_d = nullptr;
+  int64_t n_tiles = 0;
+  bool has_grid = false;
+
+  // state (padded)
+  void* xas_d = nullptr;
+  void* xam_d = nullptr;
+  float* aux_d = nullptr;
+  int* err_d = nullptr;
+
+  // staging
+  double* stage_d = nullptr;
+  float* Tstage_d = nullptr;
+  const float* T_last = nullptr;
+
+  // moving sources
+  std::vector<TrackDev> tracks_h;
+  std::vector<LayerDev> layers_h;
+  TrackDev* tracks_d = nullptr;
+  LayerDev* layers_d = nullptr;
+  size_t tracks_cap = 0, layers_cap = 0;
+  int slots = 0;
+  bool src_valid = false;
+  SrcLevel* levels_d = nullptr;
+  SrcEntry* entries_d = nullptr;
+  size_t levels_cap = 0, entries_cap = 0;
+
+  // time
+  int64_t step_n = 0;
+  int64_t n_base = 0;
+  double t_base = 0.0;
+  double dt = 0.0;
+
+  // counters
+  ms_stats_t st{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+  // per-launch timing of the hot kernel (MS_FLAG_TIME_KERNELS)
+  std::vector<cudaEvent_t> kev;  // pairs: start, stop
+  size_t kev_used = 0;           // pairs recorded and not yet harvested
+};
+
+namespace {
+
+ms::ModelConst make_const(const ms_params& p) {
+  const double l2e = 1.4426950408889634074;
+  ms::ModelConst m{};
+  m.T_s = float(p.T_s);
+  m.T_l = float(p.T_l);
+  m.inv_mushy = float(1.0 / (p.T_l - p.T_s));
+  m.T_as_start = float(p.T_as_start);
+  m.T_as_end = float(p.T_as_end);
+  m.T_am_start = float(p.T_am_start);
+  m.T_inf = float(p.T_inf);
+  m.kaeq_l2 = float(p.k_alpha_eq * l2e);
+  m.kam_l2 = float(p.k_am_eq * l2e);
+  m.k1 = float(p.k1);
+  m.k2 = float(p.k2);
+  m.k3_l2 = float(p.k3 * l2e);
+  m.f = float(p.f);
+  m.c_as = float(p.c_as);
+  m.c_b = float(p.c_b);
+  m.inv_c_as = float(1.0 / p.c_as);
+  m.inv_c_b = float(1.0 / p.c_b);
+  m.pa = float((p.c_as - 1.0) / p.c_as);
+  m.qa = float((p.c_as + 1.0) / p.c_as);
+  m.pb = float((p.c_b - 1.0) / p.c_b);
+  m.qb = float((p.c_b + 1.0) / p.c_b);
+  m.T_cap0 = float(p.T_as_start + p.T_reg);
+  m.inv_T_reg = float(1.0 / p.T_reg);
+  m.init_exit = float(p.init_exit);
+  m.init_exit_floor = float(p.init_exit_floor);
+  m.T_thr = float(p.T_thr);
+  m.martensite_literal = p.martensite_literal ? 1 : 0;
+  m.init_ba_steps = p.init_ba_steps ? 1 : 0;
+  return m;
+}
+
+int check_params(const ms_params& p) {
+  auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+  if (!(pos(p.T_s) && pos(p.T_l) && p.T_l > p.T_s))
+    return fail(MS_ERR_INVALID_ARG, "need 0 < T_s < T_l");
+  if (!(pos(p.T_as_end) && p.T_as_start > p.T_as_end && pos(p.T_am_start) && pos(p.T_inf)))
+    return fail(MS_ERR_INVALID_ARG, "need T_as_end < T_as_start and positive temperatures");
+  if (!(pos(p.k_alpha_eq) && pos(p.k_am_eq) && pos(p.k1) && pos(p.k3) && pos(p.f) &&
+        std::isfinite(p.k2)))
+    return fail(MS_ERR_INVALID_ARG, "rate and equilibrium constants must be positive");
+  if (!(p.c_as > 1.0 && p.c_b > 1.0 && std::isfinite(p.c_as) && std::isfinite(p.c_b)))
+    return fail(MS_ERR_INVALID_ARG, "c_as and c_b must be > 1");
+  if (!pos(p.T_reg)) return fail(MS_ERR_INVALID_ARG, "T_reg must be > 0");
+  if (!(std::isfinite(p.init_exit) && p.init_exit >= 0 && std::isfinite(p.init_exit_floor) &&
+        p.init_exit_floor >= 0))
+    return fail(MS_ERR_INVALID_ARG, "init_exit and init_exit_floor must be >= 0");
+  if (!std::isfinite(p.T_thr)) return fail(MS_ERR_INVALID_ARG, "T_thr must be finite");
+  if (p.precision != MS_F32 && p.precision != MS_F64ACC && p.precision != MS_KAHAN)
+    return fail(MS_ERR_INVALID_ARG, "unknown precision %d", p.precision);
+  if (p.precision == MS_KAHAN)
+    return fail(MS_ERR_UNSUPPORTED, "MS_KAHAN is not available in this build");
+  if (p.steps_per_launch < 1 || p.steps_per_launch > ms::MAX_LEVELS - 1)
+    return fail(MS_ERR_INVALID_ARG, "steps_per_launch must be in [1, %d]", ms::MAX_LEVELS - 1);
+  if (p.block_threads != 0 &&
+      (p.block_threads < 32 || p.block_threads > 256 || p.block_threads % 32 != 0))
+    return fail(MS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+  return MS_OK;
+}
+
+int block_threads(const ms_ctx* c) { return c->prm.block_threads ? c->prm.block_threads : 128; }
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t n) {
+  if (n <= *cap && *p) return MS_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  MS_CUDA(cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T)));
+  *cap = n;
+  return MS_OK;
+}
+
+void free_layout(ms_ctx* c) {
+  cudaFree(c->specs_d);
+  cudaFree(c->tile_spec_d);
+  cudaFree(c->xas_d);
+  cudaFree(c->xam_d);
+  cudaFree(c->aux_d);
+  cudaFree(c->stage_d);
+  cudaFree(c->Tstage_d);
+  c->specs_d = nullptr;
+  c->tile_spec_d = nullptr;
+  c->xas_d = c->xam_d = nullptr;
+  c->aux_d = nullptr;
+  c->stage_d = nullptr;
+  c->Tstage_d = nullptr;
+  c->T_last = nullptr;
+}
+
+// (Re)build the padded layout for the current specs_h and reset the state.
+int build_layout(ms_ctx* c) {
+  free_layout(c);
+  int64_t tiles = 0, pad = 0, nat = 0;
+  for (auto& s : c->specs_h) {
+    s.nat_off = nat;
+    s.pad_off = pad;
+    s.tile0 = tiles;
+    s.n_tiles = int32_t((s.n + TILE - 1) / TILE);
+    tiles += s.n_tiles;
+    pad += int64_t(s.n_tiles) * TILE;
+    nat += s.n;
+  }
+  if (tiles > INT32_MAX / 2) return fail(MS_ERR_INVALID_ARG, "too many points (%lld tiles)", (long long)tiles);
+  c->n_tiles = tiles;
+  std::vector<int32_t> ts(static_cast<size_t>(tiles));
+  for (size_t s = 0; s < c->specs_h.size(); ++s)
+    for (int32_t t = 0; t < c->specs_h[s].n_tiles; ++t) ts[size_t(c->specs_h[s].tile0 + t)] = int32_t(s);
+  const size_t np = size_t(pad);
+  MS_CUDA(cudaMalloc(&c->specs_d, c->specs_h.size() * sizeof(SpecDev)));
+  MS_CUDA(cudaMalloc(&c->tile_spec_d, ts.size() * sizeof(int32_t)));
+  MS_CUDA(cudaMalloc(&c->xas_d, np * c->fbytes));
+  MS_CUDA(cudaMalloc(&c->xam_d, np * c->fbytes));
+  MS_CUDA(cudaMalloc(&c->aux_d, np * sizeof(float)));
+  MS_CUDA(cudaMalloc(&c->stage_d, size_t(c->n_points) * 4 * sizeof(double)));
+  MS_CUDA(cudaMemcpy(c->specs_d, c->specs_h.data(), c->specs_h.size() * sizeof(SpecDev),
+                     cudaMemcpyHostToDevice));
+  MS_CUDA(cudaMemcpy(c->tile_spec_d, ts.data(), ts.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (c->fbytes == 4)
+    MS_CUDA(ms::launch_set_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
+                                        nullptr, (float*)c->xas_d, (float*)c->xam_d, c->aux_d,
+                                        c->stream));
+  else
+    MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
+                                         nullptr, (double*)c->xas_d, (double*)c->xam_d, c->aux_d,
+                                         c->stream));
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  c->step_n = c->n_base = 0;
+  c->t_base = 0.0;
+  c->src_valid = false;
+  return MS_OK;
+}
+
+// Record the start (second == false) or stop event of a timed hot-kernel launch.
+int kernel_event(ms_ctx* c, bool stop) {
+  if (!(c->prm.flags & MS_FLAG_TIME_KERNELS)) return MS_OK;
+  const size_t i = 2 * c->kev_used + (stop ? 1 : 0);
+  while (c->kev.size() <= i) {
+    cudaEvent_t e;
+    MS_CUDA(cudaEventCreate(&e));
+    c->kev.push_back(e);
+  }
+  MS_CUDA(cudaEventRecord(c->kev[i], c->stream));
+  if (stop) c->kev_used++;
+  return MS_OK;
+}
+
+// Add the recorded launch times to the counters (stream already synchronised).
+int harvest_kernel_events(ms_ctx* c) {
+  for (size_t p = 0; p < c->kev_used; ++p) {
+    float ms_ = 0.f;
+    MS_CUDA(cudaEventElapsedTime(&ms_, c->kev[2 * p], c->kev[2 * p + 1]));
+    c->st.hot_kernel_ms += ms_;
+    c->st.hot_kernel_launches++;
+  }
+  c->kev_used = 0;
+  return MS_OK;
+}
+
+int check_device_error(ms_ctx* c) {
+  int err = 0;
+  MS_CUDA(cudaMemcpyAsync(&err, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  c->st.device_error = err;
+  if (c->timed) {
+    float ms_ = 0.f;
+    if (cudaEventElapsedTime(&ms_, c->ev0, c->ev1) == cudaSuccess) c->st.last_run_ms = ms_;
+    c->timed = false;
+  }
+  int rc = harvest_kernel_events(c);
+  if (rc != MS_OK) return rc;
+  if (err & ms::DEVERR_NONFINITE) return fail(MS_ERR_NONFINITE, "a fraction became non-finite");
+  if (err & ms::DEVERR_TIMEOUT) return fail(MS_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up");
+  return MS_OK;
+}
+
+// Upload the heat sources if they differ from the cached copy.
+int set_sources(ms_ctx* c, const ms_heat_source* src) {
+  std::vector<TrackDev> tr;
+  std::vector<LayerDev> ly;
+  std::vector<SpecDev> specs = c->specs_h;
+  int slots = 1;
+  for (size_t s = 0; s < specs.size(); ++s) {
+    const ms_heat_source& h = src[s];
+    if (!(std::isfinite(h.A) && h.A >= 0 && h.k > 0 && h.alpha > 0 && std::isfinite(h.T0) &&
+          h.T0 > 0 && h.T_max > h.T0 && std::isfinite(h.t_offset) && h.z_tol >= 0 &&
+          h.n_tracks >= 0 && h.n_layers >= 1 && h.layers && (h.n_tracks == 0 || h.tracks)))
+      return fail(MS_ERR_INVALID_ARG, "invalid heat source of specimen %zu", s);
+    specs[s].A = h.A;
+    specs[s].k = h.k;
+    specs[s].alpha = h.alpha;
+    specs[s].t_offset = h.t_offset;
+    specs[s].T0 = float(h.T0);
+    specs[s].T_max = float(h.T_max);
+    specs[s].z_tol = float(h.z_tol);
+    specs[s].track0 = int32_t(tr.size());
+    specs[s].n_tracks = h.n_tracks;
+    specs[s].layer0 = int32_t(ly.size());
+    specs[s].n_layers = h.n_layers;
+    std::vector<int> per_layer(size_t(h.n_layers), 0);
+    for (int j = 0; j < h.n_tracks; ++j) {
+      const ms_track& t = h.tracks[j];
+      const double un = std::sqrt(t.ux * t.ux + t.uy * t.uy);
+      if (!(t.layer >= 0 && t.layer < h.n_layers && std::fabs(un - 1.0) < 1e-6 && t.v > 0 &&
+            std::isfinite(t.v) && t.P >= 0 && std::isfinite(t.P) && std::isfinite(t.x0) &&
+            std::isfinite(t.y0) && std::isfinite(t.t_start)))
+        return fail(MS_ERR_INVALID_ARG, "invalid track %d of specimen %zu", j, s);
+      tr.push_back(TrackDev{t.x0, t.y0, t.ux, t.uy, t.v, t.P, t.t_start, t.layer, 0});
+      slots = std::max(slots, ++per_layer[size_t(t.layer)]);
+    }
+    for (int j = 0; j < h.n_layers; ++j) {
+      const ms_layer& L = h.layers[j];
+      if (!(std::isfinite(L.z_surface) && L.t_scan_end >= L.t_begin && L.t_end >= L.t_scan_end))
+        return fail(MS_ERR_INVALID_ARG, "invalid layer %d of specimen %zu", j, s);
+      ly.push_back(LayerDev{L.z_surface, L.t_begin, L.t_scan_end, L.t_end});
+    }
+  }
+  const bool same = c->src_valid && slots == c->slots && tr.size() == c->tracks_h.size() &&
+                    ly.size() == c->layers_h.size() &&
+                    std::memcmp(specs.data(), c->specs_h.data(), specs.size() * sizeof(SpecDev)) == 0 &&
+                    (tr.empty() || std::memcmp(tr.data(), c->tracks_h.data(), tr.size() * sizeof(TrackDev)) == 0) &&
+                    std::memcmp(ly.data(), c->layers_h.data(), ly.size() * sizeof(LayerDev)) == 0;
+  if (same) return MS_OK;
+  MS_CUDA(cudaStreamSynchronize(c->stream));  // previous launches may still read the tables
+  int rc;
+  if ((rc = grow(&c->tracks_d, &c->tracks_cap, tr.size())) != MS_OK) return rc;
+  if ((rc = grow(&c->layers_d, &c->layers_cap, ly.size())) != MS_OK) return rc;
+  if (!tr.empty())
+    MS_CUDA(cudaMemcpy(c->tracks_d, tr.data(), tr.size() * sizeof(TrackDev), cudaMemcpyHostToDevice));
+  MS_CUDA(cudaMemcpy(c->layers_d, ly.data(), ly.size() * sizeof(LayerDev), cudaMemcpyHostToDevice));
+  MS_CUDA(cudaMemcpy(c->specs_d, specs.data(), specs.size() * sizeof(SpecDev), cudaMemcpyHostToDevice));
+  c->specs_h = specs;
+  c->tracks_h = tr;
+  c->layers_h = ly;
+  c->slots = slots;
+  c->src_valid = true;
+  return MS_OK;
+}
+
+int ensure_table(ms_ctx* c, int n_levels) {
+  int rc;
+  const size_t ns = c->specs_h.size();
+  if ((rc = grow(&c->levels_d, &c->levels_cap, ns * size_t(n_levels))) != MS_OK) return rc;
+  if ((rc = grow(&c->entries_d, &c->entries_cap, ns * size_t(n_levels) * size_t(c->slots))) != MS_OK)
+    return rc;
+  return MS_OK;
+}
+
+int launch_table(ms_ctx* c, int64_t level0, int n_levels) {
+  ms::TableArgs ta{};
+  ta.specs = c->specs_d;
+  ta.tracks = c->tracks_d;
+  ta.layers = c->layers_d;
+  ta.n_specs = int32_t(c->specs_h.size());
+  ta.n_levels = n_levels;
+  ta.slots = c->slots;
+  ta.n0 = level0 - c->n_base;
+  ta.t_base = c->t_base;
+  ta.dt = c->dt;
+  ta.levels = c->levels_d;
+  ta.entries = c->entries_d;
+  MS_CUDA(ms::launch_src_table(ta, c->stream));
+  c->st.launches++;
+  return MS_OK;
+}
+
+template <typename FT>
+int run_track_impl(ms_ctx* c, int64_t n_steps) {
+  const int S = c->prm.steps_per_launch;
+  int rc;
+  if ((rc = ensure_table(c, S + 1)) != MS_OK) return rc;
+  int64_t left = n_steps;
+  while (left > 0) {
+    const int steps = int(std::min<int64_t>(S, left));
+    if ((rc = launch_table(c, c->step_n, steps + 1)) != MS_OK) return rc;
+    ms::TrackArgs<FT> a{};
+    a.m = c->mc;
+    a.specs = c->specs_d;
+    a.tile_spec = c->tile_spec_d;
+    a.tile_list = nullptr;
+    a.n_work = int32_t(c->n_tiles);
+    a.n_levels = steps + 1;
+    a.slots = c->slots;
+    a.dt = float(c->dt);
+    a.levels = c->levels_d;
+    a.entries = c->entries_d;
+    a.xas = (FT*)c->xas_d;
+    a.xam = (FT*)c->xam_d;
+    a.aux = c->aux_d;
+    a.err = c->err_d;
+    if ((rc = kernel_event(c, false)) != MS_OK) return rc;
+    MS_CUDA(ms::launch_track<FT>(a, block_threads(c), c->stream));
+    if ((rc = kernel_event(c, true)) != MS_OK) return rc;
+    c->st.launches++;
+    c->step_n += steps;
+    c->st.steps += steps;
+    c->st.point_updates += int64_t(steps) * c->n_points;
+    c->st.tile_steps_total += int64_t(steps) * c->n_tiles;
+    c->st.tile_steps_active += int64_t(steps) * c->n_tiles;
+    left -= steps;
+  }
+  return MS_OK;
+}
+
+template <typename FT>
+int step_impl(ms_ctx* c, const float* T0, const float* T1) {
+  ms::StepArgs<FT> a{};
+  a.m = c->mc;
+  a.n = c->n_points;
+  a.dt = float(c->dt);
+  a.T0 = T0;
+  a.T1 = T1;
+  a.xas = (FT*)c->xas_d;
+  a.xam = (FT*)c->xam_d;
+  a.aux = c->aux_d;
+  a.err = c->err_d;
+  int rc;
+  if ((rc = kernel_event(c, false)) != MS_OK) return rc;
+  MS_CUDA(ms::launch_step_ext<FT>(a, block_threads(c), c->stream));
+  if ((rc = kernel_event(c, true)) != MS_OK) return rc;
+  c->st.launches++;
+  return MS_OK;
+}
+
+void set_dt(ms_ctx* c, double dt) {
+  if (c->dt != dt) {
+    c->t_base += double(c->step_n - c->n_base) * c->dt;
+    c->n_base = c->step_n;
+    c->dt = dt;
+  }
+}
+
+}  // namespace
+
+// =============================================================== C ABI
+extern "C" {
+
+const char* ms_version(void) { return "ms-gb300 1.0.0 (sm_103a)"; }
+
+const char* ms_strerror(int code) {
+  switch (code) {
+    case MS_OK: return "ok";
+    case MS_ERR_INVALID_ARG: return "invalid argument";
+    case MS_ERR_OOM: return "out of memory";
+    case MS_ERR_CUDA: return "CUDA error";
+    case MS_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case MS_ERR_NONFINITE: return "non-finite fraction";
+    case MS_ERR_STATE: return "call out of order";
+    case MS_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+const char* ms_last_error(void) { return g_last_error.c_str(); }
+
+size_t ms_struct_size(int which) {
+  switch (which) {
+    case 0: return sizeof(ms_params);
+    case 1: return sizeof(ms_grid);
+    case 2: return sizeof(ms_track);
+    case 3: return sizeof(ms_layer);
+    case 4: return sizeof(ms_heat_source);
+    case 5: return sizeof(ms_stats_t);
+    default: return 0;
+  }
+}
+
+int ms_params_default(ms_params* p) {
+  if (!p) return fail(MS_ERR_INVALID_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->T_s = 1878.0;          // Table 1 / Table 2
+  p->T_l = 1928.0;
+  p->T_as_start = 1273.0;   // Table 2
+  p->T_as_end = 935.0;
+  p->T_am_start = 848.0;
+  p->T_inf = 293.0;
+  p->k_alpha_eq = 0.0068;
+  p->k_am_eq = 0.00415;
+  p->c_as = 2.51;           // Table 3
+  p->c_b = 11.0;
+  p->k1 = 0.294;
+  p->k2 = 850.0;
+  p->k3 = 0.0337;
+  p->f = 3.8;
+  p->T_reg = 100.0;         // Sec. 2.2
+  p->init_exit = 1e-15;     // App. A
+  p->init_exit_floor = 1e-3;
+  p->T_thr = 0.0;
+  p->martensite_literal = 0;
+  p->init_ba_steps = 0;
+  p->precision = MS_F32;
+  p->steps_per_launch = 32;
+  p->rebuild_steps = 0;
+  p->block_threads = 0;
+  return MS_OK;
+}
+
+int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
+  if (!p || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (n_points <= 0) return fail(MS_ERR_INVALID_ARG, "n_points must be > 0");
+  int rc = check_params(*p);
+  if (rc != MS_OK) return rc;
+  ms_ctx* c = new (std::nothrow) ms_ctx();
+  if (!c) return fail(MS_ERR_OOM, "host allocation failed");
+  c->prm = *p;
+  c->mc = make_const(*p);
+  c->fbytes = p->precision == MS_F64ACC ? 8 : 4;
+  c->n_points = n_points;
+  auto bail = [&](int code) { ms_destroy(c); return code; };
+  if (cudaGetDevice(&c->device) != cudaSuccess)
+    return bail(fail(MS_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError())));
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(MS_ERR_CUDA, "stream creation failed"));
+  c->stream = c->own_stream;
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
+    return bail(fail(MS_ERR_CUDA, "event creation failed"));
+  if (cudaMalloc(&c->err_d, sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->err_d, 0, sizeof(int)) != cudaSuccess)
+    return bail(fail(MS_ERR_OOM, "device allocation failed"));
+  SpecDev s{};
+  s.nx = int32_t(std::min<int64_t>(n_points, INT32_MAX));
+  s.ny = s.nz = 1;
+  s.n = n_points;
+  c->specs_h.assign(1, s);
+  if ((rc = build_layout(c)) != MS_OK) return bail(rc);
+  *out = c;
+  return MS_OK;
+}
+
+void ms_destroy(ms_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_layout(c);
+  cudaFree(c->err_d);
+  cudaFree(c->tracks_d);
+  cudaFree(c->layers_d);
+  cudaFree(c->levels_d);
+  cudaFree(c->entries_d);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : c->kev) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+int ms_set_stream(ms_ctx* c, void* stream) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+  return MS_OK;
+}
+
+int ms_set_points(ms_ctx* c, const ms_grid* grids, int32_t n_specimens) {
+  if (!c || !grids || n_specimens <= 0) return fail(MS_ERR_INVALID_ARG, "NULL grids or n_specimens <= 0");
+  std::vector<SpecDev> specs;
+  int64_t total = 0;
+  for (int32_t s = 0; s < n_specimens; ++s) {
+    const ms_grid& g = grids[s];
+    if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1)
+      return fail(MS_ERR_INVALID_ARG, "grid %d: dims must be >= 1", s);
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(g.origin[a]) || !std::isfinite(g.spacing[a]))
+        return fail(MS_ERR_INVALID_ARG, "grid %d: non-finite origin or spacing", s);
+    SpecDev d{};
+    d.ox = float(g.origin[0]); d.oy = float(g.origin[1]); d.oz = float(g.origin[2]);
+    d.dx = float(g.spacing[0]); d.dy = float(g.spacing[1]); d.dz = float(g.spacing[2]);
+    d.nx = g.dims[0]; d.ny = g.dims[1]; d.nz = g.dims[2];
+    d.n = int64_t(g.dims[0]) * g.dims[1] * g.dims[2];
+    d.n_layers = 1;
+    total += d.n;
+    specs.push_back(d);
+  }
+  if (total != c->n_points)
+    return fail(MS_ERR_INVALID_ARG, "grids hold %lld points, context has %lld", (long long)total,
+                (long long)c->n_points);
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  c->specs_h = specs;
+  c->has_grid = true;
+  return build_layout(c);
+}
+
+int ms_set_state(ms_ctx* c, const double* xas, const double* xam, const double* aux) {
+  if (!c || !xas || !xam) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  const int64_t n = c->n_points;
+  for (int64_t i = 0; i < n; ++i) {
+    const double a = xas[i], m = xam[i];
+    if (!std::isfinite(a) || !std::isfinite(m)) return fail(MS_ERR_NONFINITE, "point %lld: non-finite fraction", (long long)i);
+    if (a < 0 || m < 0 || a + m > 0.9 + 1e-6)
+      return fail(MS_ERR_INVALID_ARG, "point %lld: need X_as, X_am >= 0 and X_as + X_am <= 0.9", (long long)i);
+    if (aux) {
+      const double v = aux[i];
+      if (!(v == 0.0 || v == -1.0 || (v > 0.0 && v < 0.9)))
+        return fail(MS_ERR_INVALID_ARG, "point %lld: aux must be 0, -1 or in (0, 0.9)", (long long)i);
+    }
+  }
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  double* d = c->stage_d;
+  MS_CUDA(cudaMemcpy(d, xas, size_t(n) * sizeof(double), cudaMemcpyHostToDevice));
+  MS_CUDA(cudaMemcpy(d + n, xam, size_t(n) * sizeof(double), cudaMemcpyHostToDevice));
+  if (aux) MS_CUDA(cudaMemcpy(d + 2 * n, aux, size_t(n) * sizeof(double), cudaMemcpyHostToDevice));
+  if (c->fbytes == 4)
+    MS_CUDA(ms::launch_set_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles, d, d + n,
+                                        aux ? d + 2 * n : nullptr, (float*)c->xas_d,
+                                        (float*)c->xam_d, c->aux_d, c->stream));
+  else
+    MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, d, d + n,
+                                         aux ? d + 2 * n : nullptr, (double*)c->xas_d,
+                                         (double*)c->xam_d, c->aux_d, c->stream));
+  MS_CUDA(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  c->step_n = c->n_base = 0;
+  c->t_base = 0.0;
+  c->T_last = nullptr;
+  return MS_OK;
+}
+
+int ms_fill_state(ms_ctx* c, double xas, double xam) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  if (!(std::isfinite(xas) && std::isfinite(xam) && xas >= 0 && xam >= 0 && xas + xam <= 0.9 + 1e-6))
+    return fail(MS_ERR_INVALID_ARG, "need X_as, X_am >= 0 and X_as + X_am <= 0.9");
+  if (c->fbytes == 4)
+    MS_CUDA(ms::launch_set_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
+                                        nullptr, (float*)c->xas_d, (float*)c->xam_d, c->aux_d,
+                                        c->stream, xas, xam));
+  else
+    MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
+                                         nullptr, (double*)c->xas_d, (double*)c->xam_d, c->aux_d,
+                                         c->stream, xas, xam));
+  c->st.launches++;
+  c->step_n = c->n_base = 0;
+  c->t_base = 0.0;
+  c->T_last = nullptr;
+  return MS_OK;
+}
+
+int ms_reset_stats(ms_ctx* c) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  const int32_t err = c->st.device_error;
+  c->st = ms_stats_t{};
+  c->st.device_error = err;
+  c->kev_used = 0;
+  c->timed = false;
+  return MS_OK;
+}
+
+int ms_step(ms_ctx* c, const float* T_prev, const float* T_new, double dt, int32_t flags) {
+  if (!c || !T_prev || !T_new) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  if (!(std::isfinite(dt) && dt > 0)) return fail(MS_ERR_INVALID_ARG, "dt must be > 0");
+  if (c->specs_h.size() != 1) return fail(MS_ERR_STATE, "ms_step needs a single-specimen context");
+  const int64_t n = c->n_points;
+  const float *t0 = T_prev, *t1 = T_new;
+  if (!(flags & MS_PTR_DEVICE)) {
+    if (!c->Tstage_d) MS_CUDA(cudaMalloc(&c->Tstage_d, size_t(n) * 2 * sizeof(float)));
+    MS_CUDA(cudaMemcpyAsync(c->Tstage_d, T_prev, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    MS_CUDA(cudaMemcpyAsync(c->Tstage_d + n, T_new, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    t0 = c->Tstage_d;
+    t1 = c->Tstage_d + n;
+  }
+  set_dt(c, dt);
+  MS_CUDA(cudaEventRecord(c->ev0, c->stream));
+  int rc = c->fbytes == 4 ? step_impl<float>(c, t0, t1) : step_impl<double>(c, t0, t1);
+  if (rc != MS_OK) return rc;
+  MS_CUDA(cudaEventRecord(c->ev1, c->stream));
+  c->timed = true;
+  c->T_last = t1;
+  c->step_n += 1;
+  c->st.steps += 1;
+  c->st.point_updates += n;
+  return MS_OK;
+}
+
+int ms_run_track(ms_ctx* c, const ms_heat_source* src, int64_t n_steps, double dt) {
+  if (!c || !src) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  if (!(std::isfinite(dt) && dt > 0)) return fail(MS_ERR_INVALID_ARG, "dt must be > 0");
+  if (n_steps < 0) return fail(MS_ERR_INVALID_ARG, "n_steps must be >= 0");
+  if (!c->has_grid) return fail(MS_ERR_STATE, "ms_set_points must come first");
+  int rc;
+  if ((rc = set_sources(c, src)) != MS_OK) return rc;
+  set_dt(c, dt);
+  c->T_last = nullptr;
+  MS_CUDA(cudaEventRecord(c->ev0, c->stream));
+  rc = c->fbytes == 4 ? run_track_impl<float>(c, n_steps) : run_track_impl<double>(c, n_steps);
+  if (rc != MS_OK) return rc;
+  MS_CUDA(cudaEventRecord(c->ev1, c->stream));
+  c->timed = true;
+  return MS_OK;
+}
+
+int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double* xliq) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  const int64_t n = c->n_points;
+  double* d = c->stage_d;
+  int rc;
+  if (xbeta || xliq) {
+    const float* T = nullptr;
+    if (c->T_last) {
+      T = c->T_last;
+    } else if (c->has_grid && c->src_valid) {
+      if ((rc = ensure_table(c, 1)) != MS_OK) return rc;
+      if ((rc = launch_table(c, c->step_n, 1)) != MS_OK) return rc;
+    } else {
+      return fail(MS_ERR_STATE, "no temperature known for X_beta / X_liq yet");
+    }
+    if (c->fbytes == 4)
+      MS_CUDA(ms::launch_fractions<float>(c->mc, c->specs_d, c->tile_spec_d, c->n_tiles,
+                                          (const float*)c->xas_d, (const float*)c->xam_d, T,
+                                          c->levels_d, c->entries_d, c->slots, d + 2 * n,
+                                          d + 3 * n, c->stream));
+    else
+      MS_CUDA(ms::launch_fractions<double>(c->mc, c->specs_d, c->tile_spec_d, c->n_tiles,
+                                           (const double*)c->xas_d, (const double*)c->xam_d, T,
+                                           c->levels_d, c->entries_d, c->slots, d + 2 * n,
+                                           d + 3 * n, c->stream));
+  }
+  if (c->fbytes == 4)
+    MS_CUDA(ms::launch_get_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles,
+                                        (const float*)c->xas_d, (const float*)c->xam_d, c->aux_d,
+                                        d, d + n, nullptr, c->stream));
+  else
+    MS_CUDA(ms::launch_get_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles,
+                                         (const double*)c->xas_d, (const double*)c->xam_d,
+                                         c->aux_d, d, d + n, nullptr, c->stream));
+  const size_t nb = size_t(n) * sizeof(double);
+  if (xas) MS_CUDA(cudaMemcpyAsync(xas, d, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (xam) MS_CUDA(cudaMemcpyAsync(xam, d + n, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (xbeta) MS_CUDA(cudaMemcpyAsync(xbeta, d + 2 * n, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (xliq) MS_CUDA(cudaMemcpyAsync(xliq, d + 3 * n, nb, cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);
+}
+
+int ms_get_aux(ms_ctx* c, double* aux) {
+  if (!c || !aux) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  double* d = c->stage_d;
+  if (c->fbytes == 4)
+    MS_CUDA(ms::launch_get_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles,
+                                        (const float*)c->xas_d, (const float*)c->xam_d, c->aux_d,
+                                        nullptr, nullptr, d, c->stream));
+  else
+    MS_CUDA(ms::launch_get_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles,
+                                         (const double*)c->xas_d, (const double*)c->xam_d,
+                                         c->aux_d, nullptr, nullptr, d, c->stream));
+  MS_CUDA(cudaMemcpyAsync(aux, d, size_t(c->n_points) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);
+}
+
+int ms_get_state(ms_ctx* c, void* blob, size_t* bytes) {
+  if (!c || !bytes) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  const size_t np = size_t(c->n_tiles) * TILE;
+  const size_t need = sizeof(BlobHeader) + np * (2 * c->fbytes + sizeof(float));
+  if (!blob) {
+    *bytes = need;
+    return MS_OK;
+  }
+  if (*bytes < need) return fail(MS_ERR_INVALID_ARG, "blob needs %zu bytes", need);
+  BlobHeader h{kBlobMagic, c->n_points, int64_t(np), c->prm.precision, 0, c->step_n, c->n_base,
+               c->t_base, c->dt};
+  char* p = static_cast<char*>(blob);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  MS_CUDA(cudaMemcpyAsync(p, c->xas_d, np * c->fbytes, cudaMemcpyDeviceToHost, c->stream));
+  p += np * c->fbytes;
+  MS_CUDA(cudaMemcpyAsync(p, c->xam_d, np * c->fbytes, cudaMemcpyDeviceToHost, c->stream));
+  p += np * c->fbytes;
+  MS_CUDA(cudaMemcpyAsync(p, c->aux_d, np * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  *bytes = need;
+  return check_device_error(c);
+}
+
+int ms_set_state_blob(ms_ctx* c, const void* blob, size_t bytes) {
+  if (!c || !blob) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  const size_t np = size_t(c->n_tiles) * TILE;
+  const size_t need = sizeof(BlobHeader) + np * (2 * c->fbytes + sizeof(float));
+  BlobHeader h;
+  if (bytes < sizeof(h)) return fail(MS_ERR_INVALID_ARG, "blob too small");
+  std::memcpy(&h, blob, sizeof(h));
+  if (h.magic != kBlobMagic || h.n_points != c->n_points || h.n_pad != int64_t(np) ||
+      h.precision != c->prm.precision || bytes != need)
+    return fail(MS_ERR_INVALID_ARG, "checkpoint does not match this context");
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  const char* p = static_cast<const char*>(blob) + sizeof(h);
+  MS_CUDA(cudaMemcpy(c->xas_d, p, np * c->fbytes, cudaMemcpyHostToDevice));
+  p += np * c->fbytes;
+  MS_CUDA(cudaMemcpy(c->xam_d, p, np * c->fbytes, cudaMemcpyHostToDevice));
+  p += np * c->fbytes;
+  MS_CUDA(cudaMemcpy(c->aux_d, p, np * sizeof(float), cudaMemcpyHostToDevice));
+  c->step_n = h.step_n;
+  c->n_base = h.n_base;
+  c->t_base = h.t_base;
+  c->dt = h.dt;
+  c->T_last = nullptr;
+  return MS_OK;
+}
+
+int ms_stats(ms_ctx* c, ms_stats_t* out) {
+  if (!c || !out) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  int rc = check_device_error(c);
+  *out = c->st;
+  return rc == MS_ERR_CUDA ? rc : MS_OK;
+}
+
+int ms_synchronize(ms_ctx* c) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  return check_device_error(c);
+}
+
+}  // extern "C"

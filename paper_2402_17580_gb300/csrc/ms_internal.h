@@ -1,0 +1,126 @@
+// Internal interface between the C-ABI layer (ms_api.cu) and the kernels
+// (ms_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/ms.h"
+#include "ms_device.cuh"
+
+namespace ms {
+
+constexpr int TILE = 128;          // points per tile = one warp x 4 points per thread
+constexpr int MAX_LEVELS = 513;    // steps_per_launch <= 512
+
+// device error word bits
+constexpr int DEVERR_NONFINITE = 1;
+constexpr int DEVERR_TIMEOUT = 2;
+
+// One specimen as the kernels see it.
+struct SpecDev {
+  float ox, oy, oz;        // grid origin
+  float dx, dy, dz;        // grid spacing
+  int32_t nx, ny, nz;
+  int32_t n_tracks;        // tracks of this specimen (all layers)
+  int64_t n;               // points
+  int64_t nat_off;         // offset in natural (user) order
+  int64_t pad_off;         // offset in the padded device arrays (multiple of TILE)
+  int64_t tile0;           // first tile
+  int32_t n_tiles;
+  int32_t track0;          // first track in the track table
+  int32_t layer0;          // first layer in the layer table
+  int32_t n_layers;
+  float z_tol;
+  float T0, T_max;
+  float pad0;
+  double A, k, alpha, t_offset;
+};
+
+struct TrackDev {
+  double x0, y0, ux, uy, v, P, t_start;
+  int32_t layer, pad;
+};
+
+struct LayerDev {
+  double z, t_begin, t_scan_end, t_end;
+};
+
+// Arguments of the source-table kernel.
+struct TableArgs {
+  const SpecDev* specs;
+  const TrackDev* tracks;
+  const LayerDev* layers;
+  int32_t n_specs;
+  int32_t n_levels;        // levels n0 .. n0 + n_levels - 1
+  int32_t slots;           // entries per (specimen, level)
+  int32_t pad;
+  int64_t n0;              // first level (steps since the time base)
+  double t_base;           // time of level 0 of the time base
+  double dt;
+  SrcLevel* levels;        // [n_specs][n_levels]
+  SrcEntry* entries;       // [n_specs][n_levels][slots]
+};
+
+// Arguments of the run-track kernel (one warp per tile).
+template <typename FT>
+struct TrackArgs {
+  ModelConst m;
+  const SpecDev* specs;
+  const int32_t* tile_spec;    // tile -> specimen
+  const int32_t* tile_list;    // optional list of tiles to process
+  int32_t n_work;              // tiles to process
+  int32_t n_levels;            // steps + 1
+  int32_t slots;
+  float dt;
+  const SrcLevel* levels;
+  const SrcEntry* entries;
+  FT* xas;
+  FT* xam;
+  float* aux;
+  int* err;
+};
+
+// Arguments of the external-temperature step kernel.
+template <typename FT>
+struct StepArgs {
+  ModelConst m;
+  int64_t n;
+  float dt;
+  const float* T0;
+  const float* T1;
+  FT* xas;
+  FT* xam;
+  float* aux;
+  int* err;
+};
+
+// Launchers (ms_kernels.cu).  All asynchronous on `stream`.
+cudaError_t launch_src_table(const TableArgs& a, cudaStream_t stream);
+template <typename FT>
+cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, cudaStream_t stream);
+template <typename FT>
+cudaError_t launch_step_ext(const StepArgs<FT>& a, int block_threads, cudaStream_t stream);
+
+// Natural-order doubles <-> padded device state (one thread per point).
+// xas == nullptr on set fills every point with (xas0, xam0, no initiation).
+template <typename FT>
+cudaError_t launch_set_state(const SpecDev* specs, const int32_t* tile_spec, int64_t n_tiles,
+                             const double* xas, const double* xam, const double* aux,
+                             FT* dxas, FT* dxam, float* daux, cudaStream_t stream,
+                             double xas0 = 0.9, double xam0 = 0.0);
+template <typename FT>
+cudaError_t launch_get_state(const SpecDev* specs, const int32_t* tile_spec, int64_t n_tiles,
+                             const FT* dxas, const FT* dxam, const float* daux,
+                             double* xas, double* xam, double* aux, cudaStream_t stream);
+
+// X_beta and X_liq in natural order.  Temperatures come either from a
+// natural-order array T (external mode) or from level 0 of a source table.
+template <typename FT>
+cudaError_t launch_fractions(const ModelConst& m, const SpecDev* specs, const int32_t* tile_spec,
+                             int64_t n_tiles, const FT* dxas, const FT* dxam, const float* T,
+                             const SrcLevel* levels, const SrcEntry* entries, int32_t slots,
+                             double* xbeta, double* xliq, cudaStream_t stream);
+
+}  // namespace ms

@@ -1,0 +1,112 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point include/ms.h declares, its struct layouts match the
+binding, its defaults are the paper's tables, and argument validation that
+happens before any device work returns the documented codes."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2402_17580_gb300 as ms
+from paper_2402_17580_gb300 import _binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ms_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ms.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", ms.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\b(ms_\w+)\b", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_struct_layouts_match():
+    lib = ms.load()
+    for i, s in enumerate(B.STRUCTS):
+        assert lib.ms_struct_size(i) == ctypes.sizeof(s), s.__name__
+    assert lib.ms_struct_size(99) == 0
+
+
+def test_defaults_are_the_paper_tables(golden):
+    p = ms.default_params()
+    t2, t3 = golden["table2_micro"], golden["table3_diffusion"]
+    for k, v in t2.items():
+        if not k.startswith("_"):
+            assert getattr(p, k) == v, k
+    for k, v in t3.items():
+        if not k.startswith("_"):
+            assert getattr(p, k) == v, k
+    assert p.T_reg == golden["T_reg"]["value"]
+    assert p.init_exit == golden["init_exit"]["value"]
+    assert p.precision == ms.MS_F32
+
+
+def test_defaults_agree_with_the_oracle():
+    import oracle
+    p = ms.default_params()
+    for k, v in oracle.DEFAULTS.items():
+        assert float(getattr(p, k)) == v, k
+
+
+def test_strerror_and_version():
+    lib = ms.load()
+    assert b"sm_103a" in lib.ms_version()
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.ms_strerror(code)
+    assert lib.ms_strerror(-99) == b"unknown status"
+
+
+def test_validation_before_device_work():
+    lib = ms.load()
+    h = ctypes.c_void_p()
+    p = ms.default_params()
+    assert lib.ms_create(ctypes.byref(p), 0, ctypes.byref(h)) == -1
+    assert lib.ms_create(None, 10, ctypes.byref(h)) == -1
+    bad = ms.default_params(c_b=1.0)
+    assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
+    bad = ms.default_params(steps_per_launch=0)
+    assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
+    bad = ms.default_params(block_threads=48)
+    assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
+    assert lib.ms_params_default(None) == -1
+    for fn, args in (("ms_set_points", (None, None, 1)), ("ms_set_state", (None, None, None, None)),
+                     ("ms_step", (None, None, None, 1e-5, 0)), ("ms_run_track", (None, None, 1, 1e-5)),
+                     ("ms_get_fractions", (None, None, None, None, None)), ("ms_get_aux", (None, None)),
+                     ("ms_stats", (None, None)), ("ms_synchronize", (None,))):
+        assert getattr(lib, fn)(*args) == -1, fn
+    lib.ms_destroy(None)
+
+
+def test_product_and_oracle_share_no_code():
+    """The CUDA path never imports the oracle and the oracle never imports the
+    CUDA path; only workloads/ (inputs, no model arithmetic) serves both."""
+    pkg = os.path.join(ROOT, "paper_2402_17580_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.findall(r"(?:import|from)\s+(\w+)", src), f
+                assert "ms_oracle" not in src, f
+    osrc = open(os.path.join(ROOT, "oracle", "ms_oracle.c")).read()
+    assert "#include \"" not in osrc
+    opy = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+    imports = re.findall(r"^\s*(?:import|from)\s+([\w.]+)", opy, flags=re.M)
+    assert not [m for m in imports if m.split(".")[0] in ("paper_2402_17580_gb300", "workloads")]

@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances.  The kernels compute in FP32 with SFU transcendentals (relative
+error ~2^-22) and store the fractions in FP32 (half an ulp of 0.9 is 3e-8).
+One step therefore agrees with the oracle to ~1e-7 absolute; 2e-6 leaves room
+for the temperature-dependent thresholds.  Long runs accumulate one rounding
+per step, so whole runs are held to the target max|dX| <= 1e-4 and the sum of
+the four fractions to 1 +- 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+import workloads as wl
+from tests._util import (gpu_workload, max_abs_diff, oracle_params, oracle_view,
+                         oracle_workload)
+
+pytestmark = pytest.mark.gpu
+
+RUN_TOL = 1e-4      # max|dX| for whole runs (FP32 path vs FP64 oracle)
+SUM_TOL = 1e-6      # |sum of the four fractions - 1|
+STEP_TOL = 2e-6     # one step
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import paper_2402_17580_gb300 as m
+    m.load()
+    return m
+
+
+def check_sum(fr):
+    s = fr[0] + fr[1] + fr[2] + fr[3]
+    assert np.max(np.abs(s - 1.0)) <= SUM_TOL
+    for a in fr:
+        assert np.all(a >= -1e-7) and np.all(a <= 1 + 1e-7)
+
+
+# ------------------------------------------------------------ single step
+@pytest.mark.parametrize("dt,block", [(1e-5, 1), (1e-3, 1), (1e-3, 10)])
+def test_single_step_every_branch(ms, dt, block):
+    """Brute force over random states x random (T^n, T^{n+1}) in every branch
+    region (ragged count), one step via ms_step with host temperature arrays."""
+    n = 6 * 128 + 37
+    xas, xam, T0, T1 = wl.random_states(n, seed=11 + block, block=block)
+    T0, T1 = T0.astype(np.float32), T1.astype(np.float32)
+    ctx = ms.Context(n)
+    ctx.set_state(xas, xam)
+    ctx.step(T0, T1, dt)
+    g = ctx.fractions()
+    st = orc.State.make(oracle_view(xas), oracle_view(xam))
+    orc.step(st, T0.astype(np.float64), T1.astype(np.float64), dt)
+    o = orc.fractions(st, T1.astype(np.float64))
+    assert max_abs_diff(g, np.stack(o)) <= STEP_TOL
+    check_sum(g)
+    gaux = ctx.aux()
+    agree = np.mean((gaux < 0) == (st.mode == orc.MODE_AS_TO_B))
+    assert agree >= 0.999
+
+
+def test_appendix_a_initiation_below_fp32_range(ms):
+    """App. A at 1200 K from (0.9, 0, 0.1): the first step's X~_beta ~ 3.6e-70
+    is far below the FP32 range; the kernel carries it in log2 form."""
+    ctx = ms.Context(1)
+    ctx.set_state([0.9], [0.0])
+    ctx.step(np.float32([1200.0]), np.float32([1200.0]), 1e-5)
+    st = orc.State.make([0.9], [0.0])
+    orc.step(st, 1200.0, 1200.0, 1e-5)
+    assert st.mode[0] == orc.MODE_AS_TO_B
+    assert ctx.aux()[0] == pytest.approx(st.xt[0], rel=1e-4)
+    for _ in range(20):
+        ctx.step(np.float32([1200.0]), np.float32([1200.0]), 1e-5)
+    orc.run_temps(st, np.full(21, 1200.0), 1e-5)
+    assert ctx.aux()[0] == pytest.approx(st.xt[0], rel=1e-4)
+
+
+def test_random_temperature_histories(ms):
+    """Many steps of random temperature walks through every branch."""
+    rng = np.random.default_rng(5)
+    n, steps, dt = 3 * 128 + 5, 300, 1e-4
+    T = np.empty((steps + 1, n), dtype=np.float32)
+    T[0] = rng.uniform(300, 2100, n)
+    for s in range(steps):
+        T[s + 1] = np.clip(T[s] + rng.normal(0, 25, n), 280, 2600)
+    xas, xam, _, _ = wl.random_states(n, seed=3)
+    ctx = ms.Context(n)
+    ctx.set_state(xas, xam)
+    for s in range(steps):
+        ctx.step(T[s], T[s + 1], dt)
+    g = ctx.fractions()
+    st = orc.State.make(oracle_view(xas), oracle_view(xam))
+    orc.run_temps(st, T.astype(np.float64), dt)
+    o = np.stack(orc.fractions(st, T[-1].astype(np.float64)))
+    assert max_abs_diff(g, o) <= RUN_TOL
+    check_sum(g)
+
+
+# ------------------------------------------------------- moving source runs
+def test_line_4096_full(ms):
+    """4096 points on a line under one moving source, 2000 steps of 1e-5 s,
+    every point against the oracle (max|dX| <= 1e-4)."""
+    w = wl.line_4096()
+    _, g = gpu_workload(w)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= RUN_TOL
+    check_sum(g)
+    assert np.max(g[3]) > 0.99        # the melt pool is there
+    assert np.max(g[1]) > 0.5         # martensite formed behind it
+
+
+def test_small_block_all_points_ragged(ms):
+    """3D block with a ragged tile tail, serpentine tracks, every point."""
+    w = wl.block_256(dims=(40, 24, 10), n_tracks=4, n_steps=1500, T_thr=0.0)
+    _, g = gpu_workload(w)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= RUN_TOL
+    check_sum(g)
+
+
+def test_batched_specimens_with_offsets(ms):
+    """Several specimens of uneven sizes and start offsets in one context."""
+    w = wl.batch_64(n_specimens=5, n_lo=200, n_hi=3000, n_steps=1200, T_thr=0.0)
+    _, g = gpu_workload(w)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= RUN_TOL
+    check_sum(g)
+
+
+def test_layers_and_interlayer_cooling(ms):
+    """Two layers: inactive points above the first surface, interlayer
+    cool-down to T0, rotated tracks of the second layer."""
+    w = wl.part_512(dims=(24, 20, 8), n_layers=2, tracks_per_layer=4, t_layer=2e-3, hatch=5e-5)
+    _, g = gpu_workload(w)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= RUN_TOL
+    check_sum(g)
+
+
+def test_block_256_full_size_sampled(ms):
+    """The full 256x256x64 block, 20 tracks, 20000 steps, in the bench's launch
+    configuration (active set on); 192 seeded sample points against the oracle."""
+    w = wl.block_256()
+    _, g = gpu_workload(w)
+    idx = np.random.default_rng(9).choice(w.n_points, 192, replace=False)
+    o = oracle_workload(w, idx)
+    assert max_abs_diff(g, o, idx) <= RUN_TOL
+    check_sum(g)
+
+
+# ------------------------------------------------------------- properties
+def test_steps_per_launch_is_bit_invariant(ms):
+    """Temporal blocking changes no arithmetic: S = 1, 7, 32, 96 and a run
+    split over several calls give identical bits."""
+    w = wl.block_256(dims=(33, 9, 5), n_tracks=3, n_steps=250, T_thr=0.0)
+    ref = None
+    for S, chunks in ((1, 1), (7, 1), (32, 3), (96, 2)):
+        _, g = gpu_workload(w, steps_per_launch=S, chunks=chunks)
+        if ref is None:
+            ref = g
+        else:
+            for a, b in zip(ref, g):
+                assert np.array_equal(a, b)
+
+
+def test_checkpoint_roundtrip_bit_exact(ms):
+    """run(2N) == run(N); checkpoint; restore into a fresh context; run(N)."""
+    w = wl.line_4096(n_points=700, n_steps=600)
+    _, full = gpu_workload(w)
+    ctx, _ = gpu_workload(w, n_steps=300)
+    blob = ctx.checkpoint()
+    ctx2 = ms.Context(w.n_points, T_thr=w.T_thr)
+    ctx2.set_points([s.grid for s in w.specimens])
+    ctx2.restore(blob)
+    ctx2.run_track([s.source for s in w.specimens], 300, w.dt)
+    for a, b in zip(full, ctx2.fractions()):
+        assert np.array_equal(a, b)
+
+
+def test_active_set_skip_error_is_bounded(ms):
+    """Reading A9: skipping cold, saturated steps changes results by less than
+    the neglected diffusion (k(600 K) * t, ~1e-5 here)."""
+    w = wl.block_256(dims=(64, 16, 8), n_tracks=3, n_steps=3000, T_thr=0.0)
+    _, a = gpu_workload(w, T_thr=0.0)
+    _, b = gpu_workload(w, T_thr=600.0)
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(a, b)) <= 2e-5
+
+
+def test_f64_accumulation_parity(ms):
+    """MS_F64ACC: FP64 fractions, FP32 rates; tighter agreement on the line."""
+    w = wl.line_4096(n_points=1024, n_steps=2000)
+    _, g = gpu_workload(w, precision=ms.MS_F64ACC)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= 3e-5
+    check_sum(g)
+
+
+def test_device_pointers_on_a_torch_stream(ms):
+    """ms_step with device temperature arrays on the caller's stream."""
+    torch = pytest.importorskip("torch")
+    n = 1000
+    xas, xam, T0, T1 = wl.random_states(n, seed=21)
+    ctx = ms.Context(n)
+    s = torch.cuda.Stream()
+    ctx.set_stream(s.cuda_stream)
+    ctx.set_state(xas, xam)
+    t0 = torch.tensor(T0, dtype=torch.float32, device="cuda")
+    t1 = torch.tensor(T1, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    ctx.step_device(t0.data_ptr(), t1.data_ptr(), 1e-4)
+    g = ctx.fractions()
+    ref = ms.Context(n)
+    ref.set_state(xas, xam)
+    ref.step(T0.astype(np.float32), T1.astype(np.float32), 1e-4)
+    for a, b in zip(g, ref.fractions()):
+        assert np.array_equal(a, b)
+    ctx.set_stream(None)
+
+
+# ------------------------------------------------------------ error paths
+def test_error_paths(ms):
+    ctx = ms.Context(10)
+    with pytest.raises(ms.MSError) as e:
+        ctx.set_state(np.full(10, np.nan), np.zeros(10))
+    assert e.value.code == -5
+    with pytest.raises(ms.MSError) as e:
+        ctx.set_state(np.full(10, 0.6), np.full(10, 0.6))
+    assert e.value.code == -1
+    with pytest.raises(ms.MSError) as e:
+        ctx.fractions()
+    assert e.value.code == -6
+    with pytest.raises(ms.MSError) as e:
+        ctx.run_track([wl.line_4096().specimens[0].source], 1, 1e-5)
+    assert e.value.code == -6
+    with pytest.raises(ms.MSError) as e:
+        ctx.step(np.zeros(10, np.float32), np.zeros(10, np.float32), -1.0)
+    assert e.value.code == -1
+    with pytest.raises(ms.MSError):
+        ms.Context(10, precision=ms.MS_KAHAN)
+    w = wl.line_4096(n_points=10)
+    with pytest.raises(ms.MSError) as e:
+        ctx.set_points([wl.Grid(dims=(11, 1, 1))])
+    assert e.value.code == -1
+    ctx.set_points([s.grid for s in w.specimens])
+    bad = wl.HeatSource(np.array([[0, 0, 1.0, 1.0, 1.0, 200.0, 0.0, 0]]), w.specimens[0].source.layers)
+    with pytest.raises(ms.MSError) as e:
+        ctx.run_track([bad], 1, 1e-5)
+    assert e.value.code == -1
