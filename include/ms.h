@@ -263,6 +263,17 @@ int ms_get_state(ms_ctx* ctx, void* blob, size_t* bytes);
  * n_points and precision.  Errors: INVALID_ARG (size / header mismatch), CUDA. */
 int ms_set_state_blob(ms_ctx* ctx, const void* blob, size_t bytes);
 
+/* Throughput probe of one SM pipe, measured on the current device so that
+ * roofline fractions use a measured peak (as Sec. 4 measures its CPUs' peak
+ * FLOP/s and DAXPY bandwidth before quoting roofline fractions): op 0
+ * ex2.approx.f32, 1 lg2.approx.f32, 2 rsqrt.approx.f32, 3 rcp.approx.f32
+ * alternating with rsqrt.approx.f32 (both counted), 4 fma.rn.f32.  About 1e10 operations, best of 3 timed repeats.
+ * *ops_per_s receives thread-level operations per second, *sm_mhz (may be
+ * NULL) the SM clock the probe saw (clock64 cycles per globaltimer ns).
+ * Allocates and frees its own small buffers and stream.
+ * Errors: INVALID_ARG (op out of range, NULL ops_per_s), CUDA. */
+int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
+
 /* Counters and the sticky device error word (synchronises the stream). */
 int ms_stats(ms_ctx* ctx, ms_stats_t* out);
 

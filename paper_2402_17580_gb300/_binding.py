@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
     lib.ms_fill_state.argtypes = [P, d, d]
     lib.ms_reset_stats.argtypes = [P]
     lib.ms_synchronize.argtypes = [P]
+    lib.ms_probe_sfu.argtypes = [ctypes.c_int, ctypes.POINTER(d), ctypes.POINTER(d)]
     for i, s in enumerate(STRUCTS):
         if lib.ms_struct_size(i) != ctypes.sizeof(s):
             raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
@@ -121,6 +122,17 @@ def load(build_if_missing: bool = True):
 def _check(rc, where):
     if rc != MS_OK:
         raise MSError(rc, where, load().ms_last_error().decode())
+
+
+PROBE_OPS = ("ex2", "lg2", "rsqrt", "rcp", "ffma")
+
+
+def probe_pipe(op: str):
+    """(thread-level ops/s, SM MHz seen) of one pipe probe on the current device."""
+    v, mhz = d(), d()
+    _check(load().ms_probe_sfu(PROBE_OPS.index(op), ctypes.byref(v), ctypes.byref(mhz)),
+           "ms_probe_sfu")
+    return v.value, mhz.value
 
 
 def default_params(**overrides) -> Params:

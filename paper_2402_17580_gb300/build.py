@@ -39,8 +39,18 @@ def _deps():
         os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _extra_flags():
+    """Extra nvcc flags from MS_NVCC_FLAGS (tuning builds, e.g. -DMS_TRACK_MINB=8)."""
+    return os.environ.get("MS_NVCC_FLAGS", "").split()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read() != " ".join(_extra_flags()):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(d) <= t for d in _deps())
@@ -55,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in _sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         log = obj + ".log"
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *_extra_flags(), "-c", src, "-o", obj]
         procs.append((subprocess.Popen(cmd, stdout=open(log, "w"), stderr=subprocess.STDOUT), src, log))
         objs.append(obj)
     failed = []
@@ -72,6 +82,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(_extra_flags()))
     return LIB
 
 

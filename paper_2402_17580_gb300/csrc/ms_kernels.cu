@@ -52,15 +52,16 @@ __global__ void k_src_table(const TableArgs a) {
     const TrackDev tr = a.tracks[sp.track0 + j];
     if (tr.layer != l || tl < tr.t_start) continue;
     const double travel = tr.v * (tl - tr.t_start);
+    const double sx = tr.x0 + tr.ux * travel, sy = tr.y0 + tr.uy * travel;
+    const double C = C0 * tr.P;
     SrcEntry e;
-    e.sx = float(tr.x0 + tr.ux * travel);
-    e.sy = float(tr.y0 + tr.uy * travel);
-    e.sz = float(L.z);
-    e.C = float(C0 * tr.P);
-    e.cR = float(cv * tr.v);
+    e.s_xi = float(sx * tr.ux + sy * tr.uy);
+    e.s_pp = float(sx * tr.uy - sy * tr.ux);
     e.ux = float(tr.ux);
     e.uy = float(tr.uy);
-    e.pad = 0.0f;
+    e.cR = float(cv * tr.v);
+    e.lC = C > 0.0 ? float(log2(C)) : -INFINITY;
+    e.pad0 = e.pad1 = 0.0f;
     out[n++] = e;
   }
   SrcLevel r;
@@ -75,19 +76,26 @@ __device__ __forceinline__ SrcEntry load_entry(const SrcEntry* p) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
   const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
   SrcEntry e;
-  e.sx = a.x; e.sy = a.y; e.sz = a.z; e.C = a.w;
-  e.cR = b.x; e.ux = b.y; e.uy = b.z; e.pad = b.w;
+  e.s_xi = a.x; e.s_pp = a.y; e.ux = a.z; e.uy = a.w;
+  e.cR = b.x; e.lC = b.y; e.pad0 = b.z; e.pad1 = b.w;
   return e;
+}
+
+__device__ __forceinline__ float depth2(float pz, float z_surf) {
+  const float dz = pz - z_surf;
+  return fmaf(dz, dz, 1e-30f);
 }
 
 // Temperatures of 4 points at one level (4 independent chains per source).
 __device__ __forceinline__ void temps4(const SrcLevel& L, const SrcEntry* en, const float* px,
                                        const float* py, const float* pz, float* T) {
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f}, dz2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dz2[q] = depth2(pz[q], L.z_surf);
   for (int j = 0; j < L.n; ++j) {
     const SrcEntry e = load_entry(en + j);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += source_term(e, px[q], py[q], pz[q]);
+    for (int q = 0; q < 4; ++q) acc[q] += source_term(e, px[q], py[q], dz2[q]);
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) T[q] = fminf(L.T0 + acc[q], L.T_max);
@@ -96,7 +104,8 @@ __device__ __forceinline__ void temps4(const SrcLevel& L, const SrcEntry* en, co
 __device__ __forceinline__ float temp1(const SrcLevel& L, const SrcEntry* en, float px, float py,
                                        float pz) {
   float acc = 0.f;
-  for (int j = 0; j < L.n; ++j) acc += source_term(load_entry(en + j), px, py, pz);
+  const float dz2 = depth2(pz, L.z_surf);
+  for (int j = 0; j < L.n; ++j) acc += source_term(load_entry(en + j), px, py, dz2);
   return fminf(L.T0 + acc, L.T_max);
 }
 
@@ -133,7 +142,13 @@ __device__ __forceinline__ bool finite_pair(FT a, FT b) {
 
 // ------------------------------------------------------------ hot kernel
 template <typename FT>
-__global__ void __launch_bounds__(256) k_track(const TrackArgs<FT> a) {
+// Minimum resident 256-thread blocks per SM for k_track: 3 caps it at 85
+// registers (24 resident warps at 128 threads per block), measured fastest on
+// the 256x256x64 block against 1 (107 registers) and 4 (64, with spills).
+#ifndef MS_TRACK_MINB
+#define MS_TRACK_MINB 3
+#endif
+__global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT> a) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (w >= a.n_work) return;
