@@ -510,7 +510,7 @@ int ms_params_default(ms_params* p) {
   p->martensite_literal = 0;
   p->init_ba_steps = 0;
   p->precision = MS_F32;
-  p->steps_per_launch = 32;
+  p->steps_per_launch = 64;
   p->rebuild_steps = 0;
   p->block_threads = 0;
   return MS_OK;
