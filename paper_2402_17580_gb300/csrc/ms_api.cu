@@ -83,6 +83,13 @@ struct ms_ctx {
   float* aux_d = nullptr;
   int* err_d = nullptr;
 
+  // active set and work distribution of the persistent hot kernel
+  int32_t* tile_list_d = nullptr;
+  float* tile_tsat_d = nullptr;
+  ms::WorkCounters* work_d = nullptr;
+  int sm_count = 0;
+  int track_grid = 0;  // persistent grid size for the current layout
+
   // staging
   double* stage_d = nullptr;
   float* Tstage_d = nullptr;
@@ -193,6 +200,10 @@ int grow(T** p, size_t* cap, size_t n) {
 }
 
 void free_layout(ms_ctx* c) {
+  cudaFree(c->tile_list_d);
+  cudaFree(c->tile_tsat_d);
+  c->tile_list_d = nullptr;
+  c->tile_tsat_d = nullptr;
   cudaFree(c->specs_d);
   cudaFree(c->tile_spec_d);
   cudaFree(c->xas_d);
@@ -234,6 +245,16 @@ int build_layout(ms_ctx* c) {
   MS_CUDA(cudaMalloc(&c->xam_d, np * c->fbytes));
   MS_CUDA(cudaMalloc(&c->aux_d, np * sizeof(float)));
   MS_CUDA(cudaMalloc(&c->stage_d, size_t(c->n_points) * 4 * sizeof(double)));
+  MS_CUDA(cudaMalloc(&c->tile_list_d, size_t(tiles) * sizeof(int32_t)));
+  MS_CUDA(cudaMalloc(&c->tile_tsat_d, size_t(tiles) * sizeof(float)));
+  MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, tiles, INFINITY, c->stream));
+  {
+    const int bt = block_threads(c);
+    const int per_sm = c->fbytes == 4 ? ms::track_blocks_per_sm<float>(bt)
+                                      : ms::track_blocks_per_sm<double>(bt);
+    const int64_t need = (tiles + bt / 32 - 1) / (bt / 32);
+    c->track_grid = int(std::min<int64_t>(int64_t(per_sm) * c->sm_count, need));
+  }
   MS_CUDA(cudaMemcpy(c->specs_d, c->specs_h.data(), c->specs_h.size() * sizeof(SpecDev),
                      cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(c->tile_spec_d, ts.data(), ts.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -280,9 +301,12 @@ int harvest_kernel_events(ms_ctx* c) {
 
 int check_device_error(ms_ctx* c) {
   int err = 0;
+  ms::WorkCounters wc{};
   MS_CUDA(cudaMemcpyAsync(&err, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  MS_CUDA(cudaMemcpyAsync(&wc, c->work_d, sizeof(wc), cudaMemcpyDeviceToHost, c->stream));
   MS_CUDA(cudaStreamSynchronize(c->stream));
   c->st.device_error = err;
+  c->st.tile_steps_active = int64_t(wc.tile_steps_active);
   if (c->timed) {
     float ms_ = 0.f;
     if (cudaEventElapsedTime(&ms_, c->ev0, c->ev1) == cudaSuccess) c->st.last_run_ms = ms_;
@@ -380,26 +404,48 @@ int launch_table(ms_ctx* c, int64_t level0, int n_levels) {
   ta.dt = c->dt;
   ta.levels = c->levels_d;
   ta.entries = c->entries_d;
-  MS_CUDA(ms::launch_src_table(ta, c->stream));
+  MS_CUDA(ms::launch_src_table(ta, c->work_d, c->stream));
   c->st.launches++;
   return MS_OK;
+}
+
+double level_time(const ms_ctx* c, int64_t level) {
+  return c->t_base + double(level - c->n_base) * c->dt;
 }
 
 template <typename FT>
 int run_track_impl(ms_ctx* c, int64_t n_steps) {
   const int S = c->prm.steps_per_launch;
+  const bool use_list = c->prm.T_thr > 0.0;
   int rc;
   if ((rc = ensure_table(c, S + 1)) != MS_OK) return rc;
   int64_t left = n_steps;
   while (left > 0) {
     const int steps = int(std::min<int64_t>(S, left));
     if ((rc = launch_table(c, c->step_n, steps + 1)) != MS_OK) return rc;
+    if (use_list) {
+      ms::ActiveArgs aa{};
+      aa.specs = c->specs_d;
+      aa.tracks = c->tracks_d;
+      aa.layers = c->layers_d;
+      aa.tile_spec = c->tile_spec_d;
+      aa.tile_tsat = c->tile_tsat_d;
+      aa.n_tiles = int32_t(c->n_tiles);
+      aa.t_a = level_time(c, c->step_n);
+      aa.t_b = level_time(c, c->step_n + steps);
+      aa.T_thr = c->prm.T_thr;
+      aa.tile_list = c->tile_list_d;
+      aa.work = c->work_d;
+      MS_CUDA(ms::launch_active(aa, c->stream));
+      c->st.launches++;
+    }
     ms::TrackArgs<FT> a{};
     a.m = c->mc;
     a.specs = c->specs_d;
     a.tile_spec = c->tile_spec_d;
-    a.tile_list = nullptr;
-    a.n_work = int32_t(c->n_tiles);
+    a.tile_list = use_list ? c->tile_list_d : nullptr;
+    a.work = c->work_d;
+    a.n_tiles = int32_t(c->n_tiles);
     a.n_levels = steps + 1;
     a.slots = c->slots;
     a.dt = float(c->dt);
@@ -408,16 +454,16 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.xas = (FT*)c->xas_d;
     a.xam = (FT*)c->xam_d;
     a.aux = c->aux_d;
+    a.tile_tsat = c->tile_tsat_d;
     a.err = c->err_d;
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
-    MS_CUDA(ms::launch_track<FT>(a, block_threads(c), c->stream));
+    MS_CUDA(ms::launch_track<FT>(a, block_threads(c), c->track_grid, c->stream));
     if ((rc = kernel_event(c, true)) != MS_OK) return rc;
     c->st.launches++;
     c->step_n += steps;
     c->st.steps += steps;
     c->st.point_updates += int64_t(steps) * c->n_points;
     c->st.tile_steps_total += int64_t(steps) * c->n_tiles;
-    c->st.tile_steps_active += int64_t(steps) * c->n_tiles;
     left -= steps;
   }
   return MS_OK;
@@ -537,8 +583,12 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
     return bail(fail(MS_ERR_CUDA, "event creation failed"));
   if (cudaMalloc(&c->err_d, sizeof(int)) != cudaSuccess ||
-      cudaMemset(c->err_d, 0, sizeof(int)) != cudaSuccess)
+      cudaMemset(c->err_d, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->work_d, sizeof(ms::WorkCounters)) != cudaSuccess ||
+      cudaMemset(c->work_d, 0, sizeof(ms::WorkCounters)) != cudaSuccess)
     return bail(fail(MS_ERR_OOM, "device allocation failed"));
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return bail(fail(MS_ERR_CUDA, "cannot query the SM count"));
   SpecDev s{};
   s.nx = int32_t(std::min<int64_t>(n_points, INT32_MAX));
   s.ny = s.nz = 1;
@@ -554,6 +604,7 @@ void ms_destroy(ms_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_layout(c);
   cudaFree(c->err_d);
+  cudaFree(c->work_d);
   cudaFree(c->tracks_d);
   cudaFree(c->layers_d);
   cudaFree(c->levels_d);
@@ -629,6 +680,7 @@ int ms_set_state(ms_ctx* c, const double* xas, const double* xam, const double* 
                                          aux ? d + 2 * n : nullptr, (double*)c->xas_d,
                                          (double*)c->xam_d, c->aux_d, c->stream));
   MS_CUDA(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+  MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, c->n_tiles, INFINITY, c->stream));
   MS_CUDA(cudaStreamSynchronize(c->stream));
   c->step_n = c->n_base = 0;
   c->t_base = 0.0;
@@ -648,7 +700,8 @@ int ms_fill_state(ms_ctx* c, double xas, double xam) {
     MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
                                          nullptr, (double*)c->xas_d, (double*)c->xam_d, c->aux_d,
                                          c->stream, xas, xam));
-  c->st.launches++;
+  MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, c->n_tiles, INFINITY, c->stream));
+  c->st.launches += 2;
   c->step_n = c->n_base = 0;
   c->t_base = 0.0;
   c->T_last = nullptr;
@@ -658,6 +711,7 @@ int ms_fill_state(ms_ctx* c, double xas, double xam) {
 int ms_reset_stats(ms_ctx* c) {
   if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
   MS_CUDA(cudaStreamSynchronize(c->stream));
+  MS_CUDA(cudaMemset(c->work_d, 0, sizeof(ms::WorkCounters)));
   const int32_t err = c->st.device_error;
   c->st = ms_stats_t{};
   c->st.device_error = err;
@@ -806,6 +860,8 @@ int ms_set_state_blob(ms_ctx* c, const void* blob, size_t bytes) {
   MS_CUDA(cudaMemcpy(c->xam_d, p, np * c->fbytes, cudaMemcpyHostToDevice));
   p += np * c->fbytes;
   MS_CUDA(cudaMemcpy(c->aux_d, p, np * sizeof(float), cudaMemcpyHostToDevice));
+  MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, c->n_tiles, INFINITY, c->stream));
+  MS_CUDA(cudaStreamSynchronize(c->stream));
   c->step_n = h.step_n;
   c->n_base = h.n_base;
   c->t_base = h.t_base;

@@ -63,14 +63,22 @@ struct TableArgs {
   SrcEntry* entries;       // [n_specs][n_levels][slots]
 };
 
-// Arguments of the run-track kernel (one warp per tile).
+// Work counters of one launch of k_track (device memory, reset per launch).
+struct WorkCounters {
+  int32_t n_active;            // tiles in the active list
+  int32_t next;                // next list position handed to a warp
+  unsigned long long tile_steps_active;  // running total of processed tile-steps
+};
+
+// Arguments of the run-track kernel (persistent warps pull 128-point tiles).
 template <typename FT>
 struct TrackArgs {
   ModelConst m;
   const SpecDev* specs;
   const int32_t* tile_spec;    // tile -> specimen
-  const int32_t* tile_list;    // optional list of tiles to process
-  int32_t n_work;              // tiles to process
+  const int32_t* tile_list;    // active tiles (nullptr: every tile 0 .. n_tiles-1)
+  WorkCounters* work;          // n_active (with a list) and the work cursor
+  int32_t n_tiles;             // tiles in the layout
   int32_t n_levels;            // steps + 1
   int32_t slots;
   float dt;
@@ -79,7 +87,25 @@ struct TrackArgs {
   FT* xas;
   FT* xam;
   float* aux;
+  float* tile_tsat;            // per tile: highest T at which formation still acts (+inf: busy)
   int* err;
+};
+
+// Arguments of the active-set builder (reading A9): a tile joins the list
+// unless it provably stays below T_thr over [t_a, t_b] and its martensite is
+// saturated at the preheat temperature.
+struct ActiveArgs {
+  const SpecDev* specs;
+  const TrackDev* tracks;
+  const LayerDev* layers;
+  const int32_t* tile_spec;
+  const float* tile_tsat;
+  int32_t n_tiles;
+  int32_t pad;
+  double t_a, t_b;             // global times of the first and last level of the launch
+  double T_thr;
+  int32_t* tile_list;
+  WorkCounters* work;
 };
 
 // Arguments of the external-temperature step kernel.
@@ -97,9 +123,14 @@ struct StepArgs {
 };
 
 // Launchers (ms_kernels.cu).  All asynchronous on `stream`.
-cudaError_t launch_src_table(const TableArgs& a, cudaStream_t stream);
+cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream);
+cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream);
+cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream);
 template <typename FT>
-cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, cudaStream_t stream);
+cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, int grid_blocks,
+                         cudaStream_t stream);
+template <typename FT>
+int track_blocks_per_sm(int block_threads);
 template <typename FT>
 cudaError_t launch_step_ext(const StepArgs<FT>& a, int block_threads, cudaStream_t stream);
 

@@ -27,8 +27,12 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.4426950408889634074;
 
 // --------------------------------------------------------- source table
-__global__ void k_src_table(const TableArgs a) {
+__global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id == 0 && work) {
+    work->n_active = 0;
+    work->next = 0;
+  }
   if (id >= a.n_specs * a.n_levels) return;
   const int s = id / a.n_levels;
   const int lv = id - s * a.n_levels;
@@ -109,6 +113,104 @@ __device__ __forceinline__ float temp1(const SrcLevel& L, const SrcEntry* en, fl
   return fminf(L.T0 + acc, L.T_max);
 }
 
+// ------------------------------------------------------------ active set
+// Upper bound of the temperature of a tile over [t_a, t_b]: every started
+// source of a layer current in the window contributes at most
+// A P / (2 pi k R_min) exp(-v xi_min / alpha), with R_min the distance between
+// the tile's bounding box and the box of the source's path in the window and
+// xi_min >= 0 the smallest along-track offset of a tile point ahead of the
+// path (R + xi >= 2 xi ahead of the source; the factor is 1 otherwise).  The
+// interlayer scale is <= 1.
+__device__ bool tile_is_active(const ActiveArgs& a, int t) {
+  const int s = a.tile_spec[t];
+  const SpecDev& sp = a.specs[s];
+  const float tsat = a.tile_tsat[t];
+  if (!(tsat <= sp.T0)) return true;  // martensite not saturated at T0, or initiation running
+  const double tla = a.t_a - sp.t_offset, tlb = a.t_b - sp.t_offset;
+  const int64_t li0 = int64_t(t - sp.tile0) * TILE;
+  const int64_t li1 = min(li0 + TILE - 1, sp.n - 1);
+  const int64_t nxy = int64_t(sp.nx) * sp.ny;
+  const int64_t k0 = li0 / nxy, k1 = li1 / nxy;
+  const int64_t j0 = (li0 - k0 * nxy) / sp.nx, j1 = (li1 - k1 * nxy) / sp.nx;
+  const int64_t i0 = li0 - k0 * nxy - j0 * sp.nx, i1 = li1 - k1 * nxy - j1 * sp.nx;
+  int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1;
+  if (k0 == k1) {
+    jlo = j0;
+    jhi = j1;
+    if (j0 == j1) {
+      ilo = i0;
+      ihi = i1;
+    }
+  }
+  const double xa = double(sp.ox) + double(ilo) * sp.dx, xb = double(sp.ox) + double(ihi) * sp.dx;
+  const double ya = double(sp.oy) + double(jlo) * sp.dy, yb = double(sp.oy) + double(jhi) * sp.dy;
+  const double za = double(sp.oz) + double(k0) * sp.dz, zb = double(sp.oz) + double(k1) * sp.dz;
+  const double bx0 = fmin(xa, xb), bx1 = fmax(xa, xb), by0 = fmin(ya, yb), by1 = fmax(ya, yb);
+  const double bz1 = fmax(za, zb);
+  int la = 0, lb = 0;
+  for (int j = 0; j < sp.n_layers; ++j) {
+    if (a.layers[sp.layer0 + j].t_begin <= tla) la = j;
+    if (a.layers[sp.layer0 + j].t_begin <= tlb) lb = j;
+  }
+  const double C0 = sp.A / (2.0 * kPi * sp.k);
+  double sum = 0.0;
+  for (int j = 0; j < sp.n_tracks; ++j) {
+    const TrackDev tr = a.tracks[sp.track0 + j];
+    if (tr.layer < la || tr.layer > lb || tr.t_start > tlb) continue;
+    const double ta = fmax(tla, tr.t_start);
+    const double pa = tr.v * (ta - tr.t_start), pb = tr.v * (tlb - tr.t_start);
+    const double sx0 = tr.x0 + tr.ux * pa, sx1 = tr.x0 + tr.ux * pb;
+    const double sy0 = tr.y0 + tr.uy * pa, sy1 = tr.y0 + tr.uy * pb;
+    const double dx = fmax(0.0, fmax(fmin(sx0, sx1) - bx1, bx0 - fmax(sx0, sx1)));
+    const double dy = fmax(0.0, fmax(fmin(sy0, sy1) - by1, by0 - fmax(sy0, sy1)));
+    const double zs = a.layers[sp.layer0 + tr.layer].z;
+    const double dz = fmax(0.0, zs - bz1);
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 > 0.0)) return true;
+    // smallest (x - x_s) . u over the box corners and the path's end points
+    double xi_min = INFINITY;
+    for (int c = 0; c < 4; ++c) {
+      const double cx = (c & 1) ? bx1 : bx0, cy = (c & 2) ? by1 : by0;
+      xi_min = fmin(xi_min, fmin((cx - sx0) * tr.ux + (cy - sy0) * tr.uy,
+                                 (cx - sx1) * tr.ux + (cy - sy1) * tr.uy));
+    }
+    const double ahead = xi_min > 0.0 ? exp(-tr.v * xi_min / sp.alpha) : 1.0;
+    sum += C0 * tr.P / sqrt(r2) * ahead;
+  }
+  return double(sp.T0) + sum >= a.T_thr - 1.0;
+}
+
+__global__ void k_active(const ActiveArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = t < a.n_tiles && tile_is_active(a, t);
+  const unsigned mask = __ballot_sync(0xffffffffu, act);
+  if (mask) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&a.work->n_active, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (act) a.tile_list[base + __popc(mask & ((1u << lane) - 1u))] = t;
+  }
+}
+
+__global__ void k_fill_f32(float* p, int64_t n, float v) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Highest T1 at which martensite formation would still change this point
+// (formation is a no-op for T1 >= the returned value); +inf while an App. A
+// initiation runs (never skip), -inf if formation can never act.
+template <typename FT>
+__device__ __forceinline__ float point_tsat(const ModelConst& m, FT xas, FT xam, float aux) {
+  if (aux != 0.0f) return INFINITY;
+  const FT q = FT(0.9) - xas;
+  if (!(q > FT(0))) return -INFINITY;
+  const float r = float(xam * FT(0.9) / q);
+  if (r >= XMAX) return -INFINITY;
+  return m.T_am_start + sfu_lg2(1.0f - r) / m.kam_l2;
+}
+
 // ---------------------------------------------------------- state access
 template <typename FT>
 struct Vec4;
@@ -141,18 +243,9 @@ __device__ __forceinline__ bool finite_pair(FT a, FT b) {
 }
 
 // ------------------------------------------------------------ hot kernel
+// One 128-point tile for the launch's S steps (4 points per lane).
 template <typename FT>
-// Minimum resident 256-thread blocks per SM for k_track: 3 caps it at 85
-// registers (24 resident warps at 128 threads per block), measured fastest on
-// the 256x256x64 block against 1 (107 registers) and 4 (64, with spills).
-#ifndef MS_TRACK_MINB
-#define MS_TRACK_MINB 3
-#endif
-__global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT> a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (w >= a.n_work) return;
-  const int tile = a.tile_list ? a.tile_list[w] : int(w);
+__device__ __forceinline__ void track_tile(const TrackArgs<FT>& a, int tile, int lane) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
@@ -212,9 +305,45 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT
   Vec4<FT>::store(a.xam + g0, xm);
   Vec4<float>::store(a.aux + g0, ax);
   bool ok = true;
+  float ts = -INFINITY;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
+  for (int q = 0; q < 4; ++q) {
+    ok = ok && finite_pair(xs[q], xm[q]);
+    if (valid[q]) ts = fmaxf(ts, point_tsat<FT>(a.m, xs[q], xm[q], ax[q]));
+  }
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
+  if (a.tile_tsat) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ts = fmaxf(ts, __shfl_xor_sync(0xffffffffu, ts, o));
+    if (lane == 0) a.tile_tsat[tile] = ts + 0.5f;  // margin against FP32 rounding
+  }
+}
+
+// Minimum resident 256-thread blocks per SM for k_track: 3 caps it at 85
+// registers (24 resident warps at 128 threads per block), measured fastest on
+// the 256x256x64 block against 1 (107 registers) and 4 (64, with spills).
+#ifndef MS_TRACK_MINB
+#define MS_TRACK_MINB 3
+#endif
+
+// Persistent hot kernel: every warp pulls tiles (from the active list, or all
+// tiles) through an atomic cursor until the work runs out, so the grid is
+// sized to the resident capacity and no launch tail is left idle.
+template <typename FT>
+__global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT> a) {
+  const int lane = threadIdx.x & 31;
+  const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
+  unsigned long long done = 0;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(&a.work->next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= n_work) break;
+    track_tile<FT>(a, a.tile_list ? a.tile_list[w] : w, lane);
+    ++done;
+  }
+  if (lane == 0 && done)
+    atomicAdd(&a.work->tile_steps_active, done * (unsigned long long)(a.n_levels - 1));
 }
 
 // ---------------------------------------------------- external T (ms_step)
@@ -334,19 +463,39 @@ inline unsigned blocks_for(int64_t n, int threads) {
 }  // namespace
 
 // ------------------------------------------------------------- launchers
-cudaError_t launch_src_table(const TableArgs& a, cudaStream_t stream) {
+cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream) {
   const int n = a.n_specs * a.n_levels;
   if (n <= 0) return cudaSuccess;
-  k_src_table<<<blocks_for(n, 128), 128, 0, stream>>>(a);
+  k_src_table<<<blocks_for(n, 128), 128, 0, stream>>>(a, work);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  k_active<<<blocks_for(a.n_tiles, 128), 128, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_f32<<<blocks_for(n, 256), 256, 0, stream>>>(p, n, v);
   return cudaGetLastError();
 }
 
 template <typename FT>
-cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, cudaStream_t stream) {
-  if (a.n_work <= 0) return cudaSuccess;
-  const int warps_per_block = block_threads / 32;
-  const unsigned grid = unsigned((a.n_work + warps_per_block - 1) / warps_per_block);
-  k_track<FT><<<grid, block_threads, 0, stream>>>(a);
+int track_blocks_per_sm(int block_threads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<FT>, block_threads, 0) !=
+      cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+template <typename FT>
+cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, int grid_blocks,
+                         cudaStream_t stream) {
+  if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
+  k_track<FT><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -390,7 +539,8 @@ cudaError_t launch_fractions(const ModelConst& m, const SpecDev* specs, const in
 }
 
 #define MS_INSTANTIATE(FT)                                                                        \
-  template cudaError_t launch_track<FT>(const TrackArgs<FT>&, int, cudaStream_t);                \
+  template int track_blocks_per_sm<FT>(int);                                                     \
+  template cudaError_t launch_track<FT>(const TrackArgs<FT>&, int, int, cudaStream_t);           \
   template cudaError_t launch_step_ext<FT>(const StepArgs<FT>&, int, cudaStream_t);              \
   template cudaError_t launch_set_state<FT>(const SpecDev*, const int32_t*, int64_t,             \
                                             const double*, const double*, const double*, FT*,    \

@@ -185,6 +185,30 @@ def test_active_set_skip_error_is_bounded(ms):
     assert max(float(np.max(np.abs(x - y))) for x, y in zip(a, b)) <= 2e-5
 
 
+def test_active_set_skips_cold_tiles_line(ms):
+    """Reading A9 with the tile bound: on the line, tiles well ahead of the
+    source are cold and saturated and skip whole launches; results stay within
+    the oracle budget and within the skip bound of the dense run."""
+    w = wl.line_4096()
+    _, dense = gpu_workload(w, T_thr=0.0)
+    ctx, g = gpu_workload(w, T_thr=600.0, steps_per_launch=32)
+    st = ctx.stats()
+    assert st.tile_steps_active < 0.75 * st.tile_steps_total
+    assert st.tile_steps_active > 0
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(dense, g)) <= 2e-5
+    assert max_abs_diff(g, oracle_workload(w)) <= RUN_TOL
+
+
+def test_active_set_batched_offsets(ms):
+    """Specimens that have not started yet are skipped until their start."""
+    w = wl.batch_64(n_specimens=6, n_lo=300, n_hi=4000, n_steps=800, T_thr=600.0)
+    ctx, g = gpu_workload(w, steps_per_launch=16)
+    st = ctx.stats()
+    assert st.tile_steps_active < st.tile_steps_total
+    assert max_abs_diff(g, oracle_workload(w)) <= RUN_TOL
+    check_sum(g)
+
+
 def test_f64_accumulation_parity(ms):
     """MS_F64ACC: FP64 fractions, FP32 rates; tighter agreement on the line."""
     w = wl.line_4096(n_points=1024, n_steps=2000)
