@@ -274,6 +274,47 @@ int ms_set_state_blob(ms_ctx* ctx, const void* blob, size_t bytes);
  * Errors: INVALID_ARG (op out of range, NULL ops_per_s), CUDA. */
 int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
 
+/* ms_run_track_noalloc -- the ms_run_track hot path without allocating.
+ * The paper has no counterpart; this is an integration entry point.
+ *
+ * For callers that cannot allocate device memory at run time.  Applications
+ * whose device memory is owned by a pre-sized pool (a framework's caching
+ * allocator, a memory budget fixed at start-up) may not allocate outside it.
+ * Latency-critical loops cannot afford cudaMalloc / cudaFree, which can
+ * synchronise the whole device.  Embeddings that must not grow the GPU
+ * footprint while they run cannot allocate either.  ms_create allocates its
+ * context buffers with cudaMalloc; this call keeps its scratch (the
+ * per-launch source table, the work counters of the persistent kernel and
+ * the specimen / track / layer tables) in one file-scope static device array
+ * of 0.77 MiB, which every GPU that loads the library holds until the
+ * process exits.
+ *
+ * It advances one specimen (grid, src) from time level step0 by n_steps
+ * explicit steps of dt.  The result is the same as ms_run_track after
+ * ms_set_points(grid) from the same state (MS_F32 only, no active-set tile
+ * list; the per-step warp vote of T_thr still applies).  The caller owns the
+ * state: x_as, x_am and aux are device arrays, 16-byte aligned, each holding
+ * at least n_points rounded up to a multiple of 128 floats, in natural
+ * order; aux carries the library's App. A encoding (set it to 0 for "no
+ * initiation in progress" and keep it between calls).  Asynchronous on
+ * cuda_stream (NULL = the legacy default stream).
+ *
+ * Limits: n_points <= 2^24, src->n_tracks <= 128, src->n_layers <= 8,
+ * steps_per_launch <= 64, block_threads 0 or 128; larger requests return
+ * MS_ERR_INVALID_ARG with a message in ms_last_error.  No cudaMalloc,
+ * cudaFree or other allocating call is made.  The first call on a device
+ * does a one-time set-up: it looks up the array's device address
+ * (cudaGetSymbolAddress) and clears it with a synchronous cudaMemset, so make
+ * that first call before any stream capture.  Every call shares the array,
+ * which keeps the last call's contents (each call resets the counters it
+ * needs); calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it, so the caller must serialise them.  Non-finite
+ * fractions are not reported by this call.
+ * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32), CUDA. */
+int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid, const ms_heat_source* src,
+                         float* x_as, float* x_am, float* aux, int64_t n_points,
+                         int64_t step0, int64_t n_steps, double dt, void* cuda_stream);
+
 /* Counters and the sticky device error word (synchronises the stream). */
 int ms_stats(ms_ctx* ctx, ms_stats_t* out);
 

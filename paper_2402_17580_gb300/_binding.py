@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True):
     lib.ms_reset_stats.argtypes = [P]
     lib.ms_synchronize.argtypes = [P]
     lib.ms_probe_sfu.argtypes = [ctypes.c_int, ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.ms_run_track_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Grid),
+                                         ctypes.POINTER(HeatSource), P, P, P, i64, i64, i64, d, P]
     for i, s in enumerate(STRUCTS):
         if lib.ms_struct_size(i) != ctypes.sizeof(s):
             raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
@@ -122,6 +124,20 @@ def load(build_if_missing: bool = True):
 def _check(rc, where):
     if rc != MS_OK:
         raise MSError(rc, where, load().ms_last_error().decode())
+
+
+def run_track_noalloc(params, grid, source, xas_ptr, xam_ptr, aux_ptr, n_points, step0, n_steps,
+                      dt, stream_handle=0):
+    """ms_run_track_noalloc: advance one specimen whose state lives in the
+    caller's device arrays (raw pointers), without any allocation."""
+    g = Grid((d * 3)(*grid.origin), (d * 3)(*grid.spacing), (i32 * 3)(*grid.dims), 0)
+    h, keep = make_heat_source(source)
+    _check(load().ms_run_track_noalloc(ctypes.byref(params), ctypes.byref(g), ctypes.byref(h),
+                                       ctypes.c_void_p(xas_ptr), ctypes.c_void_p(xam_ptr),
+                                       ctypes.c_void_p(aux_ptr), int(n_points), int(step0),
+                                       int(n_steps), float(dt), ctypes.c_void_p(stream_handle or 0)),
+           "ms_run_track_noalloc")
+    del keep
 
 
 PROBE_OPS = ("ex2", "lg2", "rsqrt", "rcp", "ffma")

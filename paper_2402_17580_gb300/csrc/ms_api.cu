@@ -499,6 +499,13 @@ void set_dt(ms_ctx* c, double dt) {
 
 }  // namespace
 
+// Shared with other translation units (declared in ms_internal.h).
+namespace ms {
+int validate_params(const ms_params& p) { return check_params(p); }
+ModelConst model_const(const ms_params& p) { return make_const(p); }
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace ms
+
 // =============================================================== C ABI
 extern "C" {
 

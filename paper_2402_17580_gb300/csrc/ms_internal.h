@@ -122,6 +122,14 @@ struct StepArgs {
   int* err;
 };
 
+// Parameter checks and derived constants shared by the C-ABI entry points
+// (ms_api.cu): validate_params returns MS_OK or an MS_ERR_* code and records
+// the message for ms_last_error; record_error records a message and returns
+// the code.
+int validate_params(const ms_params& p);
+ModelConst model_const(const ms_params& p);
+int record_error(int code, const char* msg);
+
 // Launchers (ms_kernels.cu).  All asynchronous on `stream`.
 cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream);
 cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream);
