@@ -38,6 +38,7 @@ UNIT = "point-updates/s"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_track_block_256.json")
+HBM_PEAK_GBS = 6794.8       # measured copy bandwidth of the GB300s
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -48,12 +49,16 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="block_256")
-    ap.add_argument("--precision", choices=("f32", "f64acc"), default="f32")
+    ap.add_argument("--precision", choices=("f32", "f64acc", "kahan"), default="f32")
     ap.add_argument("--steps-per-launch", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-d6", action="store_true", help="skip the external-temperature layouts")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the project autotuner (S, CTA size, graph replay)")
+    ap.add_argument("--graph", action="store_true", help="replay ms_run_track as a CUDA graph")
     return ap.parse_args()
 
 
@@ -237,6 +242,52 @@ def oracle_sample(w, seconds, seed=12345):
     return rate, idx, out, threads, desc, el
 
 
+# ------------------------------------------------------- D6 layouts (ms_step)
+def d6_layouts(ms, torch, n=1 << 24, blocks=(1, 10, 100), steps=10, warmup=3):
+    """ms_step with device temperature arrays on 2^24 points whose branch
+    choices come in blocks of 1, 10 and 100 points (the paper's synthetic
+    layouts, Sec. 4.1).  Per point-step the kernel moves 32 bytes (T^n, T^n+1,
+    X_as, X_am, aux in; X_as, X_am, aux out), so it is bound by HBM."""
+    import workloads as wl
+    out = {}
+    from paper_2402_17580_gb300._binding import MS_FLAG_TIME_KERNELS
+    for b in blocks:
+        xas, xam, T0, T1 = wl.random_states(n, seed=2402175806 + b, block=b)
+        ctx = ms.Context(n, flags=MS_FLAG_TIME_KERNELS)
+        stream = torch.cuda.Stream()
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_state(xas, xam)
+        t0 = torch.tensor(T0, dtype=torch.float32, device="cuda")
+        t1 = torch.tensor(T1, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        dt = 1e-5
+        for _ in range(warmup):
+            ctx.step_device(t0.data_ptr(), t1.data_ptr(), dt)
+        ctx.synchronize()
+        ctx.reset_stats()
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.step_device(t0.data_ptr(), t1.data_ptr(), dt)
+            e1.record(stream)
+        e1.synchronize()
+        st = ctx.stats()
+        ms_launch = st.hot_kernel_ms / st.hot_kernel_launches
+        bytes_launch = 32 * n
+        gbs = bytes_launch / (ms_launch * 1e-3) / 1e9
+        out[f"block_{b}"] = {
+            "point_updates_per_s": n * steps / (e0.elapsed_time(e1) * 1e-3),
+            "ms_per_launch": round(ms_launch, 4), "GB_per_s": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / HBM_PEAK_GBS, 4)}
+        ctx.close()
+        del t0, t1
+    return {"kernel": "k_step_ext", "bound": "hbm", "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "bytes_per_point_step": 32, "points": n, "layouts": out,
+            "note": "inputs 537 MB per step > L2, so no flush is needed"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     rank, world, local = dist_env()
@@ -250,8 +301,18 @@ def run_ours(args):
     ms.load()
 
     w = make_workload(args.workload, rank)
-    prec = ms.MS_F64ACC if args.precision == "f64acc" else ms.MS_F32
-    over = dict(T_thr=w.T_thr, precision=prec, flags=ms._binding.MS_FLAG_TIME_KERNELS)
+    prec = {"f32": ms.MS_F32, "f64acc": ms.MS_F64ACC, "kahan": ms.MS_KAHAN}[args.precision]
+    flags = ms._binding.MS_FLAG_TIME_KERNELS | (ms._binding.MS_FLAG_GRAPH if args.graph else 0)
+    over = dict(T_thr=w.T_thr, precision=prec, flags=flags)
+    tuned = None
+    if args.autotune:
+        from paper_2402_17580_gb300.autotune import autotune
+        tuned = autotune([s.grid for s in w.specimens], [s.source for s in w.specimens],
+                         w.n_points, w.dt, T_thr=w.T_thr, precision=prec,
+                         trial_steps=min(w.n_steps, 2048), repeats=1)
+        over.update(steps_per_launch=tuned.params["steps_per_launch"],
+                    block_threads=tuned.params["block_threads"],
+                    flags=ms._binding.MS_FLAG_TIME_KERNELS | tuned.params["flags"])
     if args.steps_per_launch:
         over["steps_per_launch"] = args.steps_per_launch
     ctx = ms.Context(w.n_points, **over)
@@ -347,16 +408,21 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == ms.MS_F32 else "f32+f64acc",
+        "vs_baseline": None,
+        "dtype": {ms.MS_F32: "f32", ms.MS_F64ACC: "f32+f64acc", ms.MS_KAHAN: "f32+f32x2"}[prec],
         "data": "synthetic (seeded Rosenthal-driven tracks, no dataset)",
         "config": dict(workload_config(w), parallelism=f"{world} independent blocks",
                        steps_per_launch=int(ctx.params.steps_per_launch),
+                       block_threads=int(ctx.params.block_threads) or 128,
+                       graph=bool(ctx.params.flags & ms._binding.MS_FLAG_GRAPH),
                        l2="L2 flushed (512 MiB write) between bench steps; the 50 MB state is "
                           "L2-resident inside a pass by design"),
         "wall_ms_per_step": wall / args.steps * 1e3,
         "clocks": clocks, "gpu_launches": int(st.launches), "roofline": roofline,
     }
 
+    if tuned is not None:
+        out["autotune"] = tuned.as_dict()
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_pass(ctx, w, srcs, args, ms, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -368,6 +434,9 @@ def run_ours(args):
         out["sum_err"] = float(np.max(np.abs(np.stack(g).sum(axis=0) - 1.0)))
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": desc}
+    if rank == 0 and world == 1 and not args.no_d6:
+        ctx.close()
+        out["roofline_ms_step"] = d6_layouts(ms, torch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

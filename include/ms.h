@@ -62,6 +62,11 @@ extern "C" {
 /* bits of ms_params.flags */
 #define MS_FLAG_TIME_KERNELS 1  /* time every hot-kernel launch with CUDA events on the
                                    context stream (read back by ms_stats)            */
+#define MS_FLAG_GRAPH        2  /* ms_run_track captures its launch sequence (source
+                                   table, active set, persistent hot kernel per chunk
+                                   of S steps) into a CUDA graph on first use and
+                                   replays it when called again with the same start
+                                   step, step count and dt (e.g. after ms_fill_state) */
 
 /* ---------------------------------------------------------------- params */
 /* Model constants and options.  ms_params_default() fills the paper's values:

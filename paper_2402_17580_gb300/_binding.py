@@ -21,6 +21,7 @@ ERRORS = {
 MS_F32, MS_F64ACC, MS_KAHAN = 0, 1, 2
 MS_PTR_DEVICE = 1
 MS_FLAG_TIME_KERNELS = 1
+MS_FLAG_GRAPH = 2
 
 d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
 

@@ -120,9 +120,36 @@ struct ms_ctx {
   // per-launch timing of the hot kernel (MS_FLAG_TIME_KERNELS)
   std::vector<cudaEvent_t> kev;  // pairs: start, stop
   size_t kev_used = 0;           // pairs recorded and not yet harvested
+  bool capturing = false;        // inside a stream capture (MS_FLAG_GRAPH)
+
+  // captured ms_run_track sequences (MS_FLAG_GRAPH)
+  struct Graph {
+    int64_t step0, n_steps, n_base;
+    double dt, t_base;
+    uint64_t epoch;
+    size_t kev_pairs;
+    int64_t launches;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  uint64_t epoch = 1;            // bumped whenever a captured graph may be stale
 };
 
 namespace {
+
+// Calls f with a tag carrying the fraction type of the context's precision.
+template <typename T>
+struct Tag {
+  using type = T;
+};
+template <class F>
+auto with_ft(const ms_ctx* c, F&& f) {
+  switch (c->prm.precision) {
+    case MS_F64ACC: return f(Tag<double>{});
+    case MS_KAHAN: return f(Tag<ms::KF>{});
+    default: return f(Tag<float>{});
+  }
+}
 
 ms::ModelConst make_const(const ms_params& p) {
   const double l2e = 1.4426950408889634074;
@@ -176,8 +203,6 @@ int check_params(const ms_params& p) {
   if (!std::isfinite(p.T_thr)) return fail(MS_ERR_INVALID_ARG, "T_thr must be finite");
   if (p.precision != MS_F32 && p.precision != MS_F64ACC && p.precision != MS_KAHAN)
     return fail(MS_ERR_INVALID_ARG, "unknown precision %d", p.precision);
-  if (p.precision == MS_KAHAN)
-    return fail(MS_ERR_UNSUPPORTED, "MS_KAHAN is not available in this build");
   if (p.steps_per_launch < 1 || p.steps_per_launch > ms::MAX_LEVELS - 1)
     return fail(MS_ERR_INVALID_ARG, "steps_per_launch must be in [1, %d]", ms::MAX_LEVELS - 1);
   if (p.block_threads != 0 &&
@@ -197,6 +222,12 @@ int grow(T** p, size_t* cap, size_t n) {
   MS_CUDA(cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T)));
   *cap = n;
   return MS_OK;
+}
+
+void drop_graphs(ms_ctx* c) {
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  c->epoch++;
 }
 
 void free_layout(ms_ctx* c) {
@@ -222,6 +253,7 @@ void free_layout(ms_ctx* c) {
 
 // (Re)build the padded layout for the current specs_h and reset the state.
 int build_layout(ms_ctx* c) {
+  drop_graphs(c);
   free_layout(c);
   int64_t tiles = 0, pad = 0, nat = 0;
   for (auto& s : c->specs_h) {
@@ -250,22 +282,21 @@ int build_layout(ms_ctx* c) {
   MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, tiles, INFINITY, c->stream));
   {
     const int bt = block_threads(c);
-    const int per_sm = c->fbytes == 4 ? ms::track_blocks_per_sm<float>(bt)
-                                      : ms::track_blocks_per_sm<double>(bt);
+    const int per_sm = with_ft(c, [&](auto tag) {
+      return ms::track_blocks_per_sm<typename decltype(tag)::type>(bt);
+    });
     const int64_t need = (tiles + bt / 32 - 1) / (bt / 32);
     c->track_grid = int(std::min<int64_t>(int64_t(per_sm) * c->sm_count, need));
   }
   MS_CUDA(cudaMemcpy(c->specs_d, c->specs_h.data(), c->specs_h.size() * sizeof(SpecDev),
                      cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(c->tile_spec_d, ts.data(), ts.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  if (c->fbytes == 4)
-    MS_CUDA(ms::launch_set_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
-                                        nullptr, (float*)c->xas_d, (float*)c->xam_d, c->aux_d,
-                                        c->stream));
-  else
-    MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
-                                         nullptr, (double*)c->xas_d, (double*)c->xam_d, c->aux_d,
-                                         c->stream));
+  MS_CUDA(with_ft(c, [&](auto tag) {
+      using FT = typename decltype(tag)::type;
+      return ms::launch_set_state<FT>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
+                                        nullptr, (FT*)c->xas_d, (FT*)c->xam_d, c->aux_d,
+                                        c->stream);
+    }));
   MS_CUDA(cudaStreamSynchronize(c->stream));
   c->step_n = c->n_base = 0;
   c->t_base = 0.0;
@@ -282,10 +313,14 @@ int kernel_event(ms_ctx* c, bool stop) {
     MS_CUDA(cudaEventCreate(&e));
     c->kev.push_back(e);
   }
-  MS_CUDA(cudaEventRecord(c->kev[i], c->stream));
+  if (c->capturing)
+    MS_CUDA(cudaEventRecordWithFlags(c->kev[i], c->stream, cudaEventRecordExternal));
+  else
+    MS_CUDA(cudaEventRecord(c->kev[i], c->stream));
   if (stop) c->kev_used++;
   return MS_OK;
 }
+
 
 // Add the recorded launch times to the counters (stream already synchronised).
 int harvest_kernel_events(ms_ctx* c) {
@@ -367,6 +402,7 @@ int set_sources(ms_ctx* c, const ms_heat_source* src) {
                     std::memcmp(ly.data(), c->layers_h.data(), ly.size() * sizeof(LayerDev)) == 0;
   if (same) return MS_OK;
   MS_CUDA(cudaStreamSynchronize(c->stream));  // previous launches may still read the tables
+  drop_graphs(c);
   int rc;
   if ((rc = grow(&c->tracks_d, &c->tracks_cap, tr.size())) != MS_OK) return rc;
   if ((rc = grow(&c->layers_d, &c->layers_cap, ly.size())) != MS_OK) return rc;
@@ -385,6 +421,8 @@ int set_sources(ms_ctx* c, const ms_heat_source* src) {
 int ensure_table(ms_ctx* c, int n_levels) {
   int rc;
   const size_t ns = c->specs_h.size();
+  if (ns * size_t(n_levels) > c->levels_cap || ns * size_t(n_levels) * size_t(c->slots) > c->entries_cap)
+    drop_graphs(c);
   if ((rc = grow(&c->levels_d, &c->levels_cap, ns * size_t(n_levels))) != MS_OK) return rc;
   if ((rc = grow(&c->entries_d, &c->entries_cap, ns * size_t(n_levels) * size_t(c->slots))) != MS_OK)
     return rc;
@@ -499,6 +537,73 @@ void set_dt(ms_ctx* c, double dt) {
 
 }  // namespace
 
+namespace {
+
+// Capture (first time) or replay the launch sequence of one ms_run_track call.
+int run_track_graph(ms_ctx* c, int64_t n_steps) {
+  int rc;
+  const bool timing = (c->prm.flags & MS_FLAG_TIME_KERNELS) != 0;
+  if (timing && c->kev_used) {  // pending launch timings use the same events
+    MS_CUDA(cudaStreamSynchronize(c->stream));
+    if ((rc = harvest_kernel_events(c)) != MS_OK) return rc;
+  }
+  if ((rc = ensure_table(c, c->prm.steps_per_launch + 1)) != MS_OK) return rc;
+  ms_ctx::Graph* g = nullptr;
+  for (auto& e : c->graphs)
+    if (e.step0 == c->step_n && e.n_steps == n_steps && e.n_base == c->n_base && e.dt == c->dt &&
+        e.t_base == c->t_base && e.epoch == c->epoch)
+      g = &e;
+  if (!g) {
+    const int64_t step_n = c->step_n;
+    const ms_stats_t st = c->st;
+    MS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->kev_used = 0;
+    rc = with_ft(c, [&](auto tag) { return run_track_impl<typename decltype(tag)::type>(c, n_steps); });
+    c->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+    const int64_t launches = c->st.launches - st.launches;
+    const size_t pairs = c->kev_used;
+    c->step_n = step_n;  // nothing ran yet
+    c->st = st;
+    c->kev_used = 0;
+    if (rc != MS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(MS_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(MS_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    if (c->graphs.size() >= 4) {
+      cudaGraphExecDestroy(c->graphs.front().exec);
+      c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back(ms_ctx::Graph{c->step_n, n_steps, c->n_base, c->dt, c->t_base, c->epoch,
+                                      pairs, launches, exec});
+    g = &c->graphs.back();
+  }
+  MS_CUDA(cudaEventRecord(c->ev0, c->stream));
+  MS_CUDA(cudaGraphLaunch(g->exec, c->stream));
+  MS_CUDA(cudaEventRecord(c->ev1, c->stream));
+  c->timed = true;
+  c->step_n += n_steps;
+  c->st.steps += n_steps;
+  c->st.point_updates += n_steps * c->n_points;
+  c->st.tile_steps_total += n_steps * c->n_tiles;
+  c->st.launches += g->launches;
+  if (timing) {
+    c->kev_used = g->kev_pairs;  // this replay re-recorded them
+    MS_CUDA(cudaStreamSynchronize(c->stream));
+    if ((rc = harvest_kernel_events(c)) != MS_OK) return rc;
+  }
+  return MS_OK;
+}
+
+}  // namespace
+
 // Shared with other translation units (declared in ms_internal.h).
 namespace ms {
 int validate_params(const ms_params& p) { return check_params(p); }
@@ -563,7 +668,7 @@ int ms_params_default(ms_params* p) {
   p->martensite_literal = 0;
   p->init_ba_steps = 0;
   p->precision = MS_F32;
-  p->steps_per_launch = 64;
+  p->steps_per_launch = 128;
   p->rebuild_steps = 0;
   p->block_threads = 0;
   return MS_OK;
@@ -579,7 +684,7 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
   if (!c) return fail(MS_ERR_OOM, "host allocation failed");
   c->prm = *p;
   c->mc = make_const(*p);
-  c->fbytes = p->precision == MS_F64ACC ? 8 : 4;
+  c->fbytes = p->precision == MS_F32 ? 4 : 8;  // MS_KAHAN stores two floats per fraction
   c->n_points = n_points;
   auto bail = [&](int code) { ms_destroy(c); return code; };
   if (cudaGetDevice(&c->device) != cudaSuccess)
@@ -609,6 +714,7 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
 void ms_destroy(ms_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
   free_layout(c);
   cudaFree(c->err_d);
   cudaFree(c->work_d);
@@ -678,14 +784,12 @@ int ms_set_state(ms_ctx* c, const double* xas, const double* xam, const double* 
   MS_CUDA(cudaMemcpy(d, xas, size_t(n) * sizeof(double), cudaMemcpyHostToDevice));
   MS_CUDA(cudaMemcpy(d + n, xam, size_t(n) * sizeof(double), cudaMemcpyHostToDevice));
   if (aux) MS_CUDA(cudaMemcpy(d + 2 * n, aux, size_t(n) * sizeof(double), cudaMemcpyHostToDevice));
-  if (c->fbytes == 4)
-    MS_CUDA(ms::launch_set_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles, d, d + n,
-                                        aux ? d + 2 * n : nullptr, (float*)c->xas_d,
-                                        (float*)c->xam_d, c->aux_d, c->stream));
-  else
-    MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, d, d + n,
-                                         aux ? d + 2 * n : nullptr, (double*)c->xas_d,
-                                         (double*)c->xam_d, c->aux_d, c->stream));
+  MS_CUDA(with_ft(c, [&](auto tag) {
+      using FT = typename decltype(tag)::type;
+      return ms::launch_set_state<FT>(c->specs_d, c->tile_spec_d, c->n_tiles, d, d + n,
+                                        aux ? d + 2 * n : nullptr, (FT*)c->xas_d,
+                                        (FT*)c->xam_d, c->aux_d, c->stream);
+    }));
   MS_CUDA(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
   MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, c->n_tiles, INFINITY, c->stream));
   MS_CUDA(cudaStreamSynchronize(c->stream));
@@ -699,14 +803,12 @@ int ms_fill_state(ms_ctx* c, double xas, double xam) {
   if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
   if (!(std::isfinite(xas) && std::isfinite(xam) && xas >= 0 && xam >= 0 && xas + xam <= 0.9 + 1e-6))
     return fail(MS_ERR_INVALID_ARG, "need X_as, X_am >= 0 and X_as + X_am <= 0.9");
-  if (c->fbytes == 4)
-    MS_CUDA(ms::launch_set_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
-                                        nullptr, (float*)c->xas_d, (float*)c->xam_d, c->aux_d,
-                                        c->stream, xas, xam));
-  else
-    MS_CUDA(ms::launch_set_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
-                                         nullptr, (double*)c->xas_d, (double*)c->xam_d, c->aux_d,
-                                         c->stream, xas, xam));
+  MS_CUDA(with_ft(c, [&](auto tag) {
+      using FT = typename decltype(tag)::type;
+      return ms::launch_set_state<FT>(c->specs_d, c->tile_spec_d, c->n_tiles, nullptr, nullptr,
+                                        nullptr, (FT*)c->xas_d, (FT*)c->xam_d, c->aux_d,
+                                        c->stream, xas, xam);
+    }));
   MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, c->n_tiles, INFINITY, c->stream));
   c->st.launches += 2;
   c->step_n = c->n_base = 0;
@@ -742,7 +844,7 @@ int ms_step(ms_ctx* c, const float* T_prev, const float* T_new, double dt, int32
   }
   set_dt(c, dt);
   MS_CUDA(cudaEventRecord(c->ev0, c->stream));
-  int rc = c->fbytes == 4 ? step_impl<float>(c, t0, t1) : step_impl<double>(c, t0, t1);
+  int rc = with_ft(c, [&](auto tag) { return step_impl<typename decltype(tag)::type>(c, t0, t1); });
   if (rc != MS_OK) return rc;
   MS_CUDA(cudaEventRecord(c->ev1, c->stream));
   c->timed = true;
@@ -762,8 +864,9 @@ int ms_run_track(ms_ctx* c, const ms_heat_source* src, int64_t n_steps, double d
   if ((rc = set_sources(c, src)) != MS_OK) return rc;
   set_dt(c, dt);
   c->T_last = nullptr;
+  if ((c->prm.flags & MS_FLAG_GRAPH) && n_steps > 0) return run_track_graph(c, n_steps);
   MS_CUDA(cudaEventRecord(c->ev0, c->stream));
-  rc = c->fbytes == 4 ? run_track_impl<float>(c, n_steps) : run_track_impl<double>(c, n_steps);
+  rc = with_ft(c, [&](auto tag) { return run_track_impl<typename decltype(tag)::type>(c, n_steps); });
   if (rc != MS_OK) return rc;
   MS_CUDA(cudaEventRecord(c->ev1, c->stream));
   c->timed = true;
@@ -785,25 +888,20 @@ int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double*
     } else {
       return fail(MS_ERR_STATE, "no temperature known for X_beta / X_liq yet");
     }
-    if (c->fbytes == 4)
-      MS_CUDA(ms::launch_fractions<float>(c->mc, c->specs_d, c->tile_spec_d, c->n_tiles,
-                                          (const float*)c->xas_d, (const float*)c->xam_d, T,
+    MS_CUDA(with_ft(c, [&](auto tag) {
+        using FT = typename decltype(tag)::type;
+        return ms::launch_fractions<FT>(c->mc, c->specs_d, c->tile_spec_d, c->n_tiles,
+                                          (const FT*)c->xas_d, (const FT*)c->xam_d, T,
                                           c->levels_d, c->entries_d, c->slots, d + 2 * n,
-                                          d + 3 * n, c->stream));
-    else
-      MS_CUDA(ms::launch_fractions<double>(c->mc, c->specs_d, c->tile_spec_d, c->n_tiles,
-                                           (const double*)c->xas_d, (const double*)c->xam_d, T,
-                                           c->levels_d, c->entries_d, c->slots, d + 2 * n,
-                                           d + 3 * n, c->stream));
+                                          d + 3 * n, c->stream);
+      }));
   }
-  if (c->fbytes == 4)
-    MS_CUDA(ms::launch_get_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles,
-                                        (const float*)c->xas_d, (const float*)c->xam_d, c->aux_d,
-                                        d, d + n, nullptr, c->stream));
-  else
-    MS_CUDA(ms::launch_get_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles,
-                                         (const double*)c->xas_d, (const double*)c->xam_d,
-                                         c->aux_d, d, d + n, nullptr, c->stream));
+  MS_CUDA(with_ft(c, [&](auto tag) {
+      using FT = typename decltype(tag)::type;
+      return ms::launch_get_state<FT>(c->specs_d, c->tile_spec_d, c->n_tiles,
+                                        (const FT*)c->xas_d, (const FT*)c->xam_d, c->aux_d,
+                                        d, d + n, nullptr, c->stream);
+    }));
   const size_t nb = size_t(n) * sizeof(double);
   if (xas) MS_CUDA(cudaMemcpyAsync(xas, d, nb, cudaMemcpyDeviceToHost, c->stream));
   if (xam) MS_CUDA(cudaMemcpyAsync(xam, d + n, nb, cudaMemcpyDeviceToHost, c->stream));
@@ -815,14 +913,12 @@ int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double*
 int ms_get_aux(ms_ctx* c, double* aux) {
   if (!c || !aux) return fail(MS_ERR_INVALID_ARG, "NULL argument");
   double* d = c->stage_d;
-  if (c->fbytes == 4)
-    MS_CUDA(ms::launch_get_state<float>(c->specs_d, c->tile_spec_d, c->n_tiles,
-                                        (const float*)c->xas_d, (const float*)c->xam_d, c->aux_d,
-                                        nullptr, nullptr, d, c->stream));
-  else
-    MS_CUDA(ms::launch_get_state<double>(c->specs_d, c->tile_spec_d, c->n_tiles,
-                                         (const double*)c->xas_d, (const double*)c->xam_d,
-                                         c->aux_d, nullptr, nullptr, d, c->stream));
+  MS_CUDA(with_ft(c, [&](auto tag) {
+      using FT = typename decltype(tag)::type;
+      return ms::launch_get_state<FT>(c->specs_d, c->tile_spec_d, c->n_tiles,
+                                        (const FT*)c->xas_d, (const FT*)c->xam_d, c->aux_d,
+                                        nullptr, nullptr, d, c->stream);
+    }));
   MS_CUDA(cudaMemcpyAsync(aux, d, size_t(c->n_points) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return check_device_error(c);
 }

@@ -39,6 +39,52 @@ struct ModelConst {
   int init_ba_steps;                // reading A6
 };
 
+// Compensated FP32 fraction (MS_KAHAN): an unevaluated sum hi + lo of two
+// floats (double-float).  Sums and differences are error-free transforms
+// (TwoSum, then FastTwoSum to renormalise), products carry the FMA error term,
+// so the Euler accumulation keeps ~44 bits where plain FP32 keeps 24.
+struct KF {
+  float hi, lo;
+  __host__ __device__ KF() : hi(0.0f), lo(0.0f) {}
+  __host__ __device__ KF(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit KF(double v) : hi(float(v)), lo(float(v - double(float(v)))) {}
+  __host__ __device__ explicit KF(float v) : hi(v), lo(0.0f) {}
+  __host__ __device__ explicit KF(int v) : hi(float(v)), lo(0.0f) {}
+  __host__ __device__ explicit operator float() const { return hi + lo; }
+  __host__ __device__ explicit operator double() const { return double(hi) + double(lo); }
+};
+
+__host__ __device__ __forceinline__ KF kf_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return KF(s, b - (s - a));
+}
+__host__ __device__ __forceinline__ KF operator+(KF a, KF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+  return kf_fast_two_sum(s, e);
+}
+__host__ __device__ __forceinline__ KF operator-(KF a) { return KF(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ KF operator-(KF a, KF b) { return a + (-b); }
+__host__ __device__ __forceinline__ KF operator*(KF a, KF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+  return kf_fast_two_sum(p, e);
+}
+__host__ __device__ __forceinline__ KF operator/(KF a, KF b) {
+  const float q1 = a.hi / b.hi;
+  const KF r = a - b * KF(q1);
+  return kf_fast_two_sum(q1, r.hi / b.hi);
+}
+__host__ __device__ __forceinline__ KF& operator*=(KF& a, KF b) { return a = a * b; }
+__host__ __device__ __forceinline__ bool operator<(KF a, KF b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__host__ __device__ __forceinline__ bool operator>(KF a, KF b) { return b < a; }
+__host__ __device__ __forceinline__ bool operator<=(KF a, KF b) { return !(b < a); }
+__host__ __device__ __forceinline__ bool operator>=(KF a, KF b) { return !(a < b); }
+__host__ __device__ __forceinline__ bool operator==(KF a, KF b) { return a.hi == b.hi && a.lo == b.lo; }
+
 constexpr float XMAX = 0.9f;        // bound on X_alpha used throughout Sec. 2.2
 constexpr float INV_XMAX = 1.0f / 0.9f;
 
@@ -244,25 +290,60 @@ struct SrcEntry {
 
 struct SrcLevel {
   int n;             // started sources of the current layer at this level
+  int axis;          // 1: every started source moves along +-(u0x, u0y)
   float z_surf;      // current layer surface (all its sources sit on it)
   float T0, T_max;
+  float u0x, u0y;    // common axis when axis == 1
+  float pad;
 };
 
-// Contribution of one source to a point with squared depth below the surface
-// dz2 (plus 1e-30, which keeps R > 0 and sends R = 0 to the T_max cap):
+// 1 / (1 + a) for a in [0, 1] on the FMA pipe: a least-squares quartic
+// (relative error 3e-4) refined by one Newton step (1.7e-7).  The
+// MS_RCP_MODE = 1 tuning build uses it for every second source, to share the
+// reciprocals between the SFU and the FMA pipe.
+__device__ __forceinline__ float rcp1p_fma(float a) {
+  float y = fmaf(fmaf(fmaf(fmaf(0.15224367380142212f, a, -0.5328531265258789f), a,
+                           0.8658891320228577f), a, -0.9848334193229675f), a,
+                 0.999702513217926f);
+  const float e = fmaf(-a, y, 1.0f - y);  // 1 - (1 + a) y
+  return fmaf(y, e, y);
+}
+
+// Contribution of one source to a point whose offset from the source is xi
+// along the source's direction and whose squared distance from the path's
+// line is perp2 (the squared depth below the surface plus 1e-30 is part of
+// perp2, which keeps R > 0 and sends R = 0 to the T_max cap):
 //   A P / (2 pi k R) exp(-v (R + xi) / (2 alpha)).
 // Behind the source (xi < 0) R + xi cancels; it is computed there as
 // perp^2 / (R + |xi|), algebraically equal and free of cancellation, so far
-// receding sources keep full FP32 accuracy.  16 instructions, 3 on the SFU.
+// receding sources keep full FP32 accuracy.
+template <bool FMA_RCP>
+__device__ __forceinline__ float source_term_frame(float xi, float perp2, float cR, float lC) {
+  const float r2 = fmaf(xi, xi, perp2);
+  const float rinv = sfu_rsqrt(r2);
+  const float w = fmaf(r2, rinv, fabsf(xi));          // R + |xi|
+  const float inv_w = FMA_RCP ? rcp1p_fma(fabsf(xi) * rinv) * rinv : sfu_rcp(w);
+  const float rpx = xi >= 0.0f ? w : perp2 * inv_w;
+  return rinv * sfu_ex2(fmaf(cR, rpx, lC));
+}
+
+// General frame: the point (px, py) projected on the source's own axes.
+template <bool FMA_RCP>
 __device__ __forceinline__ float source_term(const SrcEntry& e, float px, float py, float dz2) {
   const float xi = fmaf(px, e.ux, fmaf(py, e.uy, -e.s_xi));
   const float pp = fmaf(px, e.uy, fmaf(py, -e.ux, -e.s_pp));
-  const float perp2 = fmaf(pp, pp, dz2);
-  const float r2 = fmaf(xi, xi, perp2);
-  const float rinv = sfu_rsqrt(r2);
-  const float w = fmaf(r2, rinv, fabsf(xi));        // R + |xi|
-  const float rpx = xi >= 0.0f ? w : perp2 * sfu_rcp(w);
-  return rinv * sfu_ex2(fmaf(e.cR, rpx, e.lC));
+  return source_term_frame<FMA_RCP>(xi, fmaf(pp, pp, dz2), e.cR, e.lC);
+}
+
+// Common-axis frame: pa, pb are the point's coordinates along and across the
+// level's axis u0; the entry holds the sign s of u . u0 in ux, s times the
+// source's along-axis coordinate in s_xi and its across-axis coordinate in s_pp.
+template <bool FMA_RCP>
+__device__ __forceinline__ float source_term_axis(const SrcEntry& e, float pa, float pb,
+                                                  float dz2) {
+  const float xi = fmaf(e.ux, pa, -e.s_xi);
+  const float pp = pb - e.s_pp;
+  return source_term_frame<FMA_RCP>(xi, fmaf(pp, pp, dz2), e.cR, e.lC);
 }
 
 }  // namespace ms

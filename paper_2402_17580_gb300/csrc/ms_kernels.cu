@@ -51,6 +51,20 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   const double C0 = sp.A / (2.0 * kPi * sp.k) * scale;
   const double cv = -kLog2e / (2.0 * sp.alpha);
   SrcEntry* out = a.entries + (int64_t(s) * a.n_levels + lv) * a.slots;
+  // do all started sources of the level move along one axis (up to sign)?
+  double u0x = 0.0, u0y = 0.0;
+  bool axis = true, first = true;
+  for (int j = 0; j < sp.n_tracks; ++j) {
+    const TrackDev tr = a.tracks[sp.track0 + j];
+    if (tr.layer != l || tl < tr.t_start) continue;
+    if (first) {
+      u0x = tr.ux;
+      u0y = tr.uy;
+      first = false;
+    } else if (fabs(tr.ux * u0y - tr.uy * u0x) > 1e-12) {
+      axis = false;
+    }
+  }
   int n = 0;
   for (int j = 0; j < sp.n_tracks && n < a.slots; ++j) {
     const TrackDev tr = a.tracks[sp.track0 + j];
@@ -59,10 +73,18 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
     const double sx = tr.x0 + tr.ux * travel, sy = tr.y0 + tr.uy * travel;
     const double C = C0 * tr.P;
     SrcEntry e;
-    e.s_xi = float(sx * tr.ux + sy * tr.uy);
-    e.s_pp = float(sx * tr.uy - sy * tr.ux);
-    e.ux = float(tr.ux);
-    e.uy = float(tr.uy);
+    if (axis) {
+      const double sg = (tr.ux * u0x + tr.uy * u0y) >= 0.0 ? 1.0 : -1.0;
+      e.s_xi = float(sg * (sx * u0x + sy * u0y));
+      e.s_pp = float(sx * u0y - sy * u0x);
+      e.ux = float(sg);
+      e.uy = 0.0f;
+    } else {
+      e.s_xi = float(sx * tr.ux + sy * tr.uy);
+      e.s_pp = float(sx * tr.uy - sy * tr.ux);
+      e.ux = float(tr.ux);
+      e.uy = float(tr.uy);
+    }
     e.cR = float(cv * tr.v);
     e.lC = C > 0.0 ? float(log2(C)) : -INFINITY;
     e.pad0 = e.pad1 = 0.0f;
@@ -70,9 +92,13 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   }
   SrcLevel r;
   r.n = n;
+  r.axis = axis ? 1 : 0;
   r.z_surf = float(L.z);
   r.T0 = sp.T0;
   r.T_max = sp.T_max;
+  r.u0x = float(u0x);
+  r.u0y = float(u0y);
+  r.pad = 0.0f;
   a.levels[id] = r;
 }
 
@@ -90,26 +116,84 @@ __device__ __forceinline__ float depth2(float pz, float z_surf) {
   return fmaf(dz, dz, 1e-30f);
 }
 
+// Source-term variants (tuning builds): MS_RCP_MODE 1 alternates the SFU and
+// the FMA-pipe reciprocal between consecutive sources, 0 keeps every
+// reciprocal on the SFU; MS_AXIS 1 takes the common-axis frame when a level
+// has one.  Measured on the 256x256x64 block (S = 256): 0/0 gives 1.033e11
+// point-updates/s, 0/1 0.945e11, 1/0 0.942e11, 1/1 0.875e11, so both stay
+// off by default.
+#ifndef MS_RCP_MODE
+#define MS_RCP_MODE 0
+#endif
+#ifndef MS_AXIS
+#define MS_AXIS 0
+#endif
+constexpr bool kOddFmaRcp = MS_RCP_MODE == 1;
+
 // Temperatures of 4 points at one level (4 independent chains per source).
+// With kOddFmaRcp the sources alternate between the SFU reciprocal (even j)
+// and the FMA-pipe one (odd j); the sum runs in source order.
 __device__ __forceinline__ void temps4(const SrcLevel& L, const SrcEntry* en, const float* px,
                                        const float* py, const float* pz, float* T) {
   float acc[4] = {0.f, 0.f, 0.f, 0.f}, dz2[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) dz2[q] = depth2(pz[q], L.z_surf);
-  for (int j = 0; j < L.n; ++j) {
-    const SrcEntry e = load_entry(en + j);
+  if (MS_AXIS && L.axis) {
+    float pa[4], pb[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += source_term(e, px[q], py[q], dz2[q]);
+    for (int q = 0; q < 4; ++q) {
+      pa[q] = fmaf(px[q], L.u0x, py[q] * L.u0y);
+      pb[q] = fmaf(px[q], L.u0y, -py[q] * L.u0x);
+    }
+    int j = 0;
+    for (; j + 1 < L.n; j += 2) {
+      const SrcEntry e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += source_term_axis<false>(e0, pa[q], pb[q], dz2[q]);
+        acc[q] += source_term_axis<kOddFmaRcp>(e1, pa[q], pb[q], dz2[q]);
+      }
+    }
+    if (j < L.n) {
+      const SrcEntry e0 = load_entry(en + j);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += source_term_axis<false>(e0, pa[q], pb[q], dz2[q]);
+    }
+  } else {
+    int j = 0;
+    for (; j + 1 < L.n; j += 2) {
+      const SrcEntry e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += source_term<false>(e0, px[q], py[q], dz2[q]);
+        acc[q] += source_term<kOddFmaRcp>(e1, px[q], py[q], dz2[q]);
+      }
+    }
+    if (j < L.n) {
+      const SrcEntry e0 = load_entry(en + j);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += source_term<false>(e0, px[q], py[q], dz2[q]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) T[q] = fminf(L.T0 + acc[q], L.T_max);
 }
 
+// Temperature of one point; the same arithmetic and order as temps4.
 __device__ __forceinline__ float temp1(const SrcLevel& L, const SrcEntry* en, float px, float py,
                                        float pz) {
   float acc = 0.f;
   const float dz2 = depth2(pz, L.z_surf);
-  for (int j = 0; j < L.n; ++j) acc += source_term(load_entry(en + j), px, py, dz2);
+  if (MS_AXIS && L.axis) {
+    const float pa = fmaf(px, L.u0x, py * L.u0y), pb = fmaf(px, L.u0y, -py * L.u0x);
+    for (int j = 0; j < L.n; ++j)
+      acc += (j & 1) ? source_term_axis<kOddFmaRcp>(load_entry(en + j), pa, pb, dz2)
+                     : source_term_axis<false>(load_entry(en + j), pa, pb, dz2);
+  } else {
+    for (int j = 0; j < L.n; ++j)
+      acc += (j & 1) ? source_term<kOddFmaRcp>(load_entry(en + j), px, py, dz2)
+                     : source_term<false>(load_entry(en + j), px, py, dz2);
+  }
   return fminf(L.T0 + acc, L.T_max);
 }
 
@@ -237,9 +321,26 @@ struct Vec4<double> {
   }
 };
 
+template <>
+struct Vec4<KF> {
+  static __device__ __forceinline__ void load(const KF* p, KF* v) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = KF(a.x, a.y); v[1] = KF(a.z, a.w); v[2] = KF(b.x, b.y); v[3] = KF(b.z, b.w);
+  }
+  static __device__ __forceinline__ void store(KF* p, const KF* v) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+  }
+};
+
+__device__ __forceinline__ bool finite1(float a) { return ::isfinite(a); }
+__device__ __forceinline__ bool finite1(double a) { return ::isfinite(a); }
+__device__ __forceinline__ bool finite1(KF a) { return ::isfinite(a.hi) && ::isfinite(a.lo); }
+
 template <typename FT>
 __device__ __forceinline__ bool finite_pair(FT a, FT b) {
-  return isfinite(a) && isfinite(b);
+  return finite1(a) && finite1(b);
 }
 
 // ------------------------------------------------------------ hot kernel
@@ -555,5 +656,6 @@ cudaError_t launch_fractions(const ModelConst& m, const SpecDev* specs, const in
 
 MS_INSTANTIATE(float)
 MS_INSTANTIATE(double)
+MS_INSTANTIATE(KF)
 
 }  // namespace ms

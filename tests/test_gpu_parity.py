@@ -218,6 +218,52 @@ def test_f64_accumulation_parity(ms):
     check_sum(g)
 
 
+def test_kahan_compensated_parity(ms):
+    """MS_KAHAN: double-float fractions, FP32 rates; as tight as FP64
+    accumulation on the line."""
+    w = wl.line_4096(n_points=1024, n_steps=2000)
+    _, g = gpu_workload(w, precision=ms.MS_KAHAN)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= 3e-5
+    check_sum(g)
+
+
+def test_graph_replay_is_bit_identical(ms):
+    """MS_FLAG_GRAPH: the captured launch sequence (with the active set) gives
+    the same bits as direct launches, on the first (capture) and a replayed
+    pass, and counts the same launches."""
+    from paper_2402_17580_gb300._binding import MS_FLAG_GRAPH, MS_FLAG_TIME_KERNELS
+    w = wl.batch_64(n_specimens=4, n_lo=300, n_hi=3000, n_steps=500, T_thr=600.0)
+    _, ref = gpu_workload(w, steps_per_launch=32)
+    ctx = ms.Context(w.n_points, T_thr=w.T_thr, steps_per_launch=32,
+                     flags=MS_FLAG_GRAPH | MS_FLAG_TIME_KERNELS)
+    ctx.set_points([s.grid for s in w.specimens])
+    for _ in range(2):
+        ctx.fill_state(0.9, 0.0)
+        ctx.run_track([s.source for s in w.specimens], w.n_steps, w.dt)
+        g = ctx.fractions()
+        for a, b in zip(ref, g):
+            assert np.array_equal(a, b)
+    st = ctx.stats()
+    assert st.hot_kernel_launches == 2 * 16 and st.hot_kernel_ms > 0
+
+
+def test_autotuner_picks_a_measured_configuration(ms):
+    from paper_2402_17580_gb300.autotune import autotune
+    w = wl.line_4096(n_points=2048, n_steps=400)
+    res = autotune([s.grid for s in w.specimens], [s.source for s in w.specimens], w.n_points,
+                   w.dt, trial_steps=256, repeats=1,
+                   candidates={"steps_per_launch": (32, 128), "block_threads": (128,)})
+    assert len(res.table) == 4 and res.ms == min(t for _, t in res.table) and res.ms > 0
+    ctx = ms.Context(w.n_points, **res.params)
+    ctx.set_points([s.grid for s in w.specimens])
+    ctx.fill_state()
+    ctx.run_track([s.source for s in w.specimens], w.n_steps, w.dt)
+    _, dense = gpu_workload(w)
+    for a, b in zip(dense, ctx.fractions()):
+        assert np.array_equal(a, b)
+
+
 def test_device_pointers_on_a_torch_stream(ms):
     """ms_step with device temperature arrays on the caller's stream."""
     torch = pytest.importorskip("torch")
@@ -259,7 +305,7 @@ def test_error_paths(ms):
         ctx.step(np.zeros(10, np.float32), np.zeros(10, np.float32), -1.0)
     assert e.value.code == -1
     with pytest.raises(ms.MSError):
-        ms.Context(10, precision=ms.MS_KAHAN)
+        ms.Context(10, precision=7)
     w = wl.line_4096(n_points=10)
     with pytest.raises(ms.MSError) as e:
         ctx.set_points([wl.Grid(dims=(11, 1, 1))])
