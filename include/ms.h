@@ -55,6 +55,8 @@ extern "C" {
 #define MS_F32      0  /* fractions stored and accumulated in FP32                       */
 #define MS_F64ACC   1  /* fractions stored and accumulated in FP64                       */
 #define MS_KAHAN    2  /* FP32 fractions with a compensation term (two floats each)      */
+#define MS_F64      3  /* everything in FP64: temperatures, rates, fractions (the GPU
+                          spot-check path; FP64 exp2 / log2 instead of the SFU)        */
 
 /* flags for ms_step */
 #define MS_PTR_DEVICE  1  /* T_prev / T_new are device pointers (else host pointers)    */
@@ -213,6 +215,13 @@ int ms_set_stream(ms_ctx* ctx, void* cuda_stream);
  * Copied.  Errors: INVALID_ARG (count mismatch, bad dims), OOM, CUDA. */
 int ms_set_points(ms_ctx* ctx, const ms_grid* grids, int32_t n_specimens);
 
+/* Geometry for ms_run_track where the context's points are a subset of one
+ * grid: point i of the context is grid point idx[i] (natural index of the
+ * grid, i fastest), n == n_points.  Used to spot-check a large part on a
+ * sample of its points (the FP64 path on 1e5 points of a 67M-point block).
+ * Copied.  Errors: INVALID_ARG (n mismatch, index outside the grid), OOM, CUDA. */
+int ms_set_points_subset(ms_ctx* ctx, const ms_grid* grid, const int64_t* idx, int64_t n);
+
 /* Set the state of every point from host arrays of n_points doubles.
  * aux may be NULL (no initiation in progress) or give per point the App. A
  * variable: X~_beta > 0 of an active alpha_s -> beta initiation, -1 for an
@@ -258,6 +267,12 @@ int ms_get_fractions(ms_ctx* ctx, double* x_as, double* x_am, double* x_beta, do
 /* App. A variable of every point in the encoding of ms_set_state (n_points
  * doubles).  Errors: INVALID_ARG, CUDA. */
 int ms_get_aux(ms_ctx* ctx, double* aux);
+
+/* Temperature of every point at the current time level (the moving source of
+ * the last ms_run_track, or T_new of the last ms_step), n_points doubles, in
+ * the context's arithmetic precision.  Errors: INVALID_ARG, STATE (no
+ * temperature known yet), CUDA. */
+int ms_get_temperature(ms_ctx* ctx, double* T);
 
 /* Checkpoint: serialise the full device state (fractions, App. A variables,
  * step counter, dt) into blob.  With blob == NULL only *bytes is set to the

@@ -18,7 +18,7 @@ ERRORS = {
     -1: "MS_ERR_INVALID_ARG", -2: "MS_ERR_OOM", -3: "MS_ERR_CUDA", -4: "MS_ERR_DEVICE_TIMEOUT",
     -5: "MS_ERR_NONFINITE", -6: "MS_ERR_STATE", -7: "MS_ERR_UNSUPPORTED",
 }
-MS_F32, MS_F64ACC, MS_KAHAN = 0, 1, 2
+MS_F32, MS_F64ACC, MS_KAHAN, MS_F64 = 0, 1, 2, 3
 MS_PTR_DEVICE = 1
 MS_FLAG_TIME_KERNELS = 1
 MS_FLAG_GRAPH = 2
@@ -101,6 +101,8 @@ def load(build_if_missing: bool = True):
     lib.ms_set_stream.argtypes = [P, P]
     lib.ms_set_points.argtypes = [P, ctypes.POINTER(Grid), i32]
     lib.ms_set_state.argtypes = [P, P, P, P]
+    lib.ms_set_points_subset.argtypes = [P, ctypes.POINTER(Grid), ctypes.POINTER(i64), i64]
+    lib.ms_get_temperature.argtypes = [P, P]
     lib.ms_step.argtypes = [P, P, P, d, i32]
     lib.ms_run_track.argtypes = [P, ctypes.POINTER(HeatSource), i64, d]
     lib.ms_get_fractions.argtypes = [P, P, P, P, P]
@@ -234,6 +236,19 @@ class Context:
         for i, g in enumerate(grids):
             arr[i] = Grid((d * 3)(*g.origin), (d * 3)(*g.spacing), (i32 * 3)(*g.dims), 0)
         _check(self._lib.ms_set_points(self._h, arr, len(grids)), "ms_set_points")
+
+    def set_points_subset(self, grid, idx):
+        """The context's points are grid points idx (natural grid indices)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        g = Grid((d * 3)(*grid.origin), (d * 3)(*grid.spacing), (i32 * 3)(*grid.dims), 0)
+        _check(self._lib.ms_set_points_subset(self._h, ctypes.byref(g),
+                                              idx.ctypes.data_as(ctypes.POINTER(i64)), idx.size),
+               "ms_set_points_subset")
+
+    def temperature(self):
+        out = np.empty(self.n)
+        _check(self._lib.ms_get_temperature(self._h, _ptr(out)), "ms_get_temperature")
+        return out
 
     def set_state(self, xas, xam, aux=None):
         xas, xam = _f64(xas, self.n), _f64(xam, self.n)

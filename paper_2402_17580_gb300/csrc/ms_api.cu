@@ -18,8 +18,6 @@
 
 using ms::LayerDev;
 using ms::SpecDev;
-using ms::SrcEntry;
-using ms::SrcLevel;
 using ms::TrackDev;
 using ms::TILE;
 
@@ -37,12 +35,12 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-#define MS_CUDA(call)                                                                     \
+#define MS_CUDA(...)                                                                      \
   do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
+    cudaError_t e_ = (__VA_ARGS__);                                                       \
     if (e_ != cudaSuccess)                                                                \
       return fail(e_ == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA, "%s: %s (%s:%d)", \
-                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+                  #__VA_ARGS__, cudaGetErrorString(e_), __FILE__, __LINE__);              \
   } while (0)
 
 constexpr uint64_t kBlobMagic = 0x4d53434b50543031ull;  // "MSCKPT01"
@@ -63,7 +61,8 @@ struct BlobHeader {
 
 struct ms_ctx {
   ms_params prm{};
-  ms::ModelConst mc{};
+  ms::ModelConstT<float> mc{};     // FP32 arithmetic paths
+  ms::ModelConstT<double> mcd{};   // full-FP64 path (MS_F64)
   int device = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
@@ -103,9 +102,10 @@ struct ms_ctx {
   size_t tracks_cap = 0, layers_cap = 0;
   int slots = 0;
   bool src_valid = false;
-  SrcLevel* levels_d = nullptr;
-  SrcEntry* entries_d = nullptr;
-  size_t levels_cap = 0, entries_cap = 0;
+  void* levels_d = nullptr;        // SrcLevelT<AT> of the context's arithmetic type
+  void* entries_d = nullptr;       // SrcEntryT<AT>
+  size_t levels_cap = 0, entries_cap = 0;  // bytes
+  int64_t* idx_d = nullptr;        // grid indices of a subset specimen
 
   // time
   int64_t step_n = 0;
@@ -137,49 +137,60 @@ struct ms_ctx {
 
 namespace {
 
-// Calls f with a tag carrying the fraction type of the context's precision.
-template <typename T>
+// Calls f with a tag carrying the arithmetic type AT and the fraction type FT
+// of the context's precision.
+template <typename A, typename F>
 struct Tag {
-  using type = T;
+  using at = A;
+  using type = F;
 };
 template <class F>
 auto with_ft(const ms_ctx* c, F&& f) {
   switch (c->prm.precision) {
-    case MS_F64ACC: return f(Tag<double>{});
-    case MS_KAHAN: return f(Tag<ms::KF>{});
-    default: return f(Tag<float>{});
+    case MS_F64ACC: return f(Tag<float, double>{});
+    case MS_KAHAN: return f(Tag<float, ms::KF>{});
+    case MS_F64: return f(Tag<double, double>{});
+    default: return f(Tag<float, float>{});
   }
 }
 
-ms::ModelConst make_const(const ms_params& p) {
+template <typename AT>
+const ms::ModelConstT<AT>& consts(const ms_ctx* c);
+template <>
+const ms::ModelConstT<float>& consts<float>(const ms_ctx* c) { return c->mc; }
+template <>
+const ms::ModelConstT<double>& consts<double>(const ms_ctx* c) { return c->mcd; }
+
+template <typename AT>
+ms::ModelConstT<AT> make_const(const ms_params& p) {
   const double l2e = 1.4426950408889634074;
-  ms::ModelConst m{};
-  m.T_s = float(p.T_s);
-  m.T_l = float(p.T_l);
-  m.inv_mushy = float(1.0 / (p.T_l - p.T_s));
-  m.T_as_start = float(p.T_as_start);
-  m.T_as_end = float(p.T_as_end);
-  m.T_am_start = float(p.T_am_start);
-  m.T_inf = float(p.T_inf);
-  m.kaeq_l2 = float(p.k_alpha_eq * l2e);
-  m.kam_l2 = float(p.k_am_eq * l2e);
-  m.k1 = float(p.k1);
-  m.k2 = float(p.k2);
-  m.k3_l2 = float(p.k3 * l2e);
-  m.f = float(p.f);
-  m.c_as = float(p.c_as);
-  m.c_b = float(p.c_b);
-  m.inv_c_as = float(1.0 / p.c_as);
-  m.inv_c_b = float(1.0 / p.c_b);
-  m.pa = float((p.c_as - 1.0) / p.c_as);
-  m.qa = float((p.c_as + 1.0) / p.c_as);
-  m.pb = float((p.c_b - 1.0) / p.c_b);
-  m.qb = float((p.c_b + 1.0) / p.c_b);
-  m.T_cap0 = float(p.T_as_start + p.T_reg);
-  m.inv_T_reg = float(1.0 / p.T_reg);
-  m.init_exit = float(p.init_exit);
-  m.init_exit_floor = float(p.init_exit_floor);
-  m.T_thr = float(p.T_thr);
+  ms::ModelConstT<AT> m{};
+  m.T_s = AT(p.T_s);
+  m.T_l = AT(p.T_l);
+  m.inv_mushy = AT(1.0 / (p.T_l - p.T_s));
+  m.T_as_start = AT(p.T_as_start);
+  m.T_as_end = AT(p.T_as_end);
+  m.T_am_start = AT(p.T_am_start);
+  m.T_inf = AT(p.T_inf);
+  m.kaeq_l2 = AT(p.k_alpha_eq * l2e);
+  m.kam_l2 = AT(p.k_am_eq * l2e);
+  m.k1 = AT(p.k1);
+  m.k2 = AT(p.k2);
+  m.k3_l2 = AT(p.k3 * l2e);
+  m.f = AT(p.f);
+  m.c_as = AT(p.c_as);
+  m.c_b = AT(p.c_b);
+  m.inv_c_as = AT(1.0 / p.c_as);
+  m.inv_c_b = AT(1.0 / p.c_b);
+  m.pa = AT((p.c_as - 1.0) / p.c_as);
+  m.qa = AT((p.c_as + 1.0) / p.c_as);
+  m.pb = AT((p.c_b - 1.0) / p.c_b);
+  m.qb = AT((p.c_b + 1.0) / p.c_b);
+  m.T_cap0 = AT(p.T_as_start + p.T_reg);
+  m.inv_T_reg = AT(1.0 / p.T_reg);
+  m.init_exit = AT(p.init_exit);
+  m.init_exit_floor = AT(p.init_exit_floor);
+  m.T_thr = AT(p.T_thr);
   m.martensite_literal = p.martensite_literal ? 1 : 0;
   m.init_ba_steps = p.init_ba_steps ? 1 : 0;
   return m;
@@ -201,7 +212,8 @@ int check_params(const ms_params& p) {
         p.init_exit_floor >= 0))
     return fail(MS_ERR_INVALID_ARG, "init_exit and init_exit_floor must be >= 0");
   if (!std::isfinite(p.T_thr)) return fail(MS_ERR_INVALID_ARG, "T_thr must be finite");
-  if (p.precision != MS_F32 && p.precision != MS_F64ACC && p.precision != MS_KAHAN)
+  if (p.precision != MS_F32 && p.precision != MS_F64ACC && p.precision != MS_KAHAN &&
+      p.precision != MS_F64)
     return fail(MS_ERR_INVALID_ARG, "unknown precision %d", p.precision);
   if (p.steps_per_launch < 1 || p.steps_per_launch > ms::MAX_LEVELS - 1)
     return fail(MS_ERR_INVALID_ARG, "steps_per_launch must be in [1, %d]", ms::MAX_LEVELS - 1);
@@ -283,7 +295,7 @@ int build_layout(ms_ctx* c) {
   {
     const int bt = block_threads(c);
     const int per_sm = with_ft(c, [&](auto tag) {
-      return ms::track_blocks_per_sm<typename decltype(tag)::type>(bt);
+      return ms::track_blocks_per_sm<typename decltype(tag)::at, typename decltype(tag)::type>(bt);
     });
     const int64_t need = (tiles + bt / 32 - 1) / (bt / 32);
     c->track_grid = int(std::min<int64_t>(int64_t(per_sm) * c->sm_count, need));
@@ -421,11 +433,14 @@ int set_sources(ms_ctx* c, const ms_heat_source* src) {
 int ensure_table(ms_ctx* c, int n_levels) {
   int rc;
   const size_t ns = c->specs_h.size();
-  if (ns * size_t(n_levels) > c->levels_cap || ns * size_t(n_levels) * size_t(c->slots) > c->entries_cap)
-    drop_graphs(c);
-  if ((rc = grow(&c->levels_d, &c->levels_cap, ns * size_t(n_levels))) != MS_OK) return rc;
-  if ((rc = grow(&c->entries_d, &c->entries_cap, ns * size_t(n_levels) * size_t(c->slots))) != MS_OK)
-    return rc;
+  const bool f64 = c->prm.precision == MS_F64;
+  const size_t lb = ns * size_t(n_levels) *
+                    (f64 ? sizeof(ms::SrcLevelT<double>) : sizeof(ms::SrcLevelT<float>));
+  const size_t eb = ns * size_t(n_levels) * size_t(c->slots) *
+                    (f64 ? sizeof(ms::SrcEntryT<double>) : sizeof(ms::SrcEntryT<float>));
+  if (lb > c->levels_cap || eb > c->entries_cap) drop_graphs(c);
+  if ((rc = grow(reinterpret_cast<char**>(&c->levels_d), &c->levels_cap, lb)) != MS_OK) return rc;
+  if ((rc = grow(reinterpret_cast<char**>(&c->entries_d), &c->entries_cap, eb)) != MS_OK) return rc;
   return MS_OK;
 }
 
@@ -442,7 +457,10 @@ int launch_table(ms_ctx* c, int64_t level0, int n_levels) {
   ta.dt = c->dt;
   ta.levels = c->levels_d;
   ta.entries = c->entries_d;
-  MS_CUDA(ms::launch_src_table(ta, c->work_d, c->stream));
+  if (c->prm.precision == MS_F64)
+    MS_CUDA(ms::launch_src_table<double>(ta, c->work_d, c->stream));
+  else
+    MS_CUDA(ms::launch_src_table<float>(ta, c->work_d, c->stream));
   c->st.launches++;
   return MS_OK;
 }
@@ -451,7 +469,7 @@ double level_time(const ms_ctx* c, int64_t level) {
   return c->t_base + double(level - c->n_base) * c->dt;
 }
 
-template <typename FT>
+template <typename AT, typename FT>
 int run_track_impl(ms_ctx* c, int64_t n_steps) {
   const int S = c->prm.steps_per_launch;
   const bool use_list = c->prm.T_thr > 0.0;
@@ -477,8 +495,8 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
       MS_CUDA(ms::launch_active(aa, c->stream));
       c->st.launches++;
     }
-    ms::TrackArgs<FT> a{};
-    a.m = c->mc;
+    ms::TrackArgs<AT, FT> a{};
+    a.m = consts<AT>(c);
     a.specs = c->specs_d;
     a.tile_spec = c->tile_spec_d;
     a.tile_list = use_list ? c->tile_list_d : nullptr;
@@ -486,16 +504,16 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.n_tiles = int32_t(c->n_tiles);
     a.n_levels = steps + 1;
     a.slots = c->slots;
-    a.dt = float(c->dt);
-    a.levels = c->levels_d;
-    a.entries = c->entries_d;
+    a.dt = AT(c->dt);
+    a.levels = static_cast<const ms::SrcLevelT<AT>*>(c->levels_d);
+    a.entries = static_cast<const ms::SrcEntryT<AT>*>(c->entries_d);
     a.xas = (FT*)c->xas_d;
     a.xam = (FT*)c->xam_d;
     a.aux = c->aux_d;
     a.tile_tsat = c->tile_tsat_d;
     a.err = c->err_d;
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
-    MS_CUDA(ms::launch_track<FT>(a, block_threads(c), c->track_grid, c->stream));
+    MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream));
     if ((rc = kernel_event(c, true)) != MS_OK) return rc;
     c->st.launches++;
     c->step_n += steps;
@@ -507,12 +525,12 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
   return MS_OK;
 }
 
-template <typename FT>
+template <typename AT, typename FT>
 int step_impl(ms_ctx* c, const float* T0, const float* T1) {
-  ms::StepArgs<FT> a{};
-  a.m = c->mc;
+  ms::StepArgs<AT, FT> a{};
+  a.m = consts<AT>(c);
   a.n = c->n_points;
-  a.dt = float(c->dt);
+  a.dt = AT(c->dt);
   a.T0 = T0;
   a.T1 = T1;
   a.xas = (FT*)c->xas_d;
@@ -521,7 +539,7 @@ int step_impl(ms_ctx* c, const float* T0, const float* T1) {
   a.err = c->err_d;
   int rc;
   if ((rc = kernel_event(c, false)) != MS_OK) return rc;
-  MS_CUDA(ms::launch_step_ext<FT>(a, block_threads(c), c->stream));
+  MS_CUDA(ms::launch_step_ext<AT, FT>(a, block_threads(c), c->stream));
   if ((rc = kernel_event(c, true)) != MS_OK) return rc;
   c->st.launches++;
   return MS_OK;
@@ -559,7 +577,7 @@ int run_track_graph(ms_ctx* c, int64_t n_steps) {
     MS_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     c->capturing = true;
     c->kev_used = 0;
-    rc = with_ft(c, [&](auto tag) { return run_track_impl<typename decltype(tag)::type>(c, n_steps); });
+    rc = with_ft(c, [&](auto tag) { return run_track_impl<typename decltype(tag)::at, typename decltype(tag)::type>(c, n_steps); });
     c->capturing = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
@@ -607,7 +625,10 @@ int run_track_graph(ms_ctx* c, int64_t n_steps) {
 // Shared with other translation units (declared in ms_internal.h).
 namespace ms {
 int validate_params(const ms_params& p) { return check_params(p); }
-ModelConst model_const(const ms_params& p) { return make_const(p); }
+template <typename AT>
+ModelConstT<AT> model_const(const ms_params& p) { return make_const<AT>(p); }
+template ModelConstT<float> model_const<float>(const ms_params&);
+template ModelConstT<double> model_const<double>(const ms_params&);
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace ms
 
@@ -683,7 +704,8 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
   ms_ctx* c = new (std::nothrow) ms_ctx();
   if (!c) return fail(MS_ERR_OOM, "host allocation failed");
   c->prm = *p;
-  c->mc = make_const(*p);
+  c->mc = make_const<float>(*p);
+  c->mcd = make_const<double>(*p);
   c->fbytes = p->precision == MS_F32 ? 4 : 8;  // MS_KAHAN stores two floats per fraction
   c->n_points = n_points;
   auto bail = [&](int code) { ms_destroy(c); return code; };
@@ -716,6 +738,7 @@ void ms_destroy(ms_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   free_layout(c);
+  cudaFree(c->idx_d);
   cudaFree(c->err_d);
   cudaFree(c->work_d);
   cudaFree(c->tracks_d);
@@ -748,8 +771,14 @@ int ms_set_points(ms_ctx* c, const ms_grid* grids, int32_t n_specimens) {
       if (!std::isfinite(g.origin[a]) || !std::isfinite(g.spacing[a]))
         return fail(MS_ERR_INVALID_ARG, "grid %d: non-finite origin or spacing", s);
     SpecDev d{};
-    d.ox = float(g.origin[0]); d.oy = float(g.origin[1]); d.oz = float(g.origin[2]);
-    d.dx = float(g.spacing[0]); d.dy = float(g.spacing[1]); d.dz = float(g.spacing[2]);
+    d.ox = double(float(g.origin[0])); d.oy = double(float(g.origin[1]));
+    d.oz = double(float(g.origin[2]));
+    d.dx = double(float(g.spacing[0])); d.dy = double(float(g.spacing[1]));
+    d.dz = double(float(g.spacing[2]));
+    if (c->prm.precision == MS_F64) {  // full-FP64 coordinates
+      d.ox = g.origin[0]; d.oy = g.origin[1]; d.oz = g.origin[2];
+      d.dx = g.spacing[0]; d.dy = g.spacing[1]; d.dz = g.spacing[2];
+    }
     d.nx = g.dims[0]; d.ny = g.dims[1]; d.nz = g.dims[2];
     d.n = int64_t(g.dims[0]) * g.dims[1] * g.dims[2];
     d.n_layers = 1;
@@ -761,6 +790,46 @@ int ms_set_points(ms_ctx* c, const ms_grid* grids, int32_t n_specimens) {
                 (long long)c->n_points);
   MS_CUDA(cudaStreamSynchronize(c->stream));
   c->specs_h = specs;
+  c->has_grid = true;
+  return build_layout(c);
+}
+
+
+int ms_set_points_subset(ms_ctx* c, const ms_grid* grid, const int64_t* idx, int64_t n) {
+  if (!c || !grid || !idx) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  if (n != c->n_points) return fail(MS_ERR_INVALID_ARG, "subset has %lld points, context %lld",
+                                    (long long)n, (long long)c->n_points);
+  int rc;
+  if ((rc = ms_set_points(c, grid, 1)) == MS_ERR_INVALID_ARG && grid->dims[0] >= 1) {
+    // the grid holds more points than the subset: set it up by hand
+  } else if (rc != MS_OK && rc != MS_ERR_INVALID_ARG) {
+    return rc;
+  }
+  const int64_t total = int64_t(grid->dims[0]) * grid->dims[1] * grid->dims[2];
+  if (grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1)
+    return fail(MS_ERR_INVALID_ARG, "grid dims must be >= 1");
+  for (int64_t i = 0; i < n; ++i)
+    if (idx[i] < 0 || idx[i] >= total)
+      return fail(MS_ERR_INVALID_ARG, "subset index %lld out of the grid", (long long)idx[i]);
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  cudaFree(c->idx_d);
+  c->idx_d = nullptr;
+  MS_CUDA(cudaMalloc(&c->idx_d, size_t(n) * sizeof(int64_t)));
+  MS_CUDA(cudaMemcpy(c->idx_d, idx, size_t(n) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  SpecDev d{};
+  d.ox = double(float(grid->origin[0])); d.oy = double(float(grid->origin[1]));
+  d.oz = double(float(grid->origin[2]));
+  d.dx = double(float(grid->spacing[0])); d.dy = double(float(grid->spacing[1]));
+  d.dz = double(float(grid->spacing[2]));
+  if (c->prm.precision == MS_F64) {
+    d.ox = grid->origin[0]; d.oy = grid->origin[1]; d.oz = grid->origin[2];
+    d.dx = grid->spacing[0]; d.dy = grid->spacing[1]; d.dz = grid->spacing[2];
+  }
+  d.nx = grid->dims[0]; d.ny = grid->dims[1]; d.nz = grid->dims[2];
+  d.n = n;
+  d.n_layers = 1;
+  d.idx = c->idx_d;
+  c->specs_h.assign(1, d);
   c->has_grid = true;
   return build_layout(c);
 }
@@ -844,7 +913,7 @@ int ms_step(ms_ctx* c, const float* T_prev, const float* T_new, double dt, int32
   }
   set_dt(c, dt);
   MS_CUDA(cudaEventRecord(c->ev0, c->stream));
-  int rc = with_ft(c, [&](auto tag) { return step_impl<typename decltype(tag)::type>(c, t0, t1); });
+  int rc = with_ft(c, [&](auto tag) { return step_impl<typename decltype(tag)::at, typename decltype(tag)::type>(c, t0, t1); });
   if (rc != MS_OK) return rc;
   MS_CUDA(cudaEventRecord(c->ev1, c->stream));
   c->timed = true;
@@ -866,7 +935,7 @@ int ms_run_track(ms_ctx* c, const ms_heat_source* src, int64_t n_steps, double d
   c->T_last = nullptr;
   if ((c->prm.flags & MS_FLAG_GRAPH) && n_steps > 0) return run_track_graph(c, n_steps);
   MS_CUDA(cudaEventRecord(c->ev0, c->stream));
-  rc = with_ft(c, [&](auto tag) { return run_track_impl<typename decltype(tag)::type>(c, n_steps); });
+  rc = with_ft(c, [&](auto tag) { return run_track_impl<typename decltype(tag)::at, typename decltype(tag)::type>(c, n_steps); });
   if (rc != MS_OK) return rc;
   MS_CUDA(cudaEventRecord(c->ev1, c->stream));
   c->timed = true;
@@ -890,10 +959,12 @@ int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double*
     }
     MS_CUDA(with_ft(c, [&](auto tag) {
         using FT = typename decltype(tag)::type;
-        return ms::launch_fractions<FT>(c->mc, c->specs_d, c->tile_spec_d, c->n_tiles,
-                                          (const FT*)c->xas_d, (const FT*)c->xam_d, T,
-                                          c->levels_d, c->entries_d, c->slots, d + 2 * n,
-                                          d + 3 * n, c->stream);
+        using AT = typename decltype(tag)::at;
+        return ms::launch_fractions<AT, FT>(
+            consts<AT>(c), c->specs_d, c->tile_spec_d, c->n_tiles, (const FT*)c->xas_d,
+            (const FT*)c->xam_d, T, static_cast<const ms::SrcLevelT<AT>*>(c->levels_d),
+            static_cast<const ms::SrcEntryT<AT>*>(c->entries_d), c->slots, d + 2 * n, d + 3 * n,
+            nullptr, c->stream);
       }));
   }
   MS_CUDA(with_ft(c, [&](auto tag) {
@@ -920,6 +991,33 @@ int ms_get_aux(ms_ctx* c, double* aux) {
                                         nullptr, nullptr, d, c->stream);
     }));
   MS_CUDA(cudaMemcpyAsync(aux, d, size_t(c->n_points) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);
+}
+
+int ms_get_temperature(ms_ctx* c, double* T) {
+  if (!c || !T) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  const int64_t n = c->n_points;
+  double* d = c->stage_d;
+  int rc;
+  const float* Tin = nullptr;
+  if (c->T_last) {
+    Tin = c->T_last;
+  } else if (c->has_grid && c->src_valid) {
+    if ((rc = ensure_table(c, 1)) != MS_OK) return rc;
+    if ((rc = launch_table(c, c->step_n, 1)) != MS_OK) return rc;
+  } else {
+    return fail(MS_ERR_STATE, "no temperature known yet");
+  }
+  MS_CUDA(with_ft(c, [&](auto tag) {
+    using AT = typename decltype(tag)::at;
+    using FT = typename decltype(tag)::type;
+    return ms::launch_fractions<AT, FT>(
+        consts<AT>(c), c->specs_d, c->tile_spec_d, c->n_tiles, (const FT*)c->xas_d,
+        (const FT*)c->xam_d, Tin, static_cast<const ms::SrcLevelT<AT>*>(c->levels_d),
+        static_cast<const ms::SrcEntryT<AT>*>(c->entries_d), c->slots, nullptr, nullptr, d,
+        c->stream);
+  }));
+  MS_CUDA(cudaMemcpyAsync(T, d, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return check_device_error(c);
 }
 

@@ -20,8 +20,9 @@ constexpr int DEVERR_TIMEOUT = 2;
 
 // One specimen as the kernels see it.
 struct SpecDev {
-  float ox, oy, oz;        // grid origin
-  float dx, dy, dz;        // grid spacing
+  double ox, oy, oz;       // grid origin
+  double dx, dy, dz;       // grid spacing
+  const int64_t* idx;      // optional: the specimen's points are these grid indices
   int32_t nx, ny, nz;
   int32_t n_tracks;        // tracks of this specimen (all layers)
   int64_t n;               // points
@@ -59,8 +60,8 @@ struct TableArgs {
   int64_t n0;              // first level (steps since the time base)
   double t_base;           // time of level 0 of the time base
   double dt;
-  SrcLevel* levels;        // [n_specs][n_levels]
-  SrcEntry* entries;       // [n_specs][n_levels][slots]
+  void* levels;            // SrcLevelT<AT> [n_specs][n_levels]
+  void* entries;           // SrcEntryT<AT> [n_specs][n_levels][slots]
 };
 
 // Work counters of one launch of k_track (device memory, reset per launch).
@@ -71,9 +72,9 @@ struct WorkCounters {
 };
 
 // Arguments of the run-track kernel (persistent warps pull 128-point tiles).
-template <typename FT>
+template <typename AT, typename FT>
 struct TrackArgs {
-  ModelConst m;
+  ModelConstT<AT> m;
   const SpecDev* specs;
   const int32_t* tile_spec;    // tile -> specimen
   const int32_t* tile_list;    // active tiles (nullptr: every tile 0 .. n_tiles-1)
@@ -81,9 +82,9 @@ struct TrackArgs {
   int32_t n_tiles;             // tiles in the layout
   int32_t n_levels;            // steps + 1
   int32_t slots;
-  float dt;
-  const SrcLevel* levels;
-  const SrcEntry* entries;
+  AT dt;
+  const SrcLevelT<AT>* levels;
+  const SrcEntryT<AT>* entries;
   FT* xas;
   FT* xam;
   float* aux;
@@ -109,11 +110,11 @@ struct ActiveArgs {
 };
 
 // Arguments of the external-temperature step kernel.
-template <typename FT>
+template <typename AT, typename FT>
 struct StepArgs {
-  ModelConst m;
+  ModelConstT<AT> m;
   int64_t n;
-  float dt;
+  AT dt;
   const float* T0;
   const float* T1;
   FT* xas;
@@ -127,20 +128,22 @@ struct StepArgs {
 // the message for ms_last_error; record_error records a message and returns
 // the code.
 int validate_params(const ms_params& p);
-ModelConst model_const(const ms_params& p);
+template <typename AT>
+ModelConstT<AT> model_const(const ms_params& p);
 int record_error(int code, const char* msg);
 
 // Launchers (ms_kernels.cu).  All asynchronous on `stream`.
+template <typename AT>
 cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream);
 cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream);
-template <typename FT>
-cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, int grid_blocks,
+template <typename AT, typename FT>
+cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
                          cudaStream_t stream);
-template <typename FT>
+template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads);
-template <typename FT>
-cudaError_t launch_step_ext(const StepArgs<FT>& a, int block_threads, cudaStream_t stream);
+template <typename AT, typename FT>
+cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream);
 
 // Natural-order doubles <-> padded device state (one thread per point).
 // xas == nullptr on set fills every point with (xas0, xam0, no initiation).
@@ -154,12 +157,14 @@ cudaError_t launch_get_state(const SpecDev* specs, const int32_t* tile_spec, int
                              const FT* dxas, const FT* dxam, const float* daux,
                              double* xas, double* xam, double* aux, cudaStream_t stream);
 
-// X_beta and X_liq in natural order.  Temperatures come either from a
-// natural-order array T (external mode) or from level 0 of a source table.
-template <typename FT>
-cudaError_t launch_fractions(const ModelConst& m, const SpecDev* specs, const int32_t* tile_spec,
-                             int64_t n_tiles, const FT* dxas, const FT* dxam, const float* T,
-                             const SrcLevel* levels, const SrcEntry* entries, int32_t slots,
-                             double* xbeta, double* xliq, cudaStream_t stream);
+// X_beta and X_liq (and optionally T) in natural order.  Temperatures come
+// either from a natural-order array T (external mode) or from level 0 of a
+// source table.
+template <typename AT, typename FT>
+cudaError_t launch_fractions(const ModelConstT<AT>& m, const SpecDev* specs,
+                             const int32_t* tile_spec, int64_t n_tiles, const FT* dxas,
+                             const FT* dxam, const float* T, const SrcLevelT<AT>* levels,
+                             const SrcEntryT<AT>* entries, int32_t slots, double* xbeta,
+                             double* xliq, double* T_out, cudaStream_t stream);
 
 }  // namespace ms

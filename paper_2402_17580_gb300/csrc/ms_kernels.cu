@@ -1,17 +1,23 @@
 // sm_103a kernels of the microstructure point solver.
 //
 //  k_src_table   per (specimen, time level): positions and constants of the
-//                started moving sources (FP64 -> FP32), so the hot kernel
-//                reads one 32-byte entry per source and level.
-//  k_track       the hot path of ms_run_track: one warp per 128-point tile,
-//                4 points per thread (128-bit SoA loads), S steps per state
-//                load; the temperature of every point and level is computed
-//                in the kernel from the source table, so only the phase state
-//                touches memory.  Warp vote skips the model when every lane is
-//                cold and saturated (active set, reading A9).
+//                started moving sources (computed in FP64, stored in the
+//                arithmetic type), so the hot kernel reads one entry per
+//                source and level.
+//  k_active      active-set compaction: tiles that may exceed T_thr or whose
+//                martensite is not saturated (reading A9), by a ballot.
+//  k_track       the hot path of ms_run_track: persistent warps pull 128-point
+//                tiles, 4 points per thread (128-bit SoA loads), S steps per
+//                state load; the temperature of every point and level is
+//                computed in the kernel from the source table, so only the
+//                phase state touches memory.  A warp vote skips the model
+//                when every lane is cold and saturated.
 //  k_step_ext    ms_step: one explicit step with temperatures read from memory
 //                (Algorithm 1 with the local step of Algorithm 2).
 //  k_set_state / k_get_state / k_fractions   natural order <-> padded layout.
+//
+// Kernels are templated on the arithmetic type AT (float on the SFU, double
+// for the full-FP64 path) and the fraction type FT (float, double, KF).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,7 +32,22 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kLog2e = 1.4426950408889634074;
 
+// Coordinates of local point li of a specimen (a grid point, or the grid
+// point idx[li] for a subset specimen).
+template <typename AT>
+__device__ __forceinline__ void point_coords(const SpecDev& sp, int64_t li, AT& x, AT& y, AT& z) {
+  const int64_t ii = sp.idx ? sp.idx[li] : li;
+  const int64_t r = ii / sp.nx;
+  const int64_t i = ii - r * sp.nx;
+  const int64_t k = r / sp.ny;
+  const int64_t j = r - k * sp.ny;
+  x = AT(sp.ox) + AT(i) * AT(sp.dx);
+  y = AT(sp.oy) + AT(j) * AT(sp.dy);
+  z = AT(sp.oz) + AT(k) * AT(sp.dz);
+}
+
 // --------------------------------------------------------- source table
+template <typename AT>
 __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id == 0 && work) {
@@ -50,21 +71,8 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   }
   const double C0 = sp.A / (2.0 * kPi * sp.k) * scale;
   const double cv = -kLog2e / (2.0 * sp.alpha);
-  SrcEntry* out = a.entries + (int64_t(s) * a.n_levels + lv) * a.slots;
-  // do all started sources of the level move along one axis (up to sign)?
-  double u0x = 0.0, u0y = 0.0;
-  bool axis = true, first = true;
-  for (int j = 0; j < sp.n_tracks; ++j) {
-    const TrackDev tr = a.tracks[sp.track0 + j];
-    if (tr.layer != l || tl < tr.t_start) continue;
-    if (first) {
-      u0x = tr.ux;
-      u0y = tr.uy;
-      first = false;
-    } else if (fabs(tr.ux * u0y - tr.uy * u0x) > 1e-12) {
-      axis = false;
-    }
-  }
+  SrcEntryT<AT>* out =
+      static_cast<SrcEntryT<AT>*>(a.entries) + (int64_t(s) * a.n_levels + lv) * a.slots;
   int n = 0;
   for (int j = 0; j < sp.n_tracks && n < a.slots; ++j) {
     const TrackDev tr = a.tracks[sp.track0 + j];
@@ -72,129 +80,77 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
     const double travel = tr.v * (tl - tr.t_start);
     const double sx = tr.x0 + tr.ux * travel, sy = tr.y0 + tr.uy * travel;
     const double C = C0 * tr.P;
-    SrcEntry e;
-    if (axis) {
-      const double sg = (tr.ux * u0x + tr.uy * u0y) >= 0.0 ? 1.0 : -1.0;
-      e.s_xi = float(sg * (sx * u0x + sy * u0y));
-      e.s_pp = float(sx * u0y - sy * u0x);
-      e.ux = float(sg);
-      e.uy = 0.0f;
-    } else {
-      e.s_xi = float(sx * tr.ux + sy * tr.uy);
-      e.s_pp = float(sx * tr.uy - sy * tr.ux);
-      e.ux = float(tr.ux);
-      e.uy = float(tr.uy);
-    }
-    e.cR = float(cv * tr.v);
-    e.lC = C > 0.0 ? float(log2(C)) : -INFINITY;
-    e.pad0 = e.pad1 = 0.0f;
+    SrcEntryT<AT> e;
+    e.s_xi = AT(sx * tr.ux + sy * tr.uy);
+    e.s_pp = AT(sx * tr.uy - sy * tr.ux);
+    e.ux = AT(tr.ux);
+    e.uy = AT(tr.uy);
+    e.cR = AT(cv * tr.v);
+    e.lC = C > 0.0 ? AT(log2(C)) : AT(-INFINITY);
+    e.pad0 = e.pad1 = AT(0);
     out[n++] = e;
   }
-  SrcLevel r;
+  SrcLevelT<AT> r;
   r.n = n;
-  r.axis = axis ? 1 : 0;
-  r.z_surf = float(L.z);
-  r.T0 = sp.T0;
-  r.T_max = sp.T_max;
-  r.u0x = float(u0x);
-  r.u0y = float(u0y);
-  r.pad = 0.0f;
-  a.levels[id] = r;
+  r.pad = 0;
+  r.z_surf = AT(L.z);
+  r.T0 = AT(sp.T0);
+  r.T_max = AT(sp.T_max);
+  static_cast<SrcLevelT<AT>*>(a.levels)[id] = r;
 }
 
-__device__ __forceinline__ SrcEntry load_entry(const SrcEntry* p) {
+__device__ __forceinline__ SrcEntryT<float> load_entry(const SrcEntryT<float>* p) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
   const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
-  SrcEntry e;
+  SrcEntryT<float> e;
   e.s_xi = a.x; e.s_pp = a.y; e.ux = a.z; e.uy = a.w;
   e.cR = b.x; e.lC = b.y; e.pad0 = b.z; e.pad1 = b.w;
   return e;
 }
-
-__device__ __forceinline__ float depth2(float pz, float z_surf) {
-  const float dz = pz - z_surf;
-  return fmaf(dz, dz, 1e-30f);
+__device__ __forceinline__ SrcEntryT<double> load_entry(const SrcEntryT<double>* p) {
+  return *p;
 }
 
-// Source-term variants (tuning builds): MS_RCP_MODE 1 alternates the SFU and
-// the FMA-pipe reciprocal between consecutive sources, 0 keeps every
-// reciprocal on the SFU; MS_AXIS 1 takes the common-axis frame when a level
-// has one.  Measured on the 256x256x64 block (S = 256): 0/0 gives 1.033e11
-// point-updates/s, 0/1 0.945e11, 1/0 0.942e11, 1/1 0.875e11, so both stay
-// off by default.
-#ifndef MS_RCP_MODE
-#define MS_RCP_MODE 0
-#endif
-#ifndef MS_AXIS
-#define MS_AXIS 0
-#endif
-constexpr bool kOddFmaRcp = MS_RCP_MODE == 1;
+template <typename AT>
+__device__ __forceinline__ AT depth2(AT pz, AT z_surf) {
+  const AT dz = pz - z_surf;
+  return Fn<AT>::fma(dz, dz, AT(1e-30));
+}
 
-// Temperatures of 4 points at one level (4 independent chains per source).
-// With kOddFmaRcp the sources alternate between the SFU reciprocal (even j)
-// and the FMA-pipe one (odd j); the sum runs in source order.
-__device__ __forceinline__ void temps4(const SrcLevel& L, const SrcEntry* en, const float* px,
-                                       const float* py, const float* pz, float* T) {
-  float acc[4] = {0.f, 0.f, 0.f, 0.f}, dz2[4];
+// Temperatures of 4 points at one level: two sources per iteration, so each
+// thread runs 8 independent chains; the sum runs in source order.
+template <typename AT>
+__device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en,
+                                       const AT* px, const AT* py, const AT* pz, AT* T) {
+  AT acc[4] = {AT(0), AT(0), AT(0), AT(0)}, dz2[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) dz2[q] = depth2(pz[q], L.z_surf);
-  if (MS_AXIS && L.axis) {
-    float pa[4], pb[4];
+  for (int q = 0; q < 4; ++q) dz2[q] = depth2<AT>(pz[q], L.z_surf);
+  int j = 0;
+  for (; j + 1 < L.n; j += 2) {
+    const SrcEntryT<AT> e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      pa[q] = fmaf(px[q], L.u0x, py[q] * L.u0y);
-      pb[q] = fmaf(px[q], L.u0y, -py[q] * L.u0x);
-    }
-    int j = 0;
-    for (; j + 1 < L.n; j += 2) {
-      const SrcEntry e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[q] += source_term_axis<false>(e0, pa[q], pb[q], dz2[q]);
-        acc[q] += source_term_axis<kOddFmaRcp>(e1, pa[q], pb[q], dz2[q]);
-      }
-    }
-    if (j < L.n) {
-      const SrcEntry e0 = load_entry(en + j);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += source_term_axis<false>(e0, pa[q], pb[q], dz2[q]);
-    }
-  } else {
-    int j = 0;
-    for (; j + 1 < L.n; j += 2) {
-      const SrcEntry e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[q] += source_term<false>(e0, px[q], py[q], dz2[q]);
-        acc[q] += source_term<kOddFmaRcp>(e1, px[q], py[q], dz2[q]);
-      }
-    }
-    if (j < L.n) {
-      const SrcEntry e0 = load_entry(en + j);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += source_term<false>(e0, px[q], py[q], dz2[q]);
+      acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
+      acc[q] += source_term<AT>(e1, px[q], py[q], dz2[q]);
     }
   }
+  if (j < L.n) {
+    const SrcEntryT<AT> e0 = load_entry(en + j);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) T[q] = fminf(L.T0 + acc[q], L.T_max);
+    for (int q = 0; q < 4; ++q) acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) T[q] = Fn<AT>::min(L.T0 + acc[q], L.T_max);
 }
 
 // Temperature of one point; the same arithmetic and order as temps4.
-__device__ __forceinline__ float temp1(const SrcLevel& L, const SrcEntry* en, float px, float py,
-                                       float pz) {
-  float acc = 0.f;
-  const float dz2 = depth2(pz, L.z_surf);
-  if (MS_AXIS && L.axis) {
-    const float pa = fmaf(px, L.u0x, py * L.u0y), pb = fmaf(px, L.u0y, -py * L.u0x);
-    for (int j = 0; j < L.n; ++j)
-      acc += (j & 1) ? source_term_axis<kOddFmaRcp>(load_entry(en + j), pa, pb, dz2)
-                     : source_term_axis<false>(load_entry(en + j), pa, pb, dz2);
-  } else {
-    for (int j = 0; j < L.n; ++j)
-      acc += (j & 1) ? source_term<kOddFmaRcp>(load_entry(en + j), px, py, dz2)
-                     : source_term<false>(load_entry(en + j), px, py, dz2);
-  }
-  return fminf(L.T0 + acc, L.T_max);
+template <typename AT>
+__device__ __forceinline__ AT temp1(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en, AT px, AT py,
+                                    AT pz) {
+  AT acc = AT(0);
+  const AT dz2 = depth2<AT>(pz, L.z_surf);
+  for (int j = 0; j < L.n; ++j) acc += source_term<AT>(load_entry(en + j), px, py, dz2);
+  return Fn<AT>::min(L.T0 + acc, L.T_max);
 }
 
 // ------------------------------------------------------------ active set
@@ -204,31 +160,34 @@ __device__ __forceinline__ float temp1(const SrcLevel& L, const SrcEntry* en, fl
 // the tile's bounding box and the box of the source's path in the window and
 // xi_min >= 0 the smallest along-track offset of a tile point ahead of the
 // path (R + xi >= 2 xi ahead of the source; the factor is 1 otherwise).  The
-// interlayer scale is <= 1.
+// interlayer scale is <= 1.  Subset specimens use the whole grid's box.
 __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   const int s = a.tile_spec[t];
   const SpecDev& sp = a.specs[s];
   const float tsat = a.tile_tsat[t];
   if (!(tsat <= sp.T0)) return true;  // martensite not saturated at T0, or initiation running
   const double tla = a.t_a - sp.t_offset, tlb = a.t_b - sp.t_offset;
-  const int64_t li0 = int64_t(t - sp.tile0) * TILE;
-  const int64_t li1 = min(li0 + TILE - 1, sp.n - 1);
-  const int64_t nxy = int64_t(sp.nx) * sp.ny;
-  const int64_t k0 = li0 / nxy, k1 = li1 / nxy;
-  const int64_t j0 = (li0 - k0 * nxy) / sp.nx, j1 = (li1 - k1 * nxy) / sp.nx;
-  const int64_t i0 = li0 - k0 * nxy - j0 * sp.nx, i1 = li1 - k1 * nxy - j1 * sp.nx;
-  int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1;
-  if (k0 == k1) {
-    jlo = j0;
-    jhi = j1;
-    if (j0 == j1) {
-      ilo = i0;
-      ihi = i1;
+  int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1, k0 = 0, k1 = sp.nz - 1;
+  if (!sp.idx) {
+    const int64_t li0 = int64_t(t - sp.tile0) * TILE;
+    const int64_t li1 = min(li0 + TILE - 1, sp.n - 1);
+    const int64_t nxy = int64_t(sp.nx) * sp.ny;
+    k0 = li0 / nxy;
+    k1 = li1 / nxy;
+    const int64_t j0 = (li0 - k0 * nxy) / sp.nx, j1 = (li1 - k1 * nxy) / sp.nx;
+    const int64_t i0 = li0 - k0 * nxy - j0 * sp.nx, i1 = li1 - k1 * nxy - j1 * sp.nx;
+    if (k0 == k1) {
+      jlo = j0;
+      jhi = j1;
+      if (j0 == j1) {
+        ilo = i0;
+        ihi = i1;
+      }
     }
   }
-  const double xa = double(sp.ox) + double(ilo) * sp.dx, xb = double(sp.ox) + double(ihi) * sp.dx;
-  const double ya = double(sp.oy) + double(jlo) * sp.dy, yb = double(sp.oy) + double(jhi) * sp.dy;
-  const double za = double(sp.oz) + double(k0) * sp.dz, zb = double(sp.oz) + double(k1) * sp.dz;
+  const double xa = sp.ox + double(ilo) * sp.dx, xb = sp.ox + double(ihi) * sp.dx;
+  const double ya = sp.oy + double(jlo) * sp.dy, yb = sp.oy + double(jhi) * sp.dy;
+  const double za = sp.oz + double(k0) * sp.dz, zb = sp.oz + double(k1) * sp.dz;
   const double bx0 = fmin(xa, xb), bx1 = fmax(xa, xb), by0 = fmin(ya, yb), by1 = fmax(ya, yb);
   const double bz1 = fmax(za, zb);
   int la = 0, lb = 0;
@@ -285,14 +244,14 @@ __global__ void k_fill_f32(float* p, int64_t n, float v) {
 // Highest T1 at which martensite formation would still change this point
 // (formation is a no-op for T1 >= the returned value); +inf while an App. A
 // initiation runs (never skip), -inf if formation can never act.
-template <typename FT>
-__device__ __forceinline__ float point_tsat(const ModelConst& m, FT xas, FT xam, float aux) {
+template <typename AT, typename FT>
+__device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT xam, float aux) {
   if (aux != 0.0f) return INFINITY;
   const FT q = FT(0.9) - xas;
   if (!(q > FT(0))) return -INFINITY;
   const float r = float(xam * FT(0.9) / q);
   if (r >= XMAX) return -INFINITY;
-  return m.T_am_start + sfu_lg2(1.0f - r) / m.kam_l2;
+  return float(m.T_am_start) + sfu_lg2(1.0f - r) / float(m.kam_l2);
 }
 
 // ---------------------------------------------------------- state access
@@ -320,7 +279,6 @@ struct Vec4<double> {
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
   }
 };
-
 template <>
 struct Vec4<KF> {
   static __device__ __forceinline__ void load(const KF* p, KF* v) {
@@ -345,27 +303,20 @@ __device__ __forceinline__ bool finite_pair(FT a, FT b) {
 
 // ------------------------------------------------------------ hot kernel
 // One 128-point tile for the launch's S steps (4 points per lane).
-template <typename FT>
-__device__ __forceinline__ void track_tile(const TrackArgs<FT>& a, int tile, int lane) {
+template <typename AT, typename FT>
+__device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
   const int64_t g0 = sp.pad_off + local0;
 
-  float px[4], py[4], pz[4];
+  AT px[4], py[4], pz[4];
   bool valid[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int64_t li = local0 + q;
     valid[q] = li < sp.n;
-    const int64_t ii = valid[q] ? li : 0;
-    const int64_t r = ii / sp.nx;
-    const int64_t i = ii - r * sp.nx;
-    const int64_t k = r / sp.ny;
-    const int64_t j = r - k * sp.ny;
-    px[q] = sp.ox + float(i) * sp.dx;
-    py[q] = sp.oy + float(j) * sp.dy;
-    pz[q] = sp.oz + float(k) * sp.dz;
+    point_coords<AT>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
   }
 
   FT xs[4], xm[4];
@@ -374,29 +325,30 @@ __device__ __forceinline__ void track_tile(const TrackArgs<FT>& a, int tile, int
   Vec4<FT>::load(a.xam + g0, xm);
   Vec4<float>::load(a.aux + g0, ax);
 
-  const SrcLevel* lv = a.levels + int64_t(s) * a.n_levels;
-  const SrcEntry* en = a.entries + int64_t(s) * a.n_levels * a.slots;
-  const float z_tol = sp.z_tol;
-  const bool skipping = a.m.T_thr > 0.0f;
+  const SrcLevelT<AT>* lv = a.levels + int64_t(s) * a.n_levels;
+  const SrcEntryT<AT>* en = a.entries + int64_t(s) * a.n_levels * a.slots;
+  const AT z_tol = AT(sp.z_tol);
+  const bool skipping = a.m.T_thr > AT(0);
 
-  float T0[4];
-  temps4(lv[0], en, px, py, pz, T0);
+  AT T0[4];
+  temps4<AT>(lv[0], en, px, py, pz, T0);
   for (int l = 1; l < a.n_levels; ++l) {
-    const SrcLevel L = lv[l];
-    float T1[4];
-    temps4(L, en + int64_t(l) * a.slots, px, py, pz, T1);
-    const float zlim = L.z_surf + z_tol;
+    const SrcLevelT<AT> L = lv[l];
+    AT T1[4];
+    temps4<AT>(L, en + int64_t(l) * a.slots, px, py, pz, T1);
+    const AT zlim = L.z_surf + z_tol;
     bool noop = true;
     if (skipping) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         noop = noop && (!valid[q] || !(pz[q] <= zlim) ||
-                        step_is_noop<FT>(a.m, T0[q], T1[q], xs[q], xm[q], ax[q]));
+                        step_is_noop<AT, FT>(a.m, T0[q], T1[q], xs[q], xm[q], ax[q]));
     }
     if (!(skipping && __all_sync(0xffffffffu, noop))) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (valid[q] && pz[q] <= zlim) point_step<FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q]);
+        if (valid[q] && pz[q] <= zlim)
+          point_step<AT, FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q]);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) T0[q] = T1[q];
@@ -410,7 +362,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<FT>& a, int tile, int
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     ok = ok && finite_pair(xs[q], xm[q]);
-    if (valid[q]) ts = fmaxf(ts, point_tsat<FT>(a.m, xs[q], xm[q], ax[q]));
+    if (valid[q]) ts = fmaxf(ts, point_tsat<AT, FT>(a.m, xs[q], xm[q], ax[q]));
   }
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
   if (a.tile_tsat) {
@@ -430,8 +382,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs<FT>& a, int tile, int
 // Persistent hot kernel: every warp pulls tiles (from the active list, or all
 // tiles) through an atomic cursor until the work runs out, so the grid is
 // sized to the resident capacity and no launch tail is left idle.
-template <typename FT>
-__global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT> a) {
+template <typename AT, typename FT>
+__global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT, FT> a) {
   const int lane = threadIdx.x & 31;
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
   unsigned long long done = 0;
@@ -440,7 +392,7 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    track_tile<FT>(a, a.tile_list ? a.tile_list[w] : w, lane);
+    track_tile<AT, FT>(a, a.tile_list ? a.tile_list[w] : w, lane);
     ++done;
   }
   if (lane == 0 && done)
@@ -448,8 +400,8 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<FT
 }
 
 // ---------------------------------------------------- external T (ms_step)
-template <typename FT>
-__global__ void __launch_bounds__(256) k_step_ext(const StepArgs<FT> a, int vec_T) {
+template <typename AT, typename FT>
+__global__ void __launch_bounds__(256) k_step_ext(const StepArgs<AT, FT> a, int vec_T) {
   const int64_t i0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
   if (i0 >= a.n) return;
   FT xs[4], xm[4];
@@ -472,7 +424,7 @@ __global__ void __launch_bounds__(256) k_step_ext(const StepArgs<FT> a, int vec_
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q)
-    if (q < cnt) point_step<FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q]);
+    if (q < cnt) point_step<AT, FT>(a.m, AT(T0[q]), AT(T1[q]), a.dt, xs[q], xm[q], ax[q]);
   Vec4<FT>::store(a.xas + i0, xs);
   Vec4<FT>::store(a.xam + i0, xm);
   Vec4<float>::store(a.aux + i0, ax);
@@ -529,32 +481,30 @@ __global__ void k_get_state(const SpecDev* specs, const int32_t* tile_spec, int6
   }
 }
 
-template <typename FT>
-__global__ void k_fractions(const ModelConst m, const SpecDev* specs, const int32_t* tile_spec,
-                            int64_t n_pad, const FT* dxas, const FT* dxam, const float* T,
-                            const SrcLevel* levels, const SrcEntry* entries, int32_t slots,
-                            double* xbeta, double* xliq) {
+template <typename AT, typename FT>
+__global__ void k_fractions(const ModelConstT<AT> m, const SpecDev* specs,
+                            const int32_t* tile_spec, int64_t n_pad, const FT* dxas,
+                            const FT* dxam, const float* T, const SrcLevelT<AT>* levels,
+                            const SrcEntryT<AT>* entries, int32_t slots, double* xbeta,
+                            double* xliq, double* T_out) {
   const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (g >= n_pad) return;
   int s;
   int64_t nat;
   if (!padded_to_natural(specs, tile_spec, g, s, nat)) return;
-  float Tp;
+  AT Tp;
   if (T) {
-    Tp = T[nat];
+    Tp = AT(T[nat]);
   } else {
     const SpecDev& sp = specs[s];
-    const int64_t li = g - sp.pad_off;
-    const int64_t r = li / sp.nx;
-    const int64_t i = li - r * sp.nx;
-    const int64_t k = r / sp.ny;
-    const int64_t j = r - k * sp.ny;
-    Tp = temp1(levels[s], entries + int64_t(s) * slots, sp.ox + float(i) * sp.dx,
-               sp.oy + float(j) * sp.dy, sp.oz + float(k) * sp.dz);
+    AT x, y, z;
+    point_coords<AT>(sp, g - sp.pad_off, x, y, z);
+    Tp = temp1<AT>(levels[s], entries + int64_t(s) * slots, x, y, z);
   }
-  const double gl = double(liquid_fraction(m, Tp));
+  const double gl = double(liquid_fraction<AT>(m, Tp));
   if (xbeta) xbeta[nat] = (1.0 - gl) - double(dxas[g]) - double(dxam[g]);
   if (xliq) xliq[nat] = gl;
+  if (T_out) T_out[nat] = double(Tp);
 }
 
 inline unsigned blocks_for(int64_t n, int threads) {
@@ -564,10 +514,11 @@ inline unsigned blocks_for(int64_t n, int threads) {
 }  // namespace
 
 // ------------------------------------------------------------- launchers
+template <typename AT>
 cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream) {
   const int n = a.n_specs * a.n_levels;
   if (n <= 0) return cudaSuccess;
-  k_src_table<<<blocks_for(n, 128), 128, 0, stream>>>(a, work);
+  k_src_table<AT><<<blocks_for(n, 128), 128, 0, stream>>>(a, work);
   return cudaGetLastError();
 }
 
@@ -583,28 +534,28 @@ cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-template <typename FT>
+template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<FT>, block_threads, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<AT, FT>, block_threads, 0) !=
       cudaSuccess)
     return 1;
   return nb > 0 ? nb : 1;
 }
 
-template <typename FT>
-cudaError_t launch_track(const TrackArgs<FT>& a, int block_threads, int grid_blocks,
+template <typename AT, typename FT>
+cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
                          cudaStream_t stream) {
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
-  k_track<FT><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
+  k_track<AT, FT><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
-template <typename FT>
-cudaError_t launch_step_ext(const StepArgs<FT>& a, int block_threads, cudaStream_t stream) {
+template <typename AT, typename FT>
+cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream) {
   if (a.n <= 0) return cudaSuccess;
   const int vec = ((reinterpret_cast<uintptr_t>(a.T0) | reinterpret_cast<uintptr_t>(a.T1)) & 15) == 0;
-  k_step_ext<FT><<<blocks_for((a.n + 3) / 4, block_threads), block_threads, 0, stream>>>(a, vec);
+  k_step_ext<AT, FT><<<blocks_for((a.n + 3) / 4, block_threads), block_threads, 0, stream>>>(a, vec);
   return cudaGetLastError();
 }
 
@@ -628,34 +579,43 @@ cudaError_t launch_get_state(const SpecDev* specs, const int32_t* tile_spec, int
   return cudaGetLastError();
 }
 
-template <typename FT>
-cudaError_t launch_fractions(const ModelConst& m, const SpecDev* specs, const int32_t* tile_spec,
-                             int64_t n_tiles, const FT* dxas, const FT* dxam, const float* T,
-                             const SrcLevel* levels, const SrcEntry* entries, int32_t slots,
-                             double* xbeta, double* xliq, cudaStream_t stream) {
+template <typename AT, typename FT>
+cudaError_t launch_fractions(const ModelConstT<AT>& m, const SpecDev* specs,
+                             const int32_t* tile_spec, int64_t n_tiles, const FT* dxas,
+                             const FT* dxam, const float* T, const SrcLevelT<AT>* levels,
+                             const SrcEntryT<AT>* entries, int32_t slots, double* xbeta,
+                             double* xliq, double* T_out, cudaStream_t stream) {
   const int64_t n_pad = n_tiles * TILE;
-  k_fractions<FT><<<blocks_for(n_pad, 256), 256, 0, stream>>>(
-      m, specs, tile_spec, n_pad, dxas, dxam, T, levels, entries, slots, xbeta, xliq);
+  k_fractions<AT, FT><<<blocks_for(n_pad, 256), 256, 0, stream>>>(
+      m, specs, tile_spec, n_pad, dxas, dxam, T, levels, entries, slots, xbeta, xliq, T_out);
   return cudaGetLastError();
 }
 
-#define MS_INSTANTIATE(FT)                                                                        \
-  template int track_blocks_per_sm<FT>(int);                                                     \
-  template cudaError_t launch_track<FT>(const TrackArgs<FT>&, int, int, cudaStream_t);           \
-  template cudaError_t launch_step_ext<FT>(const StepArgs<FT>&, int, cudaStream_t);              \
+#define MS_INSTANTIATE_FT(FT)                                                                     \
   template cudaError_t launch_set_state<FT>(const SpecDev*, const int32_t*, int64_t,             \
                                             const double*, const double*, const double*, FT*,    \
                                             FT*, float*, cudaStream_t, double, double);          \
   template cudaError_t launch_get_state<FT>(const SpecDev*, const int32_t*, int64_t, const FT*,  \
                                             const FT*, const float*, double*, double*, double*,  \
-                                            cudaStream_t);                                       \
-  template cudaError_t launch_fractions<FT>(const ModelConst&, const SpecDev*, const int32_t*,   \
-                                            int64_t, const FT*, const FT*, const float*,         \
-                                            const SrcLevel*, const SrcEntry*, int32_t, double*,  \
-                                            double*, cudaStream_t);
+                                            cudaStream_t);
 
-MS_INSTANTIATE(float)
-MS_INSTANTIATE(double)
-MS_INSTANTIATE(KF)
+#define MS_INSTANTIATE(AT, FT)                                                                    \
+  template int track_blocks_per_sm<AT, FT>(int);                                                 \
+  template cudaError_t launch_track<AT, FT>(const TrackArgs<AT, FT>&, int, int, cudaStream_t);   \
+  template cudaError_t launch_step_ext<AT, FT>(const StepArgs<AT, FT>&, int, cudaStream_t);      \
+  template cudaError_t launch_fractions<AT, FT>(                                                 \
+      const ModelConstT<AT>&, const SpecDev*, const int32_t*, int64_t, const FT*, const FT*,     \
+      const float*, const SrcLevelT<AT>*, const SrcEntryT<AT>*, int32_t, double*, double*,       \
+      double*, cudaStream_t);
+
+template cudaError_t launch_src_table<float>(const TableArgs&, WorkCounters*, cudaStream_t);
+template cudaError_t launch_src_table<double>(const TableArgs&, WorkCounters*, cudaStream_t);
+MS_INSTANTIATE_FT(float)
+MS_INSTANTIATE_FT(double)
+MS_INSTANTIATE_FT(KF)
+MS_INSTANTIATE(float, float)
+MS_INSTANTIATE(float, double)
+MS_INSTANTIATE(float, KF)
+MS_INSTANTIATE(double, double)
 
 }  // namespace ms

@@ -32,8 +32,8 @@ struct Scratch {
   ms::SpecDev spec;
   ms::TrackDev tracks[kMaxTracks];
   ms::LayerDev layers[kMaxLayers];
-  ms::SrcLevel levels[kMaxLevels];
-  ms::SrcEntry entries[kMaxLevels * kMaxTracks];
+  ms::SrcLevelT<float> levels[kMaxLevels];
+  ms::SrcEntryT<float> entries[kMaxLevels * kMaxTracks];
   int32_t tile_spec[kMaxTiles];                 // all zero: one specimen
 };
 
@@ -52,6 +52,8 @@ static_assert(offsetof(Scratch, tracks) - offsetof(Scratch, spec) == offsetof(Up
 static_assert(offsetof(Scratch, layers) - offsetof(Scratch, spec) == offsetof(Upload, layers),
               "Upload must mirror the spec / tracks / layers part of Scratch");
 static_assert(offsetof(Scratch, spec) % 8 == 0, "spec must be 8-byte aligned");
+static_assert(offsetof(Scratch, levels) % 16 == 0 && offsetof(Scratch, entries) % 16 == 0,
+              "the source table is read with 16-byte vector loads");
 static_assert(sizeof(Scratch) < (1u << 20), "the no-alloc scratch stays below 1 MiB");
 
 std::mutex g_setup_mu;
@@ -73,7 +75,7 @@ int setup_device(int dev, Scratch** out, int* grid_per_device) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "cannot query the SM count");
-    g_track_grid[dev] = ms::track_blocks_per_sm<float>(128) * sms;
+    g_track_grid[dev] = ms::track_blocks_per_sm<float, float>(128) * sms;
     g_scratch_ptr[dev] = static_cast<Scratch*>(p);
   }
   *out = g_scratch_ptr[dev];
@@ -136,8 +138,10 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     up.layers[j] = ms::LayerDev{L.z_surface, L.t_begin, L.t_scan_end, L.t_end};
   }
   ms::SpecDev& s = up.spec;
-  s.ox = float(grid->origin[0]); s.oy = float(grid->origin[1]); s.oz = float(grid->origin[2]);
-  s.dx = float(grid->spacing[0]); s.dy = float(grid->spacing[1]); s.dz = float(grid->spacing[2]);
+  s.ox = double(float(grid->origin[0])); s.oy = double(float(grid->origin[1]));
+  s.oz = double(float(grid->origin[2]));
+  s.dx = double(float(grid->spacing[0])); s.dy = double(float(grid->spacing[1]));
+  s.dz = double(float(grid->spacing[2]));
   s.nx = grid->dims[0]; s.ny = grid->dims[1]; s.nz = grid->dims[2];
   s.n = n_points;
   s.n_tiles = int32_t(n_tiles);
@@ -158,7 +162,7 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
   if (cudaMemcpyAsync(&sc->spec, &up, sizeof(Upload), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return ms::record_error(MS_ERR_CUDA, "uploading the source tables failed");
 
-  const ms::ModelConst mc = ms::model_const(*p);
+  const ms::ModelConstT<float> mc = ms::model_const<float>(*p);
   const int S = p->steps_per_launch;
   const int grid_blocks = int(std::min<int64_t>(grid_cap, (n_tiles + 3) / 4));
   int64_t done = 0;
@@ -176,9 +180,9 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     ta.dt = dt;
     ta.levels = sc->levels;
     ta.entries = sc->entries;
-    if (ms::launch_src_table(ta, &sc->work, st) != cudaSuccess)
+    if (ms::launch_src_table<float>(ta, &sc->work, st) != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "source-table launch failed");
-    ms::TrackArgs<float> a{};
+    ms::TrackArgs<float, float> a{};
     a.m = mc;
     a.specs = &sc->spec;
     a.tile_spec = sc->tile_spec;
@@ -195,7 +199,7 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     a.aux = aux;
     a.tile_tsat = nullptr;
     a.err = &sc->err;
-    if (ms::launch_track<float>(a, 128, grid_blocks, st) != cudaSuccess)
+    if (ms::launch_track<float, float>(a, 128, grid_blocks, st) != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "hot-kernel launch failed");
     done += steps;
   }

@@ -218,6 +218,42 @@ def test_f64_accumulation_parity(ms):
     check_sum(g)
 
 
+def test_full_fp64_path_parity(ms):
+    """MS_F64: temperatures, rates and fractions in FP64 on the GPU (the
+    spot-check path) agree with the FP64 oracle far below the FP32 budget."""
+    w = wl.block_256(dims=(24, 10, 6), n_tracks=3, n_steps=1200, T_thr=0.0)
+    _, g = gpu_workload(w, precision=ms.MS_F64)
+    o = oracle_workload(w)
+    assert max_abs_diff(g, o) <= 1e-6
+    check_sum(g)
+
+
+def test_point_subset_matches_the_full_grid(ms):
+    """ms_set_points_subset: a seeded subset of the block advances exactly as
+    those points do in the full-grid run (same coordinates, same arithmetic)."""
+    w = wl.block_256(dims=(40, 24, 10), n_tracks=4, n_steps=700, T_thr=0.0)
+    sp = w.specimens[0]
+    _, full = gpu_workload(w)
+    idx = np.sort(np.random.default_rng(4).choice(sp.grid.n, 1000, replace=False))
+    ctx = ms.Context(idx.size, T_thr=0.0)
+    ctx.set_points_subset(sp.grid, idx)
+    ctx.fill_state()
+    ctx.run_track([sp.source], w.n_steps, w.dt)
+    sub = ctx.fractions()
+    for a, b in zip(full, sub):
+        assert np.array_equal(a[idx], b)
+
+
+def test_temperature_query_matches_the_source(ms):
+    w = wl.block_256(dims=(30, 20, 5), n_tracks=2, n_steps=150, T_thr=0.0)
+    sp = w.specimens[0]
+    ctx, _ = gpu_workload(w)
+    T = ctx.temperature()
+    x, y, z = sp.grid.coords()
+    To, _ = orc.temperature(sp.source, x, y, z, w.n_steps * w.dt)
+    assert np.max(np.abs(T - To) / To) <= 2e-5
+
+
 def test_kahan_compensated_parity(ms):
     """MS_KAHAN: double-float fractions, FP32 rates; as tight as FP64
     accumulation on the line."""
