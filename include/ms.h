@@ -173,6 +173,15 @@ typedef struct ms_stats_t {
   int64_t hot_kernel_launches;    /* number of launches in hot_kernel_ms          */
   int32_t device_error;           /* sticky device error word (0 = none)         */
   int32_t reserved;
+  /* hybrid mode (ms_set_surrogate), since the last reset: point-windows of
+   * MS_MLP_WINDOW steps advanced by the MLP, point-windows advanced by the
+   * explicit steps (band, initiation, layer change or a short tail), windows
+   * re-run by the judge, and the largest |dX_as| or |dX_am| the judge saw
+   * between the MLP and the explicit result of one window.                */
+  int64_t surrogate_windows;
+  int64_t ode_windows;
+  int64_t judge_samples;
+  double  judge_max_err;
 } ms_stats_t;
 
 typedef struct ms_ctx ms_ctx;
@@ -334,6 +343,80 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
 int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid, const ms_heat_source* src,
                          float* x_as, float* x_am, float* aux, int64_t n_points,
                          int64_t step0, int64_t n_steps, double dt, void* cuda_stream);
+
+/* ------------------------------------------------------ learned surrogate */
+/* A small MLP that advances a point's fractions over a window of
+ * MS_MLP_WINDOW explicit steps in one evaluation.  The paper integrates every
+ * step (Sec. 3); the surrogate is an extension of the method, used only where
+ * the explicit steps are smooth: a window falls back to the explicit steps when
+ * any of its temperatures (the window start and its MS_MLP_WINDOW new levels)
+ * lies within 40 K of T_am,start, T_as,end, T_as,start, T_as,start + T_reg,
+ * T_s or T_l or above T_s - 40 K, or when an App. A initiation is running.
+ *
+ * Network: inputs x[12] = (X_as, X_am, X_beta at the window start, the 8 new
+ * temperatures as (T - 1000 K) / 1000 K, log10(dt) + 5); hidden 64 -> 64,
+ * GELU (tanh form); outputs y[3] = 1e6 x the window's diffusive residual
+ * (X_as, X_am, X_beta at the window end minus G(start fractions), where
+ * G = g(T_8, .) o ... o g(T_1, .) applies only the correction g at the
+ * window's 8 new temperatures in turn).  An MLP window sets
+ * X = g(T_8, G(X_start) + y / 1e6): the instantaneous part (clamping, the 0.9
+ * bound, the alpha_s cap, martensite dissolution and formation) is exact along
+ * the window's temperature path and the network supplies the diffusion of
+ * Sec. 2.2.  Parameters: MS_MLP_PARAMS floats, W1[64][12], b1[64],
+ * W2[64][64], b2[64], W3[3][64], b3[3], weights row-major (out x in).
+ * Inference uses BF16 weights and activations with FP32 accumulation on the
+ * tensor cores; training keeps an FP32 master copy (Adam).                 */
+#define MS_MLP_IN      12
+#define MS_MLP_OUT     3
+#define MS_MLP_PARAMS  5187
+#define MS_MLP_WINDOW  8
+
+typedef struct ms_surrogate ms_surrogate;
+
+/* Create a surrogate from MS_MLP_PARAMS host floats (copied).  Owns its
+ * device buffers and a stream.  Errors: INVALID_ARG (NULL, non-finite), OOM,
+ * CUDA. */
+int ms_surrogate_create(const float* params, ms_surrogate** out);
+/* Free a surrogate (NULL is a no-op).  Detach it from every context first. */
+void ms_surrogate_destroy(ms_surrogate* s);
+/* Run later calls on cuda_stream (NULL = the surrogate's own stream). */
+int ms_surrogate_set_stream(ms_surrogate* s, void* cuda_stream);
+/* Copy the FP32 master parameters to a host array of MS_MLP_PARAMS floats. */
+int ms_surrogate_get_params(ms_surrogate* s, float* params);
+/* Inference on n samples: x device [n][12] FP32, y device [n][3] FP32 (the
+ * network output, i.e. 10 x increments).  Asynchronous. */
+int ms_surrogate_forward(ms_surrogate* s, const float* x, float* y, int64_t n);
+/* Mean-squared-error gradient over n samples (x device [n][12], targets t
+ * device [n][3]): loss = sum (y - t)^2 / (3 n).  The forward pass rounds the
+ * weights, inputs and hidden activations to BF16 as inference does.  grad
+ * (device, MS_MLP_PARAMS floats, may be NULL) receives dloss/dparams; loss
+ * (host, may be NULL; synchronises) the loss before the update.
+ * Errors: INVALID_ARG (NULL, n <= 0), OOM (per-sample scratch), CUDA. */
+int ms_surrogate_gradient(ms_surrogate* s, const float* x, const float* t, int64_t n,
+                          float* grad, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * gradient of n samples with learning rate lr; refreshes the BF16 copy. */
+int ms_surrogate_train_step(ms_surrogate* s, const float* x, const float* t, int64_t n,
+                            double lr, double* loss);
+
+/* Apply the correction g of eq:explicit_correction to n independent points
+ * at the temperatures T[i][0], ..., T[i][n_T - 1] in turn (T: host array of
+ * n x n_T doubles, row-major; x_as, x_am: host arrays updated in place; FP64
+ * on the device with the context's parameters).  Not a time step: it forms
+ * the surrogate's training targets.  Errors: INVALID_ARG (n_T < 1), OOM,
+ * CUDA. */
+int ms_apply_correction(ms_ctx* ctx, const double* T, int32_t n_T, double* x_as, double* x_am,
+                        int64_t n);
+
+/* Attach a surrogate to a context (NULL detaches): ms_run_track then advances
+ * whole windows of MS_MLP_WINDOW steps (counted from the call's first level)
+ * with the MLP where the band test allows and with the explicit steps
+ * elsewhere.  judge_frac in [0, 1] is the fraction of MLP windows, drawn by a
+ * counter-based hash of (point, level), that are also run with the explicit
+ * steps to measure the surrogate's error (ms_stats); the MLP result is kept.
+ * The surrogate must outlive its attachment.  Requires MS_F32 or MS_KAHAN.
+ * Errors: INVALID_ARG, UNSUPPORTED (other precisions). */
+int ms_set_surrogate(ms_ctx* ctx, const ms_surrogate* s, double judge_frac);
 
 /* Counters and the sticky device error word (synchronises the stream). */
 int ms_stats(ms_ctx* ctx, ms_stats_t* out);

@@ -100,6 +100,9 @@ def _load():
             lib.orc_run_track.argtypes = [P, P, P, i32, P, i32, i64, P, P, P, i64, i64, d,
                                           P, P, P, P, P]
             lib.orc_run_track.restype = None
+            lib.orc_run_track_windows.argtypes = [P, P, P, i32, P, i32, i64, P, P, P, i64, i64,
+                                                  d, i32, d, P, P, P, P, P]
+            lib.orc_run_track_windows.restype = None
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_param_count.restype = ctypes.c_int
             assert lib.orc_param_count() == len(PARAM_NAMES)
@@ -273,3 +276,23 @@ def run_track(state: State, src, x, y, z, n0, n_steps, dt, p=None):
                       float(dt), _ptr(state.xas), _ptr(state.xam), _ptr(state.xt),
                       _ptr(state.mode), _ptr(T_last))
     return T_last
+
+
+def run_track_windows(state: State, src, x, y, z, n0, n_steps, dt, window=8, band_half=40.0,
+                      p=None):
+    """The hybrid path's window form with a zero network (see
+    orc_run_track_windows): windows outside the band apply only the
+    correction g at their new temperatures in turn; the others take the
+    explicit steps.  Returns per point the number of such windows."""
+    assert 1 <= window <= 64
+    lib, p = _load(), _prm(p)
+    spec, tracks, layers = _src_arrays(src)
+    x, y, z = (np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (x, y, z))
+    assert x.size == state.n
+    n_mlp = np.zeros(state.n, dtype=np.int64)
+    lib.orc_run_track_windows(_ptr(p), _ptr(spec), _ptr(tracks), tracks.shape[0], _ptr(layers),
+                              layers.shape[0], state.n, _ptr(x), _ptr(y), _ptr(z), int(n0),
+                              int(n_steps), float(dt), int(window), float(band_half),
+                              _ptr(state.xas), _ptr(state.xam), _ptr(state.xt), _ptr(state.mode),
+                              _ptr(n_mlp))
+    return n_mlp

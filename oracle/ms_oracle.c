@@ -365,6 +365,61 @@ void orc_run_track(const double *p, const double *spec, const double *tracks, in
   }
 }
 
+/* The window form of the hybrid path (an extension of Sec. 3, not in the
+ * paper) for a network whose output is zero, so that the window machinery is
+ * checked apart from the network's arithmetic.  Steps are taken in windows of
+ * `window` levels from n0.  A window whose temperatures (start and new
+ * levels) all stay more than band_half away from T_am,start, T_as,end,
+ * T_as,start and T_as,start + T_reg and at or below T_s - band_half, with no
+ * App. A initiation running at its start, the point below the surface on
+ * every level and the full window length, applies only the correction g at
+ * its new temperatures in turn (no diffusion); every other window takes the
+ * explicit steps.  n_mlp[i] counts the first kind of window per point. */
+static int in_band(const double *p, double T, double h) {
+  if (!(T <= p[P_T_S] - h)) return 1;
+  if (fabs(T - p[P_T_AM_START]) < h || fabs(T - p[P_T_AS_END]) < h) return 1;
+  if (fabs(T - p[P_T_AS_START]) < h || fabs(T - (p[P_T_AS_START] + p[P_T_REG])) < h) return 1;
+  return 0;
+}
+
+void orc_run_track_windows(const double *p, const double *spec, const double *tracks,
+                           int32_t n_tracks, const double *layers, int32_t n_layers, int64_t n,
+                           const double *x, const double *y, const double *z, int64_t n0,
+                           int64_t n_steps, double dt, int32_t window, double band_half,
+                           double *xas, double *xam, double *xt, int32_t *mode, int64_t *n_mlp) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < n; ++i) {
+    double T[65];
+    int act[65];
+    int a0;
+    int64_t count = 0;
+    double T0 = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i],
+                                   (double)n0 * dt - spec[S_TOFF], &a0);
+    for (int64_t w0 = 0; w0 < n_steps; w0 += window) {
+      int64_t K = n_steps - w0 < window ? n_steps - w0 : window;
+      int band = in_band(p, T0, band_half), all_act = 1, any_act = 0;
+      T[0] = T0;
+      for (int64_t l = 1; l <= K; ++l) {
+        double tl = (double)(n0 + w0 + l) * dt - spec[S_TOFF];
+        T[l] = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i], tl,
+                                  &act[l]);
+        band |= in_band(p, T[l], band_half);
+        all_act &= act[l];
+        any_act |= act[l];
+      }
+      if (any_act && all_act && K == window && !band && mode[i] == MODE_NONE) {
+        for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);
+        ++count;
+      } else {
+        for (int64_t l = 1; l <= K; ++l)
+          if (act[l]) point_step(p, T[l - 1], T[l], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
+      }
+      T0 = T[K];
+    }
+    if (n_mlp) n_mlp[i] = count;
+  }
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -7,8 +7,8 @@ of ``include/ms.h``; this package only builds it and marshals arguments
 provides device memory and streams.
 """
 from ._binding import (MS_F32, MS_F64, MS_F64ACC, MS_KAHAN, MS_PTR_DEVICE, Context, MSError,
-                       default_params, library_path, load)
+                       Surrogate, default_params, library_path, load)
 from .build import build
 
-__all__ = ["Context", "MSError", "default_params", "load", "build", "library_path",
+__all__ = ["Context", "Surrogate", "MSError", "default_params", "load", "build", "library_path",
            "MS_F32", "MS_F64ACC", "MS_KAHAN", "MS_F64", "MS_PTR_DEVICE"]

@@ -22,6 +22,7 @@ MS_F32, MS_F64ACC, MS_KAHAN, MS_F64 = 0, 1, 2, 3
 MS_PTR_DEVICE = 1
 MS_FLAG_TIME_KERNELS = 1
 MS_FLAG_GRAPH = 2
+MS_MLP_IN, MS_MLP_OUT, MS_MLP_PARAMS, MS_MLP_WINDOW = 12, 3, 5187, 8
 
 d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
 
@@ -58,7 +59,9 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, i64) for n in ("steps", "point_updates", "tile_steps_total",
                                    "tile_steps_active", "launches")] + [
         ("last_run_ms", d), ("hot_kernel_ms", d), ("hot_kernel_launches", i64),
-        ("device_error", i32), ("reserved", i32)]
+        ("device_error", i32), ("reserved", i32),
+        ("surrogate_windows", i64), ("ode_windows", i64), ("judge_samples", i64),
+        ("judge_max_err", d)]
 
 
 STRUCTS = (Params, Grid, Track, Layer, HeatSource, Stats)
@@ -116,6 +119,16 @@ def load(build_if_missing: bool = True):
     lib.ms_probe_sfu.argtypes = [ctypes.c_int, ctypes.POINTER(d), ctypes.POINTER(d)]
     lib.ms_run_track_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Grid),
                                          ctypes.POINTER(HeatSource), P, P, P, i64, i64, i64, d, P]
+    lib.ms_surrogate_create.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(P)]
+    lib.ms_surrogate_destroy.argtypes = [P]
+    lib.ms_surrogate_destroy.restype = None
+    lib.ms_surrogate_set_stream.argtypes = [P, P]
+    lib.ms_surrogate_get_params.argtypes = [P, P]
+    lib.ms_surrogate_forward.argtypes = [P, P, P, i64]
+    lib.ms_surrogate_gradient.argtypes = [P, P, P, i64, P, ctypes.POINTER(d)]
+    lib.ms_surrogate_train_step.argtypes = [P, P, P, i64, d, ctypes.POINTER(d)]
+    lib.ms_set_surrogate.argtypes = [P, P, d]
+    lib.ms_apply_correction.argtypes = [P, P, i32, P, P, i64]
     for i, s in enumerate(STRUCTS):
         if lib.ms_struct_size(i) != ctypes.sizeof(s):
             raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
@@ -228,6 +241,24 @@ class Context:
     def handle(self):
         return self._h
 
+    def set_surrogate(self, surrogate: "Surrogate | None", judge_frac: float = 0.0):
+        """Attach (or with None detach) a surrogate: ms_run_track then runs
+        the hybrid window kernel."""
+        _check(self._lib.ms_set_surrogate(self._h, surrogate.handle if surrogate else None,
+                                          float(judge_frac)), "ms_set_surrogate")
+        self._surrogate = surrogate
+
+    def apply_correction(self, T, xas, xam):
+        """The correction g applied to independent points at the temperatures
+        T ([n] or [n, m]: m levels in turn); returns the corrected (xas, xam)."""
+        a = np.array(xas, dtype=np.float64, copy=True).ravel()
+        b = np.array(xam, dtype=np.float64, copy=True).ravel()
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(a.size, -1))
+        assert b.size == a.size
+        _check(self._lib.ms_apply_correction(self._h, _ptr(T), T.shape[1], _ptr(a), _ptr(b), a.size),
+               "ms_apply_correction")
+        return a, b
+
     def set_stream(self, stream_handle: int | None):
         _check(self._lib.ms_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)), "ms_set_stream")
 
@@ -318,3 +349,61 @@ class Context:
 
     def synchronize(self):
         _check(self._lib.ms_synchronize(self._h), "ms_synchronize")
+
+
+class Surrogate:
+    """One ms_surrogate: the window MLP's FP32 master parameters, Adam state
+    and BF16 inference copy on the current device.  Data arguments are device
+    pointers (e.g. torch.Tensor.data_ptr() of contiguous float32 tensors)."""
+
+    def __init__(self, params):
+        self._lib = load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MS_MLP_PARAMS:
+            raise ValueError(f"expected {MS_MLP_PARAMS} parameters, got {p.size}")
+        self._h = ctypes.c_void_p()
+        _check(self._lib.ms_surrogate_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                             ctypes.byref(self._h)), "ms_surrogate_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.ms_surrogate_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int | None):
+        _check(self._lib.ms_surrogate_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)),
+               "ms_surrogate_set_stream")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MS_MLP_PARAMS, dtype=np.float32)
+        _check(self._lib.ms_surrogate_get_params(self._h, _ptr(out)), "ms_surrogate_get_params")
+        return out
+
+    def forward(self, x_ptr: int, y_ptr: int, n: int):
+        _check(self._lib.ms_surrogate_forward(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                              int(n)), "ms_surrogate_forward")
+
+    def gradient(self, x_ptr: int, t_ptr: int, n: int, grad_ptr: int | None = None) -> float:
+        loss = d()
+        _check(self._lib.ms_surrogate_gradient(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr),
+                                               int(n), ctypes.c_void_p(grad_ptr or 0),
+                                               ctypes.byref(loss)), "ms_surrogate_gradient")
+        return loss.value
+
+    def train_step(self, x_ptr: int, t_ptr: int, n: int, lr: float, want_loss: bool = False):
+        loss = d()
+        _check(self._lib.ms_surrogate_train_step(self._h, ctypes.c_void_p(x_ptr),
+                                                 ctypes.c_void_p(t_ptr), int(n), float(lr),
+                                                 ctypes.byref(loss) if want_loss else None),
+               "ms_surrogate_train_step")
+        return loss.value if want_loss else None

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ms_internal.h"
@@ -88,6 +89,12 @@ struct ms_ctx {
   ms::WorkCounters* work_d = nullptr;
   int sm_count = 0;
   int track_grid = 0;  // persistent grid size for the current layout
+
+  // attached surrogate (hybrid kernel)
+  const ms::MlpDev* mlp = nullptr;
+  uint64_t judge_thresh = 0;
+  ms::HybridCounters* hyb_d = nullptr;
+  int hybrid_per_sm = 0;
 
   // staging
   double* stage_d = nullptr;
@@ -354,6 +361,16 @@ int check_device_error(ms_ctx* c) {
   MS_CUDA(cudaStreamSynchronize(c->stream));
   c->st.device_error = err;
   c->st.tile_steps_active = int64_t(wc.tile_steps_active);
+  if (c->hyb_d) {
+    ms::HybridCounters hc{};
+    MS_CUDA(cudaMemcpy(&hc, c->hyb_d, sizeof(hc), cudaMemcpyDeviceToHost));
+    c->st.surrogate_windows = int64_t(hc.surrogate_windows);
+    c->st.ode_windows = int64_t(hc.ode_windows);
+    c->st.judge_samples = int64_t(hc.judge_samples);
+    float e = 0.f;
+    std::memcpy(&e, &hc.judge_err_bits, sizeof(e));
+    c->st.judge_max_err = double(e);
+  }
   if (c->timed) {
     float ms_ = 0.f;
     if (cudaEventElapsedTime(&ms_, c->ev0, c->ev1) == cudaSuccess) c->st.last_run_ms = ms_;
@@ -513,7 +530,21 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.tile_tsat = c->tile_tsat_d;
     a.err = c->err_d;
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
-    MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream));
+    bool hybrid = false;
+    if constexpr (std::is_same<AT, float>::value &&
+                  (std::is_same<FT, float>::value || std::is_same<FT, ms::KF>::value)) {
+      if (c->mlp) {
+        a.mlp = c->mlp;
+        a.hyb = c->hyb_d;
+        a.judge_thresh = c->judge_thresh;
+        a.level0 = c->step_n;
+        const int64_t need = (c->n_tiles + ms::HYBRID_THREADS / 32 - 1) / (ms::HYBRID_THREADS / 32);
+        const int grid = int(std::min<int64_t>(int64_t(c->hybrid_per_sm) * c->sm_count, need));
+        MS_CUDA(ms::launch_track_hybrid<FT>(a, grid, c->stream));
+        hybrid = true;
+      }
+    }
+    if (!hybrid) MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream));
     if ((rc = kernel_event(c, true)) != MS_OK) return rc;
     c->st.launches++;
     c->step_n += steps;
@@ -741,6 +772,7 @@ void ms_destroy(ms_ctx* c) {
   cudaFree(c->idx_d);
   cudaFree(c->err_d);
   cudaFree(c->work_d);
+  cudaFree(c->hyb_d);
   cudaFree(c->tracks_d);
   cudaFree(c->layers_d);
   cudaFree(c->levels_d);
@@ -890,6 +922,7 @@ int ms_reset_stats(ms_ctx* c) {
   if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
   MS_CUDA(cudaStreamSynchronize(c->stream));
   MS_CUDA(cudaMemset(c->work_d, 0, sizeof(ms::WorkCounters)));
+  if (c->hyb_d) MS_CUDA(cudaMemset(c->hyb_d, 0, sizeof(ms::HybridCounters)));
   const int32_t err = c->st.device_error;
   c->st = ms_stats_t{};
   c->st.device_error = err;
@@ -1068,6 +1101,51 @@ int ms_set_state_blob(ms_ctx* c, const void* blob, size_t bytes) {
   c->t_base = h.t_base;
   c->dt = h.dt;
   c->T_last = nullptr;
+  return MS_OK;
+}
+
+int ms_apply_correction(ms_ctx* c, const double* T, int32_t n_T, double* x_as, double* x_am,
+                        int64_t n) {
+  if (!c || !T || !x_as || !x_am || n < 0 || n_T < 1) return fail(MS_ERR_INVALID_ARG, "bad argument");
+  if (n == 0) return MS_OK;
+  double* d = nullptr;
+  MS_CUDA(cudaMalloc(&d, size_t(n) * (2 + size_t(n_T)) * sizeof(double)));
+  const size_t b = size_t(n) * sizeof(double);
+  double* dT = d + 2 * n;
+  cudaError_t e = cudaMemcpyAsync(dT, T, b * size_t(n_T), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, x_as, b, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + n, x_am, b, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = ms::launch_correct(c->mcd, n, n_T, dT, d, d + n, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x_as, d, b, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x_am, d + n, b, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(e));
+  return MS_OK;
+}
+
+int ms_set_surrogate(ms_ctx* c, const ms_surrogate* s, double judge_frac) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  if (!(judge_frac >= 0.0 && judge_frac <= 1.0))
+    return fail(MS_ERR_INVALID_ARG, "judge_frac must be in [0, 1]");
+  if (s && c->prm.precision != MS_F32 && c->prm.precision != MS_KAHAN)
+    return fail(MS_ERR_UNSUPPORTED, "the hybrid path needs precision MS_F32 or MS_KAHAN");
+  MS_CUDA(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  if (!s) {
+    c->mlp = nullptr;
+    return MS_OK;
+  }
+  if (!c->hyb_d) {
+    MS_CUDA(cudaMalloc(&c->hyb_d, sizeof(ms::HybridCounters)));
+    MS_CUDA(cudaMemset(c->hyb_d, 0, sizeof(ms::HybridCounters)));
+  }
+  const int per_sm = c->prm.precision == MS_KAHAN ? ms::hybrid_blocks_per_sm<ms::KF>()
+                                                  : ms::hybrid_blocks_per_sm<float>();
+  if (per_sm <= 0) return fail(MS_ERR_CUDA, "hybrid kernel cannot be made resident");
+  c->hybrid_per_sm = per_sm;
+  c->mlp = ms::surrogate_weights(s);
+  c->judge_thresh = uint64_t(std::llround(judge_frac * 4294967296.0));
   return MS_OK;
 }
 

@@ -1,0 +1,351 @@
+// Hybrid hot kernel: ms_run_track with an attached surrogate.
+//
+// The same persistent tile loop as k_track (128-point tiles, 4 points per
+// lane, temperatures from the source table), but the launch's steps are taken
+// in windows of MLP_WINDOW = 8.  Per window and point:
+//   - the 8 new temperatures go to shared memory;
+//   - band test: the window (its start and 8 new levels) stays 40 K away from
+//     every temperature where the model switches branch (T_am,start,
+//     T_as,end, T_as,start, T_as,start + T_reg) and below T_s - 40 K, no
+//     App. A initiation is running, and the point is below the surface on
+//     every level;
+//   - passing points take X = g(T_8, G(X_start) + y / 1e6) with
+//     G = g(T_8, .) o ... o g(T_1, .): the correction g of Sec. 2.2 along the
+//     window's temperatures supplies the instantaneous part exactly
+//     (clamping, the X_alpha <= 0.9 bound, the alpha_s cap, martensite
+//     dissolution and formation, at whatever level they act) and the MLP
+//     (12 -> 64 -> 64 -> 3, BF16 on the tensor cores, one m16n8k16 row tile
+//     per 16 points, tiles with no MLP point skipped) the diffusive residual y;
+//   - the others take the 8 explicit steps of Sec. 3 (eq:explicit_integration
+//     + g), as k_track does;
+//   - a fraction of the MLP windows, chosen by a counter-based hash of
+//     (point, level), is also run with the explicit steps (the judge); the
+//     largest difference is kept in the counters and the MLP result stays.
+// Points that are cold and saturated on all 8 steps (reading A9) are left
+// unchanged, as k_track's vote would leave them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "ms_internal.h"
+#include "ms_mlp.cuh"
+#include "ms_tile.cuh"
+
+namespace ms {
+
+namespace {
+
+constexpr int HYB_WARPS = HYBRID_THREADS / 32;
+constexpr float BAND_HALF_WIDTH = 40.0f;
+
+struct HybWarp {
+  float T[MLP_WINDOW][TILE];                 // the window's new temperatures
+  __nv_bfloat16 X[TILE][MLP_X_LD];           // MLP inputs (padded rows)
+  float Y[TILE][MLP_Y_LD];                   // MLP outputs
+};
+constexpr size_t MLP_SMEM = (sizeof(MlpDev) + 127) / 128 * 128;
+constexpr size_t HYB_SMEM = MLP_SMEM + HYB_WARPS * sizeof(HybWarp);
+static_assert(sizeof(MlpDev) % 16 == 0 && sizeof(HybWarp) % 128 == 0, "16-byte copies, aligned warp areas");
+static_assert(2 * (HYB_SMEM + 1024) <= 228 * 1024, "two CTAs per SM");
+
+__device__ __forceinline__ bool near(float T, float c) { return fabsf(T - c) < BAND_HALF_WIDTH; }
+
+__device__ __forceinline__ bool in_band(const ModelConstT<float>& m, float T) {
+  return !(T <= m.T_s - BAND_HALF_WIDTH) || near(T, m.T_am_start) || near(T, m.T_as_end) ||
+         near(T, m.T_as_start) || near(T, m.T_cap0);
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014) of (point, level).
+__device__ __forceinline__ uint32_t judge_hash(uint64_t point, uint64_t level) {
+  uint64_t z = point * 0x9E3779B97F4A7C15ull + level * 0xD1B54A32D192ED03ull + 0x2402175800ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return uint32_t((z ^ (z >> 31)) >> 32);
+}
+
+template <typename FT>
+__device__ __forceinline__ float to_f(FT v) { return float(v); }
+template <>
+__device__ __forceinline__ float to_f<KF>(KF v) { return v.hi + v.lo; }
+
+struct HybCount {
+  unsigned long long surr = 0, ode = 0, judged = 0;
+  float err = 0.0f;
+};
+
+template <typename FT>
+__device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const MlpDev& W,
+                                            HybWarp& sm, int tile, int lane, float fdt,
+                                            HybCount& cnt) {
+  const unsigned full = 0xffffffffu;
+  const int s = a.tile_spec[tile];
+  const SpecDev& sp = a.specs[s];
+  const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
+  const int64_t g0 = sp.pad_off + local0;
+
+  float px[4], py[4], pz[4];
+  bool valid[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t li = local0 + q;
+    valid[q] = li < sp.n;
+    point_coords<float>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
+  }
+
+  FT xs[4], xm[4];
+  float ax[4];
+  Vec4<FT>::load(a.xas + g0, xs);
+  Vec4<FT>::load(a.xam + g0, xm);
+  Vec4<float>::load(a.aux + g0, ax);
+
+  const SrcLevelT<float>* lv = a.levels + int64_t(s) * a.n_levels;
+  const SrcEntryT<float>* en = a.entries + int64_t(s) * a.n_levels * a.slots;
+  const float z_tol = sp.z_tol;
+  const bool skipping = a.m.T_thr > 0.0f;
+  const int n_steps = a.n_levels - 1;
+
+  float T0[4];
+  temps4<float>(lv[0], en, px, py, pz, T0);
+  for (int w0 = 0; w0 < n_steps; w0 += MLP_WINDOW) {
+    const int K = min(MLP_WINDOW, n_steps - w0);
+    bool band[4], all_act[4], any_act[4], noop[4];
+    float Tp[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      band[q] = in_band(a.m, T0[q]);
+      all_act[q] = true;
+      any_act[q] = false;
+      noop[q] = true;
+      Tp[q] = T0[q];
+    }
+    for (int l = 0; l < K; ++l) {
+      const int lvl = w0 + 1 + l;
+      const SrcLevelT<float> L = lv[lvl];
+      float T1[4];
+      temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, T1);
+      *reinterpret_cast<float4*>(&sm.T[l][lane * 4]) = make_float4(T1[0], T1[1], T1[2], T1[3]);
+      const float zlim = L.z_surf + z_tol;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool act = valid[q] && pz[q] <= zlim;
+        all_act[q] = all_act[q] && act;
+        any_act[q] = any_act[q] || act;
+        band[q] = band[q] || in_band(a.m, T1[q]);
+        noop[q] = noop[q] && (!act || (skipping && step_is_noop<float, FT>(a.m, Tp[q], T1[q], xs[q],
+                                                                          xm[q], ax[q])));
+        Tp[q] = T1[q];
+      }
+    }
+
+    bool use_mlp[4], use_ode[4], judged[4];
+    bool lane_mlp = false, lane_exp = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool idle = !any_act[q] || (skipping && noop[q]);
+      use_mlp[q] = !idle && all_act[q] && K == MLP_WINDOW && !band[q] && ax[q] == 0.0f;
+      judged[q] = use_mlp[q] &&
+                  uint64_t(judge_hash(uint64_t(g0 + q), uint64_t(a.level0 + w0))) < a.judge_thresh;
+      use_ode[q] = !idle && !use_mlp[q];
+      lane_mlp = lane_mlp || use_mlp[q];
+      lane_exp = lane_exp || use_ode[q] || judged[q];
+      cnt.surr += use_mlp[q];
+      cnt.ode += use_ode[q];
+      cnt.judged += judged[q];
+    }
+
+    FT rs[4], rm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      rs[q] = xs[q];
+      rm[q] = xm[q];
+    }
+    const unsigned bal = __ballot_sync(full, lane_mlp);
+    if (bal) {
+      // inputs: fractions at the window start, the 8 new temperatures, log10(dt) + 5
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = lane * 4 + q;
+        float f[MLP_IN_PAD];
+#pragma unroll
+        for (int k = 0; k < MLP_IN_PAD; ++k) f[k] = 0.0f;
+        if (use_mlp[q]) {
+          const float fs = to_f(xs[q]), fm = to_f(xm[q]);
+          f[0] = fs;
+          f[1] = fm;
+          f[2] = 1.0f - fs - fm;
+#pragma unroll
+          for (int l = 0; l < MLP_WINDOW; ++l) f[3 + l] = (sm.T[l][row] - MLP_T_SHIFT) * MLP_T_SCALE;
+          f[11] = fdt;
+        }
+        uint4 v0, v1;
+        v0.x = pack_bf16(f[0], f[1]); v0.y = pack_bf16(f[2], f[3]);
+        v0.z = pack_bf16(f[4], f[5]); v0.w = pack_bf16(f[6], f[7]);
+        v1.x = pack_bf16(f[8], f[9]); v1.y = pack_bf16(f[10], f[11]);
+        v1.z = 0u; v1.w = 0u;
+        *reinterpret_cast<uint4*>(&sm.X[row][0]) = v0;
+        *reinterpret_cast<uint4*>(&sm.X[row][8]) = v1;
+      }
+      uint32_t mt_mask = 0;
+#pragma unroll
+      for (int mt = 0; mt < 8; ++mt)
+        if ((bal >> (4 * mt)) & 0xfu) mt_mask |= 1u << mt;
+      __syncwarp();
+      mlp_forward_warp(W, &sm.X[0][0], &sm.Y[0][0], lane, mt_mask);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (!use_mlp[q]) continue;
+        const int row = lane * 4 + q;
+        const float T8 = sm.T[MLP_WINDOW - 1][row];
+        FT nas = xs[q], nam = xm[q];
+        // the instantaneous part, exact along the window's temperature path
+        for (int l = 0; l < MLP_WINDOW; ++l) correct<float, FT>(a.m, sm.T[l][row], nas, nam);
+        nas = nas + FT(sm.Y[row][0] * (1.0f / MLP_OUT_SCALE));
+        nam = nam + FT(sm.Y[row][1] * (1.0f / MLP_OUT_SCALE));
+        correct<float, FT>(a.m, T8, nas, nam);
+        rs[q] = nas;
+        rm[q] = nam;
+      }
+    }
+
+    // explicit steps: fallback points and judged MLP windows
+    if (__any_sync(full, lane_exp)) {
+      FT es[4], em[4];
+      float ea[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        es[q] = xs[q];
+        em[q] = xm[q];
+        ea[q] = ax[q];
+        Tp[q] = T0[q];
+      }
+      for (int l = 0; l < K; ++l) {
+        const float4 tv = *reinterpret_cast<const float4*>(&sm.T[l][lane * 4]);
+        const float T1[4] = {tv.x, tv.y, tv.z, tv.w};
+        const float zlim = lv[w0 + 1 + l].z_surf + z_tol;
+        bool nop = true;
+        if (skipping) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            nop = nop && (!(use_ode[q] || judged[q]) || !(valid[q] && pz[q] <= zlim) ||
+                          step_is_noop<float, FT>(a.m, Tp[q], T1[q], es[q], em[q], ea[q]));
+        }
+        if (!(skipping && __all_sync(full, nop))) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if ((use_ode[q] || judged[q]) && valid[q] && pz[q] <= zlim)
+              point_step<float, FT>(a.m, Tp[q], T1[q], a.dt, es[q], em[q], ea[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Tp[q] = T1[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (use_ode[q]) {
+          xs[q] = es[q];
+          xm[q] = em[q];
+          ax[q] = ea[q];
+        }
+        if (judged[q]) {
+          const float e = fmaxf(fabsf(to_f(es[q]) - to_f(rs[q])), fabsf(to_f(em[q]) - to_f(rm[q])));
+          cnt.err = fmaxf(cnt.err, e);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (use_mlp[q]) {
+        xs[q] = rs[q];
+        xm[q] = rm[q];
+      }
+      T0[q] = sm.T[K - 1][lane * 4 + q];
+    }
+    __syncwarp();  // the next window overwrites sm.T and sm.X
+  }
+
+  Vec4<FT>::store(a.xas + g0, xs);
+  Vec4<FT>::store(a.xam + g0, xm);
+  Vec4<float>::store(a.aux + g0, ax);
+  bool ok = true;
+  float ts = -INFINITY;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ok = ok && finite_pair(xs[q], xm[q]);
+    if (valid[q]) ts = fmaxf(ts, point_tsat<float, FT>(a.m, xs[q], xm[q], ax[q]));
+  }
+  if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
+  if (a.tile_tsat) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ts = fmaxf(ts, __shfl_xor_sync(full, ts, o));
+    if (lane == 0) a.tile_tsat[tile] = ts + 0.5f;
+  }
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackArgs<float, FT> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  MlpDev& W = *reinterpret_cast<MlpDev*>(smem);
+  {
+    const uint4* src = static_cast<const uint4*>(a.mlp);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+    for (int i = threadIdx.x; i < int(sizeof(MlpDev) / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  HybWarp& sm = reinterpret_cast<HybWarp*>(smem + MLP_SMEM)[warp];
+  const float fdt = log10f(a.dt) + MLP_DT_SHIFT;
+  const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
+  unsigned long long done = 0;
+  HybCount cnt;
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(&a.work->next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= n_work) break;
+    hybrid_tile<FT>(a, W, sm, a.tile_list ? a.tile_list[w] : w, lane, fdt, cnt);
+    ++done;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt.surr += __shfl_xor_sync(0xffffffffu, cnt.surr, o);
+    cnt.ode += __shfl_xor_sync(0xffffffffu, cnt.ode, o);
+    cnt.judged += __shfl_xor_sync(0xffffffffu, cnt.judged, o);
+    cnt.err = fmaxf(cnt.err, __shfl_xor_sync(0xffffffffu, cnt.err, o));
+  }
+  if (lane == 0) {
+    if (done) atomicAdd(&a.work->tile_steps_active, done * (unsigned long long)(a.n_levels - 1));
+    if (cnt.surr) atomicAdd(&a.hyb->surrogate_windows, cnt.surr);
+    if (cnt.ode) atomicAdd(&a.hyb->ode_windows, cnt.ode);
+    if (cnt.judged) atomicAdd(&a.hyb->judge_samples, cnt.judged);
+    if (cnt.err > 0.0f) atomicMax(&a.hyb->judge_err_bits, __float_as_uint(cnt.err));
+  }
+}
+
+}  // namespace
+
+template <typename FT>
+int hybrid_blocks_per_sm() {
+  if (cudaFuncSetAttribute(k_track_hybrid<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(HYB_SMEM)) != cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track_hybrid<FT>, HYBRID_THREADS,
+                                                    HYB_SMEM) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+template <typename FT>
+cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int grid_blocks, cudaStream_t stream) {
+  if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
+  k_track_hybrid<FT><<<unsigned(grid_blocks), HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template int hybrid_blocks_per_sm<float>();
+template int hybrid_blocks_per_sm<KF>();
+template cudaError_t launch_track_hybrid<float>(const TrackArgs<float, float>&, int, cudaStream_t);
+template cudaError_t launch_track_hybrid<KF>(const TrackArgs<float, KF>&, int, cudaStream_t);
+
+}  // namespace ms

@@ -71,6 +71,13 @@ struct WorkCounters {
   unsigned long long tile_steps_active;  // running total of processed tile-steps
 };
 
+// Counters of the hybrid kernel (running totals, reset by ms_reset_stats).
+struct HybridCounters {
+  unsigned long long surrogate_windows, ode_windows, judge_samples;
+  unsigned int judge_err_bits;  // bits of the largest judged |dX| (>= 0, so integer order = float order)
+  unsigned int pad;
+};
+
 // Arguments of the run-track kernel (persistent warps pull 128-point tiles).
 template <typename AT, typename FT>
 struct TrackArgs {
@@ -90,6 +97,11 @@ struct TrackArgs {
   float* aux;
   float* tile_tsat;            // per tile: highest T at which formation still acts (+inf: busy)
   int* err;
+  // hybrid kernel only
+  const void* mlp;             // MlpDev of the attached surrogate
+  HybridCounters* hyb;
+  uint64_t judge_thresh;       // a window is judged if hash(point, level) < judge_thresh (2^32 = all)
+  int64_t level0;              // global index of the launch's first level
 };
 
 // Arguments of the active-set builder (reading A9): a tile joins the list
@@ -142,6 +154,22 @@ cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid
                          cudaStream_t stream);
 template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads);
+// The correction g on n independent points (device arrays, FP64) at the
+// temperatures T[i][0 .. n_T - 1] in turn.
+cudaError_t launch_correct(const ModelConstT<double>& m, int64_t n, int n_T, const double* T,
+                           double* xas, double* xam, cudaStream_t stream);
+
+// The inference weights of a surrogate (ms_surrogate.cu).
+struct MlpDev;
+const MlpDev* surrogate_weights(const ms_surrogate* s);
+
+// Hybrid hot kernel (an attached surrogate; AT = float).
+template <typename FT>
+cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int grid_blocks, cudaStream_t stream);
+template <typename FT>
+int hybrid_blocks_per_sm();
+constexpr int HYBRID_THREADS = 256;
+
 template <typename AT, typename FT>
 cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream);
 

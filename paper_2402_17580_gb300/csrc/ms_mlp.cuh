@@ -1,0 +1,165 @@
+// The learned surrogate: a 12 -> 64 -> 64 -> 3 MLP with GELU activations, BF16
+// weights and FP32 accumulation, advancing a point's fractions over a window
+// of K = 8 explicit steps.
+//
+// Inputs (12): X_as, X_am, X_beta at the window start, the 8 temperatures of
+// the window's new time levels as (T - 1000 K) / 1000 K, log10(dt) + 5.
+// Outputs (3): 1e6 x the window's diffusive residual of X_as, X_am, X_beta:
+// the fractions at the window end minus g(T_8, start fractions), g being the
+// correction of Sec. 2.2 at the window's last temperature.
+//
+// Parameter vector (FP32 master copy, 5187 values): W1[64][12], b1[64],
+// W2[64][64], b2[64], W3[3][64], b3[3] (weights row-major, out x in).
+// Inference layout (MlpDev): BF16 W1 [64][12] stored with a row stride of 24,
+// W2 [64][64] with a stride of 72, W3 [3][64] as 8 rows of stride 72 (zero
+// padding); FP32 biases.  The padded strides put the 8 rows a warp reads for
+// one B fragment of mma.m16n8k16 in 8 different groups of 4 banks, so the
+// fragment loads from shared memory are free of bank conflicts (a stride of
+// 64 BF16 = 128 bytes would put all 8 rows in the same bank).
+//
+// GELU is the tanh form 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))).
+// Activations are rounded to BF16 between layers in both the training and the
+// inference forward pass, so the two agree up to FP32 summation order.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+namespace ms {
+
+constexpr int MLP_IN = 12, MLP_H = 64, MLP_OUT = 3;
+constexpr int MLP_IN_PAD = 16, MLP_OUT_PAD = 8;
+constexpr int MLP_W1_LD = 24, MLP_W2_LD = 72, MLP_W3_LD = 72;  // BF16 row strides
+constexpr int MLP_X_LD = 24;   // row stride of the BF16 input tile [128][MLP_X_LD]
+constexpr int MLP_Y_LD = 4;    // row stride of the FP32 output tile [128][MLP_Y_LD]
+constexpr int MLP_OFF_W1 = 0;
+constexpr int MLP_OFF_B1 = MLP_OFF_W1 + MLP_H * MLP_IN;   // 768
+constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_H;            // 832
+constexpr int MLP_OFF_B2 = MLP_OFF_W2 + MLP_H * MLP_H;    // 4928
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_H;            // 4992
+constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_OUT * MLP_H;  // 5184
+constexpr int MLP_PARAMS = MLP_OFF_B3 + MLP_OUT;          // 5187
+constexpr int MLP_WINDOW = 8;                             // steps per surrogate window
+
+constexpr float MLP_T_SHIFT = 1000.0f, MLP_T_SCALE = 1.0e-3f;
+constexpr float MLP_DT_SHIFT = 5.0f, MLP_OUT_SCALE = 1.0e6f;
+
+struct MlpDev {
+  __nv_bfloat16 w1[MLP_H * MLP_W1_LD];
+  __nv_bfloat16 w2[MLP_H * MLP_W2_LD];
+  __nv_bfloat16 w3[MLP_OUT_PAD * MLP_W3_LD];
+  float b1[MLP_H];
+  float b2[MLP_H];
+  float b3[MLP_OUT_PAD];
+};
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr float GELU_C = 0.7978845608028654f;  // sqrt(2 / pi)
+constexpr float GELU_A = 0.044715f;
+
+__device__ __forceinline__ float gelu(float x) {
+  const float u = GELU_C * fmaf(GELU_A * x, x * x, x);
+  return 0.5f * x * (1.0f + tanh_approx(u));
+}
+
+__device__ __forceinline__ float gelu_grad(float x) {
+  const float u = GELU_C * fmaf(GELU_A * x, x * x, x);
+  const float th = tanh_approx(u);
+  return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * GELU_C * fmaf(3.0f * GELU_A, x * x, 1.0f);
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// D = A (16x16 bf16, row) * B (16x8 bf16, col) + C, FP32 accumulate.
+__device__ __forceinline__ void mma_bf16_16816(float* d, const uint32_t* a, uint32_t b0,
+                                               uint32_t b1, const float* c) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%10,%11,%12,%13};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]),
+        "f"(c[2]), "f"(c[3]));
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// Forward pass of one warp over 128 samples with tensor cores.  X: the
+// warp's [128][MLP_X_LD] BF16 inputs (features 12..15 zero) and Y: its
+// [128][MLP_Y_LD] FP32 outputs (columns 0..2 written), both in shared memory;
+// W: the weights (shared memory).  Rows are
+// processed in 8 tiles of 16; each layer's accumulator fragments are repacked
+// in registers as the next layer's A fragments.  Row tile mt is computed only
+// if bit mt of mt_mask (warp-uniform) is set.
+__device__ __forceinline__ void mlp_forward_warp(const MlpDev& W, const __nv_bfloat16* X, float* Y,
+                                                 int lane, uint32_t mt_mask = 0xffu) {
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll 1
+  for (int mt = 0; mt < 8; ++mt) {
+    if (!((mt_mask >> mt) & 1u)) continue;
+    const int ra = mt * 16 + g, rb = ra + 8;
+    uint32_t a[4];
+    a[0] = ld32(X + ra * MLP_X_LD + 2 * q);
+    a[1] = ld32(X + rb * MLP_X_LD + 2 * q);
+    a[2] = ld32(X + ra * MLP_X_LD + 8 + 2 * q);
+    a[3] = ld32(X + rb * MLP_X_LD + 8 + 2 * q);
+    float h[8][4];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const float c[4] = {W.b1[8 * t + 2 * q], W.b1[8 * t + 2 * q + 1], W.b1[8 * t + 2 * q],
+                          W.b1[8 * t + 2 * q + 1]};
+      const __nv_bfloat16* wr = W.w1 + (8 * t + g) * MLP_W1_LD;
+      mma_bf16_16816(h[t], a, ld32(wr + 2 * q), ld32(wr + 8 + 2 * q), c);
+    }
+    uint32_t a2[4][4];
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      a2[kc][0] = pack_bf16(gelu(h[2 * kc][0]), gelu(h[2 * kc][1]));
+      a2[kc][1] = pack_bf16(gelu(h[2 * kc][2]), gelu(h[2 * kc][3]));
+      a2[kc][2] = pack_bf16(gelu(h[2 * kc + 1][0]), gelu(h[2 * kc + 1][1]));
+      a2[kc][3] = pack_bf16(gelu(h[2 * kc + 1][2]), gelu(h[2 * kc + 1][3]));
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      h[t][0] = h[t][2] = W.b2[8 * t + 2 * q];
+      h[t][1] = h[t][3] = W.b2[8 * t + 2 * q + 1];
+      const __nv_bfloat16* wr = W.w2 + (8 * t + g) * MLP_W2_LD;
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        mma_bf16_16816(h[t], a2[kc], ld32(wr + 16 * kc + 2 * q), ld32(wr + 16 * kc + 8 + 2 * q),
+                       h[t]);
+    }
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      a2[kc][0] = pack_bf16(gelu(h[2 * kc][0]), gelu(h[2 * kc][1]));
+      a2[kc][1] = pack_bf16(gelu(h[2 * kc][2]), gelu(h[2 * kc][3]));
+      a2[kc][2] = pack_bf16(gelu(h[2 * kc + 1][0]), gelu(h[2 * kc + 1][1]));
+      a2[kc][3] = pack_bf16(gelu(h[2 * kc + 1][2]), gelu(h[2 * kc + 1][3]));
+    }
+    float y[4] = {W.b3[2 * q], W.b3[2 * q + 1], W.b3[2 * q], W.b3[2 * q + 1]};
+    const __nv_bfloat16* wr = W.w3 + g * MLP_W3_LD;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc)
+      mma_bf16_16816(y, a2[kc], ld32(wr + 16 * kc + 2 * q), ld32(wr + 16 * kc + 8 + 2 * q), y);
+    if (q < 2) {  // output columns 0..3 (3 is padding)
+      Y[ra * MLP_Y_LD + 2 * q] = y[0];
+      Y[ra * MLP_Y_LD + 2 * q + 1] = y[1];
+      Y[rb * MLP_Y_LD + 2 * q] = y[2];
+      Y[rb * MLP_Y_LD + 2 * q + 1] = y[3];
+    }
+  }
+}
+
+}  // namespace ms

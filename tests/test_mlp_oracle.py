@@ -1,0 +1,151 @@
+"""Pins of the surrogate's reference network (oracle/mlp.py) and of the
+hybrid window form of the oracle (orc_run_track_windows), on the CPU."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+import workloads
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e4, 1000), rng.normal(0, 1e-6, 1000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, -3.0078125, 65504.0]])
+    # exact ties of float32 values at bf16 precision, both parities
+    ties = (np.arange(1, 200, dtype=np.uint32) << 16 | 0x8000).view(np.float32) * np.float32(1.0)
+    x = np.concatenate([x, ties.astype(np.float64), -ties.astype(np.float64)])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(x), ref)
+
+
+def test_gelu_closed_forms():
+    x = np.linspace(-8, 8, 2001)
+    g = mlp.gelu(x)
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    np.testing.assert_allclose(g - mlp.gelu(-x), x, rtol=0, atol=1e-13)  # tanh is odd
+    assert abs(mlp.gelu(np.array([10.0]))[0] - 10.0) < 1e-12
+    assert abs(mlp.gelu(np.array([-10.0]))[0]) < 1e-12
+    # the tanh form approximates x * Phi(x) (Hendrycks and Gimpel 2016)
+    from scipy.special import erf
+    exact = 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+    assert np.max(np.abs(g - exact)) < 1e-3
+    h = 1e-6
+    fd = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    np.testing.assert_allclose(mlp.gelu_grad(x), fd, rtol=0, atol=1e-8)
+
+
+def test_single_path_network_by_hand():
+    """Only W1[5][3], W2[7][5], W3[2][7] and b3 are non-zero, so
+    y2 = c gelu(b gelu(a x3)) + d2 and y0, y1 are their biases; this fixes
+    the parameter layout (row-major out x in) and the layer order."""
+    a, b, c = 0.75, -1.25, 2.0
+    d = np.array([0.1, -0.2, 0.3])
+    p = np.zeros(mlp.N_PARAMS)
+    p[mlp.OFF_W1 + 5 * mlp.N_IN + 3] = a
+    p[mlp.OFF_W2 + 7 * mlp.N_H + 5] = b
+    p[mlp.OFF_W3 + 2 * mlp.N_H + 7] = c
+    p[mlp.OFF_B3:] = d
+    X = np.random.default_rng(2).normal(0, 1, (50, mlp.N_IN))
+
+    def g(v):
+        return 0.5 * v * (1.0 + math.tanh(math.sqrt(2.0 / math.pi) * (v + 0.044715 * v ** 3)))
+
+    y, _ = mlp.forward(p, X, bf16=False)
+    expect2 = np.array([c * g(b * g(a * x3)) + d[2] for x3 in X[:, 3]])
+    np.testing.assert_allclose(y[:, 2], expect2, rtol=1e-13, atol=1e-15)
+    np.testing.assert_array_equal(y[:, 0], d[0])
+    np.testing.assert_array_equal(y[:, 1], d[1])
+
+
+def test_gradient_against_finite_differences():
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 0.3, mlp.N_PARAMS)
+    X = rng.normal(0, 1, (40, mlp.N_IN))
+    T = rng.normal(0, 1, (40, mlp.N_OUT))
+    loss, g = mlp.loss_and_gradient(p, X, T, bf16=False)
+    blocks = [(mlp.OFF_W1, mlp.OFF_B1), (mlp.OFF_B1, mlp.OFF_W2), (mlp.OFF_W2, mlp.OFF_B2),
+              (mlp.OFF_B2, mlp.OFF_W3), (mlp.OFF_W3, mlp.OFF_B3), (mlp.OFF_B3, mlp.N_PARAMS)]
+    idx = np.concatenate([rng.choice(np.arange(lo, hi), min(12, hi - lo), replace=False)
+                          for lo, hi in blocks])
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (mlp.loss_and_gradient(pp, X, T, bf16=False)[0] -
+              mlp.loss_and_gradient(pm, X, T, bf16=False)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 + 1e-5 * abs(fd), (i, fd, g[i])
+    # the loss is the mean over samples and outputs
+    y, _ = mlp.forward(p, X, bf16=False)
+    assert abs(loss - np.mean((y - T) ** 2)) < 1e-14
+
+
+def test_zero_network_outputs_biases():
+    p = np.zeros(mlp.N_PARAMS)
+    p[mlp.OFF_B3:] = [1.0, 2.0, 3.0]
+    y, _ = mlp.forward(p, np.ones((4, mlp.N_IN)))
+    np.testing.assert_array_equal(y, np.tile([1.0, 2.0, 3.0], (4, 1)))
+
+
+# ------------------------------------------------------------ window form
+def _line(P, n=256, T0=353.0):
+    w = workloads.line_4096(n_points=n, n_steps=400)
+    src = w.specimens[0].source
+    src.tracks[:, 5] = P
+    src.T0 = T0
+    if P == 0.0:  # keep the points off the path (R = 0 gives T_max, reading A7)
+        w.specimens[0].grid.origin = (0.0, 1e-3, 0.0)
+    return w, src
+
+
+def test_windows_all_band_equal_explicit_run():
+    """A band wider than every temperature sends every window to the
+    explicit steps: the window form is then orc_run_track itself."""
+    w, src = _line(200.0)
+    x, y, z = w.specimens[0].grid.coords()
+    p = oracle.params()
+    a = oracle.State.uniform(x.size)
+    b = oracle.State.uniform(x.size)
+    oracle.run_track(a, src, x, y, z, 0, 203, w.dt, p)
+    n_mlp = oracle.run_track_windows(b, src, x, y, z, 0, 203, w.dt, band_half=1e9, p=p)
+    assert n_mlp.sum() == 0
+    np.testing.assert_array_equal(a.xas, b.xas)
+    np.testing.assert_array_equal(a.xam, b.xam)
+
+
+def test_windows_cold_quench_reduces_to_correction():
+    """No source (P = 0) at T0 = 353 K: every full window is outside the band
+    and applies g at 353 K, which from pure beta forms martensite
+    X_am = 1 - exp(-k_am (848 - 353)) (P4 quench); the short tail window
+    takes the explicit steps."""
+    w, src = _line(0.0)
+    x, y, z = w.specimens[0].grid.coords()
+    p = oracle.params()
+    st = oracle.State.uniform(x.size)
+    st.xas[:] = 0.0
+    st.xam[:] = 0.0
+    n_mlp = oracle.run_track_windows(st, src, x, y, z, 0, 8 * 5, w.dt, p=p)
+    assert np.all(n_mlp == 5)
+    np.testing.assert_allclose(st.xam, 1.0 - math.exp(-0.00415 * (848.0 - 353.0)), rtol=0,
+                               atol=1e-15)
+    assert np.all(st.xas == 0.0)
+    st2 = oracle.State.uniform(x.size)
+    n_mlp = oracle.run_track_windows(st2, src, x, y, z, 0, 8 * 5 + 3, w.dt, p=p)
+    assert np.all(n_mlp == 5)
+
+
+def test_windows_band_edges():
+    """A window whose temperatures sit inside the band takes the explicit
+    steps; just outside it keeps its fractions (zero network)."""
+    p = oracle.params()
+    for T_hold, in_band in ((848.0 + 39.0, True), (848.0 + 41.0, False), (1838.5, True),
+                            (1837.5, False), (1373.0 - 39.0, True), (1000.0, False)):
+        w, src = _line(0.0, n=4, T0=T_hold)
+        x, y, z = w.specimens[0].grid.coords()
+        st = oracle.State.uniform(4)
+        n_mlp = oracle.run_track_windows(st, src, x, y, z, 0, 16, w.dt, p=p)
+        assert np.all(n_mlp == (0 if in_band else 2)), T_hold

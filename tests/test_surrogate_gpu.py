@@ -1,0 +1,233 @@
+"""GPU tests of the window surrogate: the network kernels against the FP64
+reference network (oracle/mlp.py), the hybrid window machinery against the
+oracle's window form, and a trained surrogate against the explicit oracle.
+
+Tolerances.
+* Network: inference and training round weights, inputs and hidden
+  activations to BF16 like the reference, but evaluate tanh with
+  tanh.approx.f32 (relative error about 2^-11) and sum in FP32.  A hidden
+  activation can then land on the neighbouring BF16 value (2^-8 relative),
+  which moves an output by about |w| 2^-8 |a| ~ 1e-3 for the weight scales
+  used; outputs are held to 2e-2 x max(1, |y|) element-wise and 2e-3 on
+  average, gradients to 2e-2 of their norm.
+* Zero network: MLP windows reduce to the correction g along the window's
+  temperatures, so the hybrid is held to the explicit path's run tolerance
+  (1e-4) against the oracle's window form.
+* Trained network: no closed form; the bar is max|dX| <= 1e-2 against the
+  FP64 explicit oracle (100x the explicit FP32 path's bar), with the judge's
+  own per-window error and the zero network's error (correction g only, no
+  diffusion in MLP windows) reported beside it.  The held-out residual RMS
+  error must be below half the residuals' own RMS (the network explains at
+  least 75 % of their variance).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import workloads as wl
+from oracle import mlp as omlp
+from tests._util import max_abs_diff, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+RUN_TOL = 1e-4
+HYBRID_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import paper_2402_17580_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def _inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    xas = rng.uniform(0, 0.9, n)
+    xam = rng.uniform(0, 1, n) * (0.9 - xas)
+    T = rng.uniform(353, 1800, (n, 8))
+    x = np.empty((n, 12), dtype=np.float32)
+    x[:, 0], x[:, 1], x[:, 2] = xas, xam, 1 - xas - xam
+    x[:, 3:11] = (T - 1000) * 1e-3
+    x[:, 11] = rng.choice([0.0, -1.0, 1.0], n)
+    return x
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    p = np.empty(omlp.N_PARAMS, dtype=np.float32)
+    p[omlp.OFF_W1:omlp.OFF_B1] = rng.normal(0, 1 / math.sqrt(12), 64 * 12)
+    p[omlp.OFF_B1:omlp.OFF_W2] = rng.normal(0, 0.2, 64)
+    p[omlp.OFF_W2:omlp.OFF_B2] = rng.normal(0, 1 / 8, 64 * 64)
+    p[omlp.OFF_B2:omlp.OFF_W3] = rng.normal(0, 0.2, 64)
+    p[omlp.OFF_W3:omlp.OFF_B3] = rng.normal(0, 1 / 8, 3 * 64)
+    p[omlp.OFF_B3:] = rng.normal(0, 0.2, 3)
+    return p
+
+
+def test_forward_matches_reference_network(ms, torch):
+    n = 128 * 37 + 45  # several warps and CTAs and a ragged tail
+    x = np.concatenate([_inputs(n - 200, 1), np.random.default_rng(2).normal(0, 1, (200, 12))
+                        .astype(np.float32)])
+    p = _params(3)
+    s = ms.Surrogate(p)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    s.forward(xd.data_ptr(), yd.data_ptr(), n)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy().astype(np.float64)
+    ref, _ = omlp.forward(p.astype(np.float64), x.astype(np.float64), bf16=True)
+    err = np.abs(y - ref)
+    assert np.all(err <= 2e-2 * np.maximum(1.0, np.abs(ref))), err.max()
+    assert err.mean() <= 2e-3
+    np.testing.assert_array_equal(s.params(), p)
+    s.close()
+
+
+def test_gradient_matches_reference_network(ms, torch):
+    n = 3000
+    x = _inputs(n, 4)
+    t = np.random.default_rng(5).normal(0, 0.5, (n, 3)).astype(np.float32)
+    p = _params(6)
+    s = ms.Surrogate(p)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    gd = torch.empty(omlp.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = s.gradient(xd.data_ptr(), td.data_ptr(), n, gd.data_ptr())
+    g = gd.cpu().numpy().astype(np.float64)
+    ref_loss, ref_g = omlp.loss_and_gradient(p.astype(np.float64), x.astype(np.float64),
+                                             t.astype(np.float64), bf16=True)
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    assert np.linalg.norm(g - ref_g) <= 2e-2 * np.linalg.norm(ref_g)
+    s.close()
+
+
+def test_training_reduces_loss(ms, torch):
+    """Adam on a smooth synthetic target (numpy, seeded) lowers the loss by
+    more than 5x in 400 steps."""
+    n = 20000
+    x = _inputs(n, 7)
+    A = np.random.default_rng(8).normal(0, 1, (12, 3))
+    t = np.tanh(x.astype(np.float64) @ A).astype(np.float32)
+    from paper_2402_17580_gb300 import surrogate
+    s = ms.Surrogate(surrogate.init_params(9))
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    first = s.gradient(xd.data_ptr(), td.data_ptr(), n)
+    for _ in range(400):
+        s.train_step(xd.data_ptr(), td.data_ptr(), n, 3e-3)
+    last = s.gradient(xd.data_ptr(), td.data_ptr(), n)
+    assert last < first / 5, (first, last)
+    assert np.all(np.isfinite(s.params()))
+    s.close()
+
+
+# ------------------------------------------------------------- hybrid path
+def _run(ms, w, surrogate, judge=0.0, **kw):
+    ctx = ms.Context(w.n_points, T_thr=w.T_thr, **kw)
+    ctx.set_points([sp.grid for sp in w.specimens])
+    ctx.fill_state(w.init_xas, w.init_xam)
+    if surrogate is not None:
+        ctx.set_surrogate(surrogate, judge)
+    ctx.run_track([sp.source for sp in w.specimens], w.n_steps, w.dt)
+    return ctx, ctx.fractions()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_zero_network_hybrid_matches_window_oracle(ms, precision):
+    """A network with all parameters 0 outputs 0, so every MLP window only
+    applies g at its temperatures in turn: the hybrid
+    kernel must then follow orc_run_track_windows (band test, window
+    classification, fallback steps) on every point of the 4096-point line."""
+    w = wl.line_4096()
+    s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
+    ctx, g = _run(ms, w, s, judge=1.0, precision=precision, steps_per_launch=128)
+    st = ctx.stats()
+    sp = w.specimens[0]
+    x, y, z = sp.grid.coords()
+    o = orc.State.uniform(w.n_points, w.init_xas, w.init_xam)
+    p = oracle_params()
+    n_mlp = orc.run_track_windows(o, sp.source, x, y, z, 0, w.n_steps, w.dt, p=p)
+    T_last = orc.temperature(sp.source, x, y, z, w.n_steps * w.dt)[0]
+    of = np.stack(orc.fractions(o, T_last, p))
+    assert max_abs_diff(g, of) <= RUN_TOL
+    assert st.surrogate_windows > 0.5 * w.n_points * w.n_steps / 8
+    assert abs(st.surrogate_windows - int(n_mlp.sum())) <= 1e-3 * n_mlp.sum()
+    assert st.judge_samples == st.surrogate_windows  # judge_frac = 1
+    assert st.surrogate_windows + st.ode_windows == w.n_points * w.n_steps // 8
+    assert 0.0 < st.judge_max_err < 1.0
+    ctx.close()
+    s.close()
+
+
+def test_hybrid_rejects_fp64_and_bad_fraction(ms):
+    s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
+    ctx = ms.Context(1000, precision=ms.MS_F64)
+    with pytest.raises(ms.MSError, match="UNSUPPORTED"):
+        ctx.set_surrogate(s, 0.0)
+    ctx.close()
+    ctx = ms.Context(1000)
+    with pytest.raises(ms.MSError, match="INVALID_ARG"):
+        ctx.set_surrogate(s, 1.5)
+    ctx.set_surrogate(s, 0.5)
+    ctx.set_surrogate(None)
+    ctx.close()
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def trained(ms, torch):
+    from paper_2402_17580_gb300 import surrogate
+    w = wl.surrogate_lines(n_lines=64)
+    data = surrogate.collect_windows(w.specimens, w.n_steps, w.dt, seed=1)
+    s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2)
+    held = wl.surrogate_lines(seed=wl.SEED_BASE + 40, n_lines=16)
+    hd = surrogate.collect_windows(held.specimens, held.n_steps, held.dt, seed=3)
+    s.report = {"windows": len(data.X), "seen": data.windows_seen, "band": data.band_windows,
+                "held_out": surrogate.evaluate(s, hd.X, hd.Y)}
+    yield s
+    s.close()
+
+
+def test_trained_surrogate_held_out_error(trained):
+    r = trained.report
+    print("surrogate", r)
+    assert r["windows"] > 10000
+    h = r["held_out"]
+    assert h["rms"] < 0.5 * h["target_rms"]
+
+
+def test_trained_hybrid_against_oracle(ms, trained):
+    """A 96 x 96 x 16 block under 6 serpentine tracks (the 256^3 block's
+    process parameters), 4000 steps, T_thr = 600 K: the hybrid path against
+    the FP64 explicit oracle on 256 sampled points."""
+    w = wl.block_256(dims=(96, 96, 16), n_tracks=6, n_steps=4000)
+    ctx, g = _run(ms, w, trained, judge=0.01)
+    st = ctx.stats()
+    idx = np.random.default_rng(10).choice(w.n_points, 256, replace=False)
+    # include the points the tracks pass over
+    idx = np.unique(np.concatenate([idx, np.arange(0, w.n_points, 9973)]))
+    from tests._util import oracle_workload
+    o = oracle_workload(w, idx)
+    err = max_abs_diff(g, o, idx)
+    share = st.surrogate_windows / max(1, st.surrogate_windows + st.ode_windows)
+    zero = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
+    zctx, zg = _run(ms, w, zero)
+    err0 = max_abs_diff(zg, o, idx)
+    print(f"hybrid max|dX| {err:.3e} (zero network {err0:.3e}), MLP share {share:.3f}, "
+          f"judge {st.judge_samples} windows max {st.judge_max_err:.3e}")
+    assert st.surrogate_windows > 0 and st.judge_samples > 0
+    assert err <= HYBRID_TOL
+    zctx.close()
+    zero.close()
+    ctx.close()

@@ -23,6 +23,9 @@ v ~ 1 m/s, P ~ 200 W, hatch 80-120 um, layer 30 um):
                   rotated by 67 degrees per layer, 0.5 s per layer (scan, then
                   linear interlayer cool-down to T0).
 
+* ``surrogate_lines``  training histories of the window surrogate: short
+                  serpentines over lines at random depth and lateral offset.
+
 Seeds default to 2402175800 + the workload number (1 .. 5).
 """
 from __future__ import annotations
@@ -236,6 +239,31 @@ def part_512(dims=(512, 512, 256), n_layers=5, layer_t=30e-6, tracks_per_layer=5
 # beta range, mushy zone, melt.
 T_BANDS = ((250.0, 293.0), (293.0, 848.0), (848.0, 935.0), (935.0, 1273.0),
            (1273.0, 1373.0), (1373.0, 1878.0), (1878.0, 1928.0), (1928.0, 2600.0))
+
+
+def surrogate_lines(seed=None, n_lines=128, n_points=512, n_tracks=3, hatch=1e-4,
+                    n_steps=2800, dt=1e-5) -> Workload:
+    """Training histories of the window surrogate: n_lines specimens, each a
+    line of n_points along x (10 um spacing) at a seeded depth U(0, 100) um
+    and lateral offset U(0, (n_tracks - 1) hatch + 100 um), under a short
+    serpentine of n_tracks tracks along the line with its own P ~ U(150, 250)
+    W and v ~ U(0.8, 1.2) m/s, so the lines see single passes, reheating by
+    the neighbouring tracks and the receding-source cooling tail."""
+    seed = SEED_BASE + 4 if seed is None else seed
+    rng = np.random.default_rng(seed)
+    length = (n_points - 1) * 1e-5
+    specs = []
+    for _ in range(n_lines):
+        P = rng.uniform(150.0, 250.0, n_tracks)
+        v = rng.uniform(0.8, 1.2, n_tracks)
+        depth = rng.uniform(0.0, 1e-4)
+        y = rng.uniform(0.0, (n_tracks - 1) * hatch + 1e-4)
+        tracks, _ = serpentine_x([j * hatch for j in range(n_tracks)], 0.0, length, v, P)
+        grid = Grid((0.0, y, -depth), (1e-5, 1e-5, -1e-5), (n_points, 1, 1))
+        specs.append(Specimen(grid, HeatSource(tracks, _one_layer())))
+    w = Workload("surrogate_lines", specs, n_steps, dt, T_thr=0.0)
+    w.meta.update(seed=seed)
+    return w
 
 
 def random_states(n, seed, block=1, edge_frac=0.15):
