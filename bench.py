@@ -59,6 +59,12 @@ def parse_args():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the project autotuner (S, CTA size, graph replay)")
     ap.add_argument("--graph", action="store_true", help="replay ms_run_track as a CUDA graph")
+    ap.add_argument("--no-hybrid", dest="hybrid", action="store_false",
+                    help="skip the window-surrogate (hybrid) measurement")
+    ap.add_argument("--no-f64", dest="f64", action="store_false",
+                    help="skip the full-FP64 subset measurement")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="run only the first N time steps of the workload (stated in config)")
     return ap.parse_args()
 
 
@@ -75,6 +81,8 @@ def make_workload(name, rank=0):
         return wl.line_4096()
     if name == "batch_64":
         return wl.batch_64(seed=wl.SEED_BASE + 3 + 1000 * rank)
+    if name == "part_512":
+        return wl.part_512()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -85,6 +93,8 @@ def workload_config(w):
            "T_thr_K": w.T_thr, "point_updates_per_step": w.point_updates}
     if len(w.specimens) == 1:
         cfg["grid"] = "x".join(str(d) for d in w.specimens[0].grid.dims)
+    if "full_time_steps" in w.meta:
+        cfg["segment"] = f"first {w.n_steps} of {w.meta['full_time_steps']} time steps"
     return cfg
 
 
@@ -301,6 +311,9 @@ def run_ours(args):
     ms.load()
 
     w = make_workload(args.workload, rank)
+    if args.time_steps:
+        w.meta["full_time_steps"] = w.n_steps
+        w.n_steps = min(w.n_steps, args.time_steps)
     prec = {"f32": ms.MS_F32, "f64acc": ms.MS_F64ACC, "kahan": ms.MS_KAHAN}[args.precision]
     flags = ms._binding.MS_FLAG_TIME_KERNELS | (ms._binding.MS_FLAG_GRAPH if args.graph else 0)
     over = dict(T_thr=w.T_thr, precision=prec, flags=flags)
@@ -425,15 +438,21 @@ def run_ours(args):
         out["autotune"] = tuned.as_dict()
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e_pass(ctx, w, srcs, args, ms, torch)
+    sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g = ctx.fractions()   # state after the last full pass
         rate, idx, ofr, threads, desc, el = oracle_sample(w, args.cpu_seconds)
+        sample = (idx, ofr)
         gs = np.stack(g)[:, idx]
         out["max_abs_dX"] = float(np.max(np.abs(gs - ofr)))
         out["max_abs_dX_basis"] = f"{idx.size} seeded sample points vs the FP64 oracle"
         out["sum_err"] = float(np.max(np.abs(np.stack(g).sum(axis=0) - 1.0)))
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": desc}
+    if rank == 0 and world == 1 and args.f64 and len(w.specimens) == 1:
+        out["f64"] = f64_pass(ctx, w, srcs, ms)
+    if rank == 0 and world == 1 and args.hybrid and prec in (ms.MS_F32, ms.MS_KAHAN):
+        out["hybrid"] = hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, value, sample)
     if rank == 0 and world == 1 and not args.no_d6:
         ctx.close()
         out["roofline_ms_step"] = d6_layouts(ms, torch)
@@ -442,6 +461,81 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def f64_pass(ctx, w, srcs, ms, n_sub=100000, seed=2402175899):
+    """The full-FP64 GPU path (MS_F64: FP64 temperatures, rates and
+    fractions, no skipping) on a seeded subset of the workload's points:
+    its throughput, and max|dX| of the plain FP32 run against it on the same
+    points (the GPU spot-check of the FP32 path at full size)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(w.n_points, min(n_sub, w.n_points), replace=False))
+    c = ms.Context(idx.size, T_thr=0.0, precision=ms.MS_F64,
+                   flags=ms._binding.MS_FLAG_TIME_KERNELS)
+    c.set_points_subset(w.specimens[0].grid, idx)
+    c.fill_state(w.init_xas, w.init_xam)
+    c.run_track(srcs, 256, w.dt)          # warm-up
+    c.fill_state(w.init_xas, w.init_xam)
+    c.reset_stats()
+    c.run_track(srcs, w.n_steps, w.dt)
+    c.synchronize()
+    t = c.stats().last_run_ms
+    d, s32, s64 = ctx.verify(c, idx)      # device-side reductions (ms_verify)
+    c.close()
+    return {"value": idx.size * w.n_steps / (t * 1e-3), "unit": UNIT, "points": int(idx.size),
+            "ms": t, "max_abs_dX_f32_vs_f64": d, "sum_err_f32": s32, "sum_err_f64": s64,
+            "path": "MS_F64 on a seeded point subset (ms_set_points_subset), T_thr = 0; "
+                    "compared on the device by ms_verify"}
+
+
+def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sample):
+    """The same workload with the window surrogate attached (hybrid kernel):
+    train it (windows from the library's FP64 path on seeded training lines,
+    Adam in the library's kernels), then time the hybrid passes exactly like
+    the plain ones.  Reports its throughput, the share of MLP windows, the
+    judge's 1 % sample error and max|dX| on the oracle sample points."""
+    import numpy as np
+    from paper_2402_17580_gb300 import surrogate
+    t0 = time.perf_counter()
+    import workloads as wl
+    lines = wl.surrogate_lines(n_lines=128)
+    data = surrogate.collect_windows(lines.specimens, lines.n_steps, lines.dt, seed=1)
+    t1 = time.perf_counter()
+    s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2)
+    t2 = time.perf_counter()
+    ctx.set_surrogate(s, 0.01)
+    one = lambda: (ctx.fill_state(w.init_xas, w.init_xam), ctx.run_track(srcs, w.n_steps, w.dt))
+    one()
+    ctx.synchronize()
+    ctx.reset_stats()
+    times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one()
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = ctx.stats()
+    t = sum(times) / len(times)
+    res = {"value": w.point_updates / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+           "vs_plain": w.point_updates / (t * 1e-3) / plain_value,
+           "mlp_window_share": st.surrogate_windows / max(1, st.surrogate_windows + st.ode_windows),
+           "judge_samples": int(st.judge_samples), "judge_max_err": st.judge_max_err,
+           "training": {"windows": int(len(data.X)), "collect_s": round(t1 - t0, 2),
+                        "train_s": round(t2 - t1, 2), "iters": 20000, "batch": 32768},
+           "kernel": "k_track_hybrid (judge 1 %)"}
+    if sample is not None:
+        idx, ofr = sample
+        g = np.stack(ctx.fractions())
+        res["max_abs_dX"] = float(np.max(np.abs(g[:, idx] - ofr)))
+    ctx.set_surrogate(None)
+    s.close()
+    return res
 
 
 def e2e_pass(ctx, w, srcs, args, ms, torch):

@@ -216,7 +216,9 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out);
 void ms_destroy(ms_ctx* ctx);
 
 /* Make the context launch on an existing CUDA stream (cudaStream_t passed as
- * void*; NULL = the context's own stream).  The stream is borrowed. */
+ * void*; NULL = the context's own stream).  The stream is borrowed.  A
+ * caller whose work runs on the legacy default stream (whose handle is NULL,
+ * e.g. PyTorch's default stream) passes cudaStreamLegacy instead. */
 int ms_set_stream(ms_ctx* ctx, void* cuda_stream);
 
 /* Geometry for ms_run_track: n_specimens regular grids whose point counts add
@@ -379,7 +381,9 @@ typedef struct ms_surrogate ms_surrogate;
 int ms_surrogate_create(const float* params, ms_surrogate** out);
 /* Free a surrogate (NULL is a no-op).  Detach it from every context first. */
 void ms_surrogate_destroy(ms_surrogate* s);
-/* Run later calls on cuda_stream (NULL = the surrogate's own stream). */
+/* Run later calls on cuda_stream (NULL = the surrogate's own stream; pass
+ * cudaStreamLegacy for the legacy default stream).  Data written by other
+ * streams must be complete before a call reads it. */
 int ms_surrogate_set_stream(ms_surrogate* s, void* cuda_stream);
 /* Copy the FP32 master parameters to a host array of MS_MLP_PARAMS floats. */
 int ms_surrogate_get_params(ms_surrogate* s, float* params);
@@ -417,6 +421,21 @@ int ms_apply_correction(ms_ctx* ctx, const double* T, int32_t n_T, double* x_as,
  * The surrogate must outlive its attachment.  Requires MS_F32 or MS_KAHAN.
  * Errors: INVALID_ARG, UNSUPPORTED (other precisions). */
 int ms_set_surrogate(ms_ctx* ctx, const ms_surrogate* s, double judge_frac);
+
+/* Verification on the device, without copying the state to the host: with
+ * j = idx[i] (or i when idx is NULL), compares point j of ctx with point i of
+ * ref for i < n over the four fractions X_as, X_am, X_beta, X_liq (each with
+ * its context's current temperature) and writes
+ *   out[0] = max over i of the largest |X(ctx, j) - X(ref, i)|,
+ *   out[1] = max over ctx's points of |X_as + X_am + X_beta + X_liq - 1|,
+ *   out[2] = the same for ref's points
+ * (NaN reported as +inf).  Typical use: ref an MS_F64 context on a point
+ * subset (ms_set_points_subset) of ctx's grid, idx the subset's indices.
+ * idx is a host array (copied).  Synchronises both streams.
+ * Errors: INVALID_ARG (n larger than ref's points, or than ctx's without idx,
+ * an index out of range, contexts on different devices), STATE (no
+ * temperature known yet), NONFINITE, CUDA. */
+int ms_verify(ms_ctx* ctx, ms_ctx* ref, const int64_t* idx, int64_t n, double* out);
 
 /* Counters and the sticky device error word (synchronises the stream). */
 int ms_stats(ms_ctx* ctx, ms_stats_t* out);

@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
     lib.ms_surrogate_train_step.argtypes = [P, P, P, i64, d, ctypes.POINTER(d)]
     lib.ms_set_surrogate.argtypes = [P, P, d]
     lib.ms_apply_correction.argtypes = [P, P, i32, P, P, i64]
+    lib.ms_verify.argtypes = [P, P, P, i64, P]
     for i, s in enumerate(STRUCTS):
         if lib.ms_struct_size(i) != ctypes.sizeof(s):
             raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
@@ -247,6 +248,19 @@ class Context:
         _check(self._lib.ms_set_surrogate(self._h, surrogate.handle if surrogate else None,
                                           float(judge_frac)), "ms_set_surrogate")
         self._surrogate = surrogate
+
+    def verify(self, ref: "Context", idx=None, n=None):
+        """Device-side verification against another context (ms_verify):
+        (max |dX| over the four fractions, max |sum - 1| of self, of ref)."""
+        out = np.zeros(3)
+        if idx is not None:
+            idx = np.ascontiguousarray(idx, dtype=np.int64)
+            n = idx.size
+        elif n is None:
+            n = ref.n
+        _check(self._lib.ms_verify(self._h, ref.handle, None if idx is None else _ptr(idx), int(n),
+                                   _ptr(out)), "ms_verify")
+        return float(out[0]), float(out[1]), float(out[2])
 
     def apply_correction(self, T, xas, xam):
         """The correction g applied to independent points at the temperatures

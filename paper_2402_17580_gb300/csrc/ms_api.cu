@@ -975,12 +975,13 @@ int ms_run_track(ms_ctx* c, const ms_heat_source* src, int64_t n_steps, double d
   return MS_OK;
 }
 
-int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double* xliq) {
-  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+// The four fractions of every point in natural order into the device staging
+// buffer (X_as, X_am, then X_beta, X_liq if with_beta), on the context stream.
+int stage_fractions(ms_ctx* c, bool with_beta) {
   const int64_t n = c->n_points;
   double* d = c->stage_d;
   int rc;
-  if (xbeta || xliq) {
+  if (with_beta) {
     const float* T = nullptr;
     if (c->T_last) {
       T = c->T_last;
@@ -1006,6 +1007,15 @@ int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double*
                                         (const FT*)c->xas_d, (const FT*)c->xam_d, c->aux_d,
                                         d, d + n, nullptr, c->stream);
     }));
+  return MS_OK;
+}
+
+int ms_get_fractions(ms_ctx* c, double* xas, double* xam, double* xbeta, double* xliq) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  const int64_t n = c->n_points;
+  double* d = c->stage_d;
+  int rc;
+  if ((rc = stage_fractions(c, xbeta || xliq)) != MS_OK) return rc;
   const size_t nb = size_t(n) * sizeof(double);
   if (xas) MS_CUDA(cudaMemcpyAsync(xas, d, nb, cudaMemcpyDeviceToHost, c->stream));
   if (xam) MS_CUDA(cudaMemcpyAsync(xam, d + n, nb, cudaMemcpyDeviceToHost, c->stream));
@@ -1102,6 +1112,35 @@ int ms_set_state_blob(ms_ctx* c, const void* blob, size_t bytes) {
   c->dt = h.dt;
   c->T_last = nullptr;
   return MS_OK;
+}
+
+int ms_verify(ms_ctx* c, ms_ctx* ref, const int64_t* idx, int64_t n, double* out) {
+  if (!c || !ref || !out || n < 0) return fail(MS_ERR_INVALID_ARG, "bad argument");
+  if (n > ref->n_points || (!idx && n > c->n_points))
+    return fail(MS_ERR_INVALID_ARG, "n exceeds the points of a context");
+  if (c->device != ref->device) return fail(MS_ERR_INVALID_ARG, "contexts on different devices");
+  for (int64_t i = 0; idx && i < n; ++i)
+    if (idx[i] < 0 || idx[i] >= c->n_points) return fail(MS_ERR_INVALID_ARG, "idx[%lld] out of range", (long long)i);
+  int rc;
+  if ((rc = stage_fractions(ref, true)) != MS_OK) return rc;
+  MS_CUDA(cudaStreamSynchronize(ref->stream));
+  if ((rc = stage_fractions(c, true)) != MS_OK) return rc;
+  int64_t* idx_d = nullptr;
+  double* out_d = nullptr;
+  cudaError_t e = cudaMalloc(&out_d, 3 * sizeof(double));
+  if (e == cudaSuccess && idx && n > 0) e = cudaMalloc(&idx_d, size_t(n) * sizeof(int64_t));
+  if (e == cudaSuccess && idx_d)
+    e = cudaMemcpyAsync(idx_d, idx, size_t(n) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = ms::launch_verify(c->stage_d, c->n_points, ref->stage_d, ref->n_points, n, idx_d, out_d,
+                          c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, out_d, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(idx_d);
+  cudaFree(out_d);
+  if (e != cudaSuccess) return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(e));
+  return check_device_error(c);
 }
 
 int ms_apply_correction(ms_ctx* c, const double* T, int32_t n_T, double* x_as, double* x_am,

@@ -349,7 +349,8 @@ __device__ __forceinline__ AT source_term(const SrcEntryT<AT>& e, AT px, AT py, 
   const AT r2 = Fn<AT>::fma(xi, xi, perp2);
   const AT rinv = Fn<AT>::rsqrt(r2);
   const AT w = Fn<AT>::fma(r2, rinv, Fn<AT>::abs(xi));  // R + |xi|
-  const AT rpx = xi >= AT(0) ? w : perp2 * Fn<AT>::rcp(w);
+  const AT inv_w = Fn<AT>::rcp(w);  // unconditional, so the select below stays branch-free
+  const AT rpx = xi >= AT(0) ? w : perp2 * inv_w;
   return rinv * Fn<AT>::ex2(Fn<AT>::fma(e.cR, rpx, e.lC));
 }
 

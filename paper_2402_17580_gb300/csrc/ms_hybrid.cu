@@ -39,10 +39,13 @@ namespace {
 constexpr int HYB_WARPS = HYBRID_THREADS / 32;
 constexpr float BAND_HALF_WIDTH = 40.0f;
 
+// Point q of lane l is row l + 32 q of the warp's tile in all three arrays,
+// so a warp's per-point accesses for one q are consecutive (no bank
+// conflicts); the ODE path reads T the same way.
 struct HybWarp {
   float T[MLP_WINDOW][TILE];                 // the window's new temperatures
   __nv_bfloat16 X[TILE][MLP_X_LD];           // MLP inputs (padded rows)
-  float Y[TILE][MLP_Y_LD];                   // MLP outputs
+  float Y[MLP_Y_COLS][TILE];                 // MLP outputs, column-major
 };
 constexpr size_t MLP_SMEM = (sizeof(MlpDev) + 127) / 128 * 128;
 constexpr size_t HYB_SMEM = MLP_SMEM + HYB_WARPS * sizeof(HybWarp);
@@ -124,7 +127,8 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       const SrcLevelT<float> L = lv[lvl];
       float T1[4];
       temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, T1);
-      *reinterpret_cast<float4*>(&sm.T[l][lane * 4]) = make_float4(T1[0], T1[1], T1[2], T1[3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sm.T[l][lane + 32 * q] = T1[q];
       const float zlim = L.z_surf + z_tol;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -162,10 +166,19 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
     }
     const unsigned bal = __ballot_sync(full, lane_mlp);
     if (bal) {
+      // row tile mt holds rows 16 mt .. 16 mt + 15: point q = mt / 2 of lanes
+      // 16 (mt % 2) .. 16 (mt % 2) + 15
+      uint32_t mt_mask = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned bq = __ballot_sync(full, use_mlp[q]);
+        if (bq & 0x0000ffffu) mt_mask |= 1u << (2 * q);
+        if (bq & 0xffff0000u) mt_mask |= 2u << (2 * q);
+      }
       // inputs: fractions at the window start, the 8 new temperatures, log10(dt) + 5
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int row = lane * 4 + q;
+        const int row = lane + 32 * q;
         float f[MLP_IN_PAD];
 #pragma unroll
         for (int k = 0; k < MLP_IN_PAD; ++k) f[k] = 0.0f;
@@ -186,23 +199,19 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         *reinterpret_cast<uint4*>(&sm.X[row][0]) = v0;
         *reinterpret_cast<uint4*>(&sm.X[row][8]) = v1;
       }
-      uint32_t mt_mask = 0;
-#pragma unroll
-      for (int mt = 0; mt < 8; ++mt)
-        if ((bal >> (4 * mt)) & 0xfu) mt_mask |= 1u << mt;
       __syncwarp();
       mlp_forward_warp(W, &sm.X[0][0], &sm.Y[0][0], lane, mt_mask);
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (!use_mlp[q]) continue;
-        const int row = lane * 4 + q;
+        const int row = lane + 32 * q;
         const float T8 = sm.T[MLP_WINDOW - 1][row];
         FT nas = xs[q], nam = xm[q];
         // the instantaneous part, exact along the window's temperature path
         for (int l = 0; l < MLP_WINDOW; ++l) correct<float, FT>(a.m, sm.T[l][row], nas, nam);
-        nas = nas + FT(sm.Y[row][0] * (1.0f / MLP_OUT_SCALE));
-        nam = nam + FT(sm.Y[row][1] * (1.0f / MLP_OUT_SCALE));
+        nas = nas + FT(sm.Y[0][row] * (1.0f / MLP_OUT_SCALE));
+        nam = nam + FT(sm.Y[1][row] * (1.0f / MLP_OUT_SCALE));
         correct<float, FT>(a.m, T8, nas, nam);
         rs[q] = nas;
         rm[q] = nam;
@@ -221,8 +230,9 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         Tp[q] = T0[q];
       }
       for (int l = 0; l < K; ++l) {
-        const float4 tv = *reinterpret_cast<const float4*>(&sm.T[l][lane * 4]);
-        const float T1[4] = {tv.x, tv.y, tv.z, tv.w};
+        float T1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) T1[q] = sm.T[l][lane + 32 * q];
         const float zlim = lv[w0 + 1 + l].z_surf + z_tol;
         bool nop = true;
         if (skipping) {
@@ -259,7 +269,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         xs[q] = rs[q];
         xm[q] = rm[q];
       }
-      T0[q] = sm.T[K - 1][lane * 4 + q];
+      T0[q] = sm.T[K - 1][lane + 32 * q];
     }
     __syncwarp();  // the next window overwrites sm.T and sm.X
   }

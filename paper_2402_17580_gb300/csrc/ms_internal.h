@@ -154,6 +154,10 @@ cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid
                          cudaStream_t stream);
 template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads);
+// Verification reductions (k_verify): out[0..2] device doubles.
+cudaError_t launch_verify(const double* a, int64_t na, const double* b, int64_t nb, int64_t n,
+                          const int64_t* idx, double* out, cudaStream_t stream);
+
 // The correction g on n independent points (device arrays, FP64) at the
 // temperatures T[i][0 .. n_T - 1] in turn.
 cudaError_t launch_correct(const ModelConstT<double>& m, int64_t n, int n_T, const double* T,

@@ -17,11 +17,13 @@
 //  k_set_state / k_get_state / k_fractions   natural order <-> padded layout.
 //  k_correct     the correction g alone on independent points (FP64), for the
 //                surrogate's training targets.
+//  k_verify      max |dX| between two contexts' fractions and max |sum - 1|.
 //
 // Kernels are templated on the arithmetic type AT (float on the SFU, double
 // for the full-FP64 path) and the fraction type FT (float, double, KF).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -398,6 +400,42 @@ __global__ void k_correct(const ModelConstT<double> m, int64_t n, int n_T, const
   xam[i] = b;
 }
 
+// Verification reductions over natural-order fraction arrays a (na points)
+// and b (nb points), 4 arrays each (X_as, X_am, X_beta, X_liq):
+// out[0] = max over i < n of max_k |a_k[j] - b_k[i]| (j = idx[i], or i),
+// out[1] = max over a's points of |sum_k a_k - 1|, out[2] the same for b.
+// Non-negative doubles order like their bit patterns, so the maxima are
+// atomicMax on the bits; NaN is reported as +inf.
+__device__ __forceinline__ double nan_to_inf(double v) { return v == v ? v : INFINITY; }
+
+__global__ void k_verify(const double* a, int64_t na, const double* b, int64_t nb, int64_t n,
+                         const int64_t* idx, unsigned long long* out) {
+  double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+  const int64_t top = max(max(na, nb), n);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < top;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    if (i < n) {
+      const int64_t j = idx ? idx[i] : i;
+      double d = 0.0;
+      for (int k = 0; k < 4; ++k) d = fmax(d, nan_to_inf(fabs(a[k * na + j] - b[k * nb + i])));
+      m0 = fmax(m0, d);
+    }
+    if (i < na) m1 = fmax(m1, nan_to_inf(fabs(a[i] + a[na + i] + a[2 * na + i] + a[3 * na + i] - 1.0)));
+    if (i < nb) m2 = fmax(m2, nan_to_inf(fabs(b[i] + b[nb + i] + b[2 * nb + i] + b[3 * nb + i] - 1.0)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out + 0, (unsigned long long)__double_as_longlong(m0));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(m1));
+    atomicMax(out + 2, (unsigned long long)__double_as_longlong(m2));
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) {
   return unsigned((n + threads - 1) / threads);
 }
@@ -422,6 +460,17 @@ cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream) {
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   k_fill_f32<<<blocks_for(n, 256), 256, 0, stream>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_verify(const double* a, int64_t na, const double* b, int64_t nb, int64_t n,
+                          const int64_t* idx, double* out, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 3 * sizeof(double), stream);
+  if (e != cudaSuccess) return e;
+  const int64_t top = std::max(std::max(na, nb), n);
+  const unsigned blocks = unsigned(std::min<int64_t>((top + 255) / 256, 4096));
+  k_verify<<<blocks > 0 ? blocks : 1, 256, 0, stream>>>(
+      a, na, b, nb, n, idx, reinterpret_cast<unsigned long long*>(out));
   return cudaGetLastError();
 }
 

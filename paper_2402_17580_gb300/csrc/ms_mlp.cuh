@@ -32,7 +32,7 @@ constexpr int MLP_IN = 12, MLP_H = 64, MLP_OUT = 3;
 constexpr int MLP_IN_PAD = 16, MLP_OUT_PAD = 8;
 constexpr int MLP_W1_LD = 24, MLP_W2_LD = 72, MLP_W3_LD = 72;  // BF16 row strides
 constexpr int MLP_X_LD = 24;   // row stride of the BF16 input tile [128][MLP_X_LD]
-constexpr int MLP_Y_LD = 4;    // row stride of the FP32 output tile [128][MLP_Y_LD]
+constexpr int MLP_Y_COLS = 4;  // FP32 output tile, column-major [MLP_Y_COLS][128]
 constexpr int MLP_OFF_W1 = 0;
 constexpr int MLP_OFF_B1 = MLP_OFF_W1 + MLP_H * MLP_IN;   // 768
 constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_H;            // 832
@@ -97,9 +97,10 @@ __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) {
 }
 
 // Forward pass of one warp over 128 samples with tensor cores.  X: the
-// warp's [128][MLP_X_LD] BF16 inputs (features 12..15 zero) and Y: its
-// [128][MLP_Y_LD] FP32 outputs (columns 0..2 written), both in shared memory;
-// W: the weights (shared memory).  Rows are
+// warp's [128][MLP_X_LD] BF16 inputs (features 12..15 zero) and Y: its FP32
+// outputs, column-major [MLP_Y_COLS][128] (output c of row r at Y[c * 128 + r],
+// columns 0..2 meaningful), both in shared memory; W: the weights (shared
+// memory).  Rows are
 // processed in 8 tiles of 16; each layer's accumulator fragments are repacked
 // in registers as the next layer's A fragments.  Row tile mt is computed only
 // if bit mt of mt_mask (warp-uniform) is set.
@@ -154,10 +155,10 @@ __device__ __forceinline__ void mlp_forward_warp(const MlpDev& W, const __nv_bfl
     for (int kc = 0; kc < 4; ++kc)
       mma_bf16_16816(y, a2[kc], ld32(wr + 16 * kc + 2 * q), ld32(wr + 16 * kc + 8 + 2 * q), y);
     if (q < 2) {  // output columns 0..3 (3 is padding)
-      Y[ra * MLP_Y_LD + 2 * q] = y[0];
-      Y[ra * MLP_Y_LD + 2 * q + 1] = y[1];
-      Y[rb * MLP_Y_LD + 2 * q] = y[2];
-      Y[rb * MLP_Y_LD + 2 * q + 1] = y[3];
+      Y[(2 * q) * 128 + ra] = y[0];
+      Y[(2 * q + 1) * 128 + ra] = y[1];
+      Y[(2 * q) * 128 + rb] = y[2];
+      Y[(2 * q + 1) * 128 + rb] = y[3];
     }
   }
 }

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const MlpDev* __restrict__ wd
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(smem + sizeof(MlpDev)) + warp * 128 * ms::MLP_X_LD;
   float* Y = reinterpret_cast<float*>(smem + sizeof(MlpDev) + 4 * 128 * ms::MLP_X_LD * 2) +
-             warp * 128 * ms::MLP_Y_LD;
+             warp * 128 * ms::MLP_Y_COLS;
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(wd);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&W);
@@ -221,11 +221,11 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const MlpDev* __restrict__ wd
   for (int r = lane; r < 128; r += 32) {
     const int64_t s = base + r;
     if (s < n)
-      for (int i = 0; i < ms::MLP_OUT; ++i) y[s * ms::MLP_OUT + i] = Y[r * ms::MLP_Y_LD + i];
+      for (int i = 0; i < ms::MLP_OUT; ++i) y[s * ms::MLP_OUT + i] = Y[i * 128 + r];
   }
 }
 
-constexpr size_t kInferSmem = sizeof(MlpDev) + 4 * 128 * ms::MLP_X_LD * 2 + 4 * 128 * ms::MLP_Y_LD * 4;
+constexpr size_t kInferSmem = sizeof(MlpDev) + 4 * 128 * ms::MLP_X_LD * 2 + 4 * 128 * ms::MLP_Y_COLS * 4;
 static_assert(kInferSmem <= 48 * 1024, "k_mlp_infer stays within the default dynamic shared memory");
 static_assert(sizeof(MlpDev) % 16 == 0, "MlpDev is copied in 16-byte words");
 

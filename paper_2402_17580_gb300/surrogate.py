@@ -137,29 +137,33 @@ def train(X: np.ndarray, Y: np.ndarray, iters: int = 4000, batch: int = 16384, l
     import torch
 
     s = B.Surrogate(init if init is not None else init_params(seed))
-    stream = torch.cuda.current_stream(device)
+    # one dedicated stream for torch's minibatch gathers and the library's
+    # training kernels (a NULL handle would select the surrogate's own stream)
+    stream = torch.cuda.Stream(device)
     s.set_stream(stream.cuda_stream)
-    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(device)
-    Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).to(device)
-    n = Xd.shape[0]
-    if n == 0:
-        raise ValueError("no training windows")
-    b = min(batch, n)
-    gen = torch.Generator(device=device)
-    gen.manual_seed(seed)
-    xb = torch.empty((b, N_IN), dtype=torch.float32, device=device)
-    yb = torch.empty((b, N_OUT), dtype=torch.float32, device=device)
-    history = []
-    for it in range(iters):
-        idx = torch.randint(0, n, (b,), generator=gen, device=device)
-        torch.index_select(Xd, 0, idx, out=xb)
-        torch.index_select(Yd, 0, idx, out=yb)
-        a = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * it / max(1, iters - 1)))
-        want = bool(log_every) and (it % log_every == 0 or it == iters - 1)
-        loss = s.train_step(xb.data_ptr(), yb.data_ptr(), b, a, want_loss=want)
-        if want:
-            history.append((it, loss))
-    torch.cuda.synchronize(device)
+    with torch.cuda.stream(stream):
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(device)
+        Yd = torch.from_numpy(np.ascontiguousarray(Y, dtype=np.float32)).to(device)
+        n = Xd.shape[0]
+        if n == 0:
+            raise ValueError("no training windows")
+        b = min(batch, n)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(seed)
+        xb = torch.empty((b, N_IN), dtype=torch.float32, device=device)
+        yb = torch.empty((b, N_OUT), dtype=torch.float32, device=device)
+        history = []
+        for it in range(iters):
+            idx = torch.randint(0, n, (b,), generator=gen, device=device)
+            torch.index_select(Xd, 0, idx, out=xb)
+            torch.index_select(Yd, 0, idx, out=yb)
+            a = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * it / max(1, iters - 1)))
+            want = bool(log_every) and (it % log_every == 0 or it == iters - 1)
+            loss = s.train_step(xb.data_ptr(), yb.data_ptr(), b, a, want_loss=want)
+            if want:
+                history.append((it, loss))
+    stream.synchronize()
+    s.set_stream(None)
     s.history = history
     return s
 
@@ -169,11 +173,14 @@ def evaluate(s: B.Surrogate, X: np.ndarray, Y: np.ndarray, device: str = "cuda")
     (network output / 1e6)."""
     import torch
 
-    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(device)
-    out = torch.empty((Xd.shape[0], N_OUT), dtype=torch.float32, device=device)
-    s.set_stream(torch.cuda.current_stream(device).cuda_stream)
-    s.forward(Xd.data_ptr(), out.data_ptr(), Xd.shape[0])
-    torch.cuda.synchronize(device)
+    stream = torch.cuda.Stream(device)
+    s.set_stream(stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).to(device)
+        out = torch.empty((Xd.shape[0], N_OUT), dtype=torch.float32, device=device)
+        s.forward(Xd.data_ptr(), out.data_ptr(), Xd.shape[0])
+    stream.synchronize()
+    s.set_stream(None)
     err = (out.cpu().numpy() - Y) / OUT_SCALE
     tgt = np.asarray(Y, dtype=np.float64)[:, :2] / OUT_SCALE
     return {"rms": float(np.sqrt(np.mean(err[:, :2] ** 2))),

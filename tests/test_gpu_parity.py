@@ -351,3 +351,28 @@ def test_error_paths(ms):
     with pytest.raises(ms.MSError) as e:
         ctx.run_track([bad], 1, 1e-5)
     assert e.value.code == -1
+
+
+def test_verify_matches_host_reductions(ms):
+    """ms_verify (device reductions) against the same reductions on the host:
+    FP32 block against an MS_F64 subset context of the same grid."""
+    w = wl.block_256(dims=(64, 64, 8), n_tracks=3, n_steps=600)
+    ctx, g = gpu_workload(w)
+    g = np.stack(g)
+    idx = np.sort(np.random.default_rng(4).choice(w.n_points, 3000, replace=False))
+    ref = ms.Context(idx.size, precision=ms.MS_F64, T_thr=0.0)
+    ref.set_points_subset(w.specimens[0].grid, idx)
+    ref.fill_state(w.init_xas, w.init_xam)
+    ref.run_track([w.specimens[0].source], w.n_steps, w.dt)
+    r = np.stack(ref.fractions())
+    d, s1, s2 = ctx.verify(ref, idx)
+    assert d == np.max(np.abs(g[:, idx] - r))
+    assert abs(s1 - np.max(np.abs(g.sum(axis=0) - 1.0))) <= 1e-15
+    assert abs(s2 - np.max(np.abs(r.sum(axis=0) - 1.0))) <= 1e-15
+    assert 0 < d <= RUN_TOL and s1 <= SUM_TOL
+    # without a map: a context against itself
+    assert ctx.verify(ctx) == (0.0, s1, s1)
+    with pytest.raises(ms.MSError, match="INVALID_ARG"):
+        ctx.verify(ref, np.array([w.n_points], dtype=np.int64))
+    ref.close()
+    ctx.close()

@@ -80,7 +80,7 @@ def test_forward_matches_reference_network(ms, torch):
                         .astype(np.float32)])
     p = _params(3)
     s = ms.Surrogate(p)
-    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    # the surrogate's own stream; the results are read after a device-wide sync
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     s.forward(xd.data_ptr(), yd.data_ptr(), n)
@@ -100,7 +100,7 @@ def test_gradient_matches_reference_network(ms, torch):
     t = np.random.default_rng(5).normal(0, 0.5, (n, 3)).astype(np.float32)
     p = _params(6)
     s = ms.Surrogate(p)
-    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    # the surrogate's own stream; the results are read after a device-wide sync
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     gd = torch.empty(omlp.N_PARAMS, dtype=torch.float32, device="cuda")
     loss = s.gradient(xd.data_ptr(), td.data_ptr(), n, gd.data_ptr())
@@ -121,7 +121,7 @@ def test_training_reduces_loss(ms, torch):
     t = np.tanh(x.astype(np.float64) @ A).astype(np.float32)
     from paper_2402_17580_gb300 import surrogate
     s = ms.Surrogate(surrogate.init_params(9))
-    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    # the surrogate's own stream; the results are read after a device-wide sync
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     first = s.gradient(xd.data_ptr(), td.data_ptr(), n)
     for _ in range(400):
