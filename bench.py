@@ -196,7 +196,7 @@ def measured_sfu_rates():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("ms_device.cuh", "ms_kernels.cu"):
+    for f in ("ms_device.cuh", "ms_tile.cuh", "ms_kernels.cu"):
         with open(os.path.join(ROOT, "paper_2402_17580_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
