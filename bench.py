@@ -159,27 +159,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- algorithmic work
-def algorithmic_sfu_per_run(w):
-    """SFU operations one pass requires by the method's formulas (a lower
-    bound), split by SFU rate class: per point and step, one 1/R (rsqrt class)
-    and one exponential (ex2 class) per started moving source at the new time
-    level, plus one exponential and one reciprocal for k_as(T^n).  Counting
-    started sources needs only the track start times.  Returns (slow, ex2)."""
-    import numpy as np
-    slow = fast = 0
-    for s in w.specimens:
-        tr = s.source.tracks
-        ly = s.source.layers
-        t = (np.arange(1, w.n_steps + 1) * w.dt) - s.source.t_offset
-        layer_of = np.zeros(t.size, dtype=np.int64)
-        for j in range(len(ly)):
-            layer_of[t >= ly[j, 1]] = j
-        n_src = np.zeros(t.size, dtype=np.int64)
-        for r in tr:
-            n_src += ((layer_of == int(r[7])) & (t >= r[6])).astype(np.int64)
-        per = int(np.sum(n_src + 1))
-        slow += int(s.grid.n) * per
-        fast += int(s.grid.n) * per
+def algorithmic_sfu_ops(st):
+    """SFU operations the hot kernel's processed work requires by the method's
+    formulas (a lower bound), split by SFU rate class, from the kernel's own
+    work counters: one 1/R (rsqrt class) and one exponential (ex2 class) per
+    point and started source at every evaluated time level, plus one
+    exponential and one reciprocal for k_as(T^n) per point-step on which the
+    model ran.  Tiles the active set drops and steps the warp vote skips do
+    not count.  Returns (slow, ex2)."""
+    slow = int(st.source_evaluations) + int(st.model_point_steps)
+    fast = int(st.source_evaluations) + int(st.model_point_steps)
     return slow, fast
 
 
@@ -389,11 +378,11 @@ def run_ours(args):
     # The SFU peak is op-mix weighted: ex2 and the rsqrt class run at
     # different measured rates.
     rates = measured_sfu_rates()
-    slow_ops, ex2_ops = algorithmic_sfu_per_run(w)
+    slow_ops, ex2_ops = algorithmic_sfu_ops(st)     # totals over the timed passes
     alg_ops = slow_ops + ex2_ops
     launches_per_pass = st.hot_kernel_launches / args.steps
     kernel_ms_per_pass = st.hot_kernel_ms / args.steps
-    ops_per_launch = alg_ops / launches_per_pass
+    ops_per_launch = alg_ops / st.hot_kernel_launches
     ms_per_launch = kernel_ms_per_pass / launches_per_pass
     achieved = ops_per_launch / (ms_per_launch * 1e-3) / 1e9
     sm_cycles = slow_ops / rates["rsqrt"] + ex2_ops / rates["ex2"]    # per-SM cycles, summed
@@ -408,6 +397,10 @@ def run_ours(args):
         "algorithmic_ops_per_launch": int(ops_per_launch),
         "ms_per_launch": round(ms_per_launch, 4), "launches_per_step": launches_per_pass,
         "kernel_share_of_step": round(kernel_ms_per_pass / t_mean, 4),
+        "work": {"source_evaluations_per_step": int(st.source_evaluations) // args.steps,
+                 "model_point_steps_per_step": int(st.model_point_steps) // args.steps,
+                 "tile_steps_active_frac": round(st.tile_steps_active / max(1, st.tile_steps_total), 4),
+                 "note": "counted by k_track; algorithmic SFU ops are derived from these"},
         "peak_basis": (f"measured SFU rates {rates['rsqrt']:.2f} (rsqrt/rcp class) and "
                        f"{rates['ex2']:.2f} (ex2) per SM per clock, {SM_COUNT} SMs, "
                        f"{SM_MAX_MHZ:.0f} MHz max clock, weighted by the algorithmic op mix"),

@@ -182,6 +182,12 @@ typedef struct ms_stats_t {
   int64_t ode_windows;
   int64_t judge_samples;
   double  judge_max_err;
+  /* work of the plain hot kernel since the last reset: temperature
+   * evaluations counted per point and started source, and point-steps on
+   * which the phase model ran (the rest were skipped by the active set or the
+   * warp vote of reading A9) */
+  int64_t source_evaluations;
+  int64_t model_point_steps;
 } ms_stats_t;
 
 typedef struct ms_ctx ms_ctx;

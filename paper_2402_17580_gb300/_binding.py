@@ -61,7 +61,7 @@ class Stats(ctypes.Structure):
         ("last_run_ms", d), ("hot_kernel_ms", d), ("hot_kernel_launches", i64),
         ("device_error", i32), ("reserved", i32),
         ("surrogate_windows", i64), ("ode_windows", i64), ("judge_samples", i64),
-        ("judge_max_err", d)]
+        ("judge_max_err", d), ("source_evaluations", i64), ("model_point_steps", i64)]
 
 
 STRUCTS = (Params, Grid, Track, Layer, HeatSource, Stats)

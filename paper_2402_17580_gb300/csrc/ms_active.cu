@@ -1,0 +1,142 @@
+// Active-set compaction (reading A9): per launch, the list of tiles that
+// may get hot (a rigorous upper bound of their temperature over the launch's
+// time window reaches T_thr) or whose martensite is not saturated.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "ms_internal.h"
+
+namespace ms {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kE = 2.7182818284590452354;
+
+inline unsigned blocks_for(int64_t n, int threads) {
+  return unsigned((n + threads - 1) / threads);
+}
+
+// ------------------------------------------------------------ active set
+// Upper bound of the temperature of a tile over [t_a, t_b]: every started
+// source of a layer current in the window contributes at most
+// A P / (2 pi k) times the smaller of
+//   exp(-v xi_min / alpha) / R_min   (R + xi >= 2 xi ahead of the path) and
+//   max over R >= R_min of exp(-v rho_min^2 / (4 alpha R)) / R
+//                                    (the wake: R + xi >= rho^2 / (2 R)),
+// with R_min the distance between the tile's bounding box and the box of the
+// source's path in the window, xi_min >= 0 the smallest along-track offset of
+// a tile point ahead of the path and rho_min the distance between the tile's
+// box and the source's line.  The interlayer scale is <= 1.  Subset
+// specimens use the whole grid's box.
+__device__ bool tile_is_active(const ActiveArgs& a, int t) {
+  const int s = a.tile_spec[t];
+  const SpecDev& sp = a.specs[s];
+  const float tsat = a.tile_tsat[t];
+  if (!(tsat <= sp.T0)) return true;  // martensite not saturated at T0, or initiation running
+  const double tla = a.t_a - sp.t_offset, tlb = a.t_b - sp.t_offset;
+  int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1, k0 = 0, k1 = sp.nz - 1;
+  if (!sp.idx) {
+    const int64_t li0 = int64_t(t - sp.tile0) * TILE;
+    const int64_t li1 = min(li0 + TILE - 1, sp.n - 1);
+    const int64_t nxy = int64_t(sp.nx) * sp.ny;
+    k0 = li0 / nxy;
+    k1 = li1 / nxy;
+    const int64_t j0 = (li0 - k0 * nxy) / sp.nx, j1 = (li1 - k1 * nxy) / sp.nx;
+    const int64_t i0 = li0 - k0 * nxy - j0 * sp.nx, i1 = li1 - k1 * nxy - j1 * sp.nx;
+    if (k0 == k1) {
+      jlo = j0;
+      jhi = j1;
+      if (j0 == j1) {
+        ilo = i0;
+        ihi = i1;
+      }
+    }
+  }
+  const double xa = sp.ox + double(ilo) * sp.dx, xb = sp.ox + double(ihi) * sp.dx;
+  const double ya = sp.oy + double(jlo) * sp.dy, yb = sp.oy + double(jhi) * sp.dy;
+  const double za = sp.oz + double(k0) * sp.dz, zb = sp.oz + double(k1) * sp.dz;
+  const double bx0 = fmin(xa, xb), bx1 = fmax(xa, xb), by0 = fmin(ya, yb), by1 = fmax(ya, yb);
+  const double bz1 = fmax(za, zb);
+  int la = 0, lb = 0;
+  for (int j = 0; j < sp.n_layers; ++j) {
+    if (a.layers[sp.layer0 + j].t_begin <= tla) la = j;
+    if (a.layers[sp.layer0 + j].t_begin <= tlb) lb = j;
+  }
+  // Per source the geometry runs in FP32 on coordinates relative to the
+  // tile's centre (|offsets| up to ~1 m, FP32 error < 1e-7 m); distances are
+  // shrunk by kShrink and each term is inflated by 1 + 1e-4, so the sum stays
+  // an upper bound.
+  constexpr float kShrink = 1e-7f;
+  const double cxd = 0.5 * (bx0 + bx1), cyd = 0.5 * (by0 + by1);
+  const float hx = float(0.5 * (bx1 - bx0)), hy = float(0.5 * (by1 - by0));
+  const float inv_alpha = float(1.0 / sp.alpha);
+  const double C0 = sp.A / (2.0 * kPi * sp.k);
+  const double budget = a.T_thr - 1.0 - double(sp.T0);
+  double sum = 0.0;
+  for (int j = 0; j < sp.n_tracks; ++j) {
+    const TrackDev tr = a.tracks[sp.track0 + j];
+    if (tr.layer < la || tr.layer > lb || tr.t_start > tlb) continue;
+    const double ta = fmax(tla, tr.t_start);
+    const double pa = tr.v * (ta - tr.t_start), pb = tr.v * (tlb - tr.t_start);
+    const float ux = float(tr.ux), uy = float(tr.uy), v = float(tr.v);
+    // the source's path in the window, relative to the tile's centre
+    const float ax = float(tr.x0 + tr.ux * pa - cxd), ay = float(tr.y0 + tr.uy * pa - cyd);
+    const float bx = float(tr.x0 + tr.ux * pb - cxd), by = float(tr.y0 + tr.uy * pb - cyd);
+    const float dx = fmaxf(0.f, fmaxf(fminf(ax, bx) - hx, -hx - fmaxf(ax, bx)));
+    const float dy = fmaxf(0.f, fmaxf(fminf(ay, by) - hy, -hy - fmaxf(ay, by)));
+    const float dz = float(fmax(0.0, a.layers[sp.layer0 + tr.layer].z - bz1));
+    const float R_min = sqrtf(dx * dx + dy * dy + dz * dz) - kShrink;
+    if (!(R_min > 0.f)) return true;
+    // smallest (x - x_s) . u over the box corners and the path's end points
+    // (ahead of the path R + xi >= 2 xi), and the box corners' signed
+    // distances from the source's line (which passes through a)
+    float xi_min = INFINITY, s_lo = INFINITY, s_hi = -INFINITY;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float cx = (c & 1) ? hx : -hx, cy = (c & 2) ? hy : -hy;
+      xi_min = fminf(xi_min, fminf((cx - ax) * ux + (cy - ay) * uy, (cx - bx) * ux + (cy - by) * uy));
+      const float sd = (cx - ax) * uy - (cy - ay) * ux;
+      s_lo = fminf(s_lo, sd);
+      s_hi = fmaxf(s_hi, sd);
+    }
+    xi_min -= kShrink;
+    const float ahead = xi_min > 0.f ? __expf(-v * xi_min * inv_alpha) : 1.f;
+    // wake bound: R + xi = rho^2 / (R - xi) >= rho^2 / (2 R), rho being the
+    // distance from the source's line, so a source contributes at most
+    // C P exp(-a / R) / R with a = v rho_min^2 / (4 alpha); over R >= R_min
+    // that is largest at R = max(R_min, a).
+    const float lat =
+        (s_lo <= 0.f && s_hi >= 0.f) ? 0.f : fmaxf(0.f, fminf(fabsf(s_lo), fabsf(s_hi)) - kShrink);
+    const float aw = v * (lat * lat + dz * dz) * (0.25f * inv_alpha);
+    const float wake = R_min >= aw ? __expf(-aw / R_min) / R_min : 1.f / (float(kE) * aw);
+    sum += C0 * tr.P * double(fminf(ahead / R_min, wake)) * (1.0 + 1e-4);
+    if (sum >= budget) return true;  // already over: hot
+  }
+  return false;
+}
+
+__global__ void k_active(const ActiveArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = t < a.n_tiles && tile_is_active(a, t);
+  const unsigned mask = __ballot_sync(0xffffffffu, act);
+  if (mask) {
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&a.work->n_active, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (act) a.tile_list[base + __popc(mask & ((1u << lane) - 1u))] = t;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream) {
+  if (a.n_tiles <= 0) return cudaSuccess;
+  k_active<<<blocks_for(a.n_tiles, 128), 128, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ms

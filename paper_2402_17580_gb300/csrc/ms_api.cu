@@ -94,6 +94,7 @@ struct ms_ctx {
   const ms::MlpDev* mlp = nullptr;
   uint64_t judge_thresh = 0;
   ms::HybridCounters* hyb_d = nullptr;
+  ms::OpCounters* ops_d = nullptr;       // work done by k_track
   int hybrid_per_sm = 0;
 
   // staging
@@ -361,6 +362,12 @@ int check_device_error(ms_ctx* c) {
   MS_CUDA(cudaStreamSynchronize(c->stream));
   c->st.device_error = err;
   c->st.tile_steps_active = int64_t(wc.tile_steps_active);
+  if (c->ops_d) {
+    ms::OpCounters oc{};
+    MS_CUDA(cudaMemcpy(&oc, c->ops_d, sizeof(oc), cudaMemcpyDeviceToHost));
+    c->st.source_evaluations = int64_t(oc.source_evaluations);
+    c->st.model_point_steps = int64_t(oc.model_point_steps);
+  }
   if (c->hyb_d) {
     ms::HybridCounters hc{};
     MS_CUDA(cudaMemcpy(&hc, c->hyb_d, sizeof(hc), cudaMemcpyDeviceToHost));
@@ -529,6 +536,7 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.aux = c->aux_d;
     a.tile_tsat = c->tile_tsat_d;
     a.err = c->err_d;
+    a.ops = c->ops_d;
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
     bool hybrid = false;
     if constexpr (std::is_same<AT, float>::value &&
@@ -750,7 +758,9 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
   if (cudaMalloc(&c->err_d, sizeof(int)) != cudaSuccess ||
       cudaMemset(c->err_d, 0, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->work_d, sizeof(ms::WorkCounters)) != cudaSuccess ||
-      cudaMemset(c->work_d, 0, sizeof(ms::WorkCounters)) != cudaSuccess)
+      cudaMemset(c->work_d, 0, sizeof(ms::WorkCounters)) != cudaSuccess ||
+      cudaMalloc(&c->ops_d, sizeof(ms::OpCounters)) != cudaSuccess ||
+      cudaMemset(c->ops_d, 0, sizeof(ms::OpCounters)) != cudaSuccess)
     return bail(fail(MS_ERR_OOM, "device allocation failed"));
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     return bail(fail(MS_ERR_CUDA, "cannot query the SM count"));
@@ -773,6 +783,7 @@ void ms_destroy(ms_ctx* c) {
   cudaFree(c->err_d);
   cudaFree(c->work_d);
   cudaFree(c->hyb_d);
+  cudaFree(c->ops_d);
   cudaFree(c->tracks_d);
   cudaFree(c->layers_d);
   cudaFree(c->levels_d);
@@ -923,6 +934,7 @@ int ms_reset_stats(ms_ctx* c) {
   MS_CUDA(cudaStreamSynchronize(c->stream));
   MS_CUDA(cudaMemset(c->work_d, 0, sizeof(ms::WorkCounters)));
   if (c->hyb_d) MS_CUDA(cudaMemset(c->hyb_d, 0, sizeof(ms::HybridCounters)));
+  MS_CUDA(cudaMemset(c->ops_d, 0, sizeof(ms::OpCounters)));
   const int32_t err = c->st.device_error;
   c->st = ms_stats_t{};
   c->st.device_error = err;

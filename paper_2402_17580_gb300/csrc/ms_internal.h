@@ -71,6 +71,14 @@ struct WorkCounters {
   unsigned long long tile_steps_active;  // running total of processed tile-steps
 };
 
+// Work done by the plain hot kernel (running totals, reset by
+// ms_reset_stats): point x source evaluations of the temperature, and point
+// steps on which the model ran (not skipped by the warp vote).
+struct OpCounters {
+  unsigned long long source_evaluations;
+  unsigned long long model_point_steps;
+};
+
 // Counters of the hybrid kernel (running totals, reset by ms_reset_stats).
 struct HybridCounters {
   unsigned long long surrogate_windows, ode_windows, judge_samples;
@@ -97,6 +105,7 @@ struct TrackArgs {
   float* aux;
   float* tile_tsat;            // per tile: highest T at which formation still acts (+inf: busy)
   int* err;
+  OpCounters* ops;             // work counters of k_track (nullptr: not counted)
   // hybrid kernel only
   const void* mlp;             // MlpDev of the attached surrogate
   HybridCounters* hyb;

@@ -4,8 +4,7 @@
 //                started moving sources (computed in FP64, stored in the
 //                arithmetic type), so the hot kernel reads one entry per
 //                source and level.
-//  k_active      active-set compaction: tiles that may exceed T_thr or whose
-//                martensite is not saturated (reading A9), by a ballot.
+//  (k_active, the active-set compaction of reading A9, is in ms_active.cu)
 //  k_track       the hot path of ms_run_track: persistent warps pull 128-point
 //                tiles, 4 points per thread (128-bit SoA loads), S steps per
 //                state load; the temperature of every point and level is
@@ -92,89 +91,6 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
 }
 
 
-// ------------------------------------------------------------ active set
-// Upper bound of the temperature of a tile over [t_a, t_b]: every started
-// source of a layer current in the window contributes at most
-// A P / (2 pi k R_min) exp(-v xi_min / alpha), with R_min the distance between
-// the tile's bounding box and the box of the source's path in the window and
-// xi_min >= 0 the smallest along-track offset of a tile point ahead of the
-// path (R + xi >= 2 xi ahead of the source; the factor is 1 otherwise).  The
-// interlayer scale is <= 1.  Subset specimens use the whole grid's box.
-__device__ bool tile_is_active(const ActiveArgs& a, int t) {
-  const int s = a.tile_spec[t];
-  const SpecDev& sp = a.specs[s];
-  const float tsat = a.tile_tsat[t];
-  if (!(tsat <= sp.T0)) return true;  // martensite not saturated at T0, or initiation running
-  const double tla = a.t_a - sp.t_offset, tlb = a.t_b - sp.t_offset;
-  int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1, k0 = 0, k1 = sp.nz - 1;
-  if (!sp.idx) {
-    const int64_t li0 = int64_t(t - sp.tile0) * TILE;
-    const int64_t li1 = min(li0 + TILE - 1, sp.n - 1);
-    const int64_t nxy = int64_t(sp.nx) * sp.ny;
-    k0 = li0 / nxy;
-    k1 = li1 / nxy;
-    const int64_t j0 = (li0 - k0 * nxy) / sp.nx, j1 = (li1 - k1 * nxy) / sp.nx;
-    const int64_t i0 = li0 - k0 * nxy - j0 * sp.nx, i1 = li1 - k1 * nxy - j1 * sp.nx;
-    if (k0 == k1) {
-      jlo = j0;
-      jhi = j1;
-      if (j0 == j1) {
-        ilo = i0;
-        ihi = i1;
-      }
-    }
-  }
-  const double xa = sp.ox + double(ilo) * sp.dx, xb = sp.ox + double(ihi) * sp.dx;
-  const double ya = sp.oy + double(jlo) * sp.dy, yb = sp.oy + double(jhi) * sp.dy;
-  const double za = sp.oz + double(k0) * sp.dz, zb = sp.oz + double(k1) * sp.dz;
-  const double bx0 = fmin(xa, xb), bx1 = fmax(xa, xb), by0 = fmin(ya, yb), by1 = fmax(ya, yb);
-  const double bz1 = fmax(za, zb);
-  int la = 0, lb = 0;
-  for (int j = 0; j < sp.n_layers; ++j) {
-    if (a.layers[sp.layer0 + j].t_begin <= tla) la = j;
-    if (a.layers[sp.layer0 + j].t_begin <= tlb) lb = j;
-  }
-  const double C0 = sp.A / (2.0 * kPi * sp.k);
-  double sum = 0.0;
-  for (int j = 0; j < sp.n_tracks; ++j) {
-    const TrackDev tr = a.tracks[sp.track0 + j];
-    if (tr.layer < la || tr.layer > lb || tr.t_start > tlb) continue;
-    const double ta = fmax(tla, tr.t_start);
-    const double pa = tr.v * (ta - tr.t_start), pb = tr.v * (tlb - tr.t_start);
-    const double sx0 = tr.x0 + tr.ux * pa, sx1 = tr.x0 + tr.ux * pb;
-    const double sy0 = tr.y0 + tr.uy * pa, sy1 = tr.y0 + tr.uy * pb;
-    const double dx = fmax(0.0, fmax(fmin(sx0, sx1) - bx1, bx0 - fmax(sx0, sx1)));
-    const double dy = fmax(0.0, fmax(fmin(sy0, sy1) - by1, by0 - fmax(sy0, sy1)));
-    const double zs = a.layers[sp.layer0 + tr.layer].z;
-    const double dz = fmax(0.0, zs - bz1);
-    const double r2 = dx * dx + dy * dy + dz * dz;
-    if (!(r2 > 0.0)) return true;
-    // smallest (x - x_s) . u over the box corners and the path's end points
-    double xi_min = INFINITY;
-    for (int c = 0; c < 4; ++c) {
-      const double cx = (c & 1) ? bx1 : bx0, cy = (c & 2) ? by1 : by0;
-      xi_min = fmin(xi_min, fmin((cx - sx0) * tr.ux + (cy - sy0) * tr.uy,
-                                 (cx - sx1) * tr.ux + (cy - sy1) * tr.uy));
-    }
-    const double ahead = xi_min > 0.0 ? exp(-tr.v * xi_min / sp.alpha) : 1.0;
-    sum += C0 * tr.P / sqrt(r2) * ahead;
-  }
-  return double(sp.T0) + sum >= a.T_thr - 1.0;
-}
-
-__global__ void k_active(const ActiveArgs a) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = t < a.n_tiles && tile_is_active(a, t);
-  const unsigned mask = __ballot_sync(0xffffffffu, act);
-  if (mask) {
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&a.work->n_active, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (act) a.tile_list[base + __popc(mask & ((1u << lane) - 1u))] = t;
-  }
-}
-
 __global__ void k_fill_f32(float* p, int64_t n, float v) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -185,7 +101,8 @@ __global__ void k_fill_f32(float* p, int64_t n, float v) {
 // ------------------------------------------------------------ hot kernel
 // One 128-point tile for the launch's S steps (4 points per lane).
 template <typename AT, typename FT>
-__device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane) {
+__device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane,
+                                           unsigned long long& n_src, unsigned long long& n_model) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
@@ -211,12 +128,18 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   const AT z_tol = AT(sp.z_tol);
   const bool skipping = a.m.T_thr > AT(0);
 
+  // valid points of this tile (all lanes agree): the work counters count them
+  const int64_t rest = sp.n - int64_t(tile - sp.tile0) * TILE;
+  const unsigned long long nv = (unsigned long long)(rest < TILE ? rest : TILE);
+  unsigned long long srcs = 0, models = 0;
   AT T0[4];
   temps4<AT>(lv[0], en, px, py, pz, T0);
+  srcs += lv[0].n;
   for (int l = 1; l < a.n_levels; ++l) {
     const SrcLevelT<AT> L = lv[l];
     AT T1[4];
     temps4<AT>(L, en + int64_t(l) * a.slots, px, py, pz, T1);
+    srcs += L.n;
     const AT zlim = L.z_surf + z_tol;
     bool noop = true;
     if (skipping) {
@@ -226,6 +149,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
                         step_is_noop<AT, FT>(a.m, T0[q], T1[q], xs[q], xm[q], ax[q]));
     }
     if (!(skipping && __all_sync(0xffffffffu, noop))) {
+      ++models;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (valid[q] && pz[q] <= zlim)
@@ -245,6 +169,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     ok = ok && finite_pair(xs[q], xm[q]);
     if (valid[q]) ts = fmaxf(ts, point_tsat<AT, FT>(a.m, xs[q], xm[q], ax[q]));
   }
+  n_src += srcs * nv;
+  n_model += models * nv;
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
   if (a.tile_tsat) {
 #pragma unroll
@@ -267,17 +193,22 @@ template <typename AT, typename FT>
 __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT, FT> a) {
   const int lane = threadIdx.x & 31;
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
-  unsigned long long done = 0;
+  unsigned long long done = 0, n_src = 0, n_model = 0;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    track_tile<AT, FT>(a, a.tile_list ? a.tile_list[w] : w, lane);
+    track_tile<AT, FT>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model);
     ++done;
   }
-  if (lane == 0 && done)
+  if (lane == 0 && done) {
     atomicAdd(&a.work->tile_steps_active, done * (unsigned long long)(a.n_levels - 1));
+    if (a.ops) {
+      atomicAdd(&a.ops->source_evaluations, n_src);
+      atomicAdd(&a.ops->model_point_steps, n_model);
+    }
+  }
 }
 
 // ---------------------------------------------------- external T (ms_step)
@@ -451,11 +382,6 @@ cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream) {
-  if (a.n_tiles <= 0) return cudaSuccess;
-  k_active<<<blocks_for(a.n_tiles, 128), 128, 0, stream>>>(a);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;

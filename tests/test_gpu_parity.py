@@ -199,6 +199,22 @@ def test_active_set_skips_cold_tiles_line(ms):
     assert max_abs_diff(g, oracle_workload(w)) <= RUN_TOL
 
 
+def test_active_set_full_block_against_dense_run(ms):
+    """The tile bound must never drop a tile that gets hot: on the whole
+    256 x 256 x 64 block (every point compared), the run with T_thr = 600 K
+    stays within the reading-A9 skip bound of the run without any skipping,
+    while the bound removes a large part of the tile-steps."""
+    w = wl.block_256()
+    dctx, dense = gpu_workload(w, T_thr=0.0, steps_per_launch=256)
+    dctx.close()
+    ctx, g = gpu_workload(w, T_thr=600.0, steps_per_launch=256)
+    st = ctx.stats()
+    print("active tile-steps", st.tile_steps_active / st.tile_steps_total)
+    assert st.tile_steps_active < 0.8 * st.tile_steps_total
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(dense, g)) <= 2e-5
+    ctx.close()
+
+
 def test_active_set_batched_offsets(ms):
     """Specimens that have not started yet are skipped until their start."""
     w = wl.batch_64(n_specimens=6, n_lo=300, n_hi=4000, n_steps=800, T_thr=600.0)
