@@ -245,14 +245,15 @@ def oracle_sample(w, seconds, seed=12345):
 def d6_layouts(ms, torch, n=1 << 24, blocks=(1, 10, 100), steps=10, warmup=3):
     """ms_step with device temperature arrays on 2^24 points whose branch
     choices come in blocks of 1, 10 and 100 points (the paper's synthetic
-    layouts, Sec. 4.1).  Per point-step the kernel moves 32 bytes (T^n, T^n+1,
-    X_as, X_am, aux in; X_as, X_am, aux out), so it is bound by HBM."""
+    layouts, Sec. 4.1), for the explicit and the implicit scheme.  Per
+    point-step the kernel moves 32 bytes (T^n, T^n+1, X_as, X_am, aux in;
+    X_as, X_am, aux out), so the explicit step is bound by HBM."""
     import workloads as wl
-    out = {}
+    out, out_impl = {}, {}
     from paper_2402_17580_gb300._binding import MS_FLAG_TIME_KERNELS
-    for b in blocks:
+    for b, integ in [(b, i) for i in (ms.MS_EXPLICIT, ms.MS_IMPLICIT) for b in blocks]:
         xas, xam, T0, T1 = wl.random_states(n, seed=2402175806 + b, block=b)
-        ctx = ms.Context(n, flags=MS_FLAG_TIME_KERNELS)
+        ctx = ms.Context(n, flags=MS_FLAG_TIME_KERNELS, integrator=integ)
         stream = torch.cuda.Stream()
         ctx.set_stream(stream.cuda_stream)
         ctx.set_state(xas, xam)
@@ -276,15 +277,23 @@ def d6_layouts(ms, torch, n=1 << 24, blocks=(1, 10, 100), steps=10, warmup=3):
         ms_launch = st.hot_kernel_ms / st.hot_kernel_launches
         bytes_launch = 32 * n
         gbs = bytes_launch / (ms_launch * 1e-3) / 1e9
-        out[f"block_{b}"] = {
+        rec = {
             "point_updates_per_s": n * steps / (e0.elapsed_time(e1) * 1e-3),
             "ms_per_launch": round(ms_launch, 4), "GB_per_s": round(gbs, 1),
             "frac_of_measured_hbm": round(gbs / HBM_PEAK_GBS, 4)}
+        if integ == ms.MS_IMPLICIT:
+            rec["fp_iterations_per_point_step"] = round(st.fp_iterations / (n * steps), 3)
+            rec["fp_unconverged"] = int(st.fp_unconverged)
+            out_impl[f"block_{b}"] = rec
+        else:
+            out[f"block_{b}"] = rec
         ctx.close()
         del t0, t1
     return {"kernel": "k_step_ext", "bound": "hbm", "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "bytes_per_point_step": 32, "points": n, "layouts": out,
-            "note": "inputs 537 MB per step > L2, so no flush is needed"}
+            "bytes_per_point_step": 32, "points": n, "dt_s": 1e-5, "layouts": out,
+            "implicit_layouts": out_impl,
+            "note": "inputs 537 MB per step > L2, so no flush is needed; implicit_layouts: the "
+                    "Crank-Nicolson scheme (MS_IMPLICIT) on the same data and bytes"}
 
 
 # ------------------------------------------------------------------ our arm

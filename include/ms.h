@@ -70,6 +70,18 @@ extern "C" {
                                    replays it when called again with the same start
                                    step, step count and dt (e.g. after ms_fill_state) */
 
+/* time integration of the diffusive rates (ms_params.integrator), Sec. 3 */
+#define MS_EXPLICIT 0  /* forward Euler + correction g (eq:explicit_integration) */
+#define MS_IMPLICIT 1  /* Crank-Nicolson + g, fixed-point iteration with a WRMS
+                          stop, substeps of at most dt_sub with the temperature
+                          linear in time (eq:implicit_integration and
+                          eq:implicit_fp_iteration).  The iteration starts from
+                          g(T^{n+1}, m^n) as the paper's implicit algorithm
+                          does; w_j = 1 / (eps_abs + |m_{i+1,j}| eps_rel); App. A
+                          initiation steps take the closed form as in the
+                          explicit scheme.  MS_F32 and MS_F64 only; not with
+                          an attached surrogate or ms_run_track_noalloc.    */
+
 /* ---------------------------------------------------------------- params */
 /* Model constants and options.  ms_params_default() fills the paper's values:
  * Table 1/2 (T_s, T_l, T_as_start, T_as_end, T_am_start, T_inf, k_alpha_eq,
@@ -103,9 +115,13 @@ typedef struct ms_params {
   int32_t steps_per_launch;       /* S: steps per state load in ms_run_track (1..512) */
   int32_t rebuild_steps;          /* active-set rebuild period (multiple of S; 0 = S) */
   int32_t block_threads;          /* CTA size, multiple of 32 (0 = library choice) */
-  int32_t flags;                  /* reserved, 0                                  */
+  int32_t flags;                  /* MS_FLAG_* bits                               */
+  int32_t integrator;             /* MS_EXPLICIT or MS_IMPLICIT (Sec. 3)          */
+  double  dt_sub;                 /* implicit: largest substep [s] (Sec. 3: 0.01;
+                                     <= 0: no subcycling)                        */
+  double  fp_eps_abs, fp_eps_rel; /* implicit: WRMS tolerances (Sec. 3: 1e-10, 1e-3) */
+  int32_t fp_max_iter;            /* implicit: fixed-point iteration cap (100)    */
   int32_t reserved0;
-  double reserved[4];
 } ms_params;
 
 /* ------------------------------------------------------------ geometry */
@@ -188,6 +204,10 @@ typedef struct ms_stats_t {
    * warp vote of reading A9) */
   int64_t source_evaluations;
   int64_t model_point_steps;
+  /* MS_IMPLICIT: fixed-point iterations done, and substeps that reached
+   * fp_max_iter without meeting the WRMS stop (their last iterate is kept) */
+  int64_t fp_iterations;
+  int64_t fp_unconverged;
 } ms_stats_t;
 
 typedef struct ms_ctx ms_ctx;
@@ -347,7 +367,8 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
  * needs); calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it, so the caller must serialise them.  Non-finite
  * fractions are not reported by this call.
- * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32), CUDA. */
+ * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32, or
+ * MS_IMPLICIT), CUDA. */
 int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid, const ms_heat_source* src,
                          float* x_as, float* x_am, float* aux, int64_t n_points,
                          int64_t step0, int64_t n_steps, double dt, void* cuda_stream);

@@ -42,6 +42,7 @@ PARAM_NAMES = (
     "T_s", "T_l", "T_as_start", "T_as_end", "T_am_start", "T_inf",
     "k_alpha_eq", "k_am_eq", "c_as", "c_b", "k1", "k2", "k3", "f",
     "T_reg", "init_exit", "init_exit_floor", "martensite_literal", "init_ba_steps",
+    "integrator", "dt_sub", "fp_eps_abs", "fp_eps_rel", "fp_max_iter",
 )
 
 DEFAULTS = {
@@ -54,6 +55,10 @@ DEFAULTS = {
     # Sec. 2.2 regularisation width, App. A exit threshold, readings
     "T_reg": 100.0, "init_exit": 1e-15, "init_exit_floor": 1e-3,
     "martensite_literal": 0.0, "init_ba_steps": 0.0,
+    # Sec. 3 implicit scheme: Crank-Nicolson, substeps <= 0.01 s, WRMS
+    # tolerances 1e-10 / 1e-3; the iteration cap is this build's choice
+    "integrator": 0.0, "dt_sub": 0.01, "fp_eps_abs": 1e-10, "fp_eps_rel": 1e-3,
+    "fp_max_iter": 100.0,
 }
 
 MODE_NONE, MODE_AS_TO_B, MODE_B_TO_AS = 0, 1, 2
@@ -103,6 +108,8 @@ def _load():
             lib.orc_run_track_windows.argtypes = [P, P, P, i32, P, i32, i64, P, P, P, i64, i64,
                                                   d, i32, d, P, P, P, P, P]
             lib.orc_run_track_windows.restype = None
+            lib.orc_cn_step.argtypes, lib.orc_cn_step.restype = [P, d, d, d, P, P, P], ctypes.c_int
+            lib.orc_n_substeps.argtypes, lib.orc_n_substeps.restype = [P, d], i64
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_param_count.restype = ctypes.c_int
             assert lib.orc_param_count() == len(PARAM_NAMES)
@@ -180,6 +187,22 @@ def correct(T, xas, xam, p=None):
     return a.value, m.value
 
 
+def cn_step(T0, T1, dt, xas, xam, p=None):
+    """One Crank-Nicolson step with the fixed-point iteration (no substeps, no
+    initiation): returns (X_as, X_am, iterations, converged)."""
+    lib, p = _load(), _prm(p)
+    a, m = ctypes.c_double(float(xas)), ctypes.c_double(float(xam))
+    conv = ctypes.c_int(0)
+    it = lib.orc_cn_step(_ptr(p), float(T0), float(T1), float(dt), ctypes.byref(a),
+                         ctypes.byref(m), ctypes.byref(conv))
+    return a.value, m.value, int(it), bool(conv.value)
+
+
+def n_substeps(dt, p=None):
+    lib, p = _load(), _prm(p)
+    return int(lib.orc_n_substeps(_ptr(p), float(dt)))
+
+
 # ---------------------------------------------------------------- point state
 @dataclass
 class State:
@@ -236,7 +259,8 @@ def run_temps(state: State, T_hist, dt, p=None) -> State:
 
 
 def step(state: State, T0, T1, dt, p=None) -> State:
-    """One explicit step with per-point temperatures T0 = T^n, T1 = T^{n+1}."""
+    """One step (the parameters' integrator) with per-point temperatures
+    T0 = T^n, T1 = T^{n+1}."""
     T0 = np.broadcast_to(np.asarray(T0, dtype=np.float64), (state.n,))
     T1 = np.broadcast_to(np.asarray(T1, dtype=np.float64), (state.n,))
     return run_temps(state, np.stack([T0, T1]), dt, p)

@@ -85,6 +85,12 @@ enum {
   P_INIT_EXIT_FLOOR,/* reading A5: and X~ >= this floor                      */
   P_MART_LITERAL,   /* reading A3 flag (0/1)                                 */
   P_INIT_BA_STEPS,  /* reading A6 flag (0/1)                                 */
+  P_INTEGRATOR,     /* 0 explicit (eq:explicit_integration), 1 implicit
+                       Crank-Nicolson (eq:implicit_integration), Sec. 3       */
+  P_DT_SUB,         /* implicit: largest substep, Sec. 3: 0.01 s (<= 0: none) */
+  P_FP_EPS_ABS,     /* implicit: WRMS absolute tolerance, Sec. 3: 1e-10       */
+  P_FP_EPS_REL,     /* implicit: WRMS relative tolerance, Sec. 3: 1e-3        */
+  P_FP_MAX_ITER,    /* implicit: cap on the fixed-point iterations            */
   P_COUNT
 };
 
@@ -244,6 +250,100 @@ static void point_step(const double *p, double T0, double T1, double dt,
   *mode_io = mode;
 }
 
+/* One Crank-Nicolson step (eq:implicit_integration + eq:implicit_correction)
+ * of the diffusive rates from T0 to T1, solved by the fixed-point iteration
+ * eq:implicit_fp_iteration in the order of the paper's implicit algorithm:
+ * rates at (T0, m^n); m_0 = g(T1, m^n) (reading I1); then
+ *   m_{i+1} = g(T1, m^n + dt/2 (mdot(T1, m_i) + mdot(T0, m^n)))
+ * until the WRMS norm of dt/2 (mdot(T1, m_{i+1}) - mdot(T1, m_i)) is below 1,
+ * with w_j = 1 / (eps_abs + |m_{i+1,j}| eps_rel) (reading A10; the norm is
+ * taken without the root, as the paper writes it).  Returns the iterations
+ * done; *converged is 0 if the cap was reached. */
+static int cn_step(const double *p, double T0, double T1, double dt, double *xas_io,
+                   double *xam_io, int *converged) {
+  const double xas = *xas_io, xam = *xam_io;
+  double das0, dam0;
+  rates(p, T0, xas, xam, &das0, &dam0);
+  double mas = xas, mam = xam;
+  correct(p, T1, &mas, &mam);
+  double das, dam;
+  rates(p, T1, mas, mam, &das, &dam);
+  const int max_iter = (int)p[P_FP_MAX_ITER];
+  int it = 0;
+  *converged = 0;
+  while (it < max_iter) {
+    double nas = xas + 0.5 * dt * (das + das0);
+    double nam = xam + 0.5 * dt * (dam + dam0);
+    correct(p, T1, &nas, &nam);
+    double das1, dam1;
+    rates(p, T1, nas, nam, &das1, &dam1);
+    const double ras = 0.5 * dt * (das1 - das) / (p[P_FP_EPS_ABS] + fabs(nas) * p[P_FP_EPS_REL]);
+    const double ram = 0.5 * dt * (dam1 - dam) / (p[P_FP_EPS_ABS] + fabs(nam) * p[P_FP_EPS_REL]);
+    const double e = 0.5 * (ras * ras + ram * ram);
+    mas = nas;
+    mam = nam;
+    das = das1;
+    dam = dam1;
+    ++it;
+    if (e < 1.0) {
+      *converged = 1;
+      break;
+    }
+  }
+  *xas_io = mas;
+  *xam_io = mam;
+  return it;
+}
+
+/* Substeps of a step of size dt (Sec. 3): ceil(dt / dt_sub), at least 1; the
+ * small offset keeps an exact multiple (0.1 / 0.01) from rounding up. */
+static int64_t n_substeps(const double *p, double dt) {
+  if (!(p[P_DT_SUB] > 0.0)) return 1;
+  const double r = ceil(dt / p[P_DT_SUB] - 1e-9);
+  return r < 1.0 ? 1 : (int64_t)r;
+}
+
+/* One implicit step n -> n+1 of one point: subcycles of at most dt_sub with
+ * the temperature linear in time between T0 and T1 (reading I3); in each
+ * substep the App. A closed-form initiation takes precedence exactly as in
+ * the explicit step (Crank-Nicolson cannot leave X_as = 0 or X_alpha = 0.9
+ * either, reading I2), otherwise cn_step. */
+static void point_step_implicit(const double *p, double T0, double T1, double dt,
+                                double *xas, double *xam, double *xt, int32_t *mode,
+                                int64_t *iters, int64_t *unconverged) {
+  const int64_t ns = n_substeps(p, dt);
+  const double h = dt / (double)ns;
+  for (int64_t s = 0; s < ns; ++s) {
+    const double Ta = T0 + (T1 - T0) * ((double)s / (double)ns);
+    const double Tb = T0 + (T1 - T0) * ((double)(s + 1) / (double)ns);
+    const double xa = *xas + *xam, xeq0 = xalpha_eq(p, Ta);
+    int init = 0;
+    if (*mode == MODE_AS_TO_B && xa > xeq0) init = 1;
+    if (*mode == MODE_B_TO_AS && xa < xeq0) init = 1;
+    if (xa > xeq0 && XMAX - xa <= 0.0 && *xam == 0.0) init = 1;
+    if (xa < xeq0 && *xas == 0.0) init = 1;
+    if (init) {
+      point_step(p, Ta, Tb, h, xas, xam, xt, mode);
+    } else {
+      int conv;
+      *mode = MODE_NONE;
+      *xt = 0.0;
+      const int it = cn_step(p, Ta, Tb, h, xas, xam, &conv);
+      if (iters) *iters += it;
+      if (unconverged && !conv) *unconverged += 1;
+    }
+  }
+}
+
+/* One step with the configured integrator. */
+static void advance(const double *p, double T0, double T1, double dt, double *xas, double *xam,
+                    double *xt, int32_t *mode) {
+  if (p[P_INTEGRATOR] != 0.0)
+    point_step_implicit(p, T0, T1, dt, xas, xam, xt, mode, NULL, NULL);
+  else
+    point_step(p, T0, T1, dt, xas, xam, xt, mode);
+}
+
 /* ------------------------- exported: model pieces ------------------------- */
 
 double orc_liquid_fraction(const double *p, double T) { return liquid_fraction(p, T); }
@@ -258,6 +358,11 @@ void orc_rates(const double *p, double T, double xas, double xam, double *das, d
   rates(p, T, xas, xam, das, dam);
 }
 void orc_correct(const double *p, double T, double *xas, double *xam) { correct(p, T, xas, xam); }
+int orc_cn_step(const double *p, double T0, double T1, double dt, double *xas, double *xam,
+                int *converged) {
+  return cn_step(p, T0, T1, dt, xas, xam, converged);
+}
+int64_t orc_n_substeps(const double *p, double dt) { return n_substeps(p, dt); }
 
 /* X_beta and X_liq from the state and the temperature:
  * eq:time_integration_beta_postprocess with X_sol = 1 - g(T). */
@@ -278,7 +383,7 @@ void orc_run_temps(const double *p, int64_t n, int64_t n_steps, double dt, const
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     for (int64_t s = 0; s < n_steps; ++s)
-      point_step(p, T[s * n + i], T[(s + 1) * n + i], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
+      advance(p, T[s * n + i], T[(s + 1) * n + i], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
   }
 }
 
@@ -358,7 +463,7 @@ void orc_run_track(const double *p, const double *spec, const double *tracks, in
       double t1 = (double)(n0 + s + 1) * dt - spec[S_TOFF];
       double T1 = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i],
                                      t1, &a1);
-      if (a1) point_step(p, T0, T1, dt, &xas[i], &xam[i], &xt[i], &mode[i]);
+      if (a1) advance(p, T0, T1, dt, &xas[i], &xam[i], &xt[i], &mode[i]);
       T0 = T1;
     }
     if (T_last) T_last[i] = T0;
@@ -412,7 +517,7 @@ void orc_run_track_windows(const double *p, const double *spec, const double *tr
         ++count;
       } else {
         for (int64_t l = 1; l <= K; ++l)
-          if (act[l]) point_step(p, T[l - 1], T[l], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
+          if (act[l]) advance(p, T[l - 1], T[l], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
       }
       T0 = T[K];
     }

@@ -19,6 +19,7 @@ ERRORS = {
     -5: "MS_ERR_NONFINITE", -6: "MS_ERR_STATE", -7: "MS_ERR_UNSUPPORTED",
 }
 MS_F32, MS_F64ACC, MS_KAHAN, MS_F64 = 0, 1, 2, 3
+MS_EXPLICIT, MS_IMPLICIT = 0, 1
 MS_PTR_DEVICE = 1
 MS_FLAG_TIME_KERNELS = 1
 MS_FLAG_GRAPH = 2
@@ -32,8 +33,9 @@ class Params(ctypes.Structure):
         "T_s", "T_l", "T_as_start", "T_as_end", "T_am_start", "T_inf", "k_alpha_eq", "k_am_eq",
         "c_as", "c_b", "k1", "k2", "k3", "f", "T_reg", "init_exit", "init_exit_floor", "T_thr")] + [
         (n, i32) for n in ("martensite_literal", "init_ba_steps", "precision", "steps_per_launch",
-                           "rebuild_steps", "block_threads", "flags", "reserved0")] + [
-        ("reserved", d * 4)]
+                           "rebuild_steps", "block_threads", "flags", "integrator")] + [
+        ("dt_sub", d), ("fp_eps_abs", d), ("fp_eps_rel", d), ("fp_max_iter", i32),
+        ("reserved0", i32)]
 
 
 class Grid(ctypes.Structure):
@@ -61,7 +63,8 @@ class Stats(ctypes.Structure):
         ("last_run_ms", d), ("hot_kernel_ms", d), ("hot_kernel_launches", i64),
         ("device_error", i32), ("reserved", i32),
         ("surrogate_windows", i64), ("ode_windows", i64), ("judge_samples", i64),
-        ("judge_max_err", d), ("source_evaluations", i64), ("model_point_steps", i64)]
+        ("judge_max_err", d), ("source_evaluations", i64), ("model_point_steps", i64),
+        ("fp_iterations", i64), ("fp_unconverged", i64)]
 
 
 STRUCTS = (Params, Grid, Track, Layer, HeatSource, Stats)

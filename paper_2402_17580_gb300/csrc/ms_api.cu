@@ -201,6 +201,9 @@ ms::ModelConstT<AT> make_const(const ms_params& p) {
   m.T_thr = AT(p.T_thr);
   m.martensite_literal = p.martensite_literal ? 1 : 0;
   m.init_ba_steps = p.init_ba_steps ? 1 : 0;
+  m.fp_eps_abs = AT(p.fp_eps_abs);
+  m.fp_eps_rel = AT(p.fp_eps_rel);
+  m.fp_max_iter = p.fp_max_iter;
   return m;
 }
 
@@ -228,7 +231,24 @@ int check_params(const ms_params& p) {
   if (p.block_threads != 0 &&
       (p.block_threads < 32 || p.block_threads > 256 || p.block_threads % 32 != 0))
     return fail(MS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+  if (p.integrator != MS_EXPLICIT && p.integrator != MS_IMPLICIT)
+    return fail(MS_ERR_INVALID_ARG, "unknown integrator %d", p.integrator);
+  if (p.integrator == MS_IMPLICIT) {
+    if (p.precision != MS_F32 && p.precision != MS_F64)
+      return fail(MS_ERR_UNSUPPORTED, "MS_IMPLICIT needs precision MS_F32 or MS_F64");
+    if (!(std::isfinite(p.dt_sub) && pos(p.fp_eps_rel) && std::isfinite(p.fp_eps_abs) &&
+          p.fp_eps_abs >= 0 && p.fp_max_iter >= 1))
+      return fail(MS_ERR_INVALID_ARG, "need finite dt_sub, fp_eps_abs >= 0, fp_eps_rel > 0, fp_max_iter >= 1");
+  }
   return MS_OK;
+}
+
+// Substeps of the implicit scheme for a step of size dt: ceil(dt / dt_sub),
+// at least 1 (the small offset keeps an exact multiple from rounding up).
+int32_t n_substeps(const ms_params& p, double dt) {
+  if (p.integrator != MS_IMPLICIT || !(p.dt_sub > 0.0)) return 1;
+  const double r = std::ceil(dt / p.dt_sub - 1e-9);
+  return r < 1.0 ? 1 : (r > 1e9 ? 1000000000 : int32_t(r));
 }
 
 int block_threads(const ms_ctx* c) { return c->prm.block_threads ? c->prm.block_threads : 128; }
@@ -303,7 +323,8 @@ int build_layout(ms_ctx* c) {
   {
     const int bt = block_threads(c);
     const int per_sm = with_ft(c, [&](auto tag) {
-      return ms::track_blocks_per_sm<typename decltype(tag)::at, typename decltype(tag)::type>(bt);
+      return ms::track_blocks_per_sm<typename decltype(tag)::at, typename decltype(tag)::type>(
+          bt, c->prm.integrator == MS_IMPLICIT);
     });
     const int64_t need = (tiles + bt / 32 - 1) / (bt / 32);
     c->track_grid = int(std::min<int64_t>(int64_t(per_sm) * c->sm_count, need));
@@ -367,6 +388,8 @@ int check_device_error(ms_ctx* c) {
     MS_CUDA(cudaMemcpy(&oc, c->ops_d, sizeof(oc), cudaMemcpyDeviceToHost));
     c->st.source_evaluations = int64_t(oc.source_evaluations);
     c->st.model_point_steps = int64_t(oc.model_point_steps);
+    c->st.fp_iterations = int64_t(oc.fp_iterations);
+    c->st.fp_unconverged = int64_t(oc.fp_unconverged);
   }
   if (c->hyb_d) {
     ms::HybridCounters hc{};
@@ -537,6 +560,7 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.tile_tsat = c->tile_tsat_d;
     a.err = c->err_d;
     a.ops = c->ops_d;
+    a.n_sub = n_substeps(c->prm, c->dt);
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
     bool hybrid = false;
     if constexpr (std::is_same<AT, float>::value &&
@@ -552,7 +576,9 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
         hybrid = true;
       }
     }
-    if (!hybrid) MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream));
+    if (!hybrid)
+      MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream,
+                                       c->prm.integrator == MS_IMPLICIT));
     if ((rc = kernel_event(c, true)) != MS_OK) return rc;
     c->st.launches++;
     c->step_n += steps;
@@ -578,7 +604,10 @@ int step_impl(ms_ctx* c, const float* T0, const float* T1) {
   a.err = c->err_d;
   int rc;
   if ((rc = kernel_event(c, false)) != MS_OK) return rc;
-  MS_CUDA(ms::launch_step_ext<AT, FT>(a, block_threads(c), c->stream));
+  a.ops = c->ops_d;
+  a.n_sub = n_substeps(c->prm, c->dt);
+  MS_CUDA(ms::launch_step_ext<AT, FT>(a, block_threads(c), c->stream,
+                                      c->prm.integrator == MS_IMPLICIT));
   if ((rc = kernel_event(c, true)) != MS_OK) return rc;
   c->st.launches++;
   return MS_OK;
@@ -731,6 +760,11 @@ int ms_params_default(ms_params* p) {
   p->steps_per_launch = 128;
   p->rebuild_steps = 0;
   p->block_threads = 0;
+  p->integrator = MS_EXPLICIT;
+  p->dt_sub = 0.01;         // Sec. 3: substeps of at most 0.01 s
+  p->fp_eps_abs = 1e-10;    // Sec. 3: WRMS tolerances
+  p->fp_eps_rel = 1e-3;
+  p->fp_max_iter = 100;
   return MS_OK;
 }
 
@@ -1181,6 +1215,8 @@ int ms_set_surrogate(ms_ctx* c, const ms_surrogate* s, double judge_frac) {
     return fail(MS_ERR_INVALID_ARG, "judge_frac must be in [0, 1]");
   if (s && c->prm.precision != MS_F32 && c->prm.precision != MS_KAHAN)
     return fail(MS_ERR_UNSUPPORTED, "the hybrid path needs precision MS_F32 or MS_KAHAN");
+  if (s && c->prm.integrator != MS_EXPLICIT)
+    return fail(MS_ERR_UNSUPPORTED, "the hybrid path uses the explicit scheme");
   MS_CUDA(cudaStreamSynchronize(c->stream));
   drop_graphs(c);
   if (!s) {

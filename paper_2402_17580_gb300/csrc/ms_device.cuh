@@ -40,6 +40,8 @@ struct ModelConstT {
   AT T_thr;                         // active-set threshold
   int martensite_literal;           // reading A3
   int init_ba_steps;                // reading A6
+  AT fp_eps_abs, fp_eps_rel;        // implicit scheme: WRMS tolerances (Sec. 3)
+  int fp_max_iter;                  // implicit scheme: iteration cap
 };
 using ModelConst = ModelConstT<float>;
 
@@ -298,6 +300,103 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
   aux = a5 ? float(L) : (a6 ? 1.0f : 0.0f);
   xas_io = nas;
   xam_io = nam;
+}
+
+// ------------------------------------------------- implicit scheme (Sec. 3)
+// Diffusive rates m_diff(T, m) of eq:diff_inst_split: r1 (beta -> alpha_s)
+// and r3 (alpha_s -> beta) exclude each other, r2 (alpha_m -> alpha_s) adds;
+// powers as 2^(p log2 x), so 0^p = 0 (reading A14).
+template <typename AT, typename FT>
+__device__ __forceinline__ void diff_rates(const ModelConstT<AT>& m, AT T, FT xas, FT xam, AT& das,
+                                           AT& dam) {
+  const FT xa = xas + xam;
+  const AT xeq = xalpha_eq<AT>(m, T);
+  const AT k = k_alpha_s<AT>(m, T);
+  const bool lo = xa < FT(xeq), hi = xa > FT(xeq);
+  das = AT(0);
+  dam = AT(0);
+  AT las = AT(0);
+  if (lo || xam > FT(0)) las = Fn<AT>::lg2(AT(xas));
+  if (lo) {
+    das = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(FT(xeq) - xa)));
+  } else if (hi) {
+    const FT gap = FT(0.9) - xa;
+    const AT lg = gap > FT(0) ? Fn<AT>::lg2(AT(gap)) : AT(-INFINITY);
+    das = -(m.f * k) * Fn<AT>::ex2(m.pb * lg + m.qb * Fn<AT>::lg2(AT(xa - FT(xeq))));
+  }
+  if (xam > FT(0)) {
+    const AT r2 = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xam)));
+    das += r2;
+    dam = -r2;
+  }
+}
+
+// One Crank-Nicolson step from T0 to T1 (eq:implicit_integration +
+// eq:implicit_correction) by the fixed-point iteration eq:implicit_fp_iteration
+// in the order of the paper's implicit algorithm: m_0 = g(T1, m^n), then
+// m_{i+1} = g(T1, m^n + dt/2 (mdot(T1, m_i) + mdot(T0, m^n))) until the WRMS
+// norm of dt/2 (mdot(T1, m_{i+1}) - mdot(T1, m_i)), weights
+// 1 / (eps_abs + |m_{i+1,j}| eps_rel), is below 1.  Adds the iterations to
+// iters and returns false if the cap was reached.
+template <typename AT, typename FT>
+__device__ __forceinline__ bool cn_step(const ModelConstT<AT>& m, AT T0, AT T1, AT dt, FT& xas_io,
+                                        FT& xam_io, unsigned& iters) {
+  const FT xas = xas_io, xam = xam_io;
+  AT das0, dam0;
+  diff_rates<AT, FT>(m, T0, xas, xam, das0, dam0);
+  FT mas = xas, mam = xam;
+  correct<AT, FT>(m, T1, mas, mam);
+  AT das, dam;
+  diff_rates<AT, FT>(m, T1, mas, mam, das, dam);
+  const AT h = AT(0.5) * dt;
+  bool conv = false;
+  for (int it = 0; it < m.fp_max_iter; ++it) {
+    FT nas = xas + FT(h * (das + das0));
+    FT nam = xam + FT(h * (dam + dam0));
+    correct<AT, FT>(m, T1, nas, nam);
+    AT das1, dam1;
+    diff_rates<AT, FT>(m, T1, nas, nam, das1, dam1);
+    const AT ras = h * (das1 - das) / (m.fp_eps_abs + Fn<AT>::abs(AT(nas)) * m.fp_eps_rel);
+    const AT ram = h * (dam1 - dam) / (m.fp_eps_abs + Fn<AT>::abs(AT(nam)) * m.fp_eps_rel);
+    mas = nas;
+    mam = nam;
+    das = das1;
+    dam = dam1;
+    ++iters;
+    if (AT(0.5) * (ras * ras + ram * ram) < AT(1)) {
+      conv = true;
+      break;
+    }
+  }
+  xas_io = mas;
+  xam_io = mam;
+  return conv;
+}
+
+// One implicit step of one point: n_sub substeps with the temperature linear
+// in time between T0 and T1; in each substep an App. A initiation (aux, or
+// its entry conditions) takes the explicit closed-form step, otherwise
+// cn_step.
+template <typename AT, typename FT>
+__device__ __forceinline__ void point_step_implicit(const ModelConstT<AT>& m, AT T0, AT T1, AT dt,
+                                                    int n_sub, FT& xas, FT& xam, float& aux,
+                                                    unsigned& iters, unsigned& unconverged) {
+  const AT h = dt / AT(n_sub);
+  for (int s = 0; s < n_sub; ++s) {
+    const AT Ta = T0 + (T1 - T0) * (AT(s) / AT(n_sub));
+    const AT Tb = T0 + (T1 - T0) * (AT(s + 1) / AT(n_sub));
+    const FT xa = xas + xam;
+    const AT xeq0 = xalpha_eq<AT>(m, Ta);
+    const bool init = (aux < 0.0f && xa > FT(xeq0)) || (aux > 0.0f && xa < FT(xeq0)) ||
+                      (xa > FT(xeq0) && FT(0.9) - xa <= FT(0) && xam == FT(0)) ||
+                      (xa < FT(xeq0) && xas == FT(0));
+    if (init) {
+      point_step<AT, FT>(m, Ta, Tb, h, xas, xam, aux);
+    } else {
+      aux = 0.0f;
+      if (!cn_step<AT, FT>(m, Ta, Tb, h, xas, xam, iters)) ++unconverged;
+    }
+  }
 }
 
 // A point may skip a step (active set, reading A9) when both temperatures are

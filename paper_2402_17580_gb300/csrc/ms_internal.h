@@ -77,6 +77,8 @@ struct WorkCounters {
 struct OpCounters {
   unsigned long long source_evaluations;
   unsigned long long model_point_steps;
+  unsigned long long fp_iterations;    // implicit scheme: fixed-point iterations
+  unsigned long long fp_unconverged;   // implicit scheme: substeps that hit the cap
 };
 
 // Counters of the hybrid kernel (running totals, reset by ms_reset_stats).
@@ -106,6 +108,7 @@ struct TrackArgs {
   float* tile_tsat;            // per tile: highest T at which formation still acts (+inf: busy)
   int* err;
   OpCounters* ops;             // work counters of k_track (nullptr: not counted)
+  int32_t n_sub;               // implicit scheme: substeps per step
   // hybrid kernel only
   const void* mlp;             // MlpDev of the attached surrogate
   HybridCounters* hyb;
@@ -142,6 +145,8 @@ struct StepArgs {
   FT* xam;
   float* aux;
   int* err;
+  OpCounters* ops;             // implicit iteration counters (nullptr: not counted)
+  int32_t n_sub;               // implicit scheme: substeps per step
 };
 
 // Parameter checks and derived constants shared by the C-ABI entry points
@@ -158,11 +163,13 @@ template <typename AT>
 cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream);
 cudaError_t launch_active(const ActiveArgs& a, cudaStream_t stream);
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream);
+// implicit selects the Crank-Nicolson variant (MS_IMPLICIT; only for
+// (float, float) and (double, double), cudaErrorNotSupported otherwise).
 template <typename AT, typename FT>
 cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
-                         cudaStream_t stream);
+                         cudaStream_t stream, bool implicit = false);
 template <typename AT, typename FT>
-int track_blocks_per_sm(int block_threads);
+int track_blocks_per_sm(int block_threads, bool implicit = false);
 // Verification reductions (k_verify): out[0..2] device doubles.
 cudaError_t launch_verify(const double* a, int64_t na, const double* b, int64_t nb, int64_t n,
                           const int64_t* idx, double* out, cudaStream_t stream);
@@ -184,7 +191,8 @@ int hybrid_blocks_per_sm();
 constexpr int HYBRID_THREADS = 256;
 
 template <typename AT, typename FT>
-cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream);
+cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream,
+                            bool implicit = false);
 
 // Natural-order doubles <-> padded device state (one thread per point).
 // xas == nullptr on set fills every point with (xas0, xam0, no initiation).

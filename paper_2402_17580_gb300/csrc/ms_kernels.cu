@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "ms_internal.h"
 #include "ms_tile.cuh"
@@ -100,9 +101,10 @@ __global__ void k_fill_f32(float* p, int64_t n, float v) {
 
 // ------------------------------------------------------------ hot kernel
 // One 128-point tile for the launch's S steps (4 points per lane).
-template <typename AT, typename FT>
+template <typename AT, typename FT, bool IMPL>
 __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane,
-                                           unsigned long long& n_src, unsigned long long& n_model) {
+                                           unsigned long long& n_src, unsigned long long& n_model,
+                                           unsigned& fp_it, unsigned& fp_unconv) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
@@ -152,8 +154,13 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
       ++models;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (valid[q] && pz[q] <= zlim)
-          point_step<AT, FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q]);
+        if (valid[q] && pz[q] <= zlim) {
+          if constexpr (IMPL)
+            point_step_implicit<AT, FT>(a.m, T0[q], T1[q], a.dt, a.n_sub, xs[q], xm[q], ax[q],
+                                        fp_it, fp_unconv);
+          else
+            point_step<AT, FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) T0[q] = T1[q];
@@ -189,18 +196,32 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
 // Persistent hot kernel: every warp pulls tiles (from the active list, or all
 // tiles) through an atomic cursor until the work runs out, so the grid is
 // sized to the resident capacity and no launch tail is left idle.
-template <typename AT, typename FT>
+template <typename AT, typename FT, bool IMPL>
 __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT, FT> a) {
   const int lane = threadIdx.x & 31;
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
   unsigned long long done = 0, n_src = 0, n_model = 0;
+  unsigned fp_it = 0, fp_unconv = 0;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    track_tile<AT, FT>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model);
+    track_tile<AT, FT, IMPL>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model, fp_it,
+                             fp_unconv);
     ++done;
+  }
+  if constexpr (IMPL) {
+    unsigned long long it = fp_it, un = fp_unconv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      it += __shfl_xor_sync(0xffffffffu, it, o);
+      un += __shfl_xor_sync(0xffffffffu, un, o);
+    }
+    if (lane == 0 && a.ops && it) {
+      atomicAdd(&a.ops->fp_iterations, it);
+      if (un) atomicAdd(&a.ops->fp_unconverged, un);
+    }
   }
   if (lane == 0 && done) {
     atomicAdd(&a.work->tile_steps_active, done * (unsigned long long)(a.n_levels - 1));
@@ -212,38 +233,58 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT
 }
 
 // ---------------------------------------------------- external T (ms_step)
-template <typename AT, typename FT>
+template <typename AT, typename FT, bool IMPL>
 __global__ void __launch_bounds__(256) k_step_ext(const StepArgs<AT, FT> a, int vec_T) {
   const int64_t i0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
-  if (i0 >= a.n) return;
-  FT xs[4], xm[4];
-  float ax[4], T0[4], T1[4];
-  Vec4<FT>::load(a.xas + i0, xs);  // state arrays are padded to whole tiles
-  Vec4<FT>::load(a.xam + i0, xm);
-  Vec4<float>::load(a.aux + i0, ax);
-  const int cnt = a.n - i0 < 4 ? int(a.n - i0) : 4;
-  if (vec_T && cnt == 4) {
-    const float4 t0 = __ldcs(reinterpret_cast<const float4*>(a.T0 + i0));
-    const float4 t1 = __ldcs(reinterpret_cast<const float4*>(a.T1 + i0));
-    T0[0] = t0.x; T0[1] = t0.y; T0[2] = t0.z; T0[3] = t0.w;
-    T1[0] = t1.x; T1[1] = t1.y; T1[2] = t1.z; T1[3] = t1.w;
-  } else {
+  unsigned fp_it = 0, fp_unconv = 0;
+  if (i0 < a.n) {
+    FT xs[4], xm[4];
+    float ax[4], T0[4], T1[4];
+    Vec4<FT>::load(a.xas + i0, xs);  // state arrays are padded to whole tiles
+    Vec4<FT>::load(a.xam + i0, xm);
+    Vec4<float>::load(a.aux + i0, ax);
+    const int cnt = a.n - i0 < 4 ? int(a.n - i0) : 4;
+    if (vec_T && cnt == 4) {
+      const float4 t0 = __ldcs(reinterpret_cast<const float4*>(a.T0 + i0));
+      const float4 t1 = __ldcs(reinterpret_cast<const float4*>(a.T1 + i0));
+      T0[0] = t0.x; T0[1] = t0.y; T0[2] = t0.z; T0[3] = t0.w;
+      T1[0] = t1.x; T1[1] = t1.y; T1[2] = t1.z; T1[3] = t1.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T0[q] = q < cnt ? a.T0[i0 + q] : 300.0f;
+        T1[q] = q < cnt ? a.T1[i0 + q] : 300.0f;
+      }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      T0[q] = q < cnt ? a.T0[i0 + q] : 300.0f;
-      T1[q] = q < cnt ? a.T1[i0 + q] : 300.0f;
+      if (q >= cnt) continue;
+      if constexpr (IMPL)
+        point_step_implicit<AT, FT>(a.m, AT(T0[q]), AT(T1[q]), a.dt, a.n_sub, xs[q], xm[q], ax[q],
+                                    fp_it, fp_unconv);
+      else
+        point_step<AT, FT>(a.m, AT(T0[q]), AT(T1[q]), a.dt, xs[q], xm[q], ax[q]);
+    }
+    Vec4<FT>::store(a.xas + i0, xs);
+    Vec4<FT>::store(a.xam + i0, xm);
+    Vec4<float>::store(a.aux + i0, ax);
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
+    if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
+  }
+  if constexpr (IMPL) {
+    unsigned long long it = fp_it, un = fp_unconv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      it += __shfl_xor_sync(0xffffffffu, it, o);
+      un += __shfl_xor_sync(0xffffffffu, un, o);
+    }
+    if ((threadIdx.x & 31) == 0 && a.ops && it) {
+      atomicAdd(&a.ops->fp_iterations, it);
+      if (un) atomicAdd(&a.ops->fp_unconverged, un);
     }
   }
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (q < cnt) point_step<AT, FT>(a.m, AT(T0[q]), AT(T1[q]), a.dt, xs[q], xm[q], ax[q]);
-  Vec4<FT>::store(a.xas + i0, xs);
-  Vec4<FT>::store(a.xam + i0, xm);
-  Vec4<float>::store(a.aux + i0, ax);
-  bool ok = true;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
-  if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
 }
 
 // --------------------------------------------------------- layout kernels
@@ -407,28 +448,57 @@ cudaError_t launch_correct(const ModelConstT<double>& m, int64_t n, int n_T, con
   return cudaGetLastError();
 }
 
+// The Crank-Nicolson variants exist for (float, float) and (double, double).
 template <typename AT, typename FT>
-int track_blocks_per_sm(int block_threads) {
+constexpr bool kHasImplicit =
+    (std::is_same<AT, float>::value && std::is_same<FT, float>::value) ||
+    (std::is_same<AT, double>::value && std::is_same<FT, double>::value);
+
+template <typename AT, typename FT>
+int track_blocks_per_sm(int block_threads, bool implicit) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<AT, FT>, block_threads, 0) !=
-      cudaSuccess)
-    return 1;
+  cudaError_t e = cudaSuccess;
+  if constexpr (kHasImplicit<AT, FT>) {
+    if (implicit)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<AT, FT, true>, block_threads, 0);
+    else
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<AT, FT, false>, block_threads, 0);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track<AT, FT, false>, block_threads, 0);
+  }
+  if (e != cudaSuccess) return 1;
   return nb > 0 ? nb : 1;
 }
 
 template <typename AT, typename FT>
 cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, bool implicit) {
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
-  k_track<AT, FT><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
+  if (implicit) {
+    if constexpr (kHasImplicit<AT, FT>)
+      k_track<AT, FT, true><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
+    else
+      return cudaErrorNotSupported;
+  } else {
+    k_track<AT, FT, false><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <typename AT, typename FT>
-cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream) {
+cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream,
+                            bool implicit) {
   if (a.n <= 0) return cudaSuccess;
   const int vec = ((reinterpret_cast<uintptr_t>(a.T0) | reinterpret_cast<uintptr_t>(a.T1)) & 15) == 0;
-  k_step_ext<AT, FT><<<blocks_for((a.n + 3) / 4, block_threads), block_threads, 0, stream>>>(a, vec);
+  const unsigned blocks = blocks_for((a.n + 3) / 4, block_threads);
+  if (implicit) {
+    if constexpr (kHasImplicit<AT, FT>)
+      k_step_ext<AT, FT, true><<<blocks, block_threads, 0, stream>>>(a, vec);
+    else
+      return cudaErrorNotSupported;
+  } else {
+    k_step_ext<AT, FT, false><<<blocks, block_threads, 0, stream>>>(a, vec);
+  }
   return cudaGetLastError();
 }
 
@@ -473,9 +543,10 @@ cudaError_t launch_fractions(const ModelConstT<AT>& m, const SpecDev* specs,
                                             cudaStream_t);
 
 #define MS_INSTANTIATE(AT, FT)                                                                    \
-  template int track_blocks_per_sm<AT, FT>(int);                                                 \
-  template cudaError_t launch_track<AT, FT>(const TrackArgs<AT, FT>&, int, int, cudaStream_t);   \
-  template cudaError_t launch_step_ext<AT, FT>(const StepArgs<AT, FT>&, int, cudaStream_t);      \
+  template int track_blocks_per_sm<AT, FT>(int, bool);                                           \
+  template cudaError_t launch_track<AT, FT>(const TrackArgs<AT, FT>&, int, int, cudaStream_t,    \
+                                            bool);                                               \
+  template cudaError_t launch_step_ext<AT, FT>(const StepArgs<AT, FT>&, int, cudaStream_t, bool); \
   template cudaError_t launch_fractions<AT, FT>(                                                 \
       const ModelConstT<AT>&, const SpecDev*, const int32_t*, int64_t, const FT*, const FT*,     \
       const float*, const SrcLevelT<AT>*, const SrcEntryT<AT>*, int32_t, double*, double*,       \

@@ -392,3 +392,86 @@ def test_verify_matches_host_reductions(ms):
         ctx.verify(ref, np.array([w.n_points], dtype=np.int64))
     ref.close()
     ctx.close()
+
+
+# ------------------------------------------------ implicit scheme (Sec. 3)
+IMPL_STEP_TOL = 1e-5   # one implicit step: FP32 rounding over the iterations and substeps
+
+
+@pytest.mark.parametrize("dt", [1e-5, 1e-3, 0.05])
+def test_implicit_single_step_every_branch(ms, dt):
+    """MS_IMPLICIT through ms_step against the oracle's Crank-Nicolson step on
+    random states and temperature pairs of every branch (dt = 0.05 s takes 5
+    substeps of 0.01 s).  Both sides stop on the same WRMS rule; they can
+    differ in the stop only when the norm lands within rounding of 1."""
+    n = 6 * 128 + 37
+    xas, xam, T0, T1 = wl.random_states(n, seed=91, block=1)
+    T0, T1 = T0.astype(np.float32), T1.astype(np.float32)
+    ctx = ms.Context(n, integrator=ms.MS_IMPLICIT)
+    ctx.set_state(xas, xam)
+    ctx.step(T0, T1, dt)
+    g = ctx.fractions()
+    st = ctx.stats()
+    p = oracle_params(ctx.params)
+    s = orc.State.make(oracle_view(xas), oracle_view(xam))
+    orc.step(s, T0.astype(np.float64), T1.astype(np.float64), dt, p)
+    o = orc.fractions(s, T1.astype(np.float64), p)
+    assert max_abs_diff(g, np.stack(o)) <= IMPL_STEP_TOL
+    check_sum(g)
+    assert st.fp_iterations > 0 and st.fp_unconverged == 0
+
+
+def test_implicit_line_run(ms):
+    """The 4096-point line, 2000 steps, Crank-Nicolson in the hot kernel."""
+    w = wl.line_4096()
+    ctx, g = gpu_workload(w, integrator=1)
+    p = oracle_params(ctx.params)
+    assert max_abs_diff(g, oracle_workload(w, p=p)) <= RUN_TOL
+    check_sum(g)
+    st = ctx.stats()
+    assert st.fp_iterations > 0 and st.fp_unconverged == 0
+
+
+def test_implicit_full_fp64_path(ms):
+    """MS_F64 with MS_IMPLICIT against the oracle on a small block."""
+    w = wl.block_256(dims=(48, 16, 6), n_tracks=2, n_steps=900)
+    ctx, g = gpu_workload(w, integrator=1, precision=ms.MS_F64)
+    p = oracle_params(ctx.params)
+    assert max_abs_diff(g, oracle_workload(w, p=p)) <= 1e-6
+
+
+def test_implicit_cooldown_with_large_steps(ms):
+    """The paper's use: cool-down steps of 0.05 s (5 substeps each) through
+    ms_step with external temperatures, 40 steps on random histories."""
+    n = 3 * 128 + 11
+    rng = np.random.default_rng(5)
+    xas, xam, _, _ = wl.random_states(n, seed=93, block=1)
+    T = np.empty((41, n))
+    T[0] = rng.uniform(900, 1500, n)
+    for k in range(40):
+        T[k + 1] = np.maximum(353.0, T[k] - rng.uniform(0, 40, n))
+    T = T.astype(np.float32)
+    ctx = ms.Context(n, integrator=ms.MS_IMPLICIT)
+    ctx.set_state(xas, xam)
+    for k in range(40):
+        ctx.step(T[k], T[k + 1], 0.05)
+    g = ctx.fractions()
+    p = oracle_params(ctx.params)
+    s = orc.State.make(oracle_view(xas), oracle_view(xam))
+    orc.run_temps(s, T.astype(np.float64), 0.05, p)
+    o = orc.fractions(s, T[-1].astype(np.float64), p)
+    assert max_abs_diff(g, np.stack(o)) <= RUN_TOL
+    assert ctx.stats().fp_unconverged == 0
+
+
+def test_implicit_unsupported_combinations(ms):
+    with pytest.raises(ms.MSError, match="UNSUPPORTED"):
+        ms.Context(1000, integrator=ms.MS_IMPLICIT, precision=ms.MS_KAHAN)
+    with pytest.raises(ms.MSError, match="INVALID_ARG"):
+        ms.Context(1000, integrator=7)
+    ctx = ms.Context(1000, integrator=ms.MS_IMPLICIT)
+    s = ms.Surrogate(np.zeros(5187, dtype=np.float32))
+    with pytest.raises(ms.MSError, match="UNSUPPORTED"):
+        ctx.set_surrogate(s, 0.0)
+    s.close()
+    ctx.close()

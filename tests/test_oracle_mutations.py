@@ -42,6 +42,12 @@ MUTANTS = {
     "source_depth_dropped": ("dx * dx + dy * dy + dz * dz", "dx * dx + dy * dy"),
     "interlayer_dropped": ("double T = spec[S_T0] + scale * sum;", "double T = spec[S_T0] + sum;"),
     "clamp_dropped": ("  if (xas < 0.0) xas = 0.0;\n", ""),
+    "cn_half_dropped": ("double nas = xas + 0.5 * dt * (das + das0);",
+                        "double nas = xas + dt * (das + das0);"),
+    "cn_old_rates_at_T1": ("rates(p, T0, xas, xam, &das0, &dam0);",
+                           "rates(p, T1, xas, xam, &das0, &dam0);"),
+    "substep_temperature_frozen": ("const double Tb = T0 + (T1 - T0) * ((double)(s + 1) / (double)ns);",
+                                   "const double Tb = T0 + (T1 - T0) * ((double)s / (double)ns);"),
 }
 
 

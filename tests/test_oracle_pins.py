@@ -465,3 +465,108 @@ def test_dt_halving_on_a_moving_source_run():
     e = [np.max(np.abs(res[d] - ref)) for d in (8e-6, 4e-6, 2e-6, 1e-6)]
     assert e[-1] < 1e-4
     assert all(e[i + 1] < 0.75 * e[i] for i in range(3)), e
+
+
+# --------------------------------------- implicit scheme (Sec. 3, eq:implicit_*)
+def _implicit(**kw):
+    base = dict(integrator=1, dt_sub=0.0, fp_eps_abs=1e-16, fp_eps_rel=1e-13, fp_max_iter=500)
+    base.update(kw)
+    return orc.params(**base)
+
+
+def test_implicit_crank_nicolson_is_second_order():
+    """eq:beta_to_alpha_s at 900 K from X_as = 0.1 (no initiation, X_am = 0):
+    Crank-Nicolson with the iteration converged tightly approaches the closed
+    form with error ratio ~4 per dt halving; forward Euler with ~2."""
+    T, X0, t_end = 900.0, 0.1, 4.0
+    D, k, c = 0.9, orc.k_alpha_s(T), 2.51
+    exact = orc.logistic_step(X0, D, k, c, t_end)
+    errs = {}
+    for name, p in (("cn", _implicit()), ("euler", orc.params())):
+        errs[name] = []
+        for dt in (0.4, 0.2, 0.1):
+            s = orc.State.uniform(1, X0, 0.0)
+            n = int(round(t_end / dt))
+            orc.run_temps(s, np.full(n + 1, T), dt, p)
+            errs[name].append(abs(s.xas[0] - exact))
+    e = errs["cn"]
+    assert 3.5 < e[0] / e[1] < 4.6 and 3.5 < e[1] / e[2] < 4.6, e
+    f = errs["euler"]
+    assert 1.6 < f[0] / f[1] < 2.5, f
+    assert e[2] < f[2] / 20
+
+
+def test_implicit_step_solves_its_equation():
+    """A converged Crank-Nicolson step satisfies
+    m = g(T1, m^n + dt/2 (mdot(T1, m) + mdot(T0, m^n))) (eq:implicit_integration
+    with eq:implicit_correction), checked with the rate and correction
+    functions pinned above, on states and temperature pairs of every branch."""
+    import workloads as wl
+    p = _implicit()
+    xas, xam, T0, T1 = wl.random_states(400, seed=77)
+    checked = 0
+    for i in range(400):
+        if xas[i] == 0.0 or xas[i] + xam[i] >= 0.9:   # initiation states
+            continue
+        for dt in (1e-4, 1e-2):
+            a, m, it, conv = orc.cn_step(T0[i], T1[i], dt, xas[i], xam[i], p)
+            assert conv and it >= 1
+            r0 = orc.rates(T0[i], xas[i], xam[i], p)
+            r1 = orc.rates(T1[i], a, m, p)
+            ea, em = orc.correct(T1[i], xas[i] + 0.5 * dt * (r1[0] + r0[0]),
+                                 xam[i] + 0.5 * dt * (r1[1] + r0[1]), p)
+            assert abs(ea - a) < 1e-12 and abs(em - m) < 1e-12, (i, dt, a, ea, m, em)
+            checked += 1
+    assert checked > 400
+
+
+def test_implicit_wrms_stop_and_iteration_count():
+    """The WRMS stop (Sec. 3: eps_abs 1e-10, eps_rel 1e-3, no root): small
+    steps converge in one or two iterations, larger steps need more; the
+    stopped iterate lies within the tolerance of the tightly converged one."""
+    p = orc.params(integrator=1)
+    a1, m1, it_small, ok1 = orc.cn_step(1100.0, 1099.0, 1e-5, 0.3, 0.2, p)
+    a2, m2, it_big, ok2 = orc.cn_step(1100.0, 1099.0, 0.01, 0.3, 0.2, p)
+    assert ok1 and ok2 and it_small <= 2 and it_big >= it_small
+    at, mt, _, _ = orc.cn_step(1100.0, 1099.0, 0.01, 0.3, 0.2, _implicit())
+    assert abs(a2 - at) <= 1e-3 * 0.3 and abs(m2 - mt) <= 1e-3 * 0.2
+
+
+def test_implicit_subcycling_is_substeps_with_linear_temperature():
+    """One step of 0.1 s with dt_sub = 0.01 s is 10 substeps with the
+    temperature linear in time (reading I3); exact multiples are not rounded
+    up (0.1 / 0.01 -> 10 substeps)."""
+    p = orc.params(integrator=1, dt_sub=0.01)
+    assert orc.n_substeps(0.1, p) == 10 and orc.n_substeps(0.01, p) == 1
+    assert orc.n_substeps(0.0101, p) == 2 and orc.n_substeps(1e-5, p) == 1
+    T0, T1 = 1150.0, 700.0
+    a = orc.State.uniform(3, 0.0, 0.0)
+    a.xas[:] = [0.3, 0.6, 0.05]
+    a.xam[:] = [0.2, 0.0, 0.4]
+    b = a.copy()
+    orc.step(a, T0, T1, 0.1, p)
+    hist = np.array([[T0 + (T1 - T0) * (s / 10)] * 3 for s in range(11)])
+    orc.run_temps(b, hist, 0.01, orc.params(integrator=1, dt_sub=0.0))
+    np.testing.assert_array_equal(a.xas, b.xas)
+    np.testing.assert_array_equal(a.xam, b.xam)
+
+
+def test_implicit_reaches_equilibria_and_quench_values():
+    """With large steps (0.1 s, substeps of 0.01 s) the implicit scheme reaches
+    the P3 equilibrium at 1000 K from pure beta (initiated by the App. A
+    closed form, reading I2) as the explicit scheme does, and an instant drop
+    gives the P4 quench value."""
+    p = orc.params(integrator=1, dt_sub=0.01)
+    s = orc.State.uniform(1, 0.0, 0.0)
+    orc.run_temps(s, np.full(4001, 1000.0), 0.1, p)
+    # the approach is a power law (gap^((c+1)/c)), as in the explicit P3 pin
+    assert abs(s.xas[0] - (1 - math.exp(-0.0068 * 273.0))) < 3e-3
+    e = orc.State.uniform(1, 0.0, 0.0)
+    orc.run_temps(e, np.full(40001, 1000.0), 0.01)
+    assert abs(s.xas[0] - e.xas[0]) < 1e-4
+    # an instant drop is one step without substeps (with substeps the 0.5 s
+    # step cools linearly and a little alpha_s forms on the way)
+    q = orc.State.uniform(1, 0.0, 0.0)
+    orc.step(q, 1400.0, 353.0, 0.5, orc.params(integrator=1, dt_sub=0.0))
+    assert q.xam[0] == pytest.approx(1 - math.exp(-0.00415 * (848 - 353)), rel=1e-12)
+    assert q.xas[0] == 0.0
