@@ -63,6 +63,8 @@ def parse_args():
                     help="skip the window-surrogate (hybrid) measurement")
     ap.add_argument("--no-f64", dest="f64", action="store_false",
                     help="skip the full-FP64 subset measurement")
+    ap.add_argument("--no-coupled", dest="coupled", action="store_false",
+                    help="skip the coupled thermal-solver + phase-model measurement")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="run only the first N time steps of the workload (stated in config)")
     return ap.parse_args()
@@ -453,6 +455,8 @@ def run_ours(args):
                                "sample": desc}
     if rank == 0 and world == 1 and args.f64 and len(w.specimens) == 1:
         out["f64"] = f64_pass(ctx, w, srcs, ms)
+    if rank == 0 and world == 1 and args.coupled and len(w.specimens) == 1:
+        out["coupled"] = coupled_pass(w, ms, torch)
     if rank == 0 and world == 1 and args.hybrid and prec in (ms.MS_F32, ms.MS_KAHAN):
         out["hybrid"] = hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, value, sample)
     if rank == 0 and world == 1 and not args.no_d6:
@@ -489,6 +493,46 @@ def f64_pass(ctx, w, srcs, ms, n_sub=100000, seed=2402175899):
             "ms": t, "max_abs_dX_f32_vs_f64": d, "sum_err_f32": s32, "sum_err_f64": s64,
             "path": "MS_F64 on a seeded point subset (ms_set_points_subset), T_thr = 0; "
                     "compared on the device by ms_verify"}
+
+
+def coupled_pass(w, ms, torch, n_steps=2000, warmup=200):
+    """The grid thermal solver (FP32 explicit finite volumes, the paper's
+    cylindrical laser on the workload's tracks) driving ms_step on the same
+    grid, n_steps steps of the workload's dt on one stream: throughput of the
+    coupled step and the phase model's share (the paper reports the phase
+    model at ~10 % of its thermal model)."""
+    from paper_2402_17580_gb300._binding import MS_FLAG_TIME_KERNELS
+    sp = w.specimens[0]
+    th = ms.Thermal(sp.grid)
+    th.set_source(sp.source)
+    ctx = ms.Context(w.n_points, flags=MS_FLAG_TIME_KERNELS)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    ctx.fill_state(w.init_xas, w.init_xam)
+    th.run_coupled(ctx, warmup, w.dt)
+    ctx.reset_stats()
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        th.run_coupled(ctx, n_steps, w.dt)
+        e1.record(stream)
+    e1.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    tst = th.stats()
+    micro_ms = st.hot_kernel_ms
+    res = {"value": w.point_updates / w.n_steps * n_steps / (total_ms * 1e-3), "unit": UNIT,
+           "steps": n_steps, "ms_per_step": total_ms / n_steps,
+           "phase_model_ms_per_step": micro_ms / n_steps,
+           "thermal_ms_per_step": (total_ms - micro_ms) / n_steps,
+           "phase_model_share_of_thermal": micro_ms / max(1e-9, total_ms - micro_ms),
+           "thermal_substeps_per_step": tst["substeps"] / (n_steps + warmup),
+           "path": "ms_thermal_run_coupled: k_heat substeps, then ms_step (k_step_ext) with "
+                   "device temperature pointers, on one stream"}
+    th.close()
+    ctx.close()
+    return res
 
 
 def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sample):

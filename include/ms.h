@@ -449,6 +449,66 @@ int ms_apply_correction(ms_ctx* ctx, const double* T, int32_t n_T, double* x_as,
  * Errors: INVALID_ARG, UNSUPPORTED (other precisions). */
 int ms_set_surrogate(ms_ctx* ctx, const ms_surrogate* s, double judge_frac);
 
+/* ------------------------------------------------- grid thermal solver */
+/* An explicit finite-volume solver of the heat equation of Sec. 2.1 on a
+ * regular grid, to feed ms_step with T^n and T^{n+1} (the paper's one-way
+ * coupling): rho c dT/dt = div(k grad T) + q_vol with
+ * k = (1 - r_c) k_p + r_c k_ms (eq:material_parameter_interp, k_m = k_s),
+ * r_c the running maximum of g(T) (eq:consolidated_fraction; nodes within
+ * h_powder of the top surface start as powder, r_c = 0), harmonic-mean face
+ * conductances, the cylindrical laser source eq:heat_soruce_cylindrical in
+ * the nodes within h_powder of the top surface (the laser on a track from the
+ * track's start to the next track's start, the last track of a layer to the
+ * layer's scan end; W_eff = the track's P), radiation eps sigma (T^4 - T_inf^4)
+ * from the top layer of nodes, T0 on the bottom layer (Dirichlet), adiabatic
+ * sides.  Explicit Euler substeps: ceil(dt / (0.9 dt_stab)) with
+ * dt_stab = rho c / (k_ms (2/dx^2 + 2/dy^2 + 2/dz^2)); after each substep T is
+ * capped at T_max (the paper's limit T_v + 1000 K, which stands in for the
+ * evaporation losses here) and r_c <- max(r_c, g(T)).  FP32 on the device.
+ * Fields are float arrays in natural grid order (x fastest). */
+typedef struct ms_thermal_params {
+  double rho, c;                  /* density, heat capacity (Table 1)            */
+  double k_ms, k_p;               /* conductivity of melt/solid and powder       */
+  double T_s, T_l;                /* solidus, liquidus [K]                        */
+  double T0, T_inf;               /* preheat (initial and Dirichlet), ambient [K] */
+  double emissivity;              /* top-surface radiation (Table 1: 0.7)         */
+  double T_max;                   /* temperature cap [K] (T_v + 1000 K)           */
+  double beam_radius;             /* R of the cylindrical source [m] (Table 5)    */
+  double h_powder;                /* powder layer thickness [m]                   */
+  int32_t radiation;              /* 1: radiation from the top layer              */
+  int32_t dirichlet_bottom;       /* 1: bottom layer held at T0                   */
+  int32_t cap;                    /* 1: cap at T_max                              */
+  int32_t reserved;
+} ms_thermal_params;
+
+typedef struct ms_thermal ms_thermal;
+
+/* Table 1 / Table 5 values, T0 = 353 K, h_powder = 30 um, all options on. */
+int ms_thermal_params_default(ms_thermal_params* p);
+/* A solver on grid (dims >= 1, finite non-zero spacing); T = T0.  Owns its
+ * device fields and a stream.  Errors: INVALID_ARG, OOM, CUDA. */
+int ms_thermal_create(const ms_thermal_params* p, const ms_grid* grid, ms_thermal** out);
+void ms_thermal_destroy(ms_thermal* th);
+int ms_thermal_set_stream(ms_thermal* th, void* cuda_stream);
+/* T = T0, r_c from the powder layer, time 0 (synchronises). */
+int ms_thermal_reset(ms_thermal* th);
+/* The laser path: src's tracks sorted by start time per layer (copied). */
+int ms_thermal_set_source(ms_thermal* th, const ms_heat_source* src);
+/* Advance by dt (synchronises, adds the device time to ms_thermal_stats). */
+int ms_thermal_step(ms_thermal* th, double dt);
+/* Device pointers (valid until the next step or reset) of T at the start
+ * and at the end of the last step and of r_c; any may be NULL. */
+int ms_thermal_fields(ms_thermal* th, const float** T_prev, const float** T_cur, const float** rc);
+/* Host copies (n doubles each, natural order); either may be NULL. */
+int ms_thermal_get(ms_thermal* th, double* T, double* rc);
+/* Simulated time, substeps taken, device time of ms_thermal_step calls. */
+int ms_thermal_stats(ms_thermal* th, double* time_s, int64_t* substeps, double* kernel_ms);
+/* n_steps coupled steps of dt on ctx's stream: a thermal step, then
+ * ms_step(ctx, T_prev, T_cur, dt, MS_PTR_DEVICE).  ctx must hold one
+ * specimen of the same number of points, in the grid's natural order.
+ * Errors: INVALID_ARG, the errors of ms_step. */
+int ms_thermal_run_coupled(ms_thermal* th, ms_ctx* ctx, int64_t n_steps, double dt);
+
 /* Verification on the device, without copying the state to the host: with
  * j = idx[i] (or i when idx is NULL), compares point j of ctx with point i of
  * ref for i < n over the four fractions X_as, X_am, X_beta, X_liq (each with

@@ -7,10 +7,10 @@ of ``include/ms.h``; this package only builds it and marshals arguments
 provides device memory and streams.
 """
 from ._binding import (MS_EXPLICIT, MS_F32, MS_F64, MS_F64ACC, MS_IMPLICIT, MS_KAHAN,
-                       MS_PTR_DEVICE, Context, MSError, Surrogate, default_params, library_path,
-                       load)
+                       MS_PTR_DEVICE, Context, MSError, Surrogate, Thermal, default_params,
+                       library_path, load, thermal_params)
 from .build import build
 
-__all__ = ["Context", "Surrogate", "MSError", "default_params", "load", "build", "library_path",
+__all__ = ["Context", "Surrogate", "Thermal", "thermal_params", "MSError", "default_params", "load", "build", "library_path",
            "MS_F32", "MS_F64ACC", "MS_KAHAN", "MS_F64", "MS_PTR_DEVICE", "MS_EXPLICIT",
            "MS_IMPLICIT"]

@@ -67,7 +67,13 @@ class Stats(ctypes.Structure):
         ("fp_iterations", i64), ("fp_unconverged", i64)]
 
 
-STRUCTS = (Params, Grid, Track, Layer, HeatSource, Stats)
+class ThermalParams(ctypes.Structure):
+    _fields_ = [(n, d) for n in ("rho", "c", "k_ms", "k_p", "T_s", "T_l", "T0", "T_inf",
+                                 "emissivity", "T_max", "beam_radius", "h_powder")] + [
+        (n, i32) for n in ("radiation", "dirichlet_bottom", "cap", "reserved")]
+
+
+STRUCTS = (Params, Grid, Track, Layer, HeatSource, Stats, ThermalParams)
 
 _lib = None
 
@@ -133,6 +139,19 @@ def load(build_if_missing: bool = True):
     lib.ms_set_surrogate.argtypes = [P, P, d]
     lib.ms_apply_correction.argtypes = [P, P, i32, P, P, i64]
     lib.ms_verify.argtypes = [P, P, P, i64, P]
+    lib.ms_thermal_params_default.argtypes = [ctypes.POINTER(ThermalParams)]
+    lib.ms_thermal_create.argtypes = [ctypes.POINTER(ThermalParams), ctypes.POINTER(Grid),
+                                      ctypes.POINTER(P)]
+    lib.ms_thermal_destroy.argtypes = [P]
+    lib.ms_thermal_destroy.restype = None
+    lib.ms_thermal_set_stream.argtypes = [P, P]
+    lib.ms_thermal_reset.argtypes = [P]
+    lib.ms_thermal_set_source.argtypes = [P, ctypes.POINTER(HeatSource)]
+    lib.ms_thermal_step.argtypes = [P, d]
+    lib.ms_thermal_fields.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]
+    lib.ms_thermal_get.argtypes = [P, P, P]
+    lib.ms_thermal_stats.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d)]
+    lib.ms_thermal_run_coupled.argtypes = [P, P, i64, d]
     for i, s in enumerate(STRUCTS):
         if lib.ms_struct_size(i) != ctypes.sizeof(s):
             raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
@@ -424,3 +443,80 @@ class Surrogate:
                                                  ctypes.byref(loss) if want_loss else None),
                "ms_surrogate_train_step")
         return loss.value if want_loss else None
+
+
+def thermal_params(**overrides) -> ThermalParams:
+    p = ThermalParams()
+    _check(load().ms_thermal_params_default(ctypes.byref(p)), "ms_thermal_params_default")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Thermal:
+    """One ms_thermal: the grid thermal solver on the current device."""
+
+    def __init__(self, grid, params: ThermalParams | None = None, **overrides):
+        self._lib = load()
+        p = params if params is not None else thermal_params(**overrides)
+        self.params = p
+        g = Grid((d * 3)(*grid.origin), (d * 3)(*grid.spacing), (i32 * 3)(*grid.dims), 0)
+        self.n = int(grid.dims[0]) * int(grid.dims[1]) * int(grid.dims[2])
+        self._h = ctypes.c_void_p()
+        _check(self._lib.ms_thermal_create(ctypes.byref(p), ctypes.byref(g), ctypes.byref(self._h)),
+               "ms_thermal_create")
+        self._keep = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.ms_thermal_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle: int | None):
+        _check(self._lib.ms_thermal_set_stream(self._h, ctypes.c_void_p(stream_handle or 0)),
+               "ms_thermal_set_stream")
+
+    def reset(self):
+        _check(self._lib.ms_thermal_reset(self._h), "ms_thermal_reset")
+
+    def set_source(self, source):
+        h, keep = make_heat_source(source)
+        self._keep = keep
+        _check(self._lib.ms_thermal_set_source(self._h, ctypes.byref(h)), "ms_thermal_set_source")
+
+    def step(self, dt: float):
+        _check(self._lib.ms_thermal_step(self._h, float(dt)), "ms_thermal_step")
+
+    def fields(self):
+        """Device pointers (T_prev, T_cur, r_c) as integers."""
+        a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(self._lib.ms_thermal_fields(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "ms_thermal_fields")
+        return a.value, b.value, c.value
+
+    def get(self):
+        T, rc = np.empty(self.n), np.empty(self.n)
+        _check(self._lib.ms_thermal_get(self._h, _ptr(T), _ptr(rc)), "ms_thermal_get")
+        return T, rc
+
+    def stats(self):
+        t, n, ms_ = d(), i64(), d()
+        _check(self._lib.ms_thermal_stats(self._h, ctypes.byref(t), ctypes.byref(n), ctypes.byref(ms_)),
+               "ms_thermal_stats")
+        return {"time_s": t.value, "substeps": n.value, "kernel_ms": ms_.value}
+
+    def run_coupled(self, ctx: Context, n_steps: int, dt: float):
+        _check(self._lib.ms_thermal_run_coupled(self._h, ctx.handle, int(n_steps), float(dt)),
+               "ms_thermal_run_coupled")

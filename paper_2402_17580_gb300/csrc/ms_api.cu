@@ -698,6 +698,8 @@ ModelConstT<AT> model_const(const ms_params& p) { return make_const<AT>(p); }
 template ModelConstT<float> model_const<float>(const ms_params&);
 template ModelConstT<double> model_const<double>(const ms_params&);
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+void* ctx_stream(ms_ctx* c) { return c->stream; }
+int64_t ctx_points(const ms_ctx* c) { return c->n_points; }
 }  // namespace ms
 
 // =============================================================== C ABI
@@ -729,6 +731,7 @@ size_t ms_struct_size(int which) {
     case 3: return sizeof(ms_layer);
     case 4: return sizeof(ms_heat_source);
     case 5: return sizeof(ms_stats_t);
+    case 6: return sizeof(ms_thermal_params);
     default: return 0;
   }
 }

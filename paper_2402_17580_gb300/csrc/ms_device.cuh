@@ -140,6 +140,15 @@ struct Fn<double> {
 
 constexpr float XMAX = 0.9f;  // bound on X_alpha used throughout Sec. 2.2
 
+// An equilibrium value in the fraction type.  Its plateau 0.9 maps to FT(0.9)
+// (from the double 0.9), the value a state set to 0.9 holds, so that states
+// on the bound compare equal to the plateau also when FT is wider than AT
+// (MS_F64ACC, MS_KAHAN: FT(0.9f) would sit 2.4e-8 below FT(0.9)).
+template <typename AT, typename FT>
+__device__ __forceinline__ FT eq_ft(AT v) {
+  return v == AT(0.9) ? FT(0.9) : FT(v);
+}
+
 // ------------------------------------------------------------ equilibria
 // eq:equilibrium_phase_as
 template <typename AT>
@@ -215,9 +224,9 @@ __device__ __forceinline__ void correct(const ModelConstT<AT>& m, AT T, FT& xas,
     const AT cap = Fn<AT>::max(AT(0.9) * (m.T_cap0 - T) * m.inv_T_reg, AT(0));
     if (xas > FT(cap)) xas = FT(cap);
   }
-  const AT xeq = xalpha_eq<AT>(m, T);
-  if (xas + xam > FT(xeq)) {
-    const FT v = FT(xeq) - xas;
+  const FT xeq = eq_ft<AT, FT>(xalpha_eq<AT>(m, T));
+  if (xas + xam > xeq) {
+    const FT v = xeq - xas;
     xam = v > FT(0) ? v : FT(0);
   }
   if (T < m.T_am_start) {
@@ -239,10 +248,13 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
   const AT k = k_alpha_s<AT>(m, T0);
   const AT kb = m.f * k;
 
+  const FT xeq0f = eq_ft<AT, FT>(xeq0);
+  // App. A's alpha_s -> beta initiation needs D = 0.9 - X_alpha^eq > 0
+  const bool can5 = xeq0 < AT(0.9);
   bool a5 = aux < 0.0f, a6 = aux > 0.0f;
-  if (a5 && !(xa > FT(xeq0))) a5 = false;
-  if (a6 && !(xa < FT(xeq0))) a6 = false;
-  const bool enter5 = !a5 && !a6 && xa > FT(xeq0) && FT(0.9) - xa <= FT(0) && xam == FT(0);
+  if (a5 && !(can5 && xa > xeq0f)) a5 = false;
+  if (a6 && !(xa < xeq0f)) a6 = false;
+  const bool enter5 = !a5 && !a6 && can5 && xa > xeq0f && FT(0.9) - xa <= FT(0) && xam == FT(0);
 
   FT nas, nam;
   AT L = AT(0);
@@ -253,9 +265,9 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
     nas = FT(0.9) - FT(Fn<AT>::ex2(L));
     nam = xam;
     a5 = true;
-  } else if (xa < FT(xeq0) && (xas == FT(0) || a6)) {
+  } else if (xa < xeq0f && (xas == FT(0) || a6)) {
     // reading A6: beta -> alpha_s initiation, D = X_alpha^eq - X_am, alpha_m frozen
-    const AT D = AT(FT(xeq0) - xam);
+    const AT D = AT(xeq0f - xam);
     const AT las = xas > FT(0) ? Fn<AT>::lg2(AT(xas)) : AT(-INFINITY);
     AT r2 = AT(0);
     if (xam > FT(0)) r2 = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xam)));
@@ -266,16 +278,16 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
   } else {
     // eq:explicit_integration with the rates at T^n.  r1 and r3 exclude each
     // other and share one lg2 / lg2 / ex2 triple.
-    const bool lo = xa < FT(xeq0), hi = xa > FT(xeq0);
+    const bool lo = xa < xeq0f, hi = xa > xeq0f;
     AT d_as = AT(0), d_am = AT(0);
     AT las = AT(0);
     if (lo || xam > FT(0)) las = Fn<AT>::lg2(AT(xas));
     if (lo) {
-      d_as = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(FT(xeq0) - xa)));
+      d_as = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xeq0f - xa)));
     } else if (hi) {
       const FT gap = FT(0.9) - xa;
       const AT lg = gap > FT(0) ? Fn<AT>::lg2(AT(gap)) : AT(-INFINITY);
-      d_as = -kb * Fn<AT>::ex2(m.pb * lg + m.qb * Fn<AT>::lg2(AT(xa - FT(xeq0))));
+      d_as = -kb * Fn<AT>::ex2(m.pb * lg + m.qb * Fn<AT>::lg2(AT(xa - xeq0f)));
     }
     if (xam > FT(0)) {
       const AT r2 = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xam)));
@@ -310,19 +322,19 @@ template <typename AT, typename FT>
 __device__ __forceinline__ void diff_rates(const ModelConstT<AT>& m, AT T, FT xas, FT xam, AT& das,
                                            AT& dam) {
   const FT xa = xas + xam;
-  const AT xeq = xalpha_eq<AT>(m, T);
+  const FT xeq = eq_ft<AT, FT>(xalpha_eq<AT>(m, T));
   const AT k = k_alpha_s<AT>(m, T);
-  const bool lo = xa < FT(xeq), hi = xa > FT(xeq);
+  const bool lo = xa < xeq, hi = xa > xeq;
   das = AT(0);
   dam = AT(0);
   AT las = AT(0);
   if (lo || xam > FT(0)) las = Fn<AT>::lg2(AT(xas));
   if (lo) {
-    das = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(FT(xeq) - xa)));
+    das = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xeq - xa)));
   } else if (hi) {
     const FT gap = FT(0.9) - xa;
     const AT lg = gap > FT(0) ? Fn<AT>::lg2(AT(gap)) : AT(-INFINITY);
-    das = -(m.f * k) * Fn<AT>::ex2(m.pb * lg + m.qb * Fn<AT>::lg2(AT(xa - FT(xeq))));
+    das = -(m.f * k) * Fn<AT>::ex2(m.pb * lg + m.qb * Fn<AT>::lg2(AT(xa - xeq)));
   }
   if (xam > FT(0)) {
     const AT r2 = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xam)));
@@ -387,9 +399,11 @@ __device__ __forceinline__ void point_step_implicit(const ModelConstT<AT>& m, AT
     const AT Tb = T0 + (T1 - T0) * (AT(s + 1) / AT(n_sub));
     const FT xa = xas + xam;
     const AT xeq0 = xalpha_eq<AT>(m, Ta);
-    const bool init = (aux < 0.0f && xa > FT(xeq0)) || (aux > 0.0f && xa < FT(xeq0)) ||
-                      (xa > FT(xeq0) && FT(0.9) - xa <= FT(0) && xam == FT(0)) ||
-                      (xa < FT(xeq0) && xas == FT(0));
+    const FT xeq0f = eq_ft<AT, FT>(xeq0);
+    const bool can5 = xeq0 < AT(0.9);
+    const bool init = (aux < 0.0f && can5 && xa > xeq0f) || (aux > 0.0f && xa < xeq0f) ||
+                      (can5 && xa > xeq0f && FT(0.9) - xa <= FT(0) && xam == FT(0)) ||
+                      (xa < xeq0f && xas == FT(0));
     if (init) {
       point_step<AT, FT>(m, Ta, Tb, h, xas, xam, aux);
     } else {

@@ -179,6 +179,10 @@ cudaError_t launch_verify(const double* a, int64_t na, const double* b, int64_t 
 cudaError_t launch_correct(const ModelConstT<double>& m, int64_t n, int n_T, const double* T,
                            double* xas, double* xam, cudaStream_t stream);
 
+// The stream and the number of points of a context (for the coupled runner).
+void* ctx_stream(ms_ctx* c);
+int64_t ctx_points(const ms_ctx* c);
+
 // The inference weights of a surrogate (ms_surrogate.cu).
 struct MlpDev;
 const MlpDev* surrogate_weights(const ms_surrogate* s);
