@@ -86,6 +86,18 @@ def test_validation_before_device_work():
     assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
     bad = ms.default_params(block_threads=48)
     assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
+    bad = ms.default_params(integrator=7)
+    assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
+    bad = ms.default_params(integrator=1, precision=2)          # implicit + compensated
+    assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -7
+    bad = ms.default_params(integrator=1, fp_max_iter=0)
+    assert lib.ms_create(ctypes.byref(bad), 10, ctypes.byref(h)) == -1
+    tp = ms.thermal_params(k_ms=-1.0)
+    g = ms._binding.Grid((ctypes.c_double * 3)(0, 0, 0), (ctypes.c_double * 3)(1e-5, 1e-5, -1e-5),
+                         (ctypes.c_int32 * 3)(4, 4, 4), 0)
+    assert lib.ms_thermal_create(ctypes.byref(tp), ctypes.byref(g), ctypes.byref(h)) == -1
+    assert lib.ms_thermal_create(None, ctypes.byref(g), ctypes.byref(h)) == -1
+    assert lib.ms_thermal_params_default(None) == -1
     assert lib.ms_params_default(None) == -1
     for fn, args in (("ms_set_points", (None, None, 1)), ("ms_set_state", (None, None, None, None)),
                      ("ms_step", (None, None, None, 1e-5, 0)), ("ms_run_track", (None, None, 1, 1e-5)),

@@ -393,6 +393,27 @@ def test_error_paths(ms):
     assert e.value.code == -1
 
 
+def test_edge_cases(ms):
+    """Degenerate and extreme inputs: zero steps, one point (a tile of 127
+    padding lanes), the largest launch (512 steps), large explicit steps
+    (invariants of P6 hold: every fraction in [0, 1], the sum 1)."""
+    w = wl.line_4096(n_points=1, n_steps=300)
+    ctx, g0 = gpu_workload(w, n_steps=0)
+    assert np.allclose(np.stack(g0)[:2, 0], [0.9, 0.0])
+    ctx, g = gpu_workload(w)
+    assert max_abs_diff(g, oracle_workload(w)) <= RUN_TOL
+    w = wl.line_4096(n_points=700, n_steps=1100)
+    _, a = gpu_workload(w, steps_per_launch=512)
+    _, b = gpu_workload(w, steps_per_launch=128)
+    assert max_abs_diff(a, np.stack(b)) == 0.0
+    xas, xam, T0, T1 = wl.random_states(4 * 128 + 3, seed=21)
+    c = ms.Context(xas.size)
+    c.set_state(xas, xam)
+    for _ in range(20):
+        c.step(T0.astype(np.float32), T1.astype(np.float32), 0.05)
+    check_sum(c.fractions())
+
+
 def test_verify_matches_host_reductions(ms):
     """ms_verify (device reductions) against the same reductions on the host:
     FP32 block against an MS_F64 subset context of the same grid."""
