@@ -411,6 +411,7 @@ def run_ours(args):
         "work": {"source_evaluations_per_step": int(st.source_evaluations) // args.steps,
                  "model_point_steps_per_step": int(st.model_point_steps) // args.steps,
                  "tile_steps_active_frac": round(st.tile_steps_active / max(1, st.tile_steps_total), 4),
+                 "model_run_frac": round(st.model_point_steps / max(1, 128 * st.tile_steps_active), 4),
                  "note": "counted by k_track; algorithmic SFU ops are derived from these"},
         "peak_basis": (f"measured SFU rates {rates['rsqrt']:.2f} (rsqrt/rcp class) and "
                        f"{rates['ex2']:.2f} (ex2) per SM per clock, {SM_COUNT} SMs, "
