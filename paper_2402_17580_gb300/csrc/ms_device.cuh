@@ -442,7 +442,7 @@ using SrcEntry = SrcEntryT<float>;
 template <typename AT>
 struct alignas(16) SrcLevelT {
   int n;          // started sources of the current layer at this level
-  int pad;
+  int axis;       // 1: every source of the level has u_y == 0 (moves along +-x)
   AT z_surf;      // current layer surface (all its sources sit on it)
   AT T0, T_max;
 };
@@ -454,17 +454,35 @@ using SrcLevel = SrcLevelT<float>;
 // Behind the source (xi < 0) R + xi cancels; it is computed there as
 // perp^2 / (R + |xi|), algebraically equal and free of cancellation, so far
 // receding sources keep full accuracy.  In FP32: 16 instructions, 3 on the SFU.
+//
+// The offsets are xi = px u_x + (py u_y - s_xi) and pp = px u_y + (py (-u_x)
+// - s_pp); the bracketed parts and, when u_y == 0, perp^2 do not depend on
+// px, so points that share py and pz may compute them once (source_offsets,
+// source_term_x) and get the same bits.
 template <typename AT>
-__device__ __forceinline__ AT source_term(const SrcEntryT<AT>& e, AT px, AT py, AT dz2) {
-  const AT xi = Fn<AT>::fma(px, e.ux, Fn<AT>::fma(py, e.uy, -e.s_xi));
-  const AT pp = Fn<AT>::fma(px, e.uy, Fn<AT>::fma(py, -e.ux, -e.s_pp));
-  const AT perp2 = Fn<AT>::fma(pp, pp, dz2);
+__device__ __forceinline__ AT source_term_x(const SrcEntryT<AT>& e, AT xi, AT perp2) {
   const AT r2 = Fn<AT>::fma(xi, xi, perp2);
   const AT rinv = Fn<AT>::rsqrt(r2);
   const AT w = Fn<AT>::fma(r2, rinv, Fn<AT>::abs(xi));  // R + |xi|
   const AT inv_w = Fn<AT>::rcp(w);  // unconditional, so the select below stays branch-free
   const AT rpx = xi >= AT(0) ? w : perp2 * inv_w;
   return rinv * Fn<AT>::ex2(Fn<AT>::fma(e.cR, rpx, e.lC));
+}
+
+// The parts of xi and pp that do not depend on px.
+template <typename AT>
+__device__ __forceinline__ void source_offsets(const SrcEntryT<AT>& e, AT py, AT& c_xi, AT& c_pp) {
+  c_xi = Fn<AT>::fma(py, e.uy, -e.s_xi);
+  c_pp = Fn<AT>::fma(py, -e.ux, -e.s_pp);
+}
+
+template <typename AT>
+__device__ __forceinline__ AT source_term(const SrcEntryT<AT>& e, AT px, AT py, AT dz2) {
+  AT c_xi, c_pp;
+  source_offsets<AT>(e, py, c_xi, c_pp);
+  const AT xi = Fn<AT>::fma(px, e.ux, c_xi);
+  const AT pp = Fn<AT>::fma(px, e.uy, c_pp);
+  return source_term_x<AT>(e, xi, Fn<AT>::fma(pp, pp, dz2));
 }
 
 }  // namespace ms

@@ -95,6 +95,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
     valid[q] = li < sp.n;
     point_coords<float>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
   }
+  const bool row = tile_in_one_row(sp, tile);
 
   FT xs[4], xm[4];
   float ax[4];
@@ -109,7 +110,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   const int n_steps = a.n_levels - 1;
 
   float T0[4];
-  temps4<float>(lv[0], en, px, py, pz, T0);
+  temps4<float>(lv[0], en, px, py, pz, false, T0);  // once per tile: the general form (same bits)
   for (int w0 = 0; w0 < n_steps; w0 += MLP_WINDOW) {
     const int K = min(MLP_WINDOW, n_steps - w0);
     bool band[4], all_act[4], any_act[4], noop[4];
@@ -126,7 +127,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       const int lvl = w0 + 1 + l;
       const SrcLevelT<float> L = lv[lvl];
       float T1[4];
-      temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, T1);
+      temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, row, T1);
 #pragma unroll
       for (int q = 0; q < 4; ++q) sm.T[l][lane + 32 * q] = T1[q];
       const float zlim = L.z_surf + z_tol;

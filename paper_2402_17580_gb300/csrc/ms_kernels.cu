@@ -65,7 +65,7 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   const double cv = -kLog2e / (2.0 * sp.alpha);
   SrcEntryT<AT>* out =
       static_cast<SrcEntryT<AT>*>(a.entries) + (int64_t(s) * a.n_levels + lv) * a.slots;
-  int n = 0;
+  int n = 0, axis = 1;
   for (int j = 0; j < sp.n_tracks && n < a.slots; ++j) {
     const TrackDev tr = a.tracks[sp.track0 + j];
     if (tr.layer != l || tl < tr.t_start) continue;
@@ -80,11 +80,12 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
     e.cR = AT(cv * tr.v);
     e.lC = C > 0.0 ? AT(log2(C)) : AT(-INFINITY);
     e.pad0 = e.pad1 = AT(0);
+    if (!(e.uy == AT(0))) axis = 0;
     out[n++] = e;
   }
   SrcLevelT<AT> r;
   r.n = n;
-  r.pad = 0;
+  r.axis = axis;
   r.z_surf = AT(L.z);
   r.T0 = AT(sp.T0);
   r.T_max = AT(sp.T_max);
@@ -118,6 +119,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     valid[q] = li < sp.n;
     point_coords<AT>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
   }
+  const bool row = tile_in_one_row(sp, tile);
 
   FT xs[4], xm[4];
   float ax[4];
@@ -135,13 +137,16 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   const unsigned long long nv = (unsigned long long)(rest < TILE ? rest : TILE);
   unsigned long long srcs = 0, models = 0;
   AT T0[4];
-  temps4<AT>(lv[0], en, px, py, pz, T0);
-  srcs += lv[0].n;
-  for (int l = 1; l < a.n_levels; ++l) {
+  for (int l = 0; l < a.n_levels; ++l) {  // level 0 only sets T0 (one inlined temps4)
     const SrcLevelT<AT> L = lv[l];
     AT T1[4];
-    temps4<AT>(L, en + int64_t(l) * a.slots, px, py, pz, T1);
+    temps4<AT>(L, en + int64_t(l) * a.slots, px, py, pz, row, T1);
     srcs += L.n;
+    if (l == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) T0[q] = T1[q];
+      continue;
+    }
     const AT zlim = L.z_surf + z_tol;
     bool noop = true;
     if (skipping) {

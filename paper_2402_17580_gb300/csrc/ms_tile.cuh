@@ -27,6 +27,17 @@ __device__ __forceinline__ void point_coords(const SpecDev& sp, int64_t li, AT& 
   z = AT(sp.oz) + AT(k) * AT(sp.dz);
 }
 
+// Every point of the tile lies in one grid row (shares y and z): a full-grid
+// specimen whose first and last point of the tile have the same row index.
+// The tile's padding points take point 0's coordinates; their temperatures
+// are never used.
+__device__ __forceinline__ bool tile_in_one_row(const SpecDev& sp, int tile) {
+  if (sp.idx) return false;
+  const int64_t li0 = int64_t(tile - sp.tile0) * TILE;
+  const int64_t li1 = li0 + TILE - 1 < sp.n - 1 ? li0 + TILE - 1 : sp.n - 1;
+  return li0 / sp.nx == li1 / sp.nx;
+}
+
 __device__ __forceinline__ SrcEntryT<float> load_entry(const SrcEntryT<float>* p) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
   const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
@@ -47,25 +58,66 @@ __device__ __forceinline__ AT depth2(AT pz, AT z_surf) {
 
 // Temperatures of 4 points at one level: two sources per iteration, so each
 // thread runs 8 independent chains; the sum runs in source order.
+//
+// row (warp-uniform) says that every point of the tile shares py[0] and pz[0]
+// (a tile inside one grid row).  Then the parts of a source's offsets that do
+// not depend on x, and for a level whose sources all move along +-x the whole
+// perp^2, are computed once per source instead of once per point: the same
+// operations on the same operands, so the bits do not change (see
+// source_term).  Per point and source that leaves 12 instructions instead of
+// 16 when the level is axis-aligned.
 template <typename AT>
 __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en,
-                                       const AT* px, const AT* py, const AT* pz, AT* T) {
-  AT acc[4] = {AT(0), AT(0), AT(0), AT(0)}, dz2[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dz2[q] = depth2<AT>(pz[q], L.z_surf);
+                                       const AT* px, const AT* py, const AT* pz, bool row,
+                                       AT* T) {
+  AT acc[4] = {AT(0), AT(0), AT(0), AT(0)};
   int j = 0;
-  for (; j + 1 < L.n; j += 2) {
-    const SrcEntryT<AT> e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
+  if (row && L.axis) {
+    const AT dz2 = depth2<AT>(pz[0], L.z_surf);
+    for (; j + 1 < L.n; j += 2) {
+      const SrcEntryT<AT> e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
+      AT x0, p0, x1, p1;
+      source_offsets<AT>(e0, py[0], x0, p0);
+      source_offsets<AT>(e1, py[0], x1, p1);
+      const AT q0 = Fn<AT>::fma(p0, p0, dz2), q1 = Fn<AT>::fma(p1, p1, dz2);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
-      acc[q] += source_term<AT>(e1, px[q], py[q], dz2[q]);
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), q0);
+        acc[q] += source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), q1);
+      }
+    }
+  } else if (row) {
+    const AT dz2 = depth2<AT>(pz[0], L.z_surf);
+    for (; j + 1 < L.n; j += 2) {
+      const SrcEntryT<AT> e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
+      AT x0, p0, x1, p1;
+      source_offsets<AT>(e0, py[0], x0, p0);
+      source_offsets<AT>(e1, py[0], x1, p1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const AT pp0 = Fn<AT>::fma(px[q], e0.uy, p0), pp1 = Fn<AT>::fma(px[q], e1.uy, p1);
+        acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), Fn<AT>::fma(pp0, pp0, dz2));
+        acc[q] += source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), Fn<AT>::fma(pp1, pp1, dz2));
+      }
+    }
+  } else {
+    AT dz2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dz2[q] = depth2<AT>(pz[q], L.z_surf);
+    for (; j + 1 < L.n; j += 2) {
+      const SrcEntryT<AT> e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
+        acc[q] += source_term<AT>(e1, px[q], py[q], dz2[q]);
+      }
     }
   }
   if (j < L.n) {
     const SrcEntryT<AT> e0 = load_entry(en + j);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
+    for (int q = 0; q < 4; ++q)
+      acc[q] += source_term<AT>(e0, px[q], py[q], depth2<AT>(pz[q], L.z_surf));
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) T[q] = Fn<AT>::min(L.T0 + acc[q], L.T_max);

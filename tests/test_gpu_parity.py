@@ -284,6 +284,44 @@ def test_point_subset_matches_the_full_grid(ms):
         assert np.array_equal(a[idx], b)
 
 
+@pytest.mark.parametrize("case", ["axis", "rotated", "axis_skip", "hybrid"])
+def test_row_tiles_match_the_general_form(ms, case):
+    """Tiles inside one grid row (rows of 128 points here) compute the
+    x-independent parts of every source's offsets once per source, and for
+    levels whose sources all move along +-x the whole perpendicular distance;
+    a subset specimen holding the same points takes the per-point form.  Both
+    must give identical bits: serpentine along x, a second layer rotated by
+    67 degrees (mixed levels), the active set on, and the hybrid kernel with a
+    zero network."""
+    if case == "rotated":
+        w = wl.part_512(dims=(128, 10, 6), n_layers=2, tracks_per_layer=3, t_layer=5e-3,
+                        hatch=3e-5)
+    else:
+        w = wl.block_256(dims=(128, 6, 5), n_tracks=3, n_steps=600)
+    T_thr = 600.0 if case == "axis_skip" else 0.0
+    sp = w.specimens[0]
+    idx = np.arange(sp.grid.n, dtype=np.int64)
+    zero = ms.Surrogate(np.zeros(5187, dtype=np.float32)) if case == "hybrid" else None
+    out = []
+    for subset in (False, True):
+        ctx = ms.Context(sp.grid.n, T_thr=T_thr, steps_per_launch=128)
+        if subset:
+            ctx.set_points_subset(sp.grid, idx)
+        else:
+            ctx.set_points([sp.grid])
+        ctx.fill_state(w.init_xas, w.init_xam)
+        if zero is not None:
+            ctx.set_surrogate(zero, 0.0)
+        ctx.run_track([sp.source], w.n_steps, w.dt)
+        out.append((np.stack(ctx.fractions()), ctx.aux(), ctx.temperature()))
+        ctx.close()
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    assert np.max(np.abs(out[0][0][0] - 0.9)) > 0.5   # the tracks transformed alpha_s
+    if zero is not None:
+        zero.close()
+
+
 def test_temperature_query_matches_the_source(ms):
     w = wl.block_256(dims=(30, 20, 5), n_tracks=2, n_steps=150, T_thr=0.0)
     sp = w.specimens[0]
