@@ -12,7 +12,6 @@ namespace ms {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
 constexpr double kE = 2.7182818284590452354;
 
 inline unsigned blocks_for(int64_t n, int threads) {
@@ -30,13 +29,13 @@ inline unsigned blocks_for(int64_t n, int threads) {
 // source's path in the window, xi_min >= 0 the smallest along-track offset of
 // a tile point ahead of the path and rho_min the distance between the tile's
 // box and the source's line.  The interlayer scale is <= 1.  Subset
-// specimens use the whole grid's box.
+// specimens use the whole grid's box.  The path of every track in the window
+// comes from the source-table launch (TrackWin, FP64).
 __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   const int s = a.tile_spec[t];
   const SpecDev& sp = a.specs[s];
   const float tsat = a.tile_tsat[t];
   if (!(tsat <= sp.T0)) return true;  // martensite not saturated at T0, or initiation running
-  const double tla = a.t_a - sp.t_offset, tlb = a.t_b - sp.t_offset;
   int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1, k0 = 0, k1 = sp.nz - 1;
   if (!sp.idx) {
     const int64_t li0 = int64_t(t - sp.tile0) * TILE;
@@ -59,35 +58,28 @@ __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   const double ya = sp.oy + double(jlo) * sp.dy, yb = sp.oy + double(jhi) * sp.dy;
   const double za = sp.oz + double(k0) * sp.dz, zb = sp.oz + double(k1) * sp.dz;
   const double bx0 = fmin(xa, xb), bx1 = fmax(xa, xb), by0 = fmin(ya, yb), by1 = fmax(ya, yb);
-  const double bz1 = fmax(za, zb);
-  int la = 0, lb = 0;
-  for (int j = 0; j < sp.n_layers; ++j) {
-    if (a.layers[sp.layer0 + j].t_begin <= tla) la = j;
-    if (a.layers[sp.layer0 + j].t_begin <= tlb) lb = j;
-  }
+  const float bz1 = float(fmax(za, zb));
   // Per source the geometry runs in FP32 on coordinates relative to the
   // tile's centre (|offsets| up to ~1 m, FP32 error < 1e-7 m); distances are
-  // shrunk by kShrink and each term is inflated by 1 + 1e-4, so the sum stays
-  // an upper bound.
+  // shrunk by kShrink and each term is inflated by 1 + 1e-4, which also
+  // covers the FP32 rounding of the coefficient, the layer height and the
+  // sum (n terms: n 2^-24 relative).
   constexpr float kShrink = 1e-7f;
   const double cxd = 0.5 * (bx0 + bx1), cyd = 0.5 * (by0 + by1);
   const float hx = float(0.5 * (bx1 - bx0)), hy = float(0.5 * (by1 - by0));
   const float inv_alpha = float(1.0 / sp.alpha);
-  const double C0 = sp.A / (2.0 * kPi * sp.k);
-  const double budget = a.T_thr - 1.0 - double(sp.T0);
-  double sum = 0.0;
+  const float budget = float(a.T_thr - 1.0 - double(sp.T0));
+  float sum = 0.0f;
   for (int j = 0; j < sp.n_tracks; ++j) {
-    const TrackDev tr = a.tracks[sp.track0 + j];
-    if (tr.layer < la || tr.layer > lb || tr.t_start > tlb) continue;
-    const double ta = fmax(tla, tr.t_start);
-    const double pa = tr.v * (ta - tr.t_start), pb = tr.v * (tlb - tr.t_start);
-    const float ux = float(tr.ux), uy = float(tr.uy), v = float(tr.v);
+    const TrackWin& tw = a.win[sp.track0 + j];
+    if (!tw.on) continue;
+    const float ux = tw.ux, uy = tw.uy, v = tw.v;
     // the source's path in the window, relative to the tile's centre
-    const float ax = float(tr.x0 + tr.ux * pa - cxd), ay = float(tr.y0 + tr.uy * pa - cyd);
-    const float bx = float(tr.x0 + tr.ux * pb - cxd), by = float(tr.y0 + tr.uy * pb - cyd);
+    const float ax = float(tw.ax - cxd), ay = float(tw.ay - cyd);
+    const float bx = float(tw.bx - cxd), by = float(tw.by - cyd);
     const float dx = fmaxf(0.f, fmaxf(fminf(ax, bx) - hx, -hx - fmaxf(ax, bx)));
     const float dy = fmaxf(0.f, fmaxf(fminf(ay, by) - hy, -hy - fmaxf(ay, by)));
-    const float dz = float(fmax(0.0, a.layers[sp.layer0 + tr.layer].z - bz1));
+    const float dz = fmaxf(0.f, tw.z - bz1);
     const float R_min = sqrtf(dx * dx + dy * dy + dz * dz) - kShrink;
     if (!(R_min > 0.f)) return true;
     // smallest (x - x_s) . u over the box corners and the path's end points
@@ -112,7 +104,7 @@ __device__ bool tile_is_active(const ActiveArgs& a, int t) {
         (s_lo <= 0.f && s_hi >= 0.f) ? 0.f : fmaxf(0.f, fminf(fabsf(s_lo), fabsf(s_hi)) - kShrink);
     const float aw = v * (lat * lat + dz * dz) * (0.25f * inv_alpha);
     const float wake = R_min >= aw ? __expf(-aw / R_min) / R_min : 1.f / (float(kE) * aw);
-    sum += C0 * tr.P * double(fminf(ahead / R_min, wake)) * (1.0 + 1e-4);
+    sum += tw.cp * fminf(ahead / R_min, wake) * 1.0001f;
     if (sum >= budget) return true;  // already over: hot
   }
   return false;

@@ -107,7 +107,8 @@ struct ms_ctx {
   std::vector<LayerDev> layers_h;
   TrackDev* tracks_d = nullptr;
   LayerDev* layers_d = nullptr;
-  size_t tracks_cap = 0, layers_cap = 0;
+  ms::TrackWin* win_d = nullptr;   // the tracks over the current launch's window (active set)
+  size_t tracks_cap = 0, layers_cap = 0, win_cap = 0;
   int slots = 0;
   bool src_valid = false;
   void* levels_d = nullptr;        // SrcLevelT<AT> of the context's arithmetic type
@@ -444,7 +445,7 @@ int set_sources(ms_ctx* c, const ms_heat_source* src) {
             std::isfinite(t.v) && t.P >= 0 && std::isfinite(t.P) && std::isfinite(t.x0) &&
             std::isfinite(t.y0) && std::isfinite(t.t_start)))
         return fail(MS_ERR_INVALID_ARG, "invalid track %d of specimen %zu", j, s);
-      tr.push_back(TrackDev{t.x0, t.y0, t.ux, t.uy, t.v, t.P, t.t_start, t.layer, 0});
+      tr.push_back(TrackDev{t.x0, t.y0, t.ux, t.uy, t.v, t.P, t.t_start, t.layer, int32_t(s)});
       slots = std::max(slots, ++per_layer[size_t(t.layer)]);
     }
     for (int j = 0; j < h.n_layers; ++j) {
@@ -464,6 +465,7 @@ int set_sources(ms_ctx* c, const ms_heat_source* src) {
   drop_graphs(c);
   int rc;
   if ((rc = grow(&c->tracks_d, &c->tracks_cap, tr.size())) != MS_OK) return rc;
+  if ((rc = grow(&c->win_d, &c->win_cap, tr.size())) != MS_OK) return rc;
   if ((rc = grow(&c->layers_d, &c->layers_cap, ly.size())) != MS_OK) return rc;
   if (!tr.empty())
     MS_CUDA(cudaMemcpy(c->tracks_d, tr.data(), tr.size() * sizeof(TrackDev), cudaMemcpyHostToDevice));
@@ -491,7 +493,13 @@ int ensure_table(ms_ctx* c, int n_levels) {
   return MS_OK;
 }
 
-int launch_table(ms_ctx* c, int64_t level0, int n_levels) {
+double level_time(const ms_ctx* c, int64_t level) {
+  return c->t_base + double(level - c->n_base) * c->dt;
+}
+
+// The source table of levels level0 .. level0 + n_levels - 1; with_window
+// also writes every track's path over that window for the active set.
+int launch_table(ms_ctx* c, int64_t level0, int n_levels, bool with_window = false) {
   ms::TableArgs ta{};
   ta.specs = c->specs_d;
   ta.tracks = c->tracks_d;
@@ -504,6 +512,12 @@ int launch_table(ms_ctx* c, int64_t level0, int n_levels) {
   ta.dt = c->dt;
   ta.levels = c->levels_d;
   ta.entries = c->entries_d;
+  if (with_window && !c->tracks_h.empty()) {
+    ta.win = c->win_d;
+    ta.n_tracks = int32_t(c->tracks_h.size());
+    ta.t_a = level_time(c, level0);
+    ta.t_b = level_time(c, level0 + n_levels - 1);
+  }
   if (c->prm.precision == MS_F64)
     MS_CUDA(ms::launch_src_table<double>(ta, c->work_d, c->stream));
   else
@@ -512,9 +526,6 @@ int launch_table(ms_ctx* c, int64_t level0, int n_levels) {
   return MS_OK;
 }
 
-double level_time(const ms_ctx* c, int64_t level) {
-  return c->t_base + double(level - c->n_base) * c->dt;
-}
 
 template <typename AT, typename FT>
 int run_track_impl(ms_ctx* c, int64_t n_steps) {
@@ -525,17 +536,14 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
   int64_t left = n_steps;
   while (left > 0) {
     const int steps = int(std::min<int64_t>(S, left));
-    if ((rc = launch_table(c, c->step_n, steps + 1)) != MS_OK) return rc;
+    if ((rc = launch_table(c, c->step_n, steps + 1, use_list)) != MS_OK) return rc;
     if (use_list) {
       ms::ActiveArgs aa{};
       aa.specs = c->specs_d;
-      aa.tracks = c->tracks_d;
-      aa.layers = c->layers_d;
+      aa.win = c->tracks_h.empty() ? nullptr : c->win_d;
       aa.tile_spec = c->tile_spec_d;
       aa.tile_tsat = c->tile_tsat_d;
       aa.n_tiles = int32_t(c->n_tiles);
-      aa.t_a = level_time(c, c->step_n);
-      aa.t_b = level_time(c, c->step_n + steps);
       aa.T_thr = c->prm.T_thr;
       aa.tile_list = c->tile_list_d;
       aa.work = c->work_d;
@@ -822,6 +830,7 @@ void ms_destroy(ms_ctx* c) {
   cudaFree(c->hyb_d);
   cudaFree(c->ops_d);
   cudaFree(c->tracks_d);
+  cudaFree(c->win_d);
   cudaFree(c->layers_d);
   cudaFree(c->levels_d);
   cudaFree(c->entries_d);

@@ -41,7 +41,19 @@ struct SpecDev {
 
 struct TrackDev {
   double x0, y0, ux, uy, v, P, t_start;
-  int32_t layer, pad;
+  int32_t layer;
+  int32_t spec;            // specimen of the track
+};
+
+// One track over an active-set window [t_a, t_b] (written with the source
+// table of the launch): the source's path in the window, absolute.
+struct TrackWin {
+  double ax, ay;           // position at max(t_a, t_start)
+  double bx, by;           // position at t_b
+  float ux, uy, v;         // direction and speed
+  float cp;                // A P / (2 pi k) (the bound inflates it)
+  float z;                 // surface of the track's layer
+  int32_t on;              // started by t_b and on a layer current in the window
 };
 
 struct LayerDev {
@@ -62,6 +74,11 @@ struct TableArgs {
   double dt;
   void* levels;            // SrcLevelT<AT> [n_specs][n_levels]
   void* entries;           // SrcEntryT<AT> [n_specs][n_levels][slots]
+  // optional, for the active set: every track over the window [t_a, t_b]
+  TrackWin* win;           // [n_tracks] or nullptr
+  int32_t n_tracks;        // tracks of all specimens
+  int32_t pad2;
+  double t_a, t_b;
 };
 
 // Work counters of one launch of k_track (device memory, reset per launch).
@@ -121,13 +138,11 @@ struct TrackArgs {
 // saturated at the preheat temperature.
 struct ActiveArgs {
   const SpecDev* specs;
-  const TrackDev* tracks;
-  const LayerDev* layers;
+  const TrackWin* win;         // the tracks over the launch's window (source-table launch)
   const int32_t* tile_spec;
   const float* tile_tsat;
   int32_t n_tiles;
   int32_t pad;
-  double t_a, t_b;             // global times of the first and last level of the launch
   double T_thr;
   int32_t* tile_list;
   WorkCounters* work;

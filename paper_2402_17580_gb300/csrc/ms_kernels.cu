@@ -39,14 +39,13 @@ constexpr double kLog2e = 1.4426950408889634074;
 
 
 // --------------------------------------------------------- source table
+// One warp per (specimen, level): the lanes take the specimen's tracks 32 at
+// a time, a ballot numbers the started ones of the current layer in track
+// order (their table slots), and each lane computes its own entry in FP64.
+// Warps past the table write the active set's per-track window (TrackWin),
+// one thread per track.
 template <typename AT>
-__global__ void k_src_table(const TableArgs a, WorkCounters* work) {
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id == 0 && work) {
-    work->n_active = 0;
-    work->next = 0;
-  }
-  if (id >= a.n_specs * a.n_levels) return;
+__device__ __forceinline__ void table_level(const TableArgs& a, int id, int lane) {
   const int s = id / a.n_levels;
   const int lv = id - s * a.n_levels;
   const SpecDev& sp = a.specs[s];
@@ -65,31 +64,87 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   const double cv = -kLog2e / (2.0 * sp.alpha);
   SrcEntryT<AT>* out =
       static_cast<SrcEntryT<AT>*>(a.entries) + (int64_t(s) * a.n_levels + lv) * a.slots;
-  int n = 0, axis = 1;
-  for (int j = 0; j < sp.n_tracks && n < a.slots; ++j) {
-    const TrackDev tr = a.tracks[sp.track0 + j];
-    if (tr.layer != l || tl < tr.t_start) continue;
-    const double travel = tr.v * (tl - tr.t_start);
-    const double sx = tr.x0 + tr.ux * travel, sy = tr.y0 + tr.uy * travel;
-    const double C = C0 * tr.P;
-    SrcEntryT<AT> e;
-    e.s_xi = AT(sx * tr.ux + sy * tr.uy);
-    e.s_pp = AT(sx * tr.uy - sy * tr.ux);
-    e.ux = AT(tr.ux);
-    e.uy = AT(tr.uy);
-    e.cR = AT(cv * tr.v);
-    e.lC = C > 0.0 ? AT(log2(C)) : AT(-INFINITY);
-    e.pad0 = e.pad1 = AT(0);
-    if (!(e.uy == AT(0))) axis = 0;
-    out[n++] = e;
+  int n = 0;
+  bool axis = true;
+  for (int j0 = 0; j0 < sp.n_tracks && n < a.slots; j0 += 32) {
+    const int j = j0 + lane;
+    TrackDev tr{};
+    bool on = false;
+    if (j < sp.n_tracks) {
+      tr = a.tracks[sp.track0 + j];
+      on = tr.layer == l && !(tl < tr.t_start);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    const int slot = n + __popc(m & ((1u << lane) - 1u));
+    if (on && slot < a.slots) {
+      const double travel = tr.v * (tl - tr.t_start);
+      const double sx = tr.x0 + tr.ux * travel, sy = tr.y0 + tr.uy * travel;
+      const double C = C0 * tr.P;
+      SrcEntryT<AT> e;
+      e.s_xi = AT(sx * tr.ux + sy * tr.uy);
+      e.s_pp = AT(sx * tr.uy - sy * tr.ux);
+      e.ux = AT(tr.ux);
+      e.uy = AT(tr.uy);
+      e.cR = AT(cv * tr.v);
+      e.lC = C > 0.0 ? AT(log2(C)) : AT(-INFINITY);
+      e.pad0 = e.pad1 = AT(0);
+      out[slot] = e;
+      axis = axis && e.uy == AT(0);
+    }
+    axis = __all_sync(0xffffffffu, axis);
+    n += __popc(m);
   }
-  SrcLevelT<AT> r;
-  r.n = n;
-  r.axis = axis;
-  r.z_surf = AT(L.z);
-  r.T0 = AT(sp.T0);
-  r.T_max = AT(sp.T_max);
-  static_cast<SrcLevelT<AT>*>(a.levels)[id] = r;
+  if (lane == 0) {
+    SrcLevelT<AT> r;
+    r.n = n < a.slots ? n : a.slots;
+    r.axis = axis ? 1 : 0;
+    r.z_surf = AT(L.z);
+    r.T0 = AT(sp.T0);
+    r.T_max = AT(sp.T_max);
+    static_cast<SrcLevelT<AT>*>(a.levels)[id] = r;
+  }
+}
+
+__device__ __forceinline__ void track_window(const TableArgs& a, int t) {
+  const TrackDev tr = a.tracks[t];
+  const SpecDev& sp = a.specs[tr.spec];
+  const double tla = a.t_a - sp.t_offset, tlb = a.t_b - sp.t_offset;
+  int la = 0, lb = 0;
+  for (int j = 0; j < sp.n_layers; ++j) {
+    if (a.layers[sp.layer0 + j].t_begin <= tla) la = j;
+    if (a.layers[sp.layer0 + j].t_begin <= tlb) lb = j;
+  }
+  TrackWin w;
+  w.on = !(tr.layer < la || tr.layer > lb || tr.t_start > tlb);
+  const double ta = fmax(tla, tr.t_start);
+  const double pa = tr.v * (ta - tr.t_start), pb = tr.v * (tlb - tr.t_start);
+  w.ax = tr.x0 + tr.ux * pa;
+  w.ay = tr.y0 + tr.uy * pa;
+  w.bx = tr.x0 + tr.ux * pb;
+  w.by = tr.y0 + tr.uy * pb;
+  w.ux = float(tr.ux);
+  w.uy = float(tr.uy);
+  w.v = float(tr.v);
+  w.cp = float(sp.A / (2.0 * kPi * sp.k) * tr.P);
+  w.z = float(a.layers[sp.layer0 + tr.layer].z);
+  a.win[t] = w;
+}
+
+template <typename AT>
+__global__ void k_src_table(const TableArgs a, WorkCounters* work) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt == 0 && work) {
+    work->n_active = 0;
+    work->next = 0;
+  }
+  const int warp = gt >> 5, lane = threadIdx.x & 31;
+  const int n_table = a.n_specs * a.n_levels;
+  if (warp < n_table) {
+    table_level<AT>(a, warp, lane);
+  } else if (a.win) {
+    const int t = gt - n_table * 32;
+    if (t < a.n_tracks) track_window(a, t);
+  }
 }
 
 
@@ -422,7 +477,7 @@ inline unsigned blocks_for(int64_t n, int threads) {
 // ------------------------------------------------------------- launchers
 template <typename AT>
 cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream) {
-  const int n = a.n_specs * a.n_levels;
+  const int64_t n = int64_t(a.n_specs) * a.n_levels * 32 + (a.win ? a.n_tracks : 0);
   if (n <= 0) return cudaSuccess;
   k_src_table<AT><<<blocks_for(n, 128), 128, 0, stream>>>(a, work);
   return cudaGetLastError();

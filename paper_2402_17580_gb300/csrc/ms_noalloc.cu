@@ -130,7 +130,7 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
           std::isfinite(t.v) && t.P >= 0 && std::isfinite(t.P) && std::isfinite(t.x0) &&
           std::isfinite(t.y0) && std::isfinite(t.t_start)))
       return ms::record_error(MS_ERR_INVALID_ARG, "invalid track");
-    up.tracks[j] = ms::TrackDev{t.x0, t.y0, t.ux, t.uy, t.v, t.P, t.t_start, t.layer, 0};
+    up.tracks[j] = ms::TrackDev{t.x0, t.y0, t.ux, t.uy, t.v, t.P, t.t_start, t.layer, 0};  // one specimen
     if (++per_layer[t.layer] > slots) slots = per_layer[t.layer];
   }
   for (int j = 0; j < src->n_layers; ++j) {
