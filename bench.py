@@ -163,14 +163,17 @@ class ClockSampler:
 # ------------------------------------------------------------- algorithmic work
 def algorithmic_sfu_ops(st):
     """SFU operations the hot kernel's processed work requires by the method's
-    formulas (a lower bound), split by SFU rate class, from the kernel's own
-    work counters: one 1/R (rsqrt class) and one exponential (ex2 class) per
-    point and started source at every evaluated time level, plus one
-    exponential and one reciprocal for k_as(T^n) per point-step on which the
-    model ran.  Tiles the active set drops and steps the warp vote skips do
-    not count.  Returns (slow, ex2)."""
-    slow = int(st.source_evaluations) + int(st.model_point_steps)
-    fast = int(st.source_evaluations) + int(st.model_point_steps)
+    formulas, split by SFU rate class, from the kernel's own work counters:
+    one 1/R (rsqrt class) and one exponential (ex2 class) per point and
+    started source at every evaluated time level (the moving-source
+    temperature), plus the phase model's transcendentals on the point-steps
+    where it ran, counted by k_track on the branch each point took: the
+    exponentials of X_alpha^eq, X_am^eq and k_as, the reciprocal of k_as, the
+    powers x^p = 2^(p log2 x) of the diffusive rates and the App. A closed
+    form.  Tiles the active set drops and steps the warp vote skips do not
+    count.  Returns (slow, ex2)."""
+    slow = int(st.source_evaluations) + int(st.model_sfu_slow)
+    fast = int(st.source_evaluations) + int(st.model_sfu_ex2)
     return slow, fast
 
 
@@ -412,6 +415,9 @@ def run_ours(args):
                  "model_point_steps_per_step": int(st.model_point_steps) // args.steps,
                  "tile_steps_active_frac": round(st.tile_steps_active / max(1, st.tile_steps_total), 4),
                  "model_run_frac": round(st.model_point_steps / max(1, 128 * st.tile_steps_active), 4),
+                 "model_sfu_per_model_point_step": {
+                     "ex2": round(st.model_sfu_ex2 / max(1, st.model_point_steps), 3),
+                     "log2_rcp": round(st.model_sfu_slow / max(1, st.model_point_steps), 3)},
                  "note": "counted by k_track; algorithmic SFU ops are derived from these"},
         "peak_basis": (f"measured SFU rates {rates['rsqrt']:.2f} (rsqrt/rcp class) and "
                        f"{rates['ex2']:.2f} (ex2) per SM per clock, {SM_COUNT} SMs, "

@@ -208,6 +208,13 @@ typedef struct ms_stats_t {
    * fp_max_iter without meeting the WRMS stop (their last iterate is kept) */
   int64_t fp_iterations;
   int64_t fp_unconverged;
+  /* explicit scheme, plain hot kernel: transcendental operations of the
+   * phase model on the point-steps where it ran, counted on the branch each
+   * point took (Sec. 2.2: exponentials of the equilibria and of k_as, the
+   * powers x^p = 2^(p log2 x) of the rates, the reciprocal of k_as, and the
+   * App. A closed form): ex2 class, and the log2 / reciprocal class        */
+  int64_t model_sfu_ex2;
+  int64_t model_sfu_slow;
 } ms_stats_t;
 
 typedef struct ms_ctx ms_ctx;

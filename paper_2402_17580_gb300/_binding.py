@@ -64,7 +64,8 @@ class Stats(ctypes.Structure):
         ("device_error", i32), ("reserved", i32),
         ("surrogate_windows", i64), ("ode_windows", i64), ("judge_samples", i64),
         ("judge_max_err", d), ("source_evaluations", i64), ("model_point_steps", i64),
-        ("fp_iterations", i64), ("fp_unconverged", i64)]
+        ("fp_iterations", i64), ("fp_unconverged", i64), ("model_sfu_ex2", i64),
+        ("model_sfu_slow", i64)]
 
 
 class ThermalParams(ctypes.Structure):

@@ -391,6 +391,8 @@ int check_device_error(ms_ctx* c) {
     c->st.model_point_steps = int64_t(oc.model_point_steps);
     c->st.fp_iterations = int64_t(oc.fp_iterations);
     c->st.fp_unconverged = int64_t(oc.fp_unconverged);
+    c->st.model_sfu_ex2 = int64_t(oc.model_sfu_ex2);
+    c->st.model_sfu_slow = int64_t(oc.model_sfu_slow);
   }
   if (c->hyb_d) {
     ms::HybridCounters hc{};

@@ -149,21 +149,42 @@ __device__ __forceinline__ FT eq_ft(AT v) {
   return v == AT(0.9) ? FT(0.9) : FT(v);
 }
 
+// ------------------------------------------------- transcendental counts
+// The hot kernel's roofline counts the transcendental operations that the
+// model's formulas require on the branch each point takes: ex2 (exp) and the
+// slower class of lg2 (log, powers as 2^(p log2 x)) and rcp (division).  The
+// model functions take a counter; NoCount compiles to
+// nothing, SfuCount packs both classes into one word (ex2 in the low 16 bits,
+// one add per branch) that the kernel drains per tile, before either half can
+// reach 2^16 (at most 512 steps x 4 points x 12 operations of a class).
+struct NoCount {
+  __device__ __forceinline__ void add(unsigned, unsigned) {}
+};
+struct SfuCount {
+  unsigned packed = 0;
+  __device__ __forceinline__ void add(unsigned ex2, unsigned slow) { packed += ex2 | (slow << 16); }
+};
+
 // ------------------------------------------------------------ equilibria
 // eq:equilibrium_phase_as
-template <typename AT>
-__device__ __forceinline__ AT xalpha_eq(const ModelConstT<AT>& m, AT T) {
+template <typename AT, typename OC = NoCount>
+__device__ __forceinline__ AT xalpha_eq(const ModelConstT<AT>& m, AT T, OC&& oc = OC()) {
   if (T < m.T_as_end) return AT(0.9);
-  if (T <= m.T_as_start) return AT(1) - Fn<AT>::ex2(m.kaeq_l2 * (T - m.T_as_start));
+  if (T <= m.T_as_start) {
+    oc.add(1, 0);
+    return AT(1) - Fn<AT>::ex2(m.kaeq_l2 * (T - m.T_as_start));
+  }
   return AT(0);
 }
 
 // eq:equilibrium_phase_am0, third branch at T > T_am,start and capped at 0.9
-template <typename AT>
-__device__ __forceinline__ AT xam0_eq(const ModelConstT<AT>& m, AT T) {
+template <typename AT, typename OC = NoCount>
+__device__ __forceinline__ AT xam0_eq(const ModelConstT<AT>& m, AT T, OC&& oc = OC()) {
   if (T < m.T_inf) return AT(0.9);
-  if (T <= m.T_am_start)
+  if (T <= m.T_am_start) {
+    oc.add(1, 0);
     return Fn<AT>::min(AT(1) - Fn<AT>::ex2(m.kam_l2 * (T - m.T_am_start)), AT(0.9));
+  }
   return AT(0);
 }
 
@@ -193,11 +214,14 @@ __device__ __forceinline__ AT softplus2(AT y) {
 // X^{n+1} = D / (1 + w^-c), w = u + D k dt / c.  lX is log2 X^n (-inf for
 // X = 0); returns log2 X^{n+1}.  The log form keeps values far below the FP32
 // range (X~ ~ 1e-70 after one step at 1200 K) representable.
-template <typename AT>
-__device__ __forceinline__ AT logistic_step_log2(AT lX, AT D, AT k, AT c, AT inv_c, AT dt) {
+template <typename AT, typename OC = NoCount>
+__device__ __forceinline__ AT logistic_step_log2(AT lX, AT D, AT k, AT c, AT inv_c, AT dt,
+                                                 OC&& oc = OC()) {
   const AT lD = Fn<AT>::lg2(D);
   AT u = AT(0);
+  oc.add(1, 3);  // lg2 D, lg2 w, softplus2's 2^y and lg2
   if (lX > AT(-1.0e30)) {
+    oc.add(2, 1);
     const AT lxi = lX - lD;
     const AT xi = Fn<AT>::ex2(lxi);
     u = Fn<AT>::ex2((lxi - Fn<AT>::lg2(AT(1) - xi)) * inv_c);
@@ -210,8 +234,9 @@ __device__ __forceinline__ AT logistic_step_log2(AT lX, AT D, AT k, AT c, AT inv
 // eq:explicit_correction: clamp negatives, rescale X_alpha > 0.9 keeping the
 // ratio, alpha_s regularisation above T_as,start (clamped at 0), martensite
 // dissolution if X_alpha > X_alpha^eq, martensite formation below T_am,start.
-template <typename AT, typename FT>
-__device__ __forceinline__ void correct(const ModelConstT<AT>& m, AT T, FT& xas, FT& xam) {
+template <typename AT, typename FT, typename OC = NoCount>
+__device__ __forceinline__ void correct(const ModelConstT<AT>& m, AT T, FT& xas, FT& xam,
+                                        OC&& oc = OC()) {
   xas = xas > FT(0) ? xas : FT(0);
   xam = xam > FT(0) ? xam : FT(0);
   const FT xa = xas + xam;
@@ -224,28 +249,37 @@ __device__ __forceinline__ void correct(const ModelConstT<AT>& m, AT T, FT& xas,
     const AT cap = Fn<AT>::max(AT(0.9) * (m.T_cap0 - T) * m.inv_T_reg, AT(0));
     if (xas > FT(cap)) xas = FT(cap);
   }
-  const FT xeq = eq_ft<AT, FT>(xalpha_eq<AT>(m, T));
+  const FT xeq = eq_ft<AT, FT>(xalpha_eq<AT>(m, T, oc));
   if (xas + xam > xeq) {
     const FT v = xeq - xas;
     xam = v > FT(0) ? v : FT(0);
   }
   if (T < m.T_am_start) {
-    const FT e = FT(xam0_eq<AT>(m, T)) * (FT(0.9) - xas) * FT(1.0 / 0.9);
+    const FT e = FT(xam0_eq<AT>(m, T, oc)) * (FT(0.9) - xas) * FT(1.0 / 0.9);
     if (m.martensite_literal) xam = e;
     else if (e > xam) xam = e;
   }
 }
 
 // ------------------------------------------------------------ point step
+// A diffusive rate k x^p y^q as k 2^(p log2 x + q log2 y), log2 x given (it
+// is shared between rates); the exponent is one explicit FMA, so every caller
+// rounds it the same way.  x = 0 or y = 0 give 2^-inf = 0 (reading A14).
+template <typename AT>
+__device__ __forceinline__ AT pow_rate(AT k, AT p, AT lx, AT q, AT y) {
+  return k * Fn<AT>::ex2(Fn<AT>::fma(q, Fn<AT>::lg2(y), p * lx));
+}
+
 // aux encodes the App. A initiation: 0 none; < 0 alpha_s -> beta in progress
 // with aux = log2 X~_beta; > 0 (1.0) persisted beta -> alpha_s (init_ba_steps).
-template <typename AT, typename FT>
+template <typename AT, typename FT, typename OC = NoCount>
 __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T1, AT dt,
-                                           FT& xas_io, FT& xam_io, float& aux) {
+                                           FT& xas_io, FT& xam_io, float& aux, OC&& oc = OC()) {
   const FT xas = xas_io, xam = xam_io;
   const FT xa = xas + xam;
-  const AT xeq0 = xalpha_eq<AT>(m, T0);
+  const AT xeq0 = xalpha_eq<AT>(m, T0, oc);
   const AT k = k_alpha_s<AT>(m, T0);
+  oc.add(1, 1);  // k_as: exp and reciprocal
   const AT kb = m.f * k;
 
   const FT xeq0f = eq_ft<AT, FT>(xeq0);
@@ -261,7 +295,8 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
   if (a5 || enter5) {
     // App. A: X~ = X_beta - 0.1, equilibrium D = X_beta^eq - 0.1, rate k_beta
     const AT D = AT(0.9) - xeq0;
-    L = logistic_step_log2<AT>(a5 ? AT(aux) : AT(-INFINITY), D, kb, m.c_b, m.inv_c_b, dt);
+    L = logistic_step_log2<AT>(a5 ? AT(aux) : AT(-INFINITY), D, kb, m.c_b, m.inv_c_b, dt, oc);
+    oc.add(1, 0);
     nas = FT(0.9) - FT(Fn<AT>::ex2(L));
     nam = xam;
     a5 = true;
@@ -269,9 +304,14 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
     // reading A6: beta -> alpha_s initiation, D = X_alpha^eq - X_am, alpha_m frozen
     const AT D = AT(xeq0f - xam);
     const AT las = xas > FT(0) ? Fn<AT>::lg2(AT(xas)) : AT(-INFINITY);
+    if (xas > FT(0)) oc.add(0, 1);
     AT r2 = AT(0);
-    if (xam > FT(0)) r2 = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xam)));
-    const AT lX = logistic_step_log2<AT>(las, D, k, m.c_as, m.inv_c_as, dt);
+    if (xam > FT(0)) {
+      oc.add(1, 1);
+      r2 = pow_rate<AT>(k, m.pa, las, m.qa, AT(xam));
+    }
+    const AT lX = logistic_step_log2<AT>(las, D, k, m.c_as, m.inv_c_as, dt, oc);
+    oc.add(1, 0);
     nas = FT(Fn<AT>::ex2(lX)) + FT(dt * r2);
     nam = xam - FT(dt * r2);
     if (m.init_ba_steps) a6 = true;
@@ -283,14 +323,17 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
     AT las = AT(0);
     if (lo || xam > FT(0)) las = Fn<AT>::lg2(AT(xas));
     if (lo) {
-      d_as = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xeq0f - xa)));
+      oc.add(1, 2);  // lg2 X_as, lg2 (X_eq - X_a), ex2
+      d_as = pow_rate<AT>(k, m.pa, las, m.qa, AT(xeq0f - xa));
     } else if (hi) {
       const FT gap = FT(0.9) - xa;
       const AT lg = gap > FT(0) ? Fn<AT>::lg2(AT(gap)) : AT(-INFINITY);
-      d_as = -kb * Fn<AT>::ex2(m.pb * lg + m.qb * Fn<AT>::lg2(AT(xa - xeq0f)));
+      oc.add(1, gap > FT(0) ? 2 : 1);
+      d_as = pow_rate<AT>(-kb, m.pb, lg, m.qb, AT(xa - xeq0f));
     }
     if (xam > FT(0)) {
-      const AT r2 = k * Fn<AT>::ex2(m.pa * las + m.qa * Fn<AT>::lg2(AT(xam)));
+      oc.add(1, lo ? 1 : 2);  // lg2 X_am, ex2, and lg2 X_as unless r1 took it
+      const AT r2 = pow_rate<AT>(k, m.pa, las, m.qa, AT(xam));
       d_as += r2;
       d_am = -r2;
     }
@@ -299,7 +342,7 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
   }
 
   const FT before = nas;
-  correct<AT, FT>(m, T1, nas, nam);
+  correct<AT, FT>(m, T1, nas, nam, oc);
 
   if (a5) {
     const AT xt = Fn<AT>::ex2(L);
@@ -435,7 +478,8 @@ struct alignas(16) SrcEntryT {
   AT ux, uy;      // direction
   AT cR;          // -v / (2 alpha) * log2(e)
   AT lC;          // log2(A P / (2 pi k) * interlayer scale); -inf when 0
-  AT pad0, pad1;
+  AT hcR;         // -cR / 2 (the Newton correction of R + xi, source_term_x)
+  AT pad1;
 };
 using SrcEntry = SrcEntryT<float>;
 
@@ -451,9 +495,18 @@ using SrcLevel = SrcLevelT<float>;
 // Contribution of one source to a point with squared depth below the surface
 // dz2 (plus a tiny constant, which keeps R > 0 and sends R = 0 to the T_max
 // cap):  A P / (2 pi k R) exp(-v (R + xi) / (2 alpha)).
-// Behind the source (xi < 0) R + xi cancels; it is computed there as
-// perp^2 / (R + |xi|), algebraically equal and free of cancellation, so far
-// receding sources keep full accuracy.  In FP32: 16 instructions, 3 on the SFU.
+// Behind the source (xi < 0) R + xi cancels: R carries the rounding of r2
+// and of the approximate 1/sqrt, and a far receding source would lose its
+// exponent to it.  So d = R + xi from the approximate R is refined by one
+// Newton step on f(d) = d (d - 2 xi) - perp^2, which is 0 at the exact
+// d = R + xi since (R + xi)(R - xi) = R^2 - xi^2 = perp^2:
+//   d <- d - f(d) / f'(d),  f'(d) = 2 (d - xi) = 2 R ~ 2 / rinv.
+// f(d) is one FMA of exact-or-once-rounded operands, so the refined d keeps
+// its relative accuracy on both sides of the source with no reciprocal and no
+// branch.  The correction is folded into the exponent:
+//   cR d = cR d0 + hcR * (rinv f(d0)),  hcR = -cR / 2.
+// In FP32: 10 instructions, 2 on the SFU; the offsets add 1 per point in a
+// row tile (source_term_x) and 5 in the general form (source_term).
 //
 // The offsets are xi = px u_x + (py u_y - s_xi) and pp = px u_y + (py (-u_x)
 // - s_pp); the bracketed parts and, when u_y == 0, perp^2 do not depend on
@@ -463,10 +516,10 @@ template <typename AT>
 __device__ __forceinline__ AT source_term_x(const SrcEntryT<AT>& e, AT xi, AT perp2) {
   const AT r2 = Fn<AT>::fma(xi, xi, perp2);
   const AT rinv = Fn<AT>::rsqrt(r2);
-  const AT w = Fn<AT>::fma(r2, rinv, Fn<AT>::abs(xi));  // R + |xi|
-  const AT inv_w = Fn<AT>::rcp(w);  // unconditional, so the select below stays branch-free
-  const AT rpx = xi >= AT(0) ? w : perp2 * inv_w;
-  return rinv * Fn<AT>::ex2(Fn<AT>::fma(e.cR, rpx, e.lC));
+  const AT d = Fn<AT>::fma(r2, rinv, xi);                                  // R + xi, approximate
+  const AT f = Fn<AT>::fma(d, Fn<AT>::fma(AT(-2), xi, d), -perp2);        // d (d - 2 xi) - perp^2
+  const AT a = Fn<AT>::fma(e.hcR, rinv * f, Fn<AT>::fma(e.cR, d, e.lC));  // cR (R + xi) + lC
+  return rinv * Fn<AT>::ex2(a);
 }
 
 // The parts of xi and pp that do not depend on px.

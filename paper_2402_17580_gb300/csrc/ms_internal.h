@@ -96,6 +96,8 @@ struct OpCounters {
   unsigned long long model_point_steps;
   unsigned long long fp_iterations;    // implicit scheme: fixed-point iterations
   unsigned long long fp_unconverged;   // implicit scheme: substeps that hit the cap
+  unsigned long long model_sfu_ex2;    // explicit scheme: the model's exponentials
+  unsigned long long model_sfu_slow;   // explicit scheme: the model's logarithms and reciprocals
 };
 
 // Counters of the hybrid kernel (running totals, reset by ms_reset_stats).

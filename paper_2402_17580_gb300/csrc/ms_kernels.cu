@@ -87,7 +87,8 @@ __device__ __forceinline__ void table_level(const TableArgs& a, int id, int lane
       e.uy = AT(tr.uy);
       e.cR = AT(cv * tr.v);
       e.lC = C > 0.0 ? AT(log2(C)) : AT(-INFINITY);
-      e.pad0 = e.pad1 = AT(0);
+      e.hcR = AT(-0.5 * cv * tr.v);
+      e.pad1 = AT(0);
       out[slot] = e;
       axis = axis && e.uy == AT(0);
     }
@@ -156,11 +157,17 @@ __global__ void k_fill_f32(float* p, int64_t n, float v) {
 
 
 // ------------------------------------------------------------ hot kernel
+// The FP32 explicit path advances a thread's four points in lockstep
+// (point_step4); the other paths call point_step point by point.
+template <typename AT, typename FT, bool IMPL>
+constexpr bool kLockstep = std::is_same<AT, float>::value && std::is_same<FT, float>::value && !IMPL;
+
 // One 128-point tile for the launch's S steps (4 points per lane).
 template <typename AT, typename FT, bool IMPL>
 __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane,
                                            unsigned long long& n_src, unsigned long long& n_model,
-                                           unsigned& fp_it, unsigned& fp_unconv) {
+                                           unsigned& fp_it, unsigned& fp_unconv, SfuCount& oc,
+                                           unsigned& n_ex2, unsigned& n_slow) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
@@ -212,6 +219,12 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     }
     if (!(skipping && __all_sync(0xffffffffu, noop))) {
       ++models;
+      if constexpr (kLockstep<AT, FT, IMPL>) {
+        bool run[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) run[q] = valid[q] && pz[q] <= zlim;
+        point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, oc);
+      } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (valid[q] && pz[q] <= zlim) {
@@ -219,8 +232,9 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
             point_step_implicit<AT, FT>(a.m, T0[q], T1[q], a.dt, a.n_sub, xs[q], xm[q], ax[q],
                                         fp_it, fp_unconv);
           else
-            point_step<AT, FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q]);
+            point_step<AT, FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q], oc);
         }
+      }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) T0[q] = T1[q];
@@ -229,6 +243,9 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   Vec4<FT>::store(a.xas + g0, xs);
   Vec4<FT>::store(a.xam + g0, xm);
   Vec4<float>::store(a.aux + g0, ax);
+  n_ex2 += oc.packed & 0xffffu;
+  n_slow += oc.packed >> 16;
+  oc.packed = 0;
   bool ok = true;
   float ts = -INFINITY;
 #pragma unroll
@@ -262,14 +279,28 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
   unsigned long long done = 0, n_src = 0, n_model = 0;
   unsigned fp_it = 0, fp_unconv = 0;
+  SfuCount oc;
+  unsigned n_ex2 = 0, n_slow = 0;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
     track_tile<AT, FT, IMPL>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model, fp_it,
-                             fp_unconv);
+                             fp_unconv, oc, n_ex2, n_slow);
     ++done;
+  }
+  if (a.ops) {
+    unsigned long long e = n_ex2, sl = n_slow;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    }
+    if (lane == 0 && (e || sl)) {
+      atomicAdd(&a.ops->model_sfu_ex2, e);
+      atomicAdd(&a.ops->model_sfu_slow, sl);
+    }
   }
   if constexpr (IMPL) {
     unsigned long long it = fp_it, un = fp_unconv;
@@ -296,6 +327,47 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT
 template <typename AT, typename FT, bool IMPL>
 __global__ void __launch_bounds__(256) k_step_ext(const StepArgs<AT, FT> a, int vec_T) {
   const int64_t i0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+  if constexpr (kLockstep<AT, FT, IMPL>) {
+    // every lane of the warp takes part in point_step4's votes; lanes past
+    // the end advance no point
+    float xs[4] = {0.0f, 0.0f, 0.0f, 0.0f}, xm[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float ax[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float T0[4] = {300.0f, 300.0f, 300.0f, 300.0f}, T1[4] = {300.0f, 300.0f, 300.0f, 300.0f};
+    const int cnt = i0 < a.n ? (a.n - i0 < 4 ? int(a.n - i0) : 4) : 0;
+    if (cnt > 0) {
+      Vec4<float>::load(a.xas + i0, xs);  // state arrays are padded to whole tiles
+      Vec4<float>::load(a.xam + i0, xm);
+      Vec4<float>::load(a.aux + i0, ax);
+      if (vec_T && cnt == 4) {
+        const float4 t0 = __ldcs(reinterpret_cast<const float4*>(a.T0 + i0));
+        const float4 t1 = __ldcs(reinterpret_cast<const float4*>(a.T1 + i0));
+        T0[0] = t0.x; T0[1] = t0.y; T0[2] = t0.z; T0[3] = t0.w;
+        T1[0] = t1.x; T1[1] = t1.y; T1[2] = t1.z; T1[3] = t1.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < cnt) {
+            T0[q] = a.T0[i0 + q];
+            T1[q] = a.T1[i0 + q];
+          }
+      }
+    }
+    bool run[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) run[q] = q < cnt;
+    NoCount nc;
+    point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, nc);
+    if (cnt > 0) {
+      Vec4<float>::store(a.xas + i0, xs);
+      Vec4<float>::store(a.xam + i0, xm);
+      Vec4<float>::store(a.aux + i0, ax);
+      bool ok = true;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
+      if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
+    }
+    return;
+  }
   unsigned fp_it = 0, fp_unconv = 0;
   if (i0 < a.n) {
     FT xs[4], xm[4];

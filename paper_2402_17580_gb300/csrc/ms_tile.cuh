@@ -43,7 +43,7 @@ __device__ __forceinline__ SrcEntryT<float> load_entry(const SrcEntryT<float>* p
   const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
   SrcEntryT<float> e;
   e.s_xi = a.x; e.s_pp = a.y; e.ux = a.z; e.uy = a.w;
-  e.cR = b.x; e.lC = b.y; e.pad0 = b.z; e.pad1 = b.w;
+  e.cR = b.x; e.lC = b.y; e.hcR = b.z; e.pad1 = b.w;
   return e;
 }
 __device__ __forceinline__ SrcEntryT<double> load_entry(const SrcEntryT<double>* p) {
@@ -64,8 +64,8 @@ __device__ __forceinline__ AT depth2(AT pz, AT z_surf) {
 // not depend on x, and for a level whose sources all move along +-x the whole
 // perp^2, are computed once per source instead of once per point: the same
 // operations on the same operands, so the bits do not change (see
-// source_term).  Per point and source that leaves 12 instructions instead of
-// 16 when the level is axis-aligned.
+// source_term).  Per point and source that leaves 11 instructions instead of
+// 15 when the level is axis-aligned.
 template <typename AT>
 __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en,
                                        const AT* px, const AT* py, const AT* pz, bool row,
@@ -144,6 +144,180 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
   const float r = float(xam * FT(0.9) / q);
   if (r >= XMAX) return -INFINITY;
   return float(m.T_am_start) + sfu_lg2(1.0f - r) / float(m.kam_l2);
+}
+
+// ------------------------------------------------ four points in lockstep
+// The explicit step of a thread's four points in the FP32 path.  point_step
+// is one dependent chain with branches for every point, so the four points of
+// a thread run one after another.  Here the model's common branch is written
+// as straight-line code over the four points, so their chains interleave.
+// The common branch: no App. A initiation running (aux = 0) or starting
+// (reading A5: X_alpha > X_alpha^eq on the bound 0.9 with no martensite;
+// reading A6: X_as = 0 below X_alpha^eq).  If any point of the warp leaves
+// it, the warp takes point_step for its points.  The optional parts (the
+// exponentials of the equilibria, the alpha_s -> beta rate, alpha_m ->
+// alpha_s, the rescale of X_alpha > 0.9, the regularisation cap, martensite
+// formation) run when any point of the warp needs them.  Every value is the
+// same operation on the same operands as in point_step and correct, so the
+// two give the same bits (a subset specimen, whose warps hold other points,
+// checks that).  run[q] marks the points to advance; every lane of the warp
+// must call this.
+template <typename OC>
+__device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const float* T0,
+                                            const float* T1, float dt, const bool* run,
+                                            float* xs, float* xm, float* ax, OC& oc) {
+  constexpr unsigned FULL = 0xffffffffu;
+  using F = Fn<float>;
+  float xa[4], xeq0[4];
+  bool mid0[4], any = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    xa[q] = xs[q] + xm[q];
+    mid0[q] = !(T0[q] < m.T_as_end) && T0[q] <= m.T_as_start;
+    any = any || (run[q] && mid0[q]);
+  }
+  // X_alpha^eq(T^n) (eq:equilibrium_phase_as)
+  if (__any_sync(FULL, any)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float e = 1.0f - F::ex2(m.kaeq_l2 * (T0[q] - m.T_as_start));
+      xeq0[q] = T0[q] < m.T_as_end ? 0.9f : (mid0[q] ? e : 0.0f);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xeq0[q] = T0[q] < m.T_as_end ? 0.9f : 0.0f;
+  }
+  bool rare = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool enter5 = xeq0[q] < 0.9f && xa[q] > xeq0[q] && 0.9f - xa[q] <= 0.0f && xm[q] == 0.0f;
+    const bool enter6 = xa[q] < xeq0[q] && xs[q] == 0.0f;
+    rare = rare || (run[q] && (ax[q] != 0.0f || enter5 || enter6));
+  }
+  if (__any_sync(FULL, rare)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (run[q]) point_step<float, float>(m, T0[q], T1[q], dt, xs[q], xm[q], ax[q], oc);
+    return;
+  }
+
+  // eq:explicit_integration with the rates at T^n; r1 and r3 exclude each
+  // other and share one lg2 / lg2 / ex2 triple
+  float k[4], las[4], lg[4], nas[4], nam[4];
+  bool any_hi = false, any_am = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    k[q] = k_alpha_s<float>(m, T0[q]);
+    las[q] = F::lg2(xs[q]);
+    lg[q] = 0.0f;
+    any_hi = any_hi || (run[q] && xa[q] > xeq0[q]);
+    any_am = any_am || (run[q] && xm[q] > 0.0f);
+  }
+  if (__any_sync(FULL, any_hi)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float gap = 0.9f - xa[q];
+      lg[q] = gap > 0.0f ? F::lg2(gap) : -INFINITY;
+    }
+  }
+  any_am = __any_sync(FULL, any_am);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool lo = xa[q] < xeq0[q], hi = xa[q] > xeq0[q];
+    const float kb = m.f * k[q];
+    const float r = pow_rate<float>(lo ? k[q] : -kb, lo ? m.pa : m.pb, lo ? las[q] : lg[q],
+                                    lo ? m.qa : m.qb, lo ? xeq0[q] - xa[q] : xa[q] - xeq0[q]);
+    float d_as = lo || hi ? r : 0.0f, d_am = 0.0f;
+    if (any_am && xm[q] > 0.0f) {
+      const float r2 = pow_rate<float>(k[q], m.pa, las[q], m.qa, xm[q]);
+      d_as += r2;
+      d_am = -r2;
+    }
+    nas[q] = xs[q] + float(dt * d_as);
+    nam[q] = xm[q] + float(dt * d_am);
+    if (run[q]) {
+      if (mid0[q]) oc.add(1, 0);
+      oc.add(1, 1);                                      // k_as
+      if (lo) oc.add(1, 2);
+      if (hi) oc.add(1, 0.9f - xa[q] > 0.0f ? 2 : 1);
+      if (xm[q] > 0.0f) oc.add(1, lo ? 1 : 2);
+    }
+  }
+
+  // eq:explicit_correction at T^{n+1}
+  bool any_big = false, any_cap = false, any_mid1 = false, any_form = false;
+  bool mid1[4], form[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    nas[q] = nas[q] > 0.0f ? nas[q] : 0.0f;
+    nam[q] = nam[q] > 0.0f ? nam[q] : 0.0f;
+    mid1[q] = !(T1[q] < m.T_as_end) && T1[q] <= m.T_as_start;
+    form[q] = T1[q] < m.T_am_start;
+    any_big = any_big || (run[q] && nas[q] + nam[q] > 0.9f);
+    any_cap = any_cap || (run[q] && T1[q] > m.T_as_start);
+    any_mid1 = any_mid1 || (run[q] && mid1[q]);
+    any_form = any_form || (run[q] && form[q]);
+  }
+  if (__any_sync(FULL, any_big)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = nas[q] + nam[q];
+      if (x > 0.9f) {
+        const float sc = 0.9f / x;
+        nas[q] *= sc;
+        nam[q] *= sc;
+      }
+    }
+  }
+  if (__any_sync(FULL, any_cap)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (T1[q] > m.T_as_start) {
+        const float cap = F::max(0.9f * (m.T_cap0 - T1[q]) * m.inv_T_reg, 0.0f);
+        if (nas[q] > cap) nas[q] = cap;
+      }
+  }
+  float xeq1[4];
+  if (__any_sync(FULL, any_mid1)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float e = 1.0f - F::ex2(m.kaeq_l2 * (T1[q] - m.T_as_start));
+      xeq1[q] = T1[q] < m.T_as_end ? 0.9f : (mid1[q] ? e : 0.0f);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xeq1[q] = T1[q] < m.T_as_end ? 0.9f : 0.0f;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (nas[q] + nam[q] > xeq1[q]) {
+      const float v = xeq1[q] - nas[q];
+      nam[q] = v > 0.0f ? v : 0.0f;
+    }
+    if (run[q] && mid1[q]) oc.add(1, 0);
+  }
+  if (__any_sync(FULL, any_form)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool ex = !(T1[q] < m.T_inf) && T1[q] <= m.T_am_start;
+      const float x0 = T1[q] < m.T_inf
+                           ? 0.9f
+                           : (ex ? F::min(1.0f - F::ex2(m.kam_l2 * (T1[q] - m.T_am_start)), 0.9f)
+                                 : 0.0f);
+      if (form[q]) {
+        const float e = x0 * (0.9f - nas[q]) * float(1.0 / 0.9);
+        if (m.martensite_literal) nam[q] = e;
+        else if (e > nam[q]) nam[q] = e;
+        if (run[q] && ex) oc.add(1, 0);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (run[q]) {
+      xs[q] = nas[q];
+      xm[q] = nam[q];
+    }
 }
 
 // ---------------------------------------------------------- state access

@@ -322,6 +322,38 @@ def test_row_tiles_match_the_general_form(ms, case):
         zero.close()
 
 
+@pytest.mark.parametrize("T,xas,xam,ex2,slow", [
+    # 900 K: X_alpha^eq on its 0.9 plateau (no exp), k_as (exp + rcp), r1 and
+    # r2 (lg2 X_as shared, lg2 of each second factor, one exp each); g at
+    # 900 K: no exponential (plateau, above T_am,start)
+    (900.0, 0.5, 0.2, 3, 4),
+    # 1000 K: X_alpha^eq = 1 - exp(.) at T^n and again in g at T^{n+1}; k_as;
+    # r1 only (X_am = 0)
+    (1000.0, 0.5, 0.0, 4, 3),
+    # 700 K: plateau, k_as, r1 and r2, and X_am,0^eq = 1 - exp(.) in g below
+    # T_am,start
+    (700.0, 0.3, 0.1, 4, 4),
+])
+def test_model_transcendental_counts(ms, T, xas, xam, ex2, slow):
+    """The roofline's per-branch count of the model's transcendentals, pinned
+    by hand from the formulas of Sec. 2.2 on isothermal points (the source
+    starts after the run, so T = T0 everywhere and no source is evaluated)."""
+    n, steps = 3 * 128 + 5, 40
+    grid = wl.Grid((0.0, 0.0, 0.0), (1e-5, 1e-5, -1e-5), (n, 1, 1))
+    tracks = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 1.0, 0]], dtype=np.float64)
+    src = wl.HeatSource(tracks, np.array([[0.0, 0.0, 1e9, 1e9]]), T0=T)
+    ctx = ms.Context(n, T_thr=0.0)
+    ctx.set_points([grid])
+    ctx.set_state(np.full(n, xas), np.full(n, xam))
+    ctx.reset_stats()
+    ctx.run_track([src], steps, 1e-5)
+    st = ctx.stats()
+    assert st.source_evaluations == 0
+    assert st.model_point_steps == n * steps
+    assert st.model_sfu_ex2 == ex2 * n * steps
+    assert st.model_sfu_slow == slow * n * steps
+
+
 def test_temperature_query_matches_the_source(ms):
     w = wl.block_256(dims=(30, 20, 5), n_tracks=2, n_steps=150, T_thr=0.0)
     sp = w.specimens[0]
