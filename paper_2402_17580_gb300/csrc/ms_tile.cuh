@@ -65,7 +65,7 @@ __device__ __forceinline__ AT depth2(AT pz, AT z_surf) {
 // perp^2, are computed once per source instead of once per point: the same
 // operations on the same operands, so the bits do not change (see
 // source_term).  Per point and source that leaves 11 instructions instead of
-// 15 when the level is axis-aligned.
+// 15 when the level is axis-aligned.  An odd last source takes the same form.
 template <typename AT>
 __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en,
                                        const AT* px, const AT* py, const AT* pz, bool row,
@@ -86,6 +86,14 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
         acc[q] += source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), q1);
       }
     }
+    if (j < L.n) {
+      const SrcEntryT<AT> e0 = load_entry(en + j);
+      AT x0, p0;
+      source_offsets<AT>(e0, py[0], x0, p0);
+      const AT q0 = Fn<AT>::fma(p0, p0, dz2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), q0);
+    }
   } else if (row) {
     const AT dz2 = depth2<AT>(pz[0], L.z_surf);
     for (; j + 1 < L.n; j += 2) {
@@ -100,6 +108,16 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
         acc[q] += source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), Fn<AT>::fma(pp1, pp1, dz2));
       }
     }
+    if (j < L.n) {
+      const SrcEntryT<AT> e0 = load_entry(en + j);
+      AT x0, p0;
+      source_offsets<AT>(e0, py[0], x0, p0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const AT pp0 = Fn<AT>::fma(px[q], e0.uy, p0);
+        acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), Fn<AT>::fma(pp0, pp0, dz2));
+      }
+    }
   } else {
     AT dz2[4];
 #pragma unroll
@@ -112,12 +130,11 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
         acc[q] += source_term<AT>(e1, px[q], py[q], dz2[q]);
       }
     }
-  }
-  if (j < L.n) {
-    const SrcEntryT<AT> e0 = load_entry(en + j);
+    if (j < L.n) {
+      const SrcEntryT<AT> e0 = load_entry(en + j);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      acc[q] += source_term<AT>(e0, px[q], py[q], depth2<AT>(pz[q], L.z_surf));
+      for (int q = 0; q < 4; ++q) acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
+    }
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) T[q] = Fn<AT>::min(L.T0 + acc[q], L.T_max);
