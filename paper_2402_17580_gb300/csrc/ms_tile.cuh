@@ -207,7 +207,9 @@ __device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const f
   bool rare = false;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const bool enter5 = xeq0[q] < 0.9f && xa[q] > xeq0[q] && 0.9f - xa[q] <= 0.0f && xm[q] == 0.0f;
+    // point_step's entry test of A5: X_alpha^eq < 0.9 <= X_alpha (the sign of
+    // 0.9 - X_alpha is exact, and X_alpha > X_alpha^eq follows) with X_am = 0
+    const bool enter5 = xm[q] == 0.0f && xa[q] >= 0.9f && xeq0[q] < 0.9f;
     const bool enter6 = xa[q] < xeq0[q] && xs[q] == 0.0f;
     rare = rare || (run[q] && (ax[q] != 0.0f || enter5 || enter6));
   }
@@ -230,7 +232,8 @@ __device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const f
     any_hi = any_hi || (run[q] && xa[q] > xeq0[q]);
     any_am = any_am || (run[q] && xm[q] > 0.0f);
   }
-  if (__any_sync(FULL, any_hi)) {
+  any_hi = __any_sync(FULL, any_hi);
+  if (any_hi) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float gap = 0.9f - xa[q];
@@ -241,10 +244,17 @@ __device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const f
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const bool lo = xa[q] < xeq0[q], hi = xa[q] > xeq0[q];
-    const float kb = m.f * k[q];
-    const float r = pow_rate<float>(lo ? k[q] : -kb, lo ? m.pa : m.pb, lo ? las[q] : lg[q],
-                                    lo ? m.qa : m.qb, lo ? xeq0[q] - xa[q] : xa[q] - xeq0[q]);
-    float d_as = lo || hi ? r : 0.0f, d_am = 0.0f;
+    float d_as;
+    if (any_hi) {  // r1 or r3 per point
+      const float kb = m.f * k[q];
+      const float r = pow_rate<float>(lo ? k[q] : -kb, lo ? m.pa : m.pb, lo ? las[q] : lg[q],
+                                      lo ? m.qa : m.qb, lo ? xeq0[q] - xa[q] : xa[q] - xeq0[q]);
+      d_as = lo || hi ? r : 0.0f;
+    } else {       // no point of the warp above X_alpha^eq: r1 only
+      const float r = pow_rate<float>(k[q], m.pa, las[q], m.qa, xeq0[q] - xa[q]);
+      d_as = lo ? r : 0.0f;
+    }
+    float d_am = 0.0f;
     if (any_am && xm[q] > 0.0f) {
       const float r2 = pow_rate<float>(k[q], m.pa, las[q], m.qa, xm[q]);
       d_as += r2;

@@ -95,6 +95,34 @@ def test_random_temperature_histories(ms):
     check_sum(g)
 
 
+@pytest.mark.parametrize("flags", [{"martensite_literal": 1}, {"init_ba_steps": 1}])
+def test_reading_switches_match_the_oracle(ms, flags):
+    """The readings' switches (A3: martensite set to its equilibrium below
+    T_am,start; A6: the beta -> alpha_s initiation kept until the App. A exit
+    rule) on random temperature walks through ms_step and on a moving-source
+    line through ms_run_track, against the oracle with the same switches."""
+    rng = np.random.default_rng(21)
+    n, steps, dt = 2 * 128 + 9, 200, 1e-4
+    T = np.empty((steps + 1, n), dtype=np.float32)
+    T[0] = rng.uniform(300, 2100, n)
+    for s in range(steps):
+        T[s + 1] = np.clip(T[s] + rng.normal(0, 25, n), 280, 2600)
+    xas, xam, _, _ = wl.random_states(n, seed=8)
+    ctx = ms.Context(n, **flags)
+    p = oracle_params(ctx.params)
+    ctx.set_state(xas, xam)
+    for s in range(steps):
+        ctx.step(T[s], T[s + 1], dt)
+    st = orc.State.make(oracle_view(xas), oracle_view(xam))
+    orc.run_temps(st, T.astype(np.float64), dt, p)
+    o = np.stack(orc.fractions(st, T[-1].astype(np.float64), p))
+    assert max_abs_diff(ctx.fractions(), o) <= RUN_TOL
+    w = wl.line_4096(n_points=1024, n_steps=1500)
+    _, g = gpu_workload(w, **flags)
+    assert max_abs_diff(g, oracle_workload(w, p=p)) <= RUN_TOL
+    check_sum(g)
+
+
 # ------------------------------------------------------- moving source runs
 def test_line_4096_full(ms):
     """4096 points on a line under one moving source, 2000 steps of 1e-5 s,
