@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the project autotuner (S, CTA size, graph replay)")
     ap.add_argument("--graph", action="store_true", help="replay ms_run_track as a CUDA graph")
+    ap.add_argument("--no-farfield", dest="farfield", action="store_false",
+                    help="skip the far-field leg (interpolated receding sources)")
     ap.add_argument("--no-hybrid", dest="hybrid", action="store_false",
                     help="skip the window-surrogate (hybrid) measurement")
     ap.add_argument("--no-f64", dest="f64", action="store_false",
@@ -464,6 +466,9 @@ def run_ours(args):
         out["f64"] = f64_pass(ctx, w, srcs, ms)
     if rank == 0 and world == 1 and args.coupled and len(w.specimens) == 1:
         out["coupled"] = coupled_pass(w, ms, torch)
+    if rank == 0 and world == 1 and args.farfield and prec == ms.MS_F32:
+        out["farfield"] = farfield_pass(ctx, w, srcs, args, ms, torch, stream, flush, value,
+                                        sample, rates)
     if rank == 0 and world == 1 and args.hybrid and prec in (ms.MS_F32, ms.MS_KAHAN):
         out["hybrid"] = hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, value, sample)
     if rank == 0 and world == 1 and not args.no_d6:
@@ -539,6 +544,62 @@ def coupled_pass(w, ms, torch, n_steps=2000, warmup=200):
                    "device temperature pointers, on one stream"}
     th.close()
     ctx.close()
+    return res
+
+
+FARFIELD_DIST = 5e-3   # m: sources this far behind a whole row tile are interpolated
+
+
+def farfield_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sample, rates):
+    """The same pass with ms_params.farfield_dist = 5 mm: receding sources at
+    least that far behind every point of a row tile are summed at the 8
+    Chebyshev nodes of the tile's x-range and interpolated (an approximation
+    of the direct sum with a stated error bound, off by default).  Timed like
+    the plain passes; reports throughput, the share of point-source pairs
+    served by the interpolation, max|dX| on the oracle sample and the
+    kernel's SFU fraction for the work it does (direct pairs and node
+    evaluations: one 1/R and one exp each; the model as counted)."""
+    import numpy as np
+    p = type(ctx.params).from_buffer_copy(ctx.params)
+    c = ms.Context(w.n_points, p, farfield_dist=FARFIELD_DIST)
+    c.set_points([s.grid for s in w.specimens])
+    c.set_stream(stream.cuda_stream)
+    one = lambda: (c.fill_state(w.init_xas, w.init_xam), c.run_track(srcs, w.n_steps, w.dt))
+    one()
+    c.synchronize()
+    c.reset_stats()
+    times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one()
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = c.stats()
+    t = sum(times) / len(times)
+    direct = int(st.source_evaluations) + int(st.farfield_node_evaluations)
+    slow, fast = direct + int(st.model_sfu_slow), direct + int(st.model_sfu_ex2)
+    kern_s = st.hot_kernel_ms * 1e-3
+    peak_s = (slow / rates["rsqrt"] + fast / rates["ex2"]) / (SM_COUNT * SM_MAX_MHZ * 1e6)
+    pairs = int(st.farfield_point_sources) + int(st.source_evaluations)
+    res = {"value": w.point_updates / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+           "vs_plain": w.point_updates / (t * 1e-3) / plain_value,
+           "farfield_dist_m": FARFIELD_DIST,
+           "interpolated_pair_share": int(st.farfield_point_sources) / max(1, pairs),
+           "node_evaluations_per_step": int(st.farfield_node_evaluations) // args.steps,
+           "sfu_frac_of_own_work": round(peak_s / kern_s, 4) if kern_s > 0 else None,
+           "kernel": "k_track<float, float, explicit, far field>"}
+    if sample is not None:
+        idx, ofr = sample
+        g = np.stack(c.fractions())
+        res["max_abs_dX"] = float(np.max(np.abs(g[:, idx] - ofr)))
+        res["max_abs_dX_vs_direct_pass"] = float(np.max(np.abs(g[:, idx] -
+                                                               np.stack(ctx.fractions())[:, idx])))
+    c.close()
     return res
 
 

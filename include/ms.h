@@ -122,6 +122,24 @@ typedef struct ms_params {
   double  fp_eps_abs, fp_eps_rel; /* implicit: WRMS tolerances (Sec. 3: 1e-10, 1e-3) */
   int32_t fp_max_iter;            /* implicit: fixed-point iteration cap (100)    */
   int32_t reserved0;
+  /* Far field of the moving sources in ms_run_track, 0 = off (default).  In a
+   * tile of 128 points inside one grid row, at a level whose sources all move
+   * along +-x, a source that lies at least farfield_dist [m] behind every
+   * point of the tile's x-range (xi <= -farfield_dist) is evaluated at the 8
+   * Chebyshev nodes of that range, the sum over such sources is interpolated
+   * to the 128 points (Lagrange weights), and the other sources are summed
+   * point by point.  Behind a source its term (ms_heat_source) is analytic
+   * in x within a distance of the order of |xi| of the tile (the exponent
+   * v p^2 / (2 alpha (R - xi)) has a positive real part there), so the interpolation
+   * error per source is at most 4 M rho^-7 / (rho - 1) for any Bernstein
+   * ellipse rho around the range that avoids the source, M the term's bound
+   * on it; for 128 points at 10 um and farfield_dist = 5 mm, rho = 10 gives
+   * M <= A P / (2 pi k 2.1 mm) and <= 4.2e-5 K per source at P = 250 W.
+   * This is an approximation of the direct sum, for the MS_F32 explicit
+   * path (other precisions and MS_IMPLICIT return MS_ERR_UNSUPPORTED); the
+   * hybrid kernel sums point by point.  The library keeps 4 KB of
+   * interpolation weights on the device.                                   */
+  double  farfield_dist;
 } ms_params;
 
 /* ------------------------------------------------------------ geometry */
@@ -215,6 +233,12 @@ typedef struct ms_stats_t {
    * App. A closed form): ex2 class, and the log2 / reciprocal class        */
   int64_t model_sfu_ex2;
   int64_t model_sfu_slow;
+  /* far field (farfield_dist > 0): source evaluations at the interpolation
+   * nodes (8 per far source, tile and level), and point-source pairs whose
+   * term came from the interpolation instead; source_evaluations then
+   * counts the point-source pairs evaluated directly                       */
+  int64_t farfield_node_evaluations;
+  int64_t farfield_point_sources;
 } ms_stats_t;
 
 typedef struct ms_ctx ms_ctx;
@@ -374,8 +398,9 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
  * needs); calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it, so the caller must serialise them.  Non-finite
  * fractions are not reported by this call.
- * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32, or
- * MS_IMPLICIT), CUDA. */
+ * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32,
+ * MS_IMPLICIT, or farfield_dist != 0: this call sums every source
+ * directly), CUDA. */
 int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid, const ms_heat_source* src,
                          float* x_as, float* x_am, float* aux, int64_t n_points,
                          int64_t step0, int64_t n_steps, double dt, void* cuda_stream);

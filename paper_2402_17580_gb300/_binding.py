@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
         (n, i32) for n in ("martensite_literal", "init_ba_steps", "precision", "steps_per_launch",
                            "rebuild_steps", "block_threads", "flags", "integrator")] + [
         ("dt_sub", d), ("fp_eps_abs", d), ("fp_eps_rel", d), ("fp_max_iter", i32),
-        ("reserved0", i32)]
+        ("reserved0", i32), ("farfield_dist", d)]
 
 
 class Grid(ctypes.Structure):
@@ -65,7 +65,8 @@ class Stats(ctypes.Structure):
         ("surrogate_windows", i64), ("ode_windows", i64), ("judge_samples", i64),
         ("judge_max_err", d), ("source_evaluations", i64), ("model_point_steps", i64),
         ("fp_iterations", i64), ("fp_unconverged", i64), ("model_sfu_ex2", i64),
-        ("model_sfu_slow", i64)]
+        ("model_sfu_slow", i64), ("farfield_node_evaluations", i64),
+        ("farfield_point_sources", i64)]
 
 
 class ThermalParams(ctypes.Structure):

@@ -95,6 +95,7 @@ struct ms_ctx {
   uint64_t judge_thresh = 0;
   ms::HybridCounters* hyb_d = nullptr;
   ms::OpCounters* ops_d = nullptr;       // work done by k_track
+  float* ff_d = nullptr;                 // far-field weights and nodes (farfield_dist > 0)
   int hybrid_per_sm = 0;
 
   // staging
@@ -234,6 +235,10 @@ int check_params(const ms_params& p) {
     return fail(MS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
   if (p.integrator != MS_EXPLICIT && p.integrator != MS_IMPLICIT)
     return fail(MS_ERR_INVALID_ARG, "unknown integrator %d", p.integrator);
+  if (!(std::isfinite(p.farfield_dist) && p.farfield_dist >= 0.0))
+    return fail(MS_ERR_INVALID_ARG, "farfield_dist must be finite and >= 0");
+  if (p.farfield_dist > 0.0 && (p.precision != MS_F32 || p.integrator != MS_EXPLICIT))
+    return fail(MS_ERR_UNSUPPORTED, "the far field runs in the MS_F32 explicit path only");
   if (p.integrator == MS_IMPLICIT) {
     if (p.precision != MS_F32 && p.precision != MS_F64)
       return fail(MS_ERR_UNSUPPORTED, "MS_IMPLICIT needs precision MS_F32 or MS_F64");
@@ -393,6 +398,8 @@ int check_device_error(ms_ctx* c) {
     c->st.fp_unconverged = int64_t(oc.fp_unconverged);
     c->st.model_sfu_ex2 = int64_t(oc.model_sfu_ex2);
     c->st.model_sfu_slow = int64_t(oc.model_sfu_slow);
+    c->st.farfield_node_evaluations = int64_t(oc.farfield_node_evaluations);
+    c->st.farfield_point_sources = int64_t(oc.farfield_point_sources);
   }
   if (c->hyb_d) {
     ms::HybridCounters hc{};
@@ -571,6 +578,10 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.err = c->err_d;
     a.ops = c->ops_d;
     a.n_sub = n_substeps(c->prm, c->dt);
+    if constexpr (std::is_same<AT, float>::value) {
+      a.ff = c->ff_d;
+      a.ff_dist = float(c->prm.farfield_dist);
+    }
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
     bool hybrid = false;
     if constexpr (std::is_same<AT, float>::value &&
@@ -713,6 +724,29 @@ int64_t ctx_points(const ms_ctx* c) { return c->n_points; }
 }  // namespace ms
 
 // =============================================================== C ABI
+// Far-field interpolation table: the 8 Chebyshev points of the first kind on
+// [0, 1] (the tile's x-range from its first to its 128th point), and for
+// each node k and each point i at t_i = i / 127 the Lagrange weight
+// l_k(t_i) = prod_{j != k} (t_i - s_j) / (s_k - s_j), computed in double.
+static std::vector<float> farfield_weights() {
+  constexpr int K = ms::FF_NODES, N = ms::TILE;
+  const double pi = 3.14159265358979323846;
+  double sn[K];
+  for (int k = 0; k < K; ++k) sn[k] = 0.5 * (1.0 - std::cos((2 * k + 1) * pi / (2 * K)));
+  std::vector<float> w(ms::FF_FLOATS, 0.0f);
+  for (int k = 0; k < K; ++k) {
+    for (int i = 0; i < N; ++i) {
+      const double t = double(i) / double(N - 1);
+      double l = 1.0;
+      for (int j = 0; j < K; ++j)
+        if (j != k) l *= (t - sn[j]) / (sn[k] - sn[j]);
+      w[size_t(k) * N + i] = float(l);
+    }
+    w[size_t(K) * N + k] = float(sn[k]);
+  }
+  return w;
+}
+
 extern "C" {
 
 const char* ms_version(void) { return "ms-gb300 1.0.0 (sm_103a)"; }
@@ -811,6 +845,12 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
     return bail(fail(MS_ERR_OOM, "device allocation failed"));
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     return bail(fail(MS_ERR_CUDA, "cannot query the SM count"));
+  if (p->farfield_dist > 0.0) {
+    const std::vector<float> w = farfield_weights();
+    if (cudaMalloc(&c->ff_d, w.size() * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(c->ff_d, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(MS_ERR_OOM, "device allocation failed"));
+  }
   SpecDev s{};
   s.nx = int32_t(std::min<int64_t>(n_points, INT32_MAX));
   s.ny = s.nz = 1;
@@ -831,6 +871,7 @@ void ms_destroy(ms_ctx* c) {
   cudaFree(c->work_d);
   cudaFree(c->hyb_d);
   cudaFree(c->ops_d);
+  cudaFree(c->ff_d);
   cudaFree(c->tracks_d);
   cudaFree(c->win_d);
   cudaFree(c->layers_d);

@@ -98,7 +98,17 @@ struct OpCounters {
   unsigned long long fp_unconverged;   // implicit scheme: substeps that hit the cap
   unsigned long long model_sfu_ex2;    // explicit scheme: the model's exponentials
   unsigned long long model_sfu_slow;   // explicit scheme: the model's logarithms and reciprocals
+  unsigned long long farfield_node_evaluations;  // far field: source evaluations at the nodes
+  unsigned long long farfield_point_sources;     // far field: point-source pairs interpolated
 };
+
+// Far field of the moving sources (ms_params.farfield_dist): 8 Chebyshev
+// nodes over a row tile's x-range, Lagrange weights of the 128 points.
+constexpr int FF_NODES = 8;
+// Device buffer: weights [FF_NODES][TILE] (node-major, so that a warp reads
+// one node's weights of its 128 points as one float4 per lane), then the
+// nodes' positions as fractions of the range [FF_NODES], padded to 16 bytes.
+constexpr int FF_FLOATS = FF_NODES * TILE + FF_NODES;
 
 // Counters of the hybrid kernel (running totals, reset by ms_reset_stats).
 struct HybridCounters {
@@ -128,6 +138,8 @@ struct TrackArgs {
   int* err;
   OpCounters* ops;             // work counters of k_track (nullptr: not counted)
   int32_t n_sub;               // implicit scheme: substeps per step
+  const float* ff;             // far-field weights and nodes (FF_FLOATS), nullptr: off
+  float ff_dist;               // far-field distance [m]
   // hybrid kernel only
   const void* mlp;             // MlpDev of the attached surrogate
   HybridCounters* hyb;

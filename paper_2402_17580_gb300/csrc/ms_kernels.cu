@@ -163,11 +163,14 @@ template <typename AT, typename FT, bool IMPL>
 constexpr bool kLockstep = std::is_same<AT, float>::value && std::is_same<FT, float>::value && !IMPL;
 
 // One 128-point tile for the launch's S steps (4 points per lane).
-template <typename AT, typename FT, bool IMPL>
+template <typename AT, typename FT, bool IMPL, bool FAR>
 __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane,
                                            unsigned long long& n_src, unsigned long long& n_model,
                                            unsigned& fp_it, unsigned& fp_unconv, SfuCount& oc,
-                                           unsigned& n_ex2, unsigned& n_slow) {
+                                           unsigned& n_ex2, unsigned& n_slow,
+                                           unsigned long long& ff_nodes,
+                                           unsigned long long& ff_pairs, const float* ffw,
+                                           float s_node) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
@@ -182,6 +185,13 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     point_coords<AT>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
   }
   const bool row = tile_in_one_row(sp, tile);
+  // far field: the tile's x-range, first to 128th point (a row tile)
+  AT x_first = AT(0), x_span = AT(0);
+  if constexpr (FAR) {
+    const int64_t li_first = int64_t(tile - sp.tile0) * TILE;
+    x_first = AT(sp.ox) + AT(li_first % sp.nx) * AT(sp.dx);
+    x_span = AT(TILE - 1) * AT(sp.dx);
+  }
 
   FT xs[4], xm[4];
   float ax[4];
@@ -197,13 +207,26 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   // valid points of this tile (all lanes agree): the work counters count them
   const int64_t rest = sp.n - int64_t(tile - sp.tile0) * TILE;
   const unsigned long long nv = (unsigned long long)(rest < TILE ? rest : TILE);
-  unsigned long long srcs = 0, models = 0;
+  unsigned long long srcs = 0, models = 0, fsrcs = 0;
   AT T0[4];
   for (int l = 0; l < a.n_levels; ++l) {  // level 0 only sets T0 (one inlined temps4)
     const SrcLevelT<AT> L = lv[l];
     AT T1[4];
-    temps4<AT>(L, en + int64_t(l) * a.slots, px, py, pz, row, T1);
-    srcs += L.n;
+    bool done_far = false;
+    if constexpr (FAR) {
+      if (row && L.axis) {
+        int nn, nf;
+        temps4_far(L, en + int64_t(l) * a.slots, px, py[0], pz[0], x_first, x_span, a.ff_dist,
+                   s_node, ffw, lane, T1, nn, nf);
+        srcs += nn;
+        fsrcs += nf;
+        done_far = true;
+      }
+    }
+    if (!done_far) {
+      temps4<AT>(L, en + int64_t(l) * a.slots, px, py, pz, row, T1);
+      srcs += L.n;
+    }
     if (l == 0) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) T0[q] = T1[q];
@@ -255,6 +278,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   }
   n_src += srcs * nv;
   n_model += models * nv;
+  ff_nodes += fsrcs * FF_NODES;
+  ff_pairs += fsrcs * nv;
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
   if (a.tile_tsat) {
 #pragma unroll
@@ -269,25 +294,41 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
 #ifndef MS_TRACK_MINB
 #define MS_TRACK_MINB 3
 #endif
+#ifndef MS_TRACK_MINB_FAR
+#define MS_TRACK_MINB_FAR 3
+#endif
 
 // Persistent hot kernel: every warp pulls tiles (from the active list, or all
 // tiles) through an atomic cursor until the work runs out, so the grid is
 // sized to the resident capacity and no launch tail is left idle.
-template <typename AT, typename FT, bool IMPL>
-__global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT, FT> a) {
+template <typename AT, typename FT, bool IMPL, bool FAR = false>
+__global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
+    k_track(const TrackArgs<AT, FT> a) {
   const int lane = threadIdx.x & 31;
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
   unsigned long long done = 0, n_src = 0, n_model = 0;
   unsigned fp_it = 0, fp_unconv = 0;
   SfuCount oc;
   unsigned n_ex2 = 0, n_slow = 0;
+  unsigned long long ff_nodes = 0, ff_pairs = 0;
+  // far field: every block copies the interpolation weights to shared memory
+  extern __shared__ float4 ff_smem[];
+  const float* ffw = nullptr;
+  float s_node = 0.0f;
+  if constexpr (FAR) {
+    float* sm = reinterpret_cast<float*>(ff_smem);
+    for (int i = threadIdx.x; i < FF_FLOATS; i += blockDim.x) sm[i] = a.ff[i];
+    __syncthreads();
+    ffw = sm;
+    s_node = sm[FF_NODES * TILE + (lane & (FF_NODES - 1))];
+  }
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    track_tile<AT, FT, IMPL>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model, fp_it,
-                             fp_unconv, oc, n_ex2, n_slow);
+    track_tile<AT, FT, IMPL, FAR>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model, fp_it,
+                             fp_unconv, oc, n_ex2, n_slow, ff_nodes, ff_pairs, ffw, s_node);
     ++done;
   }
   if (a.ops) {
@@ -319,6 +360,10 @@ __global__ void __launch_bounds__(256, MS_TRACK_MINB) k_track(const TrackArgs<AT
     if (a.ops) {
       atomicAdd(&a.ops->source_evaluations, n_src);
       atomicAdd(&a.ops->model_point_steps, n_model);
+      if (ff_nodes) {
+        atomicAdd(&a.ops->farfield_node_evaluations, ff_nodes);
+        atomicAdd(&a.ops->farfield_point_sources, ff_pairs);
+      }
     }
   }
 }
@@ -606,13 +651,21 @@ template <typename AT, typename FT>
 cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
                          cudaStream_t stream, bool implicit) {
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
+  if constexpr (kLockstep<AT, FT, false>) {
+    if (a.ff && !implicit) {  // far field: the weights in shared memory
+      k_track<AT, FT, false, true><<<unsigned(grid_blocks), block_threads,
+                                     FF_FLOATS * sizeof(float), stream>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  const size_t smem = 0;
   if (implicit) {
     if constexpr (kHasImplicit<AT, FT>)
-      k_track<AT, FT, true><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
+      k_track<AT, FT, true><<<unsigned(grid_blocks), block_threads, smem, stream>>>(a);
     else
       return cudaErrorNotSupported;
   } else {
-    k_track<AT, FT, false><<<unsigned(grid_blocks), block_threads, 0, stream>>>(a);
+    k_track<AT, FT, false><<<unsigned(grid_blocks), block_threads, smem, stream>>>(a);
   }
   return cudaGetLastError();
 }

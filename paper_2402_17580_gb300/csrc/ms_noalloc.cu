@@ -97,6 +97,8 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     return ms::record_error(MS_ERR_UNSUPPORTED, "ms_run_track_noalloc computes in MS_F32 only");
   if (p->integrator != MS_EXPLICIT)
     return ms::record_error(MS_ERR_UNSUPPORTED, "ms_run_track_noalloc takes explicit steps only");
+  if (p->farfield_dist != 0.0)
+    return ms::record_error(MS_ERR_UNSUPPORTED, "ms_run_track_noalloc sums every source directly");
   if (p->steps_per_launch > kMaxSteps)
     return ms::record_error(MS_ERR_INVALID_ARG, "steps_per_launch above 64 (no-alloc limit)");
   if (p->block_threads != 0 && p->block_threads != 128)

@@ -140,6 +140,76 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
   for (int q = 0; q < 4; ++q) T[q] = Fn<AT>::min(L.T0 + acc[q], L.T_max);
 }
 
+// temps4 with the far field (ms_params.farfield_dist > 0) for a tile inside
+// one grid row at a level whose sources all move along +-x.  A source that
+// lies at least dist behind every point of the tile's x-range [x_first,
+// x_first + x_span] is summed at the range's FF_NODES Chebyshev nodes
+// instead of at the 128 points: lane (k, g) = (lane & 7, lane >> 3) evaluates
+// node k (at x_first + x_span s_node) for every fourth far source, the four
+// groups' partial sums are added across the warp, and each lane interpolates
+// its four points with the Lagrange weights ffw[k][point] (shared memory).
+// The other sources are summed point by point as in temps4.  n_near and
+// n_far return the level's two counts (warp-uniform).
+__device__ __forceinline__ void temps4_far(const SrcLevelT<float>& L, const SrcEntryT<float>* en,
+                                           const float* px, float py, float pz, float x_first,
+                                           float x_span, float dist, float s_node,
+                                           const float* ffw, int lane, float* T, int& n_near,
+                                           int& n_far) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const float dz2 = depth2<float>(pz, L.z_surf);
+  const int g = lane >> 3;
+  const float xk = fmaf(x_span, s_node, x_first);
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float fk = 0.0f;
+  int nn = 0, nf = 0;
+  for (int j0 = 0; j0 < L.n; j0 += 32) {
+    const int cnt = L.n - j0 < 32 ? L.n - j0 : 32;
+    bool far = false;
+    if (lane < cnt) {
+      // xi = x u_x - s_xi (u_y = 0 at this level); its largest value on the range
+      const SrcEntryT<float> e = load_entry(en + j0 + lane);
+      const float xa = fmaf(x_first, e.ux, -e.s_xi), xb = fmaf(x_first + x_span, e.ux, -e.s_xi);
+      far = fmaxf(xa, xb) <= -dist;
+    }
+    const unsigned fm = __ballot_sync(FULL, far);
+    const unsigned all = cnt == 32 ? FULL : (1u << cnt) - 1u;
+    nf += __popc(fm);
+    nn += cnt - __popc(fm);
+    for (unsigned m = all & ~fm; m; m &= m - 1) {
+      const SrcEntryT<float> e0 = load_entry(en + j0 + __ffs(m) - 1);
+      float x0, p0;
+      source_offsets<float>(e0, py, x0, p0);
+      const float q0 = fmaf(p0, p0, dz2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += source_term_x<float>(e0, fmaf(px[q], e0.ux, x0), q0);
+    }
+    for (int j = g; j < cnt; j += 4)
+      if ((fm >> j) & 1u) {
+        const SrcEntryT<float> e0 = load_entry(en + j0 + j);
+        float x0, p0;
+        source_offsets<float>(e0, py, x0, p0);
+        fk += source_term_x<float>(e0, fmaf(xk, e0.ux, x0), fmaf(p0, p0, dz2));
+      }
+  }
+  if (nf > 0) {
+    fk += __shfl_xor_sync(FULL, fk, 8);
+    fk += __shfl_xor_sync(FULL, fk, 16);
+#pragma unroll
+    for (int k = 0; k < FF_NODES; ++k) {
+      const float F = __shfl_sync(FULL, fk, k);
+      const float4 w = reinterpret_cast<const float4*>(ffw + k * TILE)[lane];
+      acc[0] = fmaf(w.x, F, acc[0]);
+      acc[1] = fmaf(w.y, F, acc[1]);
+      acc[2] = fmaf(w.z, F, acc[2]);
+      acc[3] = fmaf(w.w, F, acc[3]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) T[q] = fminf(L.T0 + acc[q], L.T_max);
+  n_near = nn;
+  n_far = nf;
+}
+
 // Temperature of one point; the same arithmetic and order as temps4.
 template <typename AT>
 __device__ __forceinline__ AT temp1(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en, AT px, AT py,

@@ -382,6 +382,29 @@ def test_model_transcendental_counts(ms, T, xas, xam, ex2, slow):
     assert st.model_sfu_slow == slow * n * steps
 
 
+def test_farfield_matches_the_direct_sum(ms):
+    """ms_params.farfield_dist: in row tiles, sources at least 5 mm behind
+    every point are summed at 8 Chebyshev nodes of the tile's x-range and
+    interpolated.  Four serpentine tracks over a 256 x 8 x 4 block, then
+    their receding sources: the run stays within 1e-5 of the direct sum's run
+    and within the run tolerance of the oracle, most point-source pairs come
+    from the interpolation, and the paths it does not serve refuse it."""
+    w = wl.block_256(dims=(256, 8, 4), n_tracks=4, n_steps=3000, T_thr=0.0)
+    _, direct = gpu_workload(w)
+    ctx, far = gpu_workload(w, farfield_dist=5e-3)
+    st = ctx.stats()
+    assert st.farfield_node_evaluations > 0
+    assert st.farfield_point_sources > 0.5 * (st.farfield_point_sources + st.source_evaluations)
+    assert max_abs_diff(far, np.stack(direct)) <= 1e-5
+    assert max_abs_diff(far, oracle_workload(w)) <= RUN_TOL
+    check_sum(far)
+    for bad in (dict(precision=ms.MS_F64ACC), dict(integrator=ms.MS_IMPLICIT)):
+        with pytest.raises(ms.MSError):
+            ms.Context(16, farfield_dist=5e-3, **bad)
+    with pytest.raises(ms.MSError):
+        ms.Context(16, farfield_dist=-1.0)
+
+
 def test_temperature_query_matches_the_source(ms):
     w = wl.block_256(dims=(30, 20, 5), n_tracks=2, n_steps=150, T_thr=0.0)
     sp = w.specimens[0]
