@@ -169,8 +169,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
                                            unsigned& fp_it, unsigned& fp_unconv, SfuCount& oc,
                                            unsigned& n_ex2, unsigned& n_slow,
                                            unsigned long long& ff_nodes,
-                                           unsigned long long& ff_pairs, const float* ffw,
-                                           float s_node) {
+                                           unsigned long long& ff_pairs) {
   const int s = a.tile_spec[tile];
   const SpecDev& sp = a.specs[s];
   const int64_t local0 = int64_t(tile - sp.tile0) * TILE + lane * 4;
@@ -207,7 +206,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   // valid points of this tile (all lanes agree): the work counters count them
   const int64_t rest = sp.n - int64_t(tile - sp.tile0) * TILE;
   const unsigned long long nv = (unsigned long long)(rest < TILE ? rest : TILE);
-  unsigned long long srcs = 0, models = 0, fsrcs = 0;
+  unsigned srcs = 0, models = 0, fsrcs = 0;  // per tile: <= 513 levels x slots
   AT T0[4];
   for (int l = 0; l < a.n_levels; ++l) {  // level 0 only sets T0 (one inlined temps4)
     const SrcLevelT<AT> L = lv[l];
@@ -217,7 +216,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
       if (row && L.axis) {
         int nn, nf;
         temps4_far(L, en + int64_t(l) * a.slots, px, py[0], pz[0], x_first, x_span, a.ff_dist,
-                   s_node, ffw, lane, T1, nn, nf);
+                   lane, T1, nn, nf);
         srcs += nn;
         fsrcs += nf;
         done_far = true;
@@ -276,10 +275,10 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     ok = ok && finite_pair(xs[q], xm[q]);
     if (valid[q]) ts = fmaxf(ts, point_tsat<AT, FT>(a.m, xs[q], xm[q], ax[q]));
   }
-  n_src += srcs * nv;
-  n_model += models * nv;
-  ff_nodes += fsrcs * FF_NODES;
-  ff_pairs += fsrcs * nv;
+  n_src += (unsigned long long)srcs * nv;
+  n_model += (unsigned long long)models * nv;
+  ff_nodes += (unsigned long long)fsrcs * FF_NODES;
+  ff_pairs += (unsigned long long)fsrcs * nv;
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
   if (a.tile_tsat) {
 #pragma unroll
@@ -312,15 +311,10 @@ __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
   unsigned n_ex2 = 0, n_slow = 0;
   unsigned long long ff_nodes = 0, ff_pairs = 0;
   // far field: every block copies the interpolation weights to shared memory
-  extern __shared__ float4 ff_smem[];
-  const float* ffw = nullptr;
-  float s_node = 0.0f;
   if constexpr (FAR) {
-    float* sm = reinterpret_cast<float*>(ff_smem);
+    float* sm = reinterpret_cast<float*>(ms_ff_smem);
     for (int i = threadIdx.x; i < FF_FLOATS; i += blockDim.x) sm[i] = a.ff[i];
     __syncthreads();
-    ffw = sm;
-    s_node = sm[FF_NODES * TILE + (lane & (FF_NODES - 1))];
   }
   for (;;) {
     int w = 0;
@@ -328,7 +322,7 @@ __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
     track_tile<AT, FT, IMPL, FAR>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model, fp_it,
-                             fp_unconv, oc, n_ex2, n_slow, ff_nodes, ff_pairs, ffw, s_node);
+                             fp_unconv, oc, n_ex2, n_slow, ff_nodes, ff_pairs);
     ++done;
   }
   if (a.ops) {

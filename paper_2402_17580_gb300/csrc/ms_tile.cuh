@@ -140,6 +140,10 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
   for (int q = 0; q < 4; ++q) T[q] = Fn<AT>::min(L.T0 + acc[q], L.T_max);
 }
 
+// Dynamic shared memory of the far-field kernel: the interpolation weights
+// and node positions (FF_FLOATS floats, see ms_internal.h).
+extern __shared__ float4 ms_ff_smem[];
+
 // temps4 with the far field (ms_params.farfield_dist > 0) for a tile inside
 // one grid row at a level whose sources all move along +-x.  A source that
 // lies at least dist behind every point of the tile's x-range [x_first,
@@ -147,18 +151,19 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
 // instead of at the 128 points: lane (k, g) = (lane & 7, lane >> 3) evaluates
 // node k (at x_first + x_span s_node) for every fourth far source, the four
 // groups' partial sums are added across the warp, and each lane interpolates
-// its four points with the Lagrange weights ffw[k][point] (shared memory).
+// its four points with the Lagrange weights [k][point] that k_track keeps in
+// shared memory (ms_ff_smem, FF_FLOATS floats).
 // The other sources are summed point by point as in temps4.  n_near and
 // n_far return the level's two counts (warp-uniform).
 __device__ __forceinline__ void temps4_far(const SrcLevelT<float>& L, const SrcEntryT<float>* en,
                                            const float* px, float py, float pz, float x_first,
-                                           float x_span, float dist, float s_node,
-                                           const float* ffw, int lane, float* T, int& n_near,
-                                           int& n_far) {
+                                           float x_span, float dist, int lane, float* T,
+                                           int& n_near, int& n_far) {
   constexpr unsigned FULL = 0xffffffffu;
+  const float* ffw = reinterpret_cast<const float*>(ms_ff_smem);
   const float dz2 = depth2<float>(pz, L.z_surf);
   const int g = lane >> 3;
-  const float xk = fmaf(x_span, s_node, x_first);
+  const float xk = fmaf(x_span, ffw[FF_NODES * TILE + (lane & (FF_NODES - 1))], x_first);
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   float fk = 0.0f;
   int nn = 0, nf = 0;
