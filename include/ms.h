@@ -474,9 +474,10 @@ int ms_apply_correction(ms_ctx* ctx, const double* T, int32_t n_T, double* x_as,
 /* Attach a surrogate to a context (NULL detaches): ms_run_track then advances
  * whole windows of MS_MLP_WINDOW steps (counted from the call's first level)
  * with the MLP where the band test allows and with the explicit steps
- * elsewhere.  judge_frac in [0, 1] is the fraction of MLP windows, drawn by a
- * counter-based hash of (point, level), that are also run with the explicit
- * steps to measure the surrogate's error (ms_stats); the MLP result is kept.
+ * elsewhere.  judge_frac in [0, 1] is the fraction of the 128-point tiles'
+ * windows, drawn by a counter-based hash of (tile, level), whose MLP points
+ * are also run with the explicit steps to measure the surrogate's error
+ * (ms_stats); the MLP result is kept.
  * The surrogate must outlive its attachment.  Requires MS_F32 or MS_KAHAN.
  * Errors: INVALID_ARG, UNSUPPORTED (other precisions). */
 int ms_set_surrogate(ms_ctx* ctx, const ms_surrogate* s, double judge_frac);

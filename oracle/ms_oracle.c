@@ -479,7 +479,12 @@ void orc_run_track(const double *p, const double *spec, const double *tracks, in
  * App. A initiation running at its start, the point below the surface on
  * every level and the full window length, applies only the correction g at
  * its new temperatures in turn (no diffusion); every other window takes the
- * explicit steps.  n_mlp[i] counts the first kind of window per point. */
+ * explicit steps.  n_mlp[i] counts the first kind of window per point.
+ * Before either, a point on the alpha_s plateau's fixed point (X_as = 0.9,
+ * X_am = 0, no initiation) whose window temperatures all stay below
+ * T_as,end keeps its state: there X_alpha^eq = 0.9, no rate acts and the
+ * correction changes nothing, so the explicit steps are the identity (the
+ * hybrid kernel skips such windows); n_fixed[i] (if given) counts them. */
 static int in_band(const double *p, double T, double h) {
   if (!(T <= p[P_T_S] - h)) return 1;
   if (fabs(T - p[P_T_AM_START]) < h || fabs(T - p[P_T_AS_END]) < h) return 1;
@@ -491,28 +496,33 @@ void orc_run_track_windows(const double *p, const double *spec, const double *tr
                            int32_t n_tracks, const double *layers, int32_t n_layers, int64_t n,
                            const double *x, const double *y, const double *z, int64_t n0,
                            int64_t n_steps, double dt, int32_t window, double band_half,
-                           double *xas, double *xam, double *xt, int32_t *mode, int64_t *n_mlp) {
+                           double *xas, double *xam, double *xt, int32_t *mode, int64_t *n_mlp,
+                           int64_t *n_fixed) {
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t i = 0; i < n; ++i) {
     double T[65];
     int act[65];
     int a0;
-    int64_t count = 0;
+    int64_t count = 0, fixed = 0;
     double T0 = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i],
                                    (double)n0 * dt - spec[S_TOFF], &a0);
     for (int64_t w0 = 0; w0 < n_steps; w0 += window) {
       int64_t K = n_steps - w0 < window ? n_steps - w0 : window;
       int band = in_band(p, T0, band_half), all_act = 1, any_act = 0;
+      int cool = T0 < p[P_T_AS_END];
       T[0] = T0;
       for (int64_t l = 1; l <= K; ++l) {
         double tl = (double)(n0 + w0 + l) * dt - spec[S_TOFF];
         T[l] = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i], tl,
                                   &act[l]);
         band |= in_band(p, T[l], band_half);
+        cool &= T[l] < p[P_T_AS_END];
         all_act &= act[l];
         any_act |= act[l];
       }
-      if (any_act && all_act && K == window && !band && mode[i] == MODE_NONE) {
+      if (cool && mode[i] == MODE_NONE && xas[i] == 0.9 && xam[i] == 0.0) {
+        ++fixed;
+      } else if (any_act && all_act && K == window && !band && mode[i] == MODE_NONE) {
         for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);
         ++count;
       } else {
@@ -522,6 +532,7 @@ void orc_run_track_windows(const double *p, const double *spec, const double *tr
       T0 = T[K];
     }
     if (n_mlp) n_mlp[i] = count;
+    if (n_fixed) n_fixed[i] = fixed;
   }
 }
 

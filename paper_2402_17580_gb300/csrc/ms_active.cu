@@ -1,6 +1,9 @@
 // Active-set compaction (reading A9): per launch, the list of tiles that
 // may get hot (a rigorous upper bound of their temperature over the launch's
-// time window reaches T_thr) or whose martensite is not saturated.
+// time window reaches T_thr) or whose martensite is not saturated.  A tile
+// whose points all sit on the alpha_s plateau's fixed point (X_as = 0.9,
+// X_am = 0: the room-temperature state no heat has touched) is hot only once
+// the bound reaches T_as,end, below which its steps are the identity.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -36,6 +39,9 @@ __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   const SpecDev& sp = a.specs[s];
   const float tsat = a.tile_tsat[t];
   if (!(tsat <= sp.T0)) return true;  // martensite not saturated at T0, or initiation running
+  // every point on the alpha_s plateau's fixed point (tsat = -inf): the
+  // steps are the identity while T < T_as,end, so only that bound matters
+  const double T_hot = tsat == -INFINITY ? fmax(a.T_thr, a.T_as_end) : a.T_thr;
   int64_t ilo = 0, ihi = sp.nx - 1, jlo = 0, jhi = sp.ny - 1, k0 = 0, k1 = sp.nz - 1;
   if (!sp.idx) {
     const int64_t li0 = int64_t(t - sp.tile0) * TILE;
@@ -68,7 +74,7 @@ __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   const double cxd = 0.5 * (bx0 + bx1), cyd = 0.5 * (by0 + by1);
   const float hx = float(0.5 * (bx1 - bx0)), hy = float(0.5 * (by1 - by0));
   const float inv_alpha = float(1.0 / sp.alpha);
-  const float budget = float(a.T_thr - 1.0 - double(sp.T0));
+  const float budget = float(T_hot - 1.0 - double(sp.T0));
   float sum = 0.0f;
   for (int j = 0; j < sp.n_tracks; ++j) {
     const TrackWin& tw = a.win[sp.track0 + j];

@@ -554,6 +554,7 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
       aa.tile_tsat = c->tile_tsat_d;
       aa.n_tiles = int32_t(c->n_tiles);
       aa.T_thr = c->prm.T_thr;
+      aa.T_as_end = c->prm.T_as_end;
       aa.tile_list = c->tile_list_d;
       aa.work = c->work_d;
       MS_CUDA(ms::launch_active(aa, c->stream));

@@ -18,11 +18,16 @@
 //     per 16 points, tiles with no MLP point skipped) the diffusive residual y;
 //   - the others take the 8 explicit steps of Sec. 3 (eq:explicit_integration
 //     + g), as k_track does;
-//   - a fraction of the MLP windows, chosen by a counter-based hash of
-//     (point, level), is also run with the explicit steps (the judge); the
-//     largest difference is kept in the counters and the MLP result stays.
+//   - a fraction of the 128-point tiles' windows, chosen by a counter-based
+//     hash of (tile, level), has its MLP points also run with the explicit
+//     steps (the judge); the largest difference is kept in the counters and
+//     the MLP result stays.  Judging whole tiles keeps the explicit steps in
+//     the few warps that judge (a per-point draw would put a judged point in
+//     nearly every warp, and the warp would take the explicit steps for it).
 // Points that are cold and saturated on all 8 steps (reading A9) are left
-// unchanged, as k_track's vote would leave them.
+// unchanged, as k_track's vote would leave them, and so are points on the
+// alpha_s plateau's fixed point (X_as = 0.9, X_am = 0) whose window stays
+// below T_as,end, where the explicit steps are the identity.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -59,9 +64,9 @@ __device__ __forceinline__ bool in_band(const ModelConstT<float>& m, float T) {
          near(T, m.T_as_start) || near(T, m.T_cap0);
 }
 
-// SplitMix64 output function (Steele, Lea, Flood 2014) of (point, level).
-__device__ __forceinline__ uint32_t judge_hash(uint64_t point, uint64_t level) {
-  uint64_t z = point * 0x9E3779B97F4A7C15ull + level * 0xD1B54A32D192ED03ull + 0x2402175800ull;
+// SplitMix64 output function (Steele, Lea, Flood 2014) of (tile, level).
+__device__ __forceinline__ uint32_t judge_hash(uint64_t tile, uint64_t level) {
+  uint64_t z = tile * 0x9E3779B97F4A7C15ull + level * 0xD1B54A32D192ED03ull + 0x2402175800ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return uint32_t((z ^ (z >> 31)) >> 32);
@@ -113,7 +118,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   temps4<float>(lv[0], en, px, py, pz, false, T0);  // once per tile: the general form (same bits)
   for (int w0 = 0; w0 < n_steps; w0 += MLP_WINDOW) {
     const int K = min(MLP_WINDOW, n_steps - w0);
-    bool band[4], all_act[4], any_act[4], noop[4];
+    bool band[4], all_act[4], any_act[4], noop[4], cool[4];
     float Tp[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -121,6 +126,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       all_act[q] = true;
       any_act[q] = false;
       noop[q] = true;
+      cool[q] = T0[q] < a.m.T_as_end;
       Tp[q] = T0[q];
     }
     for (int l = 0; l < K; ++l) {
@@ -137,6 +143,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         all_act[q] = all_act[q] && act;
         any_act[q] = any_act[q] || act;
         band[q] = band[q] || in_band(a.m, T1[q]);
+        cool[q] = cool[q] && T1[q] < a.m.T_as_end;
         noop[q] = noop[q] && (!act || (skipping && step_is_noop<float, FT>(a.m, Tp[q], T1[q], xs[q],
                                                                           xm[q], ax[q])));
         Tp[q] = T1[q];
@@ -145,12 +152,17 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
 
     bool use_mlp[4], use_ode[4], judged[4];
     bool lane_mlp = false, lane_exp = false;
+    const bool judge_tile =
+        uint64_t(judge_hash(uint64_t(tile), uint64_t(a.level0 + w0))) < a.judge_thresh;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const bool idle = !any_act[q] || (skipping && noop[q]);
+      // on the alpha_s plateau's fixed point (X_as = 0.9, X_am = 0, no
+      // initiation) with every level below T_as,end the explicit steps are
+      // the identity: the point keeps its state (no network output)
+      const bool fixed = xs[q] == FT(0.9) && xm[q] == FT(0) && ax[q] == 0.0f && cool[q];
+      const bool idle = !any_act[q] || (skipping && noop[q]) || fixed;
       use_mlp[q] = !idle && all_act[q] && K == MLP_WINDOW && !band[q] && ax[q] == 0.0f;
-      judged[q] = use_mlp[q] &&
-                  uint64_t(judge_hash(uint64_t(g0 + q), uint64_t(a.level0 + w0))) < a.judge_thresh;
+      judged[q] = use_mlp[q] && judge_tile;
       use_ode[q] = !idle && !use_mlp[q];
       lane_mlp = lane_mlp || use_mlp[q];
       lane_exp = lane_exp || use_ode[q] || judged[q];

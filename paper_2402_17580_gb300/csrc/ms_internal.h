@@ -158,6 +158,7 @@ struct ActiveArgs {
   int32_t n_tiles;
   int32_t pad;
   double T_thr;
+  double T_as_end;             // fixed-point tiles are idle below it
   int32_t* tile_list;
   WorkCounters* work;
 };

@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cmath>
 #include <cstdint>
 
@@ -227,14 +228,18 @@ __device__ __forceinline__ AT temp1(const SrcLevelT<AT>& L, const SrcEntryT<AT>*
 
 // Highest T1 at which martensite formation would still change this point
 // (formation is a no-op for T1 >= the returned value); +inf while an App. A
-// initiation runs (never skip), -inf if formation can never act.
+// initiation runs (never skip), -FLT_MAX if formation can never act, and
+// -inf only on the alpha_s plateau's fixed point (X_as = 0.9, X_am = 0, no
+// initiation): below T_as,end its step is the identity, since X_alpha^eq =
+// 0.9 there, no rate acts and g changes nothing.  A tile's maximum is -inf
+// exactly when all its points sit on that fixed point.
 template <typename AT, typename FT>
 __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT xam, float aux) {
   if (aux != 0.0f) return INFINITY;
   const FT q = FT(0.9) - xas;
-  if (!(q > FT(0))) return -INFINITY;
+  if (!(q > FT(0))) return xam == FT(0) ? -INFINITY : -FLT_MAX;
   const float r = float(xam * FT(0.9) / q);
-  if (r >= XMAX) return -INFINITY;
+  if (r >= XMAX) return -FLT_MAX;
   return float(m.T_am_start) + sfu_lg2(1.0f - r) / float(m.kam_l2);
 }
 

@@ -267,6 +267,23 @@ def test_active_set_full_block_against_dense_run(ms):
     ctx.close()
 
 
+def test_fixed_point_tiles_skip_exactly(ms):
+    """A tile whose points all sit on the alpha_s plateau's fixed point
+    (X_as = 0.9, X_am = 0, the untouched room-temperature state) stays out of
+    the active set while the rigorous temperature bound keeps it below
+    T_as,end: there every step is the identity.  With T_thr just above T0 the
+    cold skip of reading A9 has nothing to act on (the receding sources keep
+    the block above it), so the run must equal the dense run, and it skips
+    tile-steps."""
+    w = wl.block_256(dims=(128, 64, 48), n_tracks=3, n_steps=3000, T_thr=354.0)
+    ctx, g = gpu_workload(w)
+    st = ctx.stats()
+    _, dense = gpu_workload(w, T_thr=0.0)
+    assert st.tile_steps_active < 0.8 * st.tile_steps_total
+    assert max_abs_diff(g, np.stack(dense)) == 0.0
+    check_sum(g)
+
+
 def test_active_set_batched_offsets(ms):
     """Specimens that have not started yet are skipped until their start."""
     w = wl.batch_64(n_specimens=6, n_lo=300, n_hi=4000, n_steps=800, T_thr=600.0)

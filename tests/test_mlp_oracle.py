@@ -134,6 +134,8 @@ def test_windows_cold_quench_reduces_to_correction():
                                atol=1e-15)
     assert np.all(st.xas == 0.0)
     st2 = oracle.State.uniform(x.size)
+    st2.xas[:] = 0.5
+    st2.xam[:] = 0.1
     n_mlp = oracle.run_track_windows(st2, src, x, y, z, 0, 8 * 5 + 3, w.dt, p=p)
     assert np.all(n_mlp == 5)
 
@@ -147,5 +149,35 @@ def test_windows_band_edges():
         w, src = _line(0.0, n=4, T0=T_hold)
         x, y, z = w.specimens[0].grid.coords()
         st = oracle.State.uniform(4)
+        st.xas[:] = 0.6      # off the alpha_s plateau's fixed point
+        st.xam[:] = 0.1
         n_mlp = oracle.run_track_windows(st, src, x, y, z, 0, 16, w.dt, p=p)
         assert np.all(n_mlp == (0 if in_band else 2)), T_hold
+
+
+def test_windows_fixed_point_is_the_explicit_identity():
+    """The room-temperature state (0.9, 0, 0.1) is a fixed point of the
+    explicit step below T_as,end (X_alpha^eq = 0.9, no rate acts, formation's
+    target X_am^eq (0.9 - X_as) / 0.9 is 0): the explicit run leaves it
+    exactly unchanged at every constant temperature below 935 K, also inside
+    the bands at 848 K, and the window form counts those windows as fixed;
+    at 1000 K the alpha_s -> beta initiation starts and nothing is fixed."""
+    p = oracle.params()
+    for T_hold in (353.0, 600.0, 847.0, 848.0, 849.0, 900.0, 934.0):
+        w, src = _line(0.0, n=4, T0=T_hold)
+        x, y, z = w.specimens[0].grid.coords()
+        a = oracle.State.uniform(4)
+        oracle.run_track(a, src, x, y, z, 0, 40, w.dt, p)
+        assert np.all(a.xas == 0.9) and np.all(a.xam == 0.0) and np.all(a.mode == 0), T_hold
+        b = oracle.State.uniform(4)
+        n_mlp, n_fixed = oracle.run_track_windows(b, src, x, y, z, 0, 40, w.dt, p=p,
+                                                   return_fixed=True)
+        assert np.all(n_fixed == 5) and np.all(n_mlp == 0), T_hold
+    w, src = _line(0.0, n=4, T0=1000.0)
+    x, y, z = w.specimens[0].grid.coords()
+    a = oracle.State.uniform(4)
+    oracle.run_track(a, src, x, y, z, 0, 40, w.dt, p)
+    assert np.all(a.mode == oracle.MODE_AS_TO_B)   # App. A: X~_beta far below 1e-16 yet
+    n_mlp, n_fixed = oracle.run_track_windows(oracle.State.uniform(4), src, x, y, z, 0, 40, w.dt,
+                                               p=p, return_fixed=True)
+    assert np.all(n_fixed == 0)
