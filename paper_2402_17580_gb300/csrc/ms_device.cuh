@@ -457,11 +457,15 @@ __device__ __forceinline__ void point_step_implicit(const ModelConstT<AT>& m, AT
 }
 
 // A point may skip a step (active set, reading A9) when both temperatures are
-// below T_thr and martensite formation at T1 would be a no-op.
+// below T_thr and martensite formation at T1 would be a no-op, and (reading
+// A9b) on the alpha_s plateau's fixed point X_as = 0.9, X_am = 0 while both
+// are below T_as,end, where the step is the identity.
 template <typename AT, typename FT>
 __device__ __forceinline__ bool step_is_noop(const ModelConstT<AT>& m, AT T0, AT T1, FT xas,
                                              FT xam, float aux) {
-  if (!(T0 < m.T_thr && T1 < m.T_thr) || aux != 0.0f) return false;
+  if (aux != 0.0f) return false;
+  if (xas == FT(0.9) && xam == FT(0) && T0 < m.T_as_end && T1 < m.T_as_end) return true;
+  if (!(T0 < m.T_thr && T1 < m.T_thr)) return false;
   if (!(T1 < m.T_am_start)) return true;
   const FT e = FT(xam0_eq<AT>(m, T1)) * (FT(0.9) - xas) * FT(1.0 / 0.9);
   return xam >= e;

@@ -162,11 +162,15 @@ def test_zero_network_hybrid_matches_window_oracle(ms, precision):
     T_last = orc.temperature(sp.source, x, y, z, w.n_steps * w.dt)[0]
     of = np.stack(orc.fractions(o, T_last, p))
     assert max_abs_diff(g, of) <= RUN_TOL
-    assert st.surrogate_windows > 0.5 * w.n_points * w.n_steps / 8
-    assert abs(st.surrogate_windows - int(n_mlp.sum())) <= 1e-3 * n_mlp.sum()
+    # windows are g-only (MLP), explicit (ODE) or, on the alpha_s plateau's
+    # fixed point below T_as,end, left alone (most of the line's windows:
+    # the points ahead of the source and the cold tail)
+    total = w.n_points * w.n_steps // 8
+    n_m, n_f = int(n_mlp.sum()), int(n_fixed.sum())
+    assert st.surrogate_windows > 0.1 * total and n_f > 0
+    assert abs(st.surrogate_windows - n_m) <= 1e-3 * total
+    assert abs(st.ode_windows - (total - n_m - n_f)) <= 1e-3 * total
     assert st.judge_samples == st.surrogate_windows  # judge_frac = 1
-    total = w.n_points * w.n_steps // 8   # fixed-point windows are neither
-    assert abs(st.surrogate_windows + st.ode_windows + int(n_fixed.sum()) - total) <= 1e-3 * total
     assert 0.0 < st.judge_max_err < 1.0
     ctx.close()
     s.close()
