@@ -198,17 +198,23 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
+def ncu_traffic(workload, steps_per_launch):
     """DRAM bytes per launch of the hot kernel from the committed ncu summary,
-    only if the kernel source is unchanged since the capture."""
+    only if the kernel source is unchanged since the capture and the pass runs
+    the captured workload and steps per launch (the active set, and so the
+    state read per launch, depends on the launch's time window).  Returns
+    (bytes or None, the summary's description)."""
     try:
         with open(PROFILE_SUMMARY) as f:
             s = json.load(f)
     except (OSError, ValueError):
         return None, None
-    if s.get("kernel_source_hash") != kernel_source_hash():
-        return None, s.get("kernel_source_hash")
-    return s.get("dram_bytes_per_launch_full"), s.get("kernel_source_hash")
+    desc = (f"{s.get('dram_bytes_per_launch_full')} B per launch of {s.get('workload')} at "
+            f"S = {s.get('steps_per_launch')}, kernel hash {s.get('kernel_source_hash')}")
+    if (s.get("kernel_source_hash") != kernel_source_hash() or s.get("workload") != workload
+            or s.get("steps_per_launch") != steps_per_launch):
+        return None, desc
+    return s.get("dram_bytes_per_launch_full"), desc
 
 
 # ------------------------------------------------------------ oracle sample
@@ -404,12 +410,14 @@ def run_ours(args):
     sm_cycles = slow_ops / rates["rsqrt"] + ex2_ops / rates["ex2"]    # per-SM cycles, summed
     peak_time_s = sm_cycles / (SM_COUNT * SM_MAX_MHZ * 1e6)
     peak = alg_ops / peak_time_s / 1e9
-    traffic_full, prof_hash = ncu_traffic()
+    traffic_full, traffic_desc = ncu_traffic(w.name, int(ctx.params.steps_per_launch))
     state_bytes = 2 * w.n_points * (3 * 4 if prec == ms.MS_F32 else 2 * 8 + 4)
     roofline = {
         "bound": "alu", "kernel": "k_track", "achieved": round(achieved, 1), "peak": round(peak, 1),
         "unit": "Gop/s (SFU)", "frac": round(achieved / peak, 4),
         "traffic": traffic_full,
+        "traffic_basis": (traffic_desc or "no committed ncu summary") + (
+            "" if traffic_full is not None else "; null: another kernel source, workload or S"),
         "algorithmic_ops_per_launch": int(ops_per_launch),
         "ms_per_launch": round(ms_per_launch, 4), "launches_per_step": launches_per_pass,
         "kernel_share_of_step": round(kernel_ms_per_pass / t_mean, 4),
