@@ -97,7 +97,10 @@ extern "C" {
  *                       against 0.9; 0 restores the literal rule)
  *   T_thr               active-set threshold [K]: a 128-point tile may skip a
  *                       step only if it stays below T_thr and its martensite
- *                       is saturated (<= 0 disables all skipping)           */
+ *                       is saturated, or if all its points sit on the
+ *                       untouched state X_as = 0.9, X_am = 0 and it stays
+ *                       below T_as_end, where the step is the identity
+ *                       (<= 0 disables all skipping)                        */
 typedef struct ms_params {
   double T_s, T_l;                /* solidus, liquidus [K]                       */
   double T_as_start, T_as_end;    /* beta -> alpha_s range [K]                   */
