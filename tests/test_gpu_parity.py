@@ -422,6 +422,31 @@ def test_farfield_matches_the_direct_sum(ms):
         ms.Context(16, farfield_dist=-1.0)
 
 
+@pytest.mark.parametrize("case", ["batch", "layers"])
+def test_farfield_batched_and_layered(ms, case):
+    """The far field on specimens of uneven sizes with start offsets (every
+    specimen's own tiles, x-range and sources) and on two layers whose second
+    one is rotated by 67 degrees (only the first layer's levels run along x):
+    within 1e-5 of the direct sum's run and within the run tolerance of the
+    oracle."""
+    if case == "batch":
+        a = wl.block_256(seed=11, dims=(256, 6, 4), n_tracks=3, n_steps=2500, T_thr=0.0)
+        b = wl.block_256(seed=12, dims=(384, 4, 3), n_tracks=2, n_steps=2500, T_thr=0.0)
+        b.specimens[0].source.t_offset = 3e-3
+        w = wl.Workload("two_specimens", a.specimens + b.specimens, 2500, 1e-5, T_thr=0.0)
+    else:
+        w = wl.part_512(dims=(256, 12, 6), n_layers=2, tracks_per_layer=3, t_layer=1e-2,
+                        hatch=4e-5)
+    dist = 3e-3
+    _, direct = gpu_workload(w)
+    ctx, far = gpu_workload(w, farfield_dist=dist)
+    st = ctx.stats()
+    assert st.farfield_node_evaluations > 0
+    assert max_abs_diff(far, np.stack(direct)) <= 1e-5
+    assert max_abs_diff(far, oracle_workload(w)) <= RUN_TOL
+    check_sum(far)
+
+
 def test_temperature_query_matches_the_source(ms):
     w = wl.block_256(dims=(30, 20, 5), n_tracks=2, n_steps=150, T_thr=0.0)
     sp = w.specimens[0]
