@@ -209,12 +209,13 @@ def ncu_traffic(workload, steps_per_launch):
             s = json.load(f)
     except (OSError, ValueError):
         return None, None
-    desc = (f"{s.get('dram_bytes_per_launch_full')} B per launch of {s.get('workload')} at "
-            f"S = {s.get('steps_per_launch')}, kernel hash {s.get('kernel_source_hash')}")
+    by_s = s.get("dram_bytes_per_launch_by_steps", {})
+    desc = (f"ncu DRAM bytes per launch of {s.get('workload')} by steps per launch {by_s}, "
+            f"kernel hash {s.get('kernel_source_hash')}")
     if (s.get("kernel_source_hash") != kernel_source_hash() or s.get("workload") != workload
-            or s.get("steps_per_launch") != steps_per_launch):
+            or str(steps_per_launch) not in by_s):
         return None, desc
-    return s.get("dram_bytes_per_launch_full"), desc
+    return by_s[str(steps_per_launch)], desc
 
 
 # ------------------------------------------------------------ oracle sample
