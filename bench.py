@@ -310,6 +310,49 @@ def d6_layouts(ms, torch, n=1 << 24, blocks=(1, 10, 100), steps=10, warmup=3):
                     "Crank-Nicolson scheme (MS_IMPLICIT) on the same data and bytes"}
 
 
+def dense_s1(ms, torch, steps=40, warmup=4):
+    """The dense mode of the hot kernel against HBM: k_track with no
+    skipping (T_thr = 0) and one step per launch (S = 1) on the 512 x 512 x 256
+    part grid (67.1M points; 805 MB of FP32 state, far above the 129 MB L2),
+    over the first steps of its first layer (one source).  Every launch reads
+    and writes every point's state once: 24 B per point-update of algorithmic
+    traffic, against the measured HBM copy bandwidth.  With the temperature
+    computed in the kernel at both levels of the step, the per-tile set-up
+    (point coordinates, the saturation temperature) and one model step per
+    load, this launch is bound by instruction issue, not by HBM; the HBM-bound
+    form of the same step is ms_step with the temperatures in memory
+    (roofline_ms_step)."""
+    import workloads as wl
+    from paper_2402_17580_gb300._binding import MS_FLAG_TIME_KERNELS
+    w = wl.part_512()
+    sp = w.specimens[0]
+    ctx = ms.Context(w.n_points, T_thr=0.0, steps_per_launch=1, flags=MS_FLAG_TIME_KERNELS)
+    ctx.set_points([sp.grid])
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream.cuda_stream)
+    ctx.fill_state(w.init_xas, w.init_xam)
+    ctx.run_track([sp.source], warmup, w.dt)
+    ctx.synchronize()
+    ctx.reset_stats()
+    ctx.run_track([sp.source], steps, w.dt)
+    ctx.synchronize()
+    st = ctx.stats()
+    ms_launch = st.hot_kernel_ms / st.hot_kernel_launches
+    bytes_launch = 24 * w.n_points
+    gbs = bytes_launch / (ms_launch * 1e-3) / 1e9
+    ctx.close()
+    return {"kernel": "k_track", "bound": "hbm", "workload": "part_512 grid, first layer",
+            "points": w.n_points, "steps_per_launch": 1, "T_thr": 0.0,
+            "point_updates_per_s_kernel": w.n_points / (ms_launch * 1e-3),
+            "ms_per_launch": round(ms_launch, 4), "bytes_per_launch": bytes_launch,
+            "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": round(gbs / HBM_PEAK_GBS, 4),
+            "note": "24 B per point-update (X_as, X_am, aux read and written once per launch); "
+                    "state 805 MB > L2, so every launch streams it from HBM; at S = 1 the "
+                    "launch is issue-bound (two temperature levels, per-tile set-up and one "
+                    "model step per load), see roofline_ms_step for the HBM-bound step"}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     rank, world, local = dist_env()
@@ -483,6 +526,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_d6:
         ctx.close()
         out["roofline_ms_step"] = d6_layouts(ms, torch)
+        out["roofline_dense_s1"] = dense_s1(ms, torch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
