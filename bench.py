@@ -672,6 +672,7 @@ def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sampl
     s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2)
     t2 = time.perf_counter()
     ctx.set_surrogate(s, 0.01)
+    ctx.set_stream(stream.cuda_stream)   # the e2e leg leaves the context on its own stream
     one = lambda: (ctx.fill_state(w.init_xas, w.init_xam), ctx.run_track(srcs, w.n_steps, w.dt))
     one()
     ctx.synchronize()

@@ -95,11 +95,9 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   float px[4], py[4], pz[4];
   bool valid[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t li = local0 + q;
-    valid[q] = li < sp.n;
-    point_coords<float>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
-  }
+  for (int q = 0; q < 4; ++q) valid[q] = local0 + q < sp.n;
+  int64_t col;
+  point_coords4<float>(sp, local0, valid, px, py, pz, col);
   const bool row = tile_in_one_row(sp, tile);
 
   FT xs[4], xm[4];

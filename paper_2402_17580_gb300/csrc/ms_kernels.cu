@@ -178,17 +178,19 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   AT px[4], py[4], pz[4];
   bool valid[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t li = local0 + q;
-    valid[q] = li < sp.n;
-    point_coords<AT>(sp, valid[q] ? li : 0, px[q], py[q], pz[q]);
-  }
-  const bool row = tile_in_one_row(sp, tile);
+  for (int q = 0; q < 4; ++q) valid[q] = local0 + q < sp.n;
+  int64_t col;
+  point_coords4<AT>(sp, local0, valid, px, py, pz, col);
+  // the tile lies in one grid row when its first point's column (lane 0's)
+  // plus its span stays inside the row (tile_in_one_row without dividing)
+  const int64_t col0 = __shfl_sync(0xffffffffu, col, 0);
+  const int64_t li_first = int64_t(tile - sp.tile0) * TILE;
+  const int64_t span = sp.n - 1 - li_first < TILE - 1 ? sp.n - 1 - li_first : TILE - 1;
+  const bool row = !sp.idx && col0 + span < sp.nx;
   // far field: the tile's x-range, first to 128th point (a row tile)
   AT x_first = AT(0), x_span = AT(0);
   if constexpr (FAR) {
-    const int64_t li_first = int64_t(tile - sp.tile0) * TILE;
-    x_first = AT(sp.ox) + AT(li_first % sp.nx) * AT(sp.dx);
+    x_first = AT(sp.ox) + AT(col0) * AT(sp.dx);
     x_span = AT(TILE - 1) * AT(sp.dx);
   }
 
@@ -269,18 +271,18 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   n_slow += oc.packed >> 16;
   oc.packed = 0;
   bool ok = true;
-  float ts = -INFINITY;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    ok = ok && finite_pair(xs[q], xm[q]);
-    if (valid[q]) ts = fmaxf(ts, point_tsat<AT, FT>(a.m, xs[q], xm[q], ax[q]));
-  }
+  for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
   n_src += (unsigned long long)srcs * nv;
   n_model += (unsigned long long)models * nv;
   ff_nodes += (unsigned long long)fsrcs * FF_NODES;
   ff_pairs += (unsigned long long)fsrcs * nv;
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
-  if (a.tile_tsat) {
+  if (a.tile_tsat && skipping) {  // read by the active set, which runs only with T_thr > 0
+    float ts = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (valid[q]) ts = fmaxf(ts, point_tsat<AT, FT>(a.m, xs[q], xm[q], ax[q]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ts = fmaxf(ts, __shfl_xor_sync(0xffffffffu, ts, o));
     if (lane == 0) a.tile_tsat[tile] = ts + 0.5f;  // margin against FP32 rounding

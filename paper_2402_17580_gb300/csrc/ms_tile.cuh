@@ -28,6 +28,51 @@ __device__ __forceinline__ void point_coords(const SpecDev& sp, int64_t li, AT& 
   z = AT(sp.oz) + AT(k) * AT(sp.dz);
 }
 
+// Coordinates of the four consecutive local points li0 .. li0 + 3 of a
+// specimen; points with valid[q] false take point 0's, as point_coords(sp, 0)
+// gives them.  One index decomposition per thread (32-bit when the specimen
+// allows it), then a carry per point instead of a division: the same integer
+// indices, so the same coordinates.  col returns the column of point li0
+// (0 for a subset specimen).
+template <typename AT>
+__device__ __forceinline__ void point_coords4(const SpecDev& sp, int64_t li0, const bool* valid,
+                                              AT* x, AT* y, AT* z, int64_t& col) {
+  col = 0;
+  if (sp.idx) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) point_coords<AT>(sp, valid[q] ? li0 + q : 0, x[q], y[q], z[q]);
+    return;
+  }
+  int64_t i, j, k;
+  if (sp.n + 4 < (int64_t(1) << 32)) {
+    const uint32_t l = uint32_t(li0), nx = uint32_t(sp.nx), ny = uint32_t(sp.ny);
+    const uint32_t r = l / nx;
+    i = l - r * nx;
+    k = r / ny;
+    j = r - uint32_t(k) * ny;
+  } else {
+    const int64_t r = li0 / sp.nx;
+    i = li0 - r * sp.nx;
+    k = r / sp.ny;
+    j = r - k * sp.ny;
+  }
+  col = i;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q > 0 && ++i == sp.nx) {
+      i = 0;
+      if (++j == sp.ny) {
+        j = 0;
+        ++k;
+      }
+    }
+    const int64_t ii = valid[q] ? i : 0, jj = valid[q] ? j : 0, kk = valid[q] ? k : 0;
+    x[q] = AT(sp.ox) + AT(ii) * AT(sp.dx);
+    y[q] = AT(sp.oy) + AT(jj) * AT(sp.dy);
+    z[q] = AT(sp.oz) + AT(kk) * AT(sp.dz);
+  }
+}
+
 // Every point of the tile lies in one grid row (shares y and z): a full-grid
 // specimen whose first and last point of the tile have the same row index.
 // The tile's padding points take point 0's coordinates; their temperatures
