@@ -199,6 +199,37 @@ def test_block_256_full_size_sampled(ms):
     check_sum(g)
 
 
+def test_batch_64_full_size_sampled(ms):
+    """The full batched workload: 64 specimens of log-uniform sizes in
+    [1e4, 2e6] points (1.5e7 in all), each with its own power, speed, hatch and start
+    offset, 10000 steps in one context with the active set on; 256 seeded
+    sample points against the oracle."""
+    w = wl.batch_64()
+    _, g = gpu_workload(w)
+    idx = np.random.default_rng(13).choice(w.n_points, 256, replace=False)
+    o = oracle_workload(w, idx)
+    assert max_abs_diff(g, o, idx) <= RUN_TOL
+    check_sum(g)
+
+
+def test_part_512_full_size_sampled_compensated(ms):
+    """The part-scale workload at full size: 512 x 512 x 256 points, 5 layers
+    of 50 rotated serpentine tracks, 250000 steps, with the compensated
+    fraction accumulator its length needs (plain FP32 accumulates ~2e-4 over
+    the 250000 steps); 64 seeded sample points, half of them in the top 60 um
+    the tracks melt, against the oracle."""
+    w = wl.part_512()
+    _, g = gpu_workload(w, precision=ms.MS_KAHAN)
+    nx, ny, nz = w.specimens[0].grid.dims
+    rng = np.random.default_rng(17)
+    top = rng.integers(0, nx * ny * 6, 32)            # the six top layers of points
+    rest = rng.integers(0, w.n_points, 32)
+    idx = np.unique(np.concatenate([top, rest]))
+    o = oracle_workload(w, idx)
+    assert max_abs_diff(g, o, idx) <= RUN_TOL
+    check_sum(g)
+
+
 # ------------------------------------------------------------- properties
 def test_steps_per_launch_is_bit_invariant(ms):
     """Temporal blocking changes no arithmetic: S = 1, 7, 32, 96 and a run
