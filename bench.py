@@ -468,6 +468,7 @@ def run_ours(args):
         "work": {"source_evaluations_per_step": int(st.source_evaluations) // args.steps,
                  "model_point_steps_per_step": int(st.model_point_steps) // args.steps,
                  "tile_steps_active_frac": round(st.tile_steps_active / max(1, st.tile_steps_total), 4),
+                 "active_point_updates_per_s": value * st.tile_steps_active / max(1, st.tile_steps_total),
                  "model_run_frac": round(st.model_point_steps / max(1, 128 * st.tile_steps_active), 4),
                  "model_sfu_per_model_point_step": {
                      "ex2": round(st.model_sfu_ex2 / max(1, st.model_point_steps), 3),
