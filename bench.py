@@ -38,8 +38,22 @@ UNIT = "point-updates/s"
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_track_block_256.json")
-HBM_PEAK_GBS = 6794.8       # measured copy bandwidth of the GB300s
 L2_FLUSH_BYTES = 512 << 20
+
+
+def measured_hbm_gbs(default=6794.8):
+    """HBM copy bandwidth of the GB300 [GB/s] from MEASURED_PEAKS.json (a
+    STREAM-style copy measured on the device) when the file is present, else
+    the last such measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v if v > 0 else default
+    except (OSError, ValueError, KeyError, TypeError):
+        return default
+
+
+HBM_PEAK_GBS = measured_hbm_gbs()
 
 
 def parse_args():
