@@ -115,6 +115,10 @@ def test_windows_all_band_equal_explicit_run():
     assert n_mlp.sum() == 0
     np.testing.assert_array_equal(a.xas, b.xas)
     np.testing.assert_array_equal(a.xam, b.xam)
+    # the App. A state too (an initiation's X~ can sit far below what
+    # changes X_as)
+    np.testing.assert_array_equal(a.mode, b.mode)
+    np.testing.assert_array_equal(a.xt, b.xt)
 
 
 def test_windows_cold_quench_reduces_to_correction():
@@ -153,6 +157,25 @@ def test_windows_band_edges():
         st.xam[:] = 0.1
         n_mlp = oracle.run_track_windows(st, src, x, y, z, 0, 16, w.dt, p=p)
         assert np.all(n_mlp == (0 if in_band else 2)), T_hold
+
+
+def test_windows_heating_through_T_as_end_leave_the_fixed_point():
+    """A line 0.1 mm beside the track heats through T_as,end to ~1050 K: its
+    points enter the alpha_s -> beta initiation, so windows that reach
+    T_as,end are not fixed-point windows.  With every window sent to the
+    explicit steps (band wider than every temperature) the window form must
+    equal the explicit run in every variable, initiation state included."""
+    w, src = _line(200.0)
+    w.specimens[0].grid.origin = (0.0, 1e-4, 0.0)
+    x, y, z = w.specimens[0].grid.coords()
+    p = oracle.params()
+    a = oracle.State.uniform(x.size)
+    b = oracle.State.uniform(x.size)
+    oracle.run_track(a, src, x, y, z, 0, 200, w.dt, p)
+    oracle.run_track_windows(b, src, x, y, z, 0, 200, w.dt, band_half=1e9, p=p)
+    assert np.any(a.mode == oracle.MODE_AS_TO_B)
+    for f in ("xas", "xam", "xt", "mode"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
 
 
 def test_windows_fixed_point_is_the_explicit_identity():

@@ -51,9 +51,18 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
+# mistakes in the window form of the hybrid path (orc_run_track_windows),
+# caught by tests/test_mlp_oracle.py
+WINDOW_MUTANTS = {
+    "fixed_point_bound_T_as_start": ("cool &= T[l] < p[P_T_AS_END];",
+                                     "cool &= T[l] < p[P_T_AS_START];"),
+    "fixed_point_any_alpha": ("xas[i] == 0.9 && xam[i] == 0.0", "xas[i] >= 0.5"),
+    "windows_skip_correction": ("for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);",
+                                "(void)0;"),
+}
+
+
+def _run_pins_on_mutant(name, old, new, tmp_path, pins):
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     mut = tmp_path / "mutant.c"
@@ -63,6 +72,16 @@ def test_pins_catch_mutant(name, tmp_path):
                     "-shared", "-fPIC", str(mut), "-o", str(lib), "-lm"], check=True)
     env = dict(os.environ, MS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    _run_pins_on_mutant(name, *MUTANTS[name], tmp_path, "test_oracle_pins.py")
+
+
+@pytest.mark.parametrize("name", sorted(WINDOW_MUTANTS))
+def test_window_pins_catch_mutant(name, tmp_path):
+    _run_pins_on_mutant(name, *WINDOW_MUTANTS[name], tmp_path, "test_mlp_oracle.py")
