@@ -309,9 +309,12 @@ def test_fixed_point_tiles_skip_exactly(ms):
     w = wl.block_256(dims=(128, 64, 48), n_tracks=3, n_steps=3000, T_thr=354.0)
     ctx, g = gpu_workload(w)
     st = ctx.stats()
-    _, dense = gpu_workload(w, T_thr=0.0)
+    dctx, dense = gpu_workload(w, T_thr=0.0)
     assert st.tile_steps_active < 0.8 * st.tile_steps_total
     assert max_abs_diff(g, np.stack(dense)) == 0.0
+    # the App. A variable too: points heated past T_as,end start the alpha_s
+    # -> beta initiation while X_as still rounds to 0.9
+    np.testing.assert_array_equal(ctx.aux(), dctx.aux())
     check_sum(g)
 
 
