@@ -262,6 +262,16 @@ const char* ms_last_error(void);
  * 5 ms_stats_t.  Returns 0 for an unknown index. */
 size_t ms_struct_size(int which);
 
+/* The far field's interpolation table (ms_params.farfield_dist; not in the
+ * paper): the Lagrange weights of the 8 Chebyshev points of the first kind
+ * on a row tile's x-range [0, 1] at the tile's 128 points t_i = i / 127,
+ * node-major (out[k * 128 + i]), then the 8 node positions (out[1024 + k]),
+ * as the kernels use them.  Host only, no device work.  n_out is the
+ * capacity of out in floats (at least MS_FF_TABLE_FLOATS).
+ * Errors: INVALID_ARG (out NULL or too small). */
+#define MS_FF_TABLE_FLOATS 1032
+int ms_farfield_table(float* out, int32_t n_out);
+
 /* Fill *p with the paper's constants and the default readings / options.
  * Errors: MS_ERR_INVALID_ARG if p is NULL. */
 int ms_params_default(ms_params* p);

@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     lib.ms_last_error.restype = ctypes.c_char_p
     lib.ms_struct_size.restype = ctypes.c_size_t
     lib.ms_struct_size.argtypes = [ctypes.c_int]
+    lib.ms_farfield_table.argtypes = [ctypes.POINTER(ctypes.c_float), i32]
     lib.ms_params_default.argtypes = [ctypes.POINTER(Params)]
     lib.ms_create.argtypes = [ctypes.POINTER(Params), i64, ctypes.POINTER(P)]
     lib.ms_destroy.argtypes = [P]
@@ -190,6 +191,19 @@ def probe_pipe(op: str):
     _check(load().ms_probe_sfu(PROBE_OPS.index(op), ctypes.byref(v), ctypes.byref(mhz)),
            "ms_probe_sfu")
     return v.value, mhz.value
+
+
+FF_TABLE_FLOATS = 1032   # MS_FF_TABLE_FLOATS
+
+
+def farfield_table():
+    """The far field's interpolation table (ms_farfield_table): Lagrange
+    weights [8, 128] of the 8 Chebyshev nodes at a row tile's 128 points, and
+    the node positions [8] on the tile's x-range [0, 1]."""
+    out = (ctypes.c_float * FF_TABLE_FLOATS)()
+    _check(load().ms_farfield_table(out, FF_TABLE_FLOATS), "ms_farfield_table")
+    a = np.frombuffer(out, dtype=np.float32).copy()
+    return a[:1024].reshape(8, 128), a[1024:]
 
 
 def default_params(**overrides) -> Params:

@@ -768,6 +768,15 @@ const char* ms_strerror(int code) {
 
 const char* ms_last_error(void) { return g_last_error.c_str(); }
 
+int ms_farfield_table(float* out, int32_t n_out) {
+  static_assert(ms::FF_FLOATS == MS_FF_TABLE_FLOATS, "table size");
+  if (!out || n_out < ms::FF_FLOATS)
+    return fail(MS_ERR_INVALID_ARG, "need a table of at least %d floats", ms::FF_FLOATS);
+  const std::vector<float> w = farfield_weights();
+  std::copy(w.begin(), w.end(), out);
+  return MS_OK;
+}
+
 size_t ms_struct_size(int which) {
   switch (which) {
     case 0: return sizeof(ms_params);

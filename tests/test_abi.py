@@ -122,3 +122,27 @@ def test_product_and_oracle_share_no_code():
     opy = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
     imports = re.findall(r"^\s*(?:import|from)\s+([\w.]+)", opy, flags=re.M)
     assert not [m for m in imports if m.split(".")[0] in ("paper_2402_17580_gb300", "workloads")]
+
+
+def test_farfield_table_is_lagrange_interpolation_at_chebyshev_nodes():
+    """The far field's table (host-only): the nodes are the 8 Chebyshev points
+    of the first kind on [0, 1], and the weights at the tile's 128 points
+    t_i = i / 127 reproduce every polynomial of degree <= 7 (so they sum to
+    1), up to FP32 rounding of the stored table."""
+    import numpy as np
+    from paper_2402_17580_gb300._binding import farfield_table
+    w, s = farfield_table()
+    k = np.arange(8)
+    np.testing.assert_allclose(s, 0.5 * (1.0 - np.cos((2 * k + 1) * np.pi / 16)), atol=1e-7)
+    t = np.arange(128) / 127.0
+    for m in range(8):
+        np.testing.assert_allclose((w * (s.astype(np.float64)[:, None] ** m)).sum(axis=0), t ** m,
+                                   atol=2e-6)
+    # the Lebesgue function sum_k |w_k(t)| bounds how much FP32 error in the
+    # node sums the interpolation can amplify; for 8 Chebyshev nodes it is
+    # about (2 / pi) ln 8 + 1, its largest at the tile's ends t = 0, 1
+    leb = np.abs(w.astype(np.float64)).sum(axis=0)
+    assert leb.max() < 2.6, leb.max()
+    with pytest.raises(ms.MSError):
+        out = (ctypes.c_float * 10)()
+        B._check(ms.load().ms_farfield_table(out, 10), "ms_farfield_table")
