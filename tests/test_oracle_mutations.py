@@ -2,7 +2,9 @@
 
 Each case plants one mistake in a copy of oracle/ms_oracle.c (a dropped term,
 a wrong sign, index or exponent, a transposed operand), compiles it on the
-CPU and runs tests/test_oracle_pins.py against it; the pins must fail.
+CPU and runs tests/test_oracle_pins.py against it; the pins must fail.  The
+same is done for the thermal reference oracle/thermal.py, whose pins are
+tests/test_thermal_oracle.py.
 """
 import os
 import subprocess
@@ -12,6 +14,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ms_oracle.c")
+THERMAL_SRC = os.path.join(ROOT, "oracle", "thermal.py")
 
 MUTANTS = {
     "xalpha_eq_sign": ("exp(-p[P_K_ALPHA_EQ] * (p[P_T_AS_START] - T))",
@@ -85,3 +88,57 @@ def test_pins_catch_mutant(name, tmp_path):
 @pytest.mark.parametrize("name", sorted(WINDOW_MUTANTS))
 def test_window_pins_catch_mutant(name, tmp_path):
     _run_pins_on_mutant(name, *WINDOW_MUTANTS[name], tmp_path, "test_mlp_oracle.py")
+
+
+# mistakes in the thermal reference, caught by tests/test_thermal_oracle.py
+THERMAL_MUTANTS = {
+    "face_mean_arithmetic": ("2.0 * a * b / np.where(s > 0.0, s, 1.0)", "0.5 * s"),
+    "radiation_ambient_dropped": ("(Tt ** 4 - p.T_inf ** 4)", "Tt ** 4"),
+    "radiation_on_bottom": ("flux[g.top] -= p.emissivity", "flux[g.bottom] -= p.emissivity"),
+    "dirichlet_dropped": ("        Tn[g.bottom] = p.T0\n", "        pass\n"),
+    "cap_dropped": ("        Tn = np.minimum(Tn, p.T_max)\n", "        pass\n"),
+    "substeps_past_stability": ("dt / (0.9 * dt_stab)", "dt / (2.5 * dt_stab)"),
+    "z_face_area": ("(dx * dy / dz)", "(dx * dz / dy)"),
+    "x_face_area": ("(dy * dz / dx)", "(dx * dz / dy)"),
+    "source_normalisation_halved": ("2.0 * W / (math.pi", "W / (math.pi"),
+    "powder_layer_inclusive": ("inside = (depth >= 0.0) & (depth < p.h_powder)",
+                               "inside = (depth >= 0.0) & (depth <= p.h_powder)"),
+    "consolidation_not_running_max": ("rcn = np.maximum(rc, liquid_fraction(p, Tn))",
+                                      "rcn = liquid_fraction(p, Tn)"),
+    "conductivity_swapped": ("(1.0 - rc) * p.k_p + rc * p.k_ms", "rc * p.k_p + (1.0 - rc) * p.k_ms"),
+    "source_at_substep_end": ("ts = t + s * h", "ts = t + (s + 1) * h"),
+    "track_runs_to_layer_end": ("            t_end = tracks[j + 1, 6]", "            t_end = t_end"),
+    "laser_direction_reversed": ("tr[0] + tr[2] * d", "tr[0] - tr[2] * d"),
+}
+
+_IMPORT_GUARD = """import os
+from oracle import thermal
+
+
+def pytest_configure(config):
+    here = os.path.dirname(os.path.abspath(__file__))
+    assert os.path.abspath(thermal.__file__).startswith(here), thermal.__file__
+"""
+
+
+@pytest.mark.parametrize("name", sorted(THERMAL_MUTANTS))
+def test_thermal_pins_catch_mutant(name, tmp_path):
+    """The thermal reference is Python: the mutant goes into a package
+    ``oracle`` of its own beside a copy of the pins, so that the pins import
+    it and not the real one (a conftest checks that)."""
+    old, new = THERMAL_MUTANTS[name]
+    src = open(THERMAL_SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    (pkg / "__init__.py").write_text("")
+    (pkg / "thermal.py").write_text(src.replace(old, new))
+    (tmp_path / "conftest.py").write_text(_IMPORT_GUARD)
+    pins = open(os.path.join(ROOT, "tests", "test_thermal_oracle.py")).read()
+    (tmp_path / "test_thermal_oracle.py").write_text(pins)
+    env = {k: v for k, v in os.environ.items() if k != "PYTHONPATH"}
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "--rootdir", str(tmp_path), str(tmp_path / "test_thermal_oracle.py")],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    # 1: a pin failed (a conftest that rejects the import ends with another code)
+    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
