@@ -21,7 +21,8 @@ Definitions followed here, written out with numpy in float64:
 
 Pinned by tests/test_mlp_oracle.py: finite differences of the loss, closed
 forms of GELU, the rounding against torch's bfloat16 conversion, and a
-network reduced by hand to a single path.
+network reduced by hand to a single path, in float64 and in bf16 (forward,
+and the gradient with the rounded values held fixed, by the chain rule).
 """
 from __future__ import annotations
 

@@ -61,6 +61,72 @@ def test_single_path_network_by_hand():
     np.testing.assert_array_equal(y[:, 1], d[1])
 
 
+def _single_path_bf16():
+    """The one-path network of the test above with weights that bf16 cannot
+    hold exactly, and torch's bfloat16 conversion as the rounding."""
+    torch = pytest.importorskip("torch")
+
+    def r(v):
+        return torch.tensor(float(v), dtype=torch.float32).to(torch.bfloat16).double().item()
+
+    a, b, c = 0.7513, -1.2571, 2.0113
+    d = np.array([0.1, -0.2, 0.3])
+    p = np.zeros(mlp.N_PARAMS)
+    p[mlp.OFF_W1 + 5 * mlp.N_IN + 3] = a
+    p[mlp.OFF_W2 + 7 * mlp.N_H + 5] = b
+    p[mlp.OFF_W3 + 2 * mlp.N_H + 7] = c
+    p[mlp.OFF_B3:] = d
+    return r, (a, b, c, d), p
+
+
+def test_single_path_network_in_bf16():
+    """With bf16 on, the weights, the inputs and both hidden activations are
+    rounded before they are used: on the one-path network
+    y2 = r(c) r(gelu(r(b) r(gelu(r(a) r(x3))))) + d2, with r the rounding."""
+    r, (a, b, c, d), p = _single_path_bf16()
+    X = np.random.default_rng(12).normal(0, 1, (40, mlp.N_IN))
+    y, _ = mlp.forward(p, X, bf16=True)
+    for i, x3 in enumerate(X[:, 3]):
+        a1 = r(mlp.gelu(np.array([r(a) * r(x3)]))[0])
+        a2 = r(mlp.gelu(np.array([r(b) * a1]))[0])
+        assert y[i, 2] == pytest.approx(r(c) * a2 + d[2], rel=1e-14, abs=1e-15), i
+    np.testing.assert_array_equal(y[:, :2], np.tile(d[:2], (40, 1)))
+
+
+def test_single_path_gradient_in_bf16_holds_the_rounded_values():
+    """The bf16 gradient is backpropagation through the network with the
+    rounded weights, inputs and activations held fixed (rounding passes the
+    gradient unchanged): on the one-path network, by the chain rule,
+    dL/dc = sum dy r(a2), dL/db = sum dy r(c) gelu'(h2) r(a1),
+    dL/da = sum dy r(c) gelu'(h2) r(b) gelu'(h1) r(x3), and
+    dL/dW1[5][4] the same with r(x4), dy = 2 (y2 - t2) / (3 n)."""
+    r, (a, b, c, d), p = _single_path_bf16()
+    rng = np.random.default_rng(13)
+    n = 30
+    X = rng.normal(0, 1, (n, mlp.N_IN))
+    T = rng.normal(0, 1, (n, mlp.N_OUT))
+    y, _ = mlp.forward(p, X, bf16=True)
+    _, g = mlp.loss_and_gradient(p, X, T, bf16=True)
+    dc = db = da = da4 = db3 = 0.0
+    for i in range(n):
+        dy = 2.0 * (y[i, 2] - T[i, 2]) / (3 * n)
+        h1 = r(a) * r(X[i, 3])
+        a1 = r(mlp.gelu(np.array([h1]))[0])
+        h2 = r(b) * a1
+        a2 = r(mlp.gelu(np.array([h2]))[0])
+        back = dy * r(c) * mlp.gelu_grad(np.array([h2]))[0]
+        dc += dy * a2
+        db += back * a1
+        da += back * r(b) * mlp.gelu_grad(np.array([h1]))[0] * r(X[i, 3])
+        da4 += back * r(b) * mlp.gelu_grad(np.array([h1]))[0] * r(X[i, 4])
+        db3 += dy
+    assert g[mlp.OFF_W3 + 2 * mlp.N_H + 7] == pytest.approx(dc, rel=1e-12)
+    assert g[mlp.OFF_W2 + 7 * mlp.N_H + 5] == pytest.approx(db, rel=1e-12)
+    assert g[mlp.OFF_W1 + 5 * mlp.N_IN + 3] == pytest.approx(da, rel=1e-12)
+    assert g[mlp.OFF_W1 + 5 * mlp.N_IN + 4] == pytest.approx(da4, rel=1e-12)
+    assert g[mlp.OFF_B3 + 2] == pytest.approx(db3, rel=1e-12)
+
+
 def test_gradient_against_finite_differences():
     rng = np.random.default_rng(3)
     p = rng.normal(0, 0.3, mlp.N_PARAMS)

@@ -3,8 +3,9 @@
 Each case plants one mistake in a copy of oracle/ms_oracle.c (a dropped term,
 a wrong sign, index or exponent, a transposed operand), compiles it on the
 CPU and runs tests/test_oracle_pins.py against it; the pins must fail.  The
-same is done for the thermal reference oracle/thermal.py, whose pins are
-tests/test_thermal_oracle.py.
+same is done for the Python parts: the thermal reference oracle/thermal.py
+(pins: tests/test_thermal_oracle.py) and the surrogate's network
+oracle/mlp.py (pins: the network tests of tests/test_mlp_oracle.py).
 """
 import os
 import subprocess
@@ -112,33 +113,69 @@ THERMAL_MUTANTS = {
 }
 
 _IMPORT_GUARD = """import os
-from oracle import thermal
+from oracle import {module}
 
 
 def pytest_configure(config):
     here = os.path.dirname(os.path.abspath(__file__))
-    assert os.path.abspath(thermal.__file__).startswith(here), thermal.__file__
+    assert os.path.abspath({module}.__file__).startswith(here), {module}.__file__
 """
 
 
-@pytest.mark.parametrize("name", sorted(THERMAL_MUTANTS))
-def test_thermal_pins_catch_mutant(name, tmp_path):
-    """The thermal reference is Python: the mutant goes into a package
-    ``oracle`` of its own beside a copy of the pins, so that the pins import
-    it and not the real one (a conftest checks that)."""
-    old, new = THERMAL_MUTANTS[name]
-    src = open(THERMAL_SRC).read()
+def _run_py_pins_on_mutant(module, name, old, new, tmp_path, pins, select=None):
+    """A Python part of the oracle: the mutant goes into a package ``oracle``
+    of its own beside a copy of the pins, so that the pins import it and not
+    the real one (a conftest checks that); the repository stays on the path
+    for the workload generators."""
+    src = open(os.path.join(ROOT, "oracle", module + ".py")).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     pkg = tmp_path / "oracle"
     pkg.mkdir()
     (pkg / "__init__.py").write_text("")
-    (pkg / "thermal.py").write_text(src.replace(old, new))
-    (tmp_path / "conftest.py").write_text(_IMPORT_GUARD)
-    pins = open(os.path.join(ROOT, "tests", "test_thermal_oracle.py")).read()
-    (tmp_path / "test_thermal_oracle.py").write_text(pins)
-    env = {k: v for k, v in os.environ.items() if k != "PYTHONPATH"}
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        "--rootdir", str(tmp_path), str(tmp_path / "test_thermal_oracle.py")],
-                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    (pkg / (module + ".py")).write_text(src.replace(old, new))
+    (tmp_path / "conftest.py").write_text(_IMPORT_GUARD.format(module=module))
+    (tmp_path / pins).write_text(open(os.path.join(ROOT, "tests", pins)).read())
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+           "--rootdir", str(tmp_path), str(tmp_path / pins)]
+    if select:
+        cmd += ["-k", select]
+    r = subprocess.run(cmd, cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
     # 1: a pin failed (a conftest that rejects the import ends with another code)
     assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
+@pytest.mark.parametrize("name", sorted(THERMAL_MUTANTS))
+def test_thermal_pins_catch_mutant(name, tmp_path):
+    _run_py_pins_on_mutant("thermal", name, *THERMAL_MUTANTS[name], tmp_path,
+                           "test_thermal_oracle.py")
+
+
+# mistakes in the surrogate's reference network, caught by the network pins
+# of tests/test_mlp_oracle.py (its window-form pins need the compiled oracle)
+MLP_MUTANTS = {
+    "layout_transposed": ("p[OFF_W1:OFF_B1].reshape(N_H, N_IN)",
+                          "p[OFF_W1:OFF_B1].reshape(N_IN, N_H).T"),
+    "gelu_constant": ("GELU_A = 0.044715", "GELU_A = 0.047715"),
+    "gelu_grad_term_dropped": ("(1.0 + 3.0 * GELU_A * x ** 2)", "1.0"),
+    "round_half_up": ("(u + 0x7FFF + lsb)", "(u + 0x7FFF)"),
+    "input_not_rounded": ("x = rnd(np.asarray(X, dtype=np.float64))",
+                          "x = np.asarray(X, dtype=np.float64)"),
+    "W1_not_rounded": ("W1, W2, W3 = rnd(W1), rnd(W2), rnd(W3)", "W2, W3 = rnd(W2), rnd(W3)"),
+    "hidden1_not_rounded": ("a1 = rnd(gelu(h1))", "a1 = gelu(h1)"),
+    "hidden2_not_rounded": ("a2 = rnd(gelu(h2))", "a2 = gelu(h2)"),
+    "bias_b2_dropped": ("h2 = a1 @ W2.T + b2", "h2 = a1 @ W2.T"),
+    "loss_mean_over_samples_only": ("loss = float(np.sum(r * r) / (N_OUT * n))",
+                                    "loss = float(np.sum(r * r) / n)"),
+    "gradient_unrounded_input": ("g[OFF_W1:OFF_B1] = (dh1.T @ x).ravel()",
+                                 "g[OFF_W1:OFF_B1] = (dh1.T @ np.asarray(X, dtype=np.float64)).ravel()"),
+    "backprop_unrounded_W3": ("dh2 = (dy @ W3) * gelu_grad(h2)",
+                              "dh2 = (dy @ unpack(params)[4]) * gelu_grad(h2)"),
+    "gradient_sign": ("dy = 2.0 * r / (N_OUT * n)", "dy = -2.0 * r / (N_OUT * n)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_network_pins_catch_mutant(name, tmp_path):
+    _run_py_pins_on_mutant("mlp", name, *MLP_MUTANTS[name], tmp_path, "test_mlp_oracle.py",
+                           select="not windows")
