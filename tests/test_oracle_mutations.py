@@ -52,6 +52,24 @@ MUTANTS = {
                            "rates(p, T1, xas, xam, &das0, &dam0);"),
     "substep_temperature_frozen": ("const double Tb = T0 + (T1 - T0) * ((double)(s + 1) / (double)ns);",
                                    "const double Tb = T0 + (T1 - T0) * ((double)s / (double)ns);"),
+    "xam_clamp_dropped": ("  if (xam < 0.0) xam = 0.0;\n", ""),
+    "cap_floor_dropped": ("    if (cap < 0.0) cap = 0.0;\n", ""),
+    "cap_from_T_reg_up": ("  if (T > p[P_T_AS_START]) {\n    double cap",
+                          "  if (T > p[P_T_AS_START] + p[P_T_REG]) {\n    double cap"),
+    "dissolution_ignores_X_as": ("    double v = xeq - xas;\n", "    double v = xeq;\n"),
+    "formation_literal_by_default": ("else if (e > xam) xam = e;", "else xam = e;"),
+    "xam0_eq_cap_dropped": ("return v < XMAX ? v : XMAX;", "return v;"),
+    "init_exit_without_dt": ("xt * dt > p[P_INIT_EXIT]", "xt > p[P_INIT_EXIT]"),
+    "appendix_unshifted_alpha_s": ("    nas = XMAX - xt;\n", "    nas = 1.0 - xt;\n"),
+    "appendix_entry_with_martensite": ("&& XMAX - xa <= 0.0 && xam == 0.0) {\n    mode = MODE_AS_TO_B;",
+                                       "&& XMAX - xa <= 0.0) {\n    mode = MODE_AS_TO_B;"),
+    "cap_keeps_initiation": ("if (nas < before) mode = MODE_NONE;", "if (0) mode = MODE_NONE;"),
+    "ba_initiation_drops_r2": ("nas = logistic_step(xas, D, k, ca, dt) + dt * r2;",
+                               "nas = logistic_step(xas, D, k, ca, dt);"),
+    "unstarted_tracks_heat": ("|| tl < tr[TR_TS]) continue;", ") continue;"),
+    "other_layers_tracks_heat": ("if ((int32_t)tr[TR_LAYER] != l || tl < tr[TR_TS]) continue;",
+                                 "if (tl < tr[TR_TS]) continue;"),
+    "undeposited_points_advance": ("if (a1) advance(", "(void)a1; advance("),
 }
 
 

@@ -311,6 +311,8 @@ def test_correction_clamp_and_rescale():
     scaled back to 0.9 keeping X_as / X_am."""
     xas, xam = orc.correct(900.0, -0.1, 0.3)
     assert xas == 0.0 and xam == 0.3
+    xas, xam = orc.correct(900.0, 0.3, -0.1)
+    assert xas == 0.3 and xam == 0.0
     xas, xam = orc.correct(900.0, 0.6, 0.4)
     assert xas + xam == pytest.approx(0.9, abs=1e-15) and xas / xam == pytest.approx(1.5, rel=1e-13)
 
@@ -442,9 +444,84 @@ def test_source_superposition_cap_and_layers():
     assert T_scan[0] > T_mid[0]
     _, act = orc.temperature(src, [1e-3], [0], [-1e-5], 0.015)
     assert list(act) == [1]
+    # layer 1 has begun but its track has not: the receding layer-0 source
+    # (15 mm down the line, ~70 K of tail here) belongs to the old layer
+    T_l1, _ = orc.temperature(src, [1e-3, 5e-3], [0, 0], [0.0, -3e-5], 0.015)
+    assert np.all(T_l1 == 353.0)
+    # tracks that have not started add nothing, also near their start
+    xs, ys, zs = np.array([-4e-4, 0.0, 2e-4]), np.array([1e-4] * 3), np.array([-1e-5] * 3)
+    assert np.array_equal(orc.temperature(both, xs, ys, zs, 0.5e-3)[0],
+                          orc.temperature(a, xs, ys, zs, 0.5e-3)[0])
     # before the specimen's start offset nothing is hot
     off = HeatSource(tr[:1], L, t_offset=0.5)
     assert orc.temperature(off, 1e-4, 0, 0, 0.3)[0][0] == 353.0
+
+
+def test_points_above_the_surface_are_not_advanced():
+    """A point above the current layer's surface is not yet deposited: it
+    keeps its state while the layer below is scanned right under it (the
+    same point one layer down melts and re-forms), and takes part once its
+    own layer begins."""
+    tr = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0, 0],
+                   [0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0105, 1]])
+    L = np.array([[-3e-5, 0.0, 0.004, 0.01], [0.0, 0.01, 0.014, 0.02]])
+    src = HeatSource(tr, L)
+    x, y, z = np.array([1e-3, 1e-3]), np.array([0.0, 0.0]), np.array([-1e-5, -3e-5])
+    s = orc.State.uniform(2, 0.9, 0.0)
+    dt = 1e-5
+    orc.run_track(s, src, x, y, z, 0, 999, dt)          # layer 0 only
+    assert s.xas[0] == 0.9 and s.xam[0] == 0.0
+    assert s.xam[1] > 0.5                                # melted and quenched
+    orc.run_track(s, src, x, y, z, 999, 1000, dt)        # into layer 1
+    assert s.xam[0] > 0.5
+
+
+# ------------------------------------------- App. A entry, exits and r2
+def test_full_alpha_with_martensite_dissolves_instantly():
+    """A full alpha state with martensite (X_alpha = 0.9, X_am > 0) heated
+    above T_as,end: r3 is zero (its factor 0.9 - X_alpha is), so alpha_s
+    gains only the small alpha_m -> alpha_s transfer r2 dt in the step, and
+    eq:inst_martensite_dissolution cuts X_am to X_alpha^eq - X_as at once
+    (1000 K: X_alpha^eq = 0.843766, P3); the App. A alpha_s -> beta
+    initiation is not entered (it starts from martensite-free full alpha)."""
+    assert 0.5 + 0.4 == 0.9                              # X_alpha exactly 0.9
+    s = orc.State.make([0.5], [0.4])
+    orc.run_temps(s, np.array([1000.0, 1000.0]), 1e-5)
+    assert 0.5 <= s.xas[0] < 0.5 + 1e-6
+    assert s.xas[0] + s.xam[0] == pytest.approx(0.843766, abs=1e-6)
+    assert s.mode[0] == orc.MODE_NONE
+
+
+def test_regularisation_cap_ends_the_initiation():
+    """Reading A5: once the alpha_s cap of the regularisation (Sec. 2.2) sets
+    X_as, the App. A initiation ends; alpha_s -> beta then goes on by r3
+    (X_alpha < 0.9 now), so at the same temperature the next step takes X_as
+    strictly below the cap."""
+    s = orc.State.uniform(1, 0.9, 0.0)
+    orc.run_temps(s, np.array([1200.0, 1200.0, 1330.0]), 1e-5)
+    cap = 0.9 * (1373.0 - 1330.0) / 100.0
+    assert s.mode[0] == orc.MODE_NONE and s.xt[0] == 0.0
+    assert s.xas[0] == pytest.approx(cap, abs=1e-14)
+    orc.run_temps(s, np.array([1330.0, 1330.0]), 1e-3)
+    assert s.xas[0] < cap - 1e-6
+
+
+def test_persisted_beta_to_alpha_s_initiation_keeps_alpha_m_transfer():
+    """Reading A6 with INIT_BA_STEPS: while the closed-form initiation
+    advances alpha_s (D = X_alpha^eq - X_am), the alpha_m -> alpha_s rate r2
+    (eq:alpha_m_to_alpha_s) still moves alpha_m into alpha_s, so X_alpha
+    changes by the closed form's increment alone and X_am falls."""
+    p = orc.params(init_ba_steps=1, init_exit=1e300)
+    T, dt, xas0, xam0 = 900.0, 1e-2, 0.05, 0.3
+    s = orc.State.make([xas0], [xam0])
+    s.mode[:] = orc.MODE_B_TO_AS
+    orc.run_temps(s, np.array([T, T]), dt, p)
+    D, k, c = 0.9 - xam0, orc.k_alpha_s(T), 2.51
+    # time at which the closed form (P1) passes X_as0, then dt later
+    t0 = (c / (D * k)) * (xas0 / (D - xas0)) ** (1.0 / c)
+    assert s.xas[0] + s.xam[0] - (xas0 + xam0) == pytest.approx(
+        closed_form(t0 + dt, D, k, c) - xas0, rel=1e-9)
+    assert s.xam[0] < xam0 - 1e-6
 
 
 # ------------------------------------------------------------- dt halving
