@@ -70,6 +70,18 @@ MUTANTS = {
     "other_layers_tracks_heat": ("if ((int32_t)tr[TR_LAYER] != l || tl < tr[TR_TS]) continue;",
                                  "if (tl < tr[TR_TS]) continue;"),
     "undeposited_points_advance": ("if (a1) advance(", "(void)a1; advance("),
+    "cn_iterate_rates_at_T0": ("rates(p, T1, nas, nam, &das1, &dam1);",
+                               "rates(p, T0, nas, nam, &das1, &dam1);"),
+    "cn_iterate_without_g": ("    correct(p, T1, &nas, &nam);\n    double das1", "    double das1"),
+    "cn_stops_after_one_iteration": ("    if (e < 1.0) {", "    if (1) {"),
+    "substeps_round_up_decimal_multiples": ("ceil(dt / p[P_DT_SUB] - 1e-9)", "ceil(dt / p[P_DT_SUB])"),
+    "substep_length_is_dt_sub": ("const double h = dt / (double)ns;",
+                                 "const double h = p[P_DT_SUB] > 0.0 ? p[P_DT_SUB] : dt;"),
+    "implicit_without_beta_to_alpha_initiation": ("    if (xa < xeq0 && *xas == 0.0) init = 1;\n", ""),
+    "implicit_without_alpha_to_beta_initiation": (
+        "    if (xa > xeq0 && XMAX - xa <= 0.0 && *xam == 0.0) init = 1;\n", ""),
+    "implicit_initiation_over_the_whole_step": ("      point_step(p, Ta, Tb, h, xas, xam, xt, mode);",
+                                                "      point_step(p, T0, T1, h, xas, xam, xt, mode);"),
 }
 
 

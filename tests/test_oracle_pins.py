@@ -616,16 +616,24 @@ def test_implicit_subcycling_is_substeps_with_linear_temperature():
     p = orc.params(integrator=1, dt_sub=0.01)
     assert orc.n_substeps(0.1, p) == 10 and orc.n_substeps(0.01, p) == 1
     assert orc.n_substeps(0.0101, p) == 2 and orc.n_substeps(1e-5, p) == 1
-    T0, T1 = 1150.0, 700.0
-    a = orc.State.uniform(3, 0.0, 0.0)
-    a.xas[:] = [0.3, 0.6, 0.05]
-    a.xam[:] = [0.2, 0.0, 0.4]
-    b = a.copy()
-    orc.step(a, T0, T1, 0.1, p)
-    hist = np.array([[T0 + (T1 - T0) * (s / 10)] * 3 for s in range(11)])
-    orc.run_temps(b, hist, 0.01, orc.params(integrator=1, dt_sub=0.0))
-    np.testing.assert_array_equal(a.xas, b.xas)
-    np.testing.assert_array_equal(a.xam, b.xam)
+    # every step written as k hundredths takes k substeps, also where the
+    # quotient rounds just above k (0.07 / 0.01 = 7.000000000000001)
+    ks = range(1, 101)
+    assert [orc.n_substeps(float(f"{k / 100:.2f}"), p) for k in ks] == list(ks)
+    # (T0, T1, dt, substeps): cooling and heating, a multiple and not one;
+    # the states include both App. A initiations (pure beta, full alpha)
+    for T0, T1, dt, n in ((1150.0, 700.0, 0.1, 10), (1150.0, 700.0, 0.015, 2),
+                          (900.0, 1210.0, 0.035, 4)):
+        a = orc.State.uniform(5, 0.0, 0.0)
+        a.xas[:] = [0.3, 0.6, 0.05, 0.0, 0.9]
+        a.xam[:] = [0.2, 0.0, 0.4, 0.0, 0.0]
+        b = a.copy()
+        orc.step(a, T0, T1, dt, p)
+        hist = np.array([[T0 + (T1 - T0) * (s / n)] * 5 for s in range(n + 1)])
+        orc.run_temps(b, hist, dt / n, orc.params(integrator=1, dt_sub=0.0))
+        np.testing.assert_array_equal(a.xas, b.xas)
+        np.testing.assert_array_equal(a.xam, b.xam)
+        np.testing.assert_array_equal(a.mode, b.mode)
 
 
 def test_implicit_reaches_equilibria_and_quench_values():
@@ -641,6 +649,12 @@ def test_implicit_reaches_equilibria_and_quench_values():
     e = orc.State.uniform(1, 0.0, 0.0)
     orc.run_temps(e, np.full(40001, 1000.0), 0.01)
     assert abs(s.xas[0] - e.xas[0]) < 1e-4
+    # from full alpha (the App. A alpha_s -> beta initiation, reading I2;
+    # its half time at 1000 K is c_beta / (D k_beta) = 176 s) it falls to the
+    # equilibrium X_alpha^eq(1000 K) = 0.843766 (P3)
+    f = orc.State.uniform(1, 0.9, 0.0)
+    orc.run_temps(f, np.full(8001, 1000.0), 0.1, p)
+    assert f.xas[0] == pytest.approx(0.843766, abs=1e-5)
     # an instant drop is one step without substeps (with substeps the 0.5 s
     # step cools linearly and a little alpha_s forms on the way)
     q = orc.State.uniform(1, 0.0, 0.0)
