@@ -270,3 +270,85 @@ def test_windows_fixed_point_is_the_explicit_identity():
     n_mlp, n_fixed = oracle.run_track_windows(oracle.State.uniform(4), src, x, y, z, 0, 40, w.dt,
                                                p=p, return_fixed=True)
     assert np.all(n_fixed == 0)
+
+
+def _hold(T_hold, n=2):
+    w, src = _line(0.0, n=n, T0=T_hold)
+    return (src,) + w.specimens[0].grid.coords() + (w.dt,)
+
+
+def test_window_starting_inside_an_initiation_takes_the_explicit_steps():
+    """Reading S1: a window with an App. A initiation running at its start
+    (here alpha_s -> beta at a constant 1000 K, outside every band) takes the
+    explicit steps, so the window form equals the explicit run."""
+    src, x, y, z, dt = _hold(1000.0)
+    p = oracle.params()
+    mk = lambda: oracle.State.make([0.9 - 1e-3] * 2, [0.0] * 2, xt=[1e-3] * 2,
+                                   mode=[oracle.MODE_AS_TO_B] * 2)
+    a, b = mk(), mk()
+    oracle.run_track(a, src, x, y, z, 0, 8, dt, p)
+    n_mlp = oracle.run_track_windows(b, src, x, y, z, 0, 8, dt, p=p)
+    assert np.all(n_mlp == 0)
+    for f in ("xas", "xam", "xt", "mode"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_window_start_level_counts_in_the_band():
+    """Reading S1: the band test covers the window's start temperature too.
+    A point held at 850 K (within 40 K of T_am,start) is heated to ~1150 K
+    (outside every band) from the first new level on by a track that starts
+    half a step after the window's start and stays 5.3 mm away: the window
+    takes the explicit steps."""
+    dt = 1e-5
+    tracks = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 40.5 * dt, 0]])
+    src = workloads.HeatSource(tracks, np.array([[0.0, 0.0, workloads.NEVER, workloads.NEVER]]),
+                               T0=850.0)
+    x, y, z = np.array([-5.3e-3]), np.array([0.0]), np.array([0.0])
+    T = np.array([oracle.temperature(src, x, y, z, (40 + l) * dt)[0][0] for l in range(9)])
+    assert T[0] == 850.0 and np.all((T[1:] > 1100.0) & (T[1:] < 1200.0))
+    p = oracle.params()
+    a, b = oracle.State.make([0.6], [0.1]), oracle.State.make([0.6], [0.1])
+    oracle.run_track(a, src, x, y, z, 40, 8, dt, p)
+    n_mlp = oracle.run_track_windows(b, src, x, y, z, 40, 8, dt, p=p)
+    assert n_mlp[0] == 0
+    np.testing.assert_array_equal(a.xas, b.xas)
+    np.testing.assert_array_equal(a.xam, b.xam)
+
+
+def test_g_only_window_corrects_at_every_level():
+    """A window outside the bands applies g at each of its new temperatures in
+    turn.  A point 100 um beside the track heats from ~420 K to ~530 K within
+    one window: from pure beta the martensite that forms is that of the
+    window's coldest (first) level, X_am = 1 - exp(-k_am (848 - T_1)) (P4),
+    and the warmer levels after it form no more (reading A3)."""
+    dt = 1e-5
+    tracks = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0, 0]])
+    src = workloads.HeatSource(tracks, np.array([[0.0, 0.0, workloads.NEVER, workloads.NEVER]]))
+    x, y, z = np.array([0.5e-3]), np.array([100e-6]), np.array([0.0])
+    n0 = 66
+    T = np.array([oracle.temperature(src, x, y, z, (n0 + l) * dt)[0][0] for l in range(9)])
+    assert np.all(np.diff(T) > 0) and T[8] < 808.0 and T[8] - T[1] > 80.0
+    st = oracle.State.make([0.0], [0.0])
+    n_mlp = oracle.run_track_windows(st, src, x, y, z, n0, 8, dt, p=oracle.params())
+    assert n_mlp[0] == 1
+    assert st.xam[0] == pytest.approx(1.0 - math.exp(-0.00415 * (848.0 - T[1])), rel=1e-12)
+    assert st.xas[0] == 0.0
+
+
+def test_windows_leave_undeposited_points_alone():
+    """Points above the current layer's surface keep their state in the
+    window form too: with every window sent to the explicit steps it equals
+    the explicit run on two layers, the undeposited point untouched through
+    the first."""
+    dt = 1e-5
+    tr = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0, 0],
+                   [0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 0.0105, 1]])
+    L = np.array([[-3e-5, 0.0, 0.004, 0.01], [0.0, 0.01, 0.014, 0.02]])
+    src = workloads.HeatSource(tr, L)
+    x, y, z = np.array([1e-3, 1e-3]), np.array([0.0, 0.0]), np.array([-1e-5, -3e-5])
+    a, b = oracle.State.uniform(2), oracle.State.uniform(2)
+    oracle.run_track(a, src, x, y, z, 0, 999, dt)
+    oracle.run_track_windows(b, src, x, y, z, 0, 999, dt, band_half=1e9)
+    assert b.xas[0] == 0.9 and b.xam[0] == 0.0
+    for f in ("xas", "xam", "xt", "mode"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f))

@@ -93,6 +93,19 @@ WINDOW_MUTANTS = {
     "fixed_point_any_alpha": ("xas[i] == 0.9 && xam[i] == 0.0", "xas[i] >= 0.5"),
     "windows_skip_correction": ("for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);",
                                 "(void)0;"),
+    "windows_correct_at_last_level_only": (
+        "for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);",
+        "correct(p, T[K], &xas[i], &xam[i]);"),
+    "band_misses_regularisation_end": (" || fabs(T - (p[P_T_AS_START] + p[P_T_REG])) < h) return 1;",
+                                       ") return 1;"),
+    "band_misses_melt": ("  if (!(T <= p[P_T_S] - h)) return 1;\n", ""),
+    "band_ignores_start_level": ("int band = in_band(p, T0, band_half), all_act",
+                                 "int band = 0, all_act"),
+    "tail_window_to_network": ("&& K == window && !band", "&& !band"),
+    "initiation_window_to_network": ("&& !band && mode[i] == MODE_NONE) {", "&& !band) {"),
+    "fixed_point_ignores_initiation": ("if (cool && mode[i] == MODE_NONE && xas[i] == 0.9",
+                                       "if (cool && xas[i] == 0.9"),
+    "windows_advance_undeposited_points": ("if (act[l]) advance(p, T[l - 1]", "advance(p, T[l - 1]"),
 }
 
 
