@@ -457,10 +457,12 @@ void ms_surrogate_destroy(ms_surrogate* s);
  * cudaStreamLegacy for the legacy default stream).  Data written by other
  * streams must be complete before a call reads it. */
 int ms_surrogate_set_stream(ms_surrogate* s, void* cuda_stream);
-/* Copy the FP32 master parameters to a host array of MS_MLP_PARAMS floats. */
+/* Copy the FP32 master parameters to a host array of MS_MLP_PARAMS floats
+ * (synchronises).  Errors: INVALID_ARG (NULL), CUDA. */
 int ms_surrogate_get_params(ms_surrogate* s, float* params);
 /* Inference on n samples: x device [n][12] FP32, y device [n][3] FP32 (the
- * network output, i.e. 10 x increments).  Asynchronous. */
+ * network output, i.e. 10 x increments).  Asynchronous.  Errors:
+ * INVALID_ARG (NULL, n < 0), CUDA (launch). */
 int ms_surrogate_forward(ms_surrogate* s, const float* x, float* y, int64_t n);
 /* Mean-squared-error gradient over n samples (x device [n][12], targets t
  * device [n][3]): loss = sum (y - t)^2 / (3 n).  The forward pass rounds the
@@ -471,7 +473,8 @@ int ms_surrogate_forward(ms_surrogate* s, const float* x, float* y, int64_t n);
 int ms_surrogate_gradient(ms_surrogate* s, const float* x, const float* t, int64_t n,
                           float* grad, double* loss);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
- * gradient of n samples with learning rate lr; refreshes the BF16 copy. */
+ * gradient of n samples with learning rate lr; refreshes the BF16 copy.
+ * Errors: those of ms_surrogate_gradient, INVALID_ARG (lr <= 0 or NaN). */
 int ms_surrogate_train_step(ms_surrogate* s, const float* x, const float* t, int64_t n,
                             double lr, double* loss);
 
@@ -534,20 +537,31 @@ int ms_thermal_params_default(ms_thermal_params* p);
 /* A solver on grid (dims >= 1, finite non-zero spacing); T = T0.  Owns its
  * device fields and a stream.  Errors: INVALID_ARG, OOM, CUDA. */
 int ms_thermal_create(const ms_thermal_params* p, const ms_grid* grid, ms_thermal** out);
+/* Free a solver (NULL is a no-op). */
 void ms_thermal_destroy(ms_thermal* th);
+/* Run later calls on cuda_stream (NULL = the solver's own stream).
+ * Errors: INVALID_ARG (NULL solver). */
 int ms_thermal_set_stream(ms_thermal* th, void* cuda_stream);
-/* T = T0, r_c from the powder layer, time 0 (synchronises). */
+/* T = T0, r_c from the powder layer, time 0 (synchronises).
+ * Errors: INVALID_ARG (NULL solver), CUDA. */
 int ms_thermal_reset(ms_thermal* th);
-/* The laser path: src's tracks sorted by start time per layer (copied). */
+/* The laser path: src's tracks, sorted by start time within each layer, and
+ * layers (copied; the time offset applies).  Errors: INVALID_ARG (NULL, no
+ * layer, a track with a bad layer index, v <= 0, P < 0 or a non-finite start,
+ * tracks of a layer out of start-time order); the old path is kept then. */
 int ms_thermal_set_source(ms_thermal* th, const ms_heat_source* src);
-/* Advance by dt (synchronises, adds the device time to ms_thermal_stats). */
+/* Advance by dt (synchronises, adds the device time to ms_thermal_stats).
+ * Errors: INVALID_ARG (NULL, dt not finite and positive), CUDA. */
 int ms_thermal_step(ms_thermal* th, double dt);
 /* Device pointers (valid until the next step or reset) of T at the start
- * and at the end of the last step and of r_c; any may be NULL. */
+ * and at the end of the last step and of r_c; any may be NULL.  Errors:
+ * INVALID_ARG (NULL solver). */
 int ms_thermal_fields(ms_thermal* th, const float** T_prev, const float** T_cur, const float** rc);
-/* Host copies (n doubles each, natural order); either may be NULL. */
+/* Host copies (n doubles each, natural order); either may be NULL
+ * (synchronises).  Errors: INVALID_ARG (NULL solver), CUDA. */
 int ms_thermal_get(ms_thermal* th, double* T, double* rc);
-/* Simulated time, substeps taken, device time of ms_thermal_step calls. */
+/* Simulated time, substeps taken, device time of ms_thermal_step calls;
+ * any output may be NULL.  Errors: INVALID_ARG (NULL solver). */
 int ms_thermal_stats(ms_thermal* th, double* time_s, int64_t* substeps, double* kernel_ms);
 /* n_steps coupled steps of dt on ctx's stream: a thermal step, then
  * ms_step(ctx, T_prev, T_cur, dt, MS_PTR_DEVICE).  ctx must hold one
@@ -570,10 +584,14 @@ int ms_thermal_run_coupled(ms_thermal* th, ms_ctx* ctx, int64_t n_steps, double 
  * temperature known yet), NONFINITE, CUDA. */
 int ms_verify(ms_ctx* ctx, ms_ctx* ref, const int64_t* idx, int64_t n, double* out);
 
-/* Counters and the sticky device error word (synchronises the stream). */
+/* Counters and the sticky device error word (synchronises the stream).
+ * Errors: INVALID_ARG (NULL), CUDA.  A sticky device error is reported in
+ * out->device_error, not as the return value (ms_synchronize returns it). */
 int ms_stats(ms_ctx* ctx, ms_stats_t* out);
 
-/* Wait for all work on the context stream; reports a sticky device error. */
+/* Wait for all work on the context stream; reports a sticky device error.
+ * Errors: INVALID_ARG (NULL), DEVICE_TIMEOUT or NONFINITE (the sticky word),
+ * CUDA. */
 int ms_synchronize(ms_ctx* ctx);
 
 #ifdef __cplusplus

@@ -341,8 +341,12 @@ int ms_thermal_set_source(ms_thermal* th, const ms_heat_source* src) {
         !std::isfinite(t.t_start))
       return ms::record_error(MS_ERR_INVALID_ARG, "invalid track");
     double t_end = src->layers[t.layer].t_scan_end;
-    if (j + 1 < src->n_tracks && src->tracks[j + 1].layer == t.layer)
+    if (j + 1 < src->n_tracks && src->tracks[j + 1].layer == t.layer) {
+      // the laser leaves a track when the next one of its layer starts
+      if (src->tracks[j + 1].t_start < t.t_start)
+        return ms::record_error(MS_ERR_INVALID_ARG, "tracks of a layer must be sorted by start time");
       t_end = src->tracks[j + 1].t_start;
+    }
     tr.push_back(Track{t.x0, t.y0, t.ux, t.uy, t.v, t.P, t.t_start + src->t_offset,
                        t_end + src->t_offset});
   }

@@ -150,5 +150,9 @@ def test_thermal_errors(ms):
         th.run_coupled(ctx, 1, 1e-5)
     with pytest.raises(ms.MSError, match="INVALID_ARG"):
         th.step(-1.0)
+    unsorted = wl.HeatSource(np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 180.0, 2e-4, 0],
+                                       [0.0, 1e-4, 1.0, 0.0, 1.0, 180.0, 1e-4, 0]]), src.layers)
+    with pytest.raises(ms.MSError, match="INVALID_ARG"):
+        th.set_source(unsorted)
     th.close()
     ctx.close()
