@@ -276,6 +276,18 @@ int ms_farfield_table(float* out, int32_t n_out);
  * Errors: MS_ERR_INVALID_ARG if p is NULL. */
 int ms_params_default(ms_params* p);
 
+/* Check a parameter set as ms_create does, without creating anything (host
+ * only, no CUDA call): the melt range 0 < T_s < T_l, T_as,end < T_as,start
+ * and positive transformation temperatures (Table 2), positive rate and
+ * equilibrium constants and c_as, c_b > 1 (Table 3), T_reg > 0, the App. A
+ * exit thresholds >= 0, a finite T_thr, a known precision and integrator,
+ * steps_per_launch and block_threads in range, farfield_dist >= 0 (and only
+ * with MS_F32 explicit), and for MS_IMPLICIT a finite dt_sub, eps_abs >= 0,
+ * eps_rel > 0, fp_max_iter >= 1 with MS_F32 or MS_F64.
+ * Returns MS_OK, MS_ERR_INVALID_ARG or MS_ERR_UNSUPPORTED, with the reason in
+ * ms_last_error. */
+int ms_params_check(const ms_params* p);
+
 /* Create a context for n_points points on the current CUDA device and
  * allocate their state (all points start at the room-temperature
  * equilibrium X_as = 0.9, X_am = 0, App. A).  The parameters are copied.

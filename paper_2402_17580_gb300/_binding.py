@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
     lib.ms_struct_size.argtypes = [ctypes.c_int]
     lib.ms_farfield_table.argtypes = [ctypes.POINTER(ctypes.c_float), i32]
     lib.ms_params_default.argtypes = [ctypes.POINTER(Params)]
+    lib.ms_params_check.argtypes = [ctypes.POINTER(Params)]
     lib.ms_create.argtypes = [ctypes.POINTER(Params), i64, ctypes.POINTER(P)]
     lib.ms_destroy.argtypes = [P]
     lib.ms_destroy.restype = None
@@ -204,6 +205,11 @@ def farfield_table():
     _check(load().ms_farfield_table(out, FF_TABLE_FLOATS), "ms_farfield_table")
     a = np.frombuffer(out, dtype=np.float32).copy()
     return a[:1024].reshape(8, 128), a[1024:]
+
+
+def check_params(p: Params) -> None:
+    """ms_params_check: raises MSError if ms_create would reject p."""
+    _check(load().ms_params_check(ctypes.byref(p)), "ms_params_check")
 
 
 def default_params(**overrides) -> Params:

@@ -790,6 +790,11 @@ size_t ms_struct_size(int which) {
   }
 }
 
+int ms_params_check(const ms_params* p) {
+  if (!p) return fail(MS_ERR_INVALID_ARG, "params is NULL");
+  return check_params(*p);
+}
+
 int ms_params_default(ms_params* p) {
   if (!p) return fail(MS_ERR_INVALID_ARG, "params is NULL");
   std::memset(p, 0, sizeof(*p));

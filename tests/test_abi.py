@@ -146,3 +146,36 @@ def test_farfield_table_is_lagrange_interpolation_at_chebyshev_nodes():
     with pytest.raises(ms.MSError):
         out = (ctypes.c_float * 10)()
         B._check(ms.load().ms_farfield_table(out, 10), "ms_farfield_table")
+
+
+def test_params_check_rules_on_the_host():
+    """ms_params_check applies ms_create's parameter checks without a GPU: the
+    paper's defaults pass, and each rule rejects one field changed away from
+    them, with the code the header names."""
+    from paper_2402_17580_gb300 import _binding as b
+    nan, inf = float("nan"), float("inf")
+    b.check_params(b.default_params())
+    b.check_params(b.default_params(integrator=b.MS_IMPLICIT, precision=b.MS_F64))
+    b.check_params(b.default_params(farfield_dist=5e-3))
+    invalid = [dict(T_s=0.0), dict(T_l=1800.0), dict(T_s=nan), dict(T_as_end=1300.0),
+               dict(T_am_start=-1.0), dict(T_inf=0.0), dict(k_alpha_eq=0.0), dict(k_am_eq=-1.0),
+               dict(k1=inf), dict(k2=nan), dict(k3=0.0), dict(f=0.0), dict(c_as=1.0),
+               dict(c_b=0.5), dict(T_reg=0.0), dict(init_exit=-1.0), dict(init_exit_floor=nan),
+               dict(T_thr=inf), dict(precision=7), dict(steps_per_launch=0),
+               dict(steps_per_launch=100000), dict(block_threads=48), dict(block_threads=512),
+               dict(integrator=2), dict(farfield_dist=-1.0), dict(farfield_dist=nan),
+               dict(integrator=b.MS_IMPLICIT, fp_eps_rel=0.0),
+               dict(integrator=b.MS_IMPLICIT, fp_eps_abs=-1.0),
+               dict(integrator=b.MS_IMPLICIT, fp_max_iter=0),
+               dict(integrator=b.MS_IMPLICIT, dt_sub=nan)]
+    for bad in invalid:
+        with pytest.raises(b.MSError, match="INVALID_ARG"):
+            b.check_params(b.default_params(**bad))
+    unsupported = [dict(farfield_dist=5e-3, precision=b.MS_F64),
+                   dict(farfield_dist=5e-3, integrator=b.MS_IMPLICIT),
+                   dict(integrator=b.MS_IMPLICIT, precision=b.MS_KAHAN),
+                   dict(integrator=b.MS_IMPLICIT, precision=b.MS_F64ACC)]
+    for bad in unsupported:
+        with pytest.raises(b.MSError, match="UNSUPPORTED"):
+            b.check_params(b.default_params(**bad))
+    assert b.load().ms_params_check(None) == -1
