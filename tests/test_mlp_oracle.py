@@ -352,3 +352,33 @@ def test_windows_leave_undeposited_points_alone():
     assert b.xas[0] == 0.9 and b.xam[0] == 0.0
     for f in ("xas", "xam", "xt", "mode"):
         np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_host_band_mask_matches_the_oracle_band():
+    """surrogate.band_mask (which windows the training data may give to the
+    network) uses the oracle window form's band: within 40 K of T_am,start,
+    T_as,end, T_as,start or T_as,start + T_reg, or above T_s - 40 K, on any
+    level of the window including its start.  Checked on windows held at
+    one temperature with the edge levels planted at the start or the end,
+    against the windows the oracle sends to the explicit steps."""
+    from paper_2402_17580_gb300 import _binding as B
+    from paper_2402_17580_gb300.surrogate import band_mask
+    p = B.default_params()
+    po = oracle.params()
+    for T_edge in (848.0 + 39.0, 848.0 + 41.0, 935.0 - 39.5, 935.0 + 40.5, 1273.0 + 39.0,
+                   1373.0 - 41.0, 1838.5, 1837.5, 600.0, 1100.0):
+        for at in (0, 8):
+            T = np.full(9, 1100.0)
+            T[at] = T_edge
+            want = bool(np.any([oracle_in_band(t, po) for t in T]))
+            assert bool(band_mask(T[None, :], p)[0]) == want, (T_edge, at)
+
+
+def oracle_in_band(T, po):
+    """Whether a window held at T is sent to the explicit steps by the
+    oracle's window form (a 16-step hold from a state off the fixed point)."""
+    w, src = _line(0.0, n=1, T0=T)
+    x, y, z = w.specimens[0].grid.coords()
+    st = oracle.State.make([0.6], [0.1])
+    n_mlp = oracle.run_track_windows(st, src, x, y, z, 0, 16, w.dt, p=po)
+    return n_mlp[0] == 0
