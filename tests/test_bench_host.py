@@ -42,3 +42,32 @@ def test_measured_hbm_peak(tmp_path, monkeypatch):
     assert bench.measured_hbm_gbs(default=1.0) == 1.0
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6500.0}))
     assert bench.measured_hbm_gbs(default=1.0) == pytest.approx(6500.0)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the FP64 oracle on the host cores and
+    prints one JSON line with the keys of the bench contract, its e2e equal to
+    its value and no host-device traffic."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--workload", "line_4096", "--steps", "2", "--warmup", "1",
+                        "--cpu-seconds", "0.2"], cwd=root, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in out, k
+    assert out["impl"] == "reference" and out["steps"] == 2 and out["warmup"] == 1
+    assert out["value"] > 0 and out["higher_is_better"] is True
+    assert out["config"]["workload"] == "line_4096"
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+    assert out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
