@@ -262,6 +262,7 @@ const char* ms_last_error(void);
  * 5 ms_stats_t.  Returns 0 for an unknown index. */
 size_t ms_struct_size(int which);
 
+#define MS_FF_TABLE_FLOATS 1032
 /* The far field's interpolation table (ms_params.farfield_dist; not in the
  * paper): the Lagrange weights of the 8 Chebyshev points of the first kind
  * on a row tile's x-range [0, 1] at the tile's 128 points t_i = i / 127,
@@ -269,7 +270,6 @@ size_t ms_struct_size(int which);
  * as the kernels use them.  Host only, no device work.  n_out is the
  * capacity of out in floats (at least MS_FF_TABLE_FLOATS).
  * Errors: INVALID_ARG (out NULL or too small). */
-#define MS_FF_TABLE_FLOATS 1032
 int ms_farfield_table(float* out, int32_t n_out);
 
 /* Fill *p with the paper's constants and the default readings / options.
@@ -300,7 +300,9 @@ void ms_destroy(ms_ctx* ctx);
 /* Make the context launch on an existing CUDA stream (cudaStream_t passed as
  * void*; NULL = the context's own stream).  The stream is borrowed.  A
  * caller whose work runs on the legacy default stream (whose handle is NULL,
- * e.g. PyTorch's default stream) passes cudaStreamLegacy instead. */
+ * e.g. PyTorch's default stream) passes cudaStreamLegacy instead.  Waits
+ * for the context's work on its old stream first.  Errors: INVALID_ARG (NULL
+ * context), CUDA. */
 int ms_set_stream(ms_ctx* ctx, void* cuda_stream);
 
 /* Geometry for ms_run_track: n_specimens regular grids whose point counts add
@@ -328,7 +330,8 @@ int ms_set_state(ms_ctx* ctx, const double* x_as, const double* x_am, const doub
  * Asynchronous.  Errors: INVALID_ARG (fractions outside [0, 0.9]), CUDA. */
 int ms_fill_state(ms_ctx* ctx, double x_as, double x_am);
 
-/* Reset the counters of ms_stats (not the state).  Synchronises the stream. */
+/* Reset the counters of ms_stats (not the state).  Synchronises the stream.
+ * Errors: INVALID_ARG (NULL), CUDA. */
 int ms_reset_stats(ms_ctx* ctx);
 
 /* One explicit step of every point with given temperatures T_prev = T^n and
@@ -467,7 +470,8 @@ int ms_surrogate_create(const float* params, ms_surrogate** out);
 void ms_surrogate_destroy(ms_surrogate* s);
 /* Run later calls on cuda_stream (NULL = the surrogate's own stream; pass
  * cudaStreamLegacy for the legacy default stream).  Data written by other
- * streams must be complete before a call reads it. */
+ * streams must be complete before a call reads it.  Errors: INVALID_ARG
+ * (NULL surrogate). */
 int ms_surrogate_set_stream(ms_surrogate* s, void* cuda_stream);
 /* Copy the FP32 master parameters to a host array of MS_MLP_PARAMS floats
  * (synchronises).  Errors: INVALID_ARG (NULL), CUDA. */
@@ -544,7 +548,8 @@ typedef struct ms_thermal_params {
 
 typedef struct ms_thermal ms_thermal;
 
-/* Table 1 / Table 5 values, T0 = 353 K, h_powder = 30 um, all options on. */
+/* Table 1 / Table 5 values, T0 = 353 K, h_powder = 30 um, all options on.
+ * Errors: INVALID_ARG (p NULL). */
 int ms_thermal_params_default(ms_thermal_params* p);
 /* A solver on grid (dims >= 1, finite non-zero spacing); T = T0.  Owns its
  * device fields and a stream.  Errors: INVALID_ARG, OOM, CUDA. */

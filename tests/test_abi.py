@@ -179,3 +179,20 @@ def test_params_check_rules_on_the_host():
         with pytest.raises(b.MSError, match="UNSUPPORTED"):
             b.check_params(b.default_params(**bad))
     assert b.load().ms_params_check(None) == -1
+
+
+def test_every_entry_point_states_its_errors():
+    """Each declaration in include/ms.h has its own comment, and every call
+    that returns a status names its errors there."""
+    import re
+    hdr = open(os.path.join(ROOT, "include", "ms.h")).read()
+    missing = []
+    for m in re.finditer(r"^(int|void|const char\*|size_t)\s+(ms_\w+)\(", hdr, re.M):
+        before = hdr[:m.start()].rstrip()
+        if not before.endswith("*/"):
+            missing.append(m.group(2) + ": no comment")
+            continue
+        comment = before[before.rfind("/*"):]
+        if m.group(1) == "int" and not re.search(r"Errors?:|MS_ERR_", comment):
+            missing.append(m.group(2) + ": no errors")
+    assert not missing, missing
