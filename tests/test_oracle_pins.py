@@ -661,3 +661,36 @@ def test_implicit_reaches_equilibria_and_quench_values():
     orc.step(q, 1400.0, 353.0, 0.5, orc.params(integrator=1, dt_sub=0.0))
     assert q.xam[0] == pytest.approx(1 - math.exp(-0.00415 * (848 - 353)), rel=1e-12)
     assert q.xas[0] == 0.0
+
+
+# ------------------------------------------------- tolerance derivation
+def test_run_tolerance_covers_fp32_level_temperature_errors():
+    """The whole-run bar max|dX| <= 1e-4 for the FP32 path, derived: on the
+    4096-point line, rounding the stored fractions to FP32 after every step
+    moves the FP64 result by ~3e-8 (no accumulation), and perturbing every
+    temperature by a relative 2^-22 (the level of the approximate ex2, lg2
+    and rsqrt) by < 1e-5, most of it in the mushy zone under the source,
+    where X_liq = (T - T_s) / 50 passes a temperature error straight on.
+    The bar leaves a factor of ten over that."""
+    import workloads as wl
+    w = wl.line_4096()
+    sp = w.specimens[0]
+    x, y, z = sp.grid.coords()
+    T = np.stack([orc.temperature(sp.source, x, y, z, l * w.dt)[0] for l in range(w.n_steps + 1)])
+    ref = orc.State.uniform(w.n_points, 0.9, 0.0)
+    orc.run_temps(ref, T, w.dt)
+    f_ref = np.stack(orc.fractions(ref, T[-1]))
+    rng = np.random.default_rng(1)
+    Tp = T * (1.0 + 2.0 ** -22 * rng.uniform(-1.0, 1.0, T.shape))
+    per = orc.State.uniform(w.n_points, 0.9, 0.0)
+    orc.run_temps(per, Tp, w.dt)
+    d = np.abs(np.stack(orc.fractions(per, Tp[-1])) - f_ref).max(axis=0)
+    assert d.max() < 1e-5
+    mushy = (T[-1] > 1878.0) & (T[-1] < 1928.0)
+    assert d.argmax() in np.nonzero(mushy)[0]
+    st = orc.State.uniform(w.n_points, 0.9, 0.0)
+    for s in range(w.n_steps):
+        orc.run_temps(st, T[s:s + 2], w.dt)
+        st.xas[:] = st.xas.astype(np.float32)
+        st.xam[:] = st.xam.astype(np.float32)
+    assert max(np.abs(st.xas - ref.xas).max(), np.abs(st.xam - ref.xam).max()) < 1e-7
