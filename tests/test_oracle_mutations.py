@@ -70,6 +70,7 @@ MUTANTS = {
     "other_layers_tracks_heat": ("if ((int32_t)tr[TR_LAYER] != l || tl < tr[TR_TS]) continue;",
                                  "if (tl < tr[TR_TS]) continue;"),
     "undeposited_points_advance": ("if (a1) advance(", "(void)a1; advance("),
+    "interlayer_factor_goes_negative": ("    if (scale < 0.0) scale = 0.0;\n", ""),
     "cn_iterate_rates_at_T0": ("rates(p, T1, nas, nam, &das1, &dam1);",
                                "rates(p, T0, nas, nam, &das1, &dam1);"),
     "cn_iterate_without_g": ("    correct(p, T1, &nas, &nam);\n    double das1", "    double das1"),

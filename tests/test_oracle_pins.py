@@ -437,6 +437,10 @@ def test_source_superposition_cap_and_layers():
     assert list(act) == [0, 1]
     T_end, _ = orc.temperature(src, 1e-3, 0.0, -3e-5, 0.00999999)
     assert T_end[0] == pytest.approx(353.0, abs=0.05)
+    # after the last layer's end the field stays at T0 (the factor does not
+    # turn negative)
+    T_after, _ = orc.temperature(src, [1e-3, 5e-3], [0.0, 1e-4], [-3e-5, 0.0], 0.08)
+    assert np.all(T_after == 353.0)
     T_mid, _ = orc.temperature(src, 1e-3, 0.0, -3e-5, 0.0075)
     T_scan, _ = orc.temperature(src, 1e-3, 0.0, -3e-5, 0.0050)
     assert (T_mid[0] - 353) == pytest.approx(0.5 * (orc.temperature(
