@@ -71,3 +71,20 @@ def test_reference_arm_prints_the_contract_line():
     assert out["cpu_baseline"]["value"] == out["value"]
     assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
+
+
+def test_profile_summaries_name_their_commands():
+    """Each ncu summary under profiles/ gives the command that made it, with
+    ncu's clocks left alone (--clock-control none), and runs committed files
+    only (nothing under the git-ignored working folder)."""
+    import glob
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    files = sorted(glob.glob(os.path.join(root, "profiles", "*.md")))
+    assert files
+    for f in files:
+        text = open(f).read()
+        assert "ommand" in text, f
+        assert "_work/" not in text, f
+        if "ncu " in text:
+            assert "--clock-control none" in text, f
