@@ -39,6 +39,15 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_track_block_256.json")
 L2_FLUSH_BYTES = 512 << 20
+# The paper's own throughput for the explicit update (Sec. 4.1): above 6e9
+# DoF/s = 2.0e9 point-updates/s (3 DoF per point) on one node of two Intel
+# Xeon Gold 6230 (40 cores), FP64 with its fast exp/ln, 72 B per point with
+# the temperatures read from memory.  Context only: other hardware, precision
+# and byte model.
+PAPER_CPU_CONTEXT = {"value": 2.0e9, "unit": UNIT, "cores": 40,
+                     "hardware": "2x Intel Xeon Gold 6230 (2.1 GHz, AVX-512)",
+                     "precision": "f64, 72 B per point, temperatures from memory",
+                     "source": "the paper, Sec. 4.1 (explicit scheme, large blocks)"}
 
 
 def measured_hbm_gbs(default=6794.8):
@@ -233,13 +242,24 @@ def ncu_traffic(workload, steps_per_launch):
 
 
 # ------------------------------------------------------------ oracle sample
-def oracle_sample(w, seconds, seed=12345):
+def oracle_sample(w, seconds, seed=12345, threads=None):
     """Run the FP64 oracle on a seeded sample of the workload's points, sized
-    for about `seconds` of CPU time; returns (point-updates/s, sample indices,
-    oracle fractions, threads, description)."""
+    for about `seconds` of CPU time, on `threads` OpenMP threads (all host
+    cores if None); returns (point-updates/s, sample indices, oracle
+    fractions, threads, description)."""
     import numpy as np
 
     import oracle as orc
+    all_threads = orc.num_threads()
+    if threads is not None:
+        orc.set_num_threads(threads)
+    try:
+        return _oracle_sample(w, seconds, seed, orc, np)
+    finally:
+        orc.set_num_threads(all_threads)
+
+
+def _oracle_sample(w, seconds, seed, orc, np):
     offs = np.cumsum([0] + [s.grid.n for s in w.specimens])
     rng = np.random.default_rng(seed)
 
@@ -257,7 +277,7 @@ def oracle_sample(w, seconds, seed=12345):
         return time.perf_counter() - t0, out
 
     threads = orc.num_threads()
-    n_probe = min(max(threads * 16, 128), w.n_points)
+    n_probe = min(max(threads * 16, 64), w.n_points)
     idx = np.sort(rng.choice(w.n_points, n_probe, replace=False))
     dt_probe, _ = run(idx)
     n = int(min(max(n_probe, n_probe * seconds / max(dt_probe, 1e-3)), 65536, w.n_points))
@@ -529,6 +549,10 @@ def run_ours(args):
         out["sum_err"] = float(np.max(np.abs(np.stack(g).sum(axis=0) - 1.0)))
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": desc}
+        rate1, _, _, _, desc1, _ = oracle_sample(w, 4.0, seed=54321, threads=1)
+        out["cpu_baseline"]["one_core"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                           "sample": desc1}
+        out["cpu_baseline"]["paper_context"] = PAPER_CPU_CONTEXT
     if rank == 0 and world == 1 and args.f64 and len(w.specimens) == 1:
         out["f64"] = f64_pass(ctx, w, srcs, ms)
     if rank == 0 and world == 1 and args.coupled and len(w.specimens) == 1:

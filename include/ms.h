@@ -411,24 +411,29 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
  * list; the per-step warp vote of T_thr still applies).  The caller owns the
  * state: x_as, x_am and aux are device arrays, 16-byte aligned, each holding
  * at least n_points rounded up to a multiple of 128 floats, in natural
- * order; aux carries the library's App. A encoding (set it to 0 for "no
- * initiation in progress" and keep it between calls).  Asynchronous on
- * cuda_stream (NULL = the legacy default stream).
+ * order; aux is the library's opaque per-point initiation state, as
+ * ms_get_aux returns it (0 means no initiation in progress; keep the array
+ * between calls).  The work is queued on cuda_stream (NULL = the legacy
+ * default stream); the call returns once that stream has finished it,
+ * because it reads the device error word of its launches.
  *
  * Limits: n_points <= 2^24, src->n_tracks <= 128, src->n_layers <= 8,
  * steps_per_launch <= 64, block_threads 0 or 128; larger requests return
  * MS_ERR_INVALID_ARG with a message in ms_last_error.  No cudaMalloc,
  * cudaFree or other allocating call is made.  The first call on a device
  * does a one-time set-up: it looks up the array's device address
- * (cudaGetSymbolAddress) and clears it with a synchronous cudaMemset, so make
- * that first call before any stream capture.  Every call shares the array,
- * which keeps the last call's contents (each call resets the counters it
- * needs); calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it, so the caller must serialise them.  Non-finite
- * fractions are not reported by this call.
+ * (cudaGetSymbolAddress), clears the array with cudaMemset and waits for the
+ * device (cudaDeviceSynchronize) so that the clear has landed before any
+ * stream touches the array; make that first call before any stream capture.
+ * Every call shares the array, which keeps the last call's contents (each
+ * call resets the error word and the counters it needs); calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it, so the
+ * caller must serialise them.
  * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32,
- * MS_IMPLICIT, or farfield_dist != 0: this call sums every source
- * directly), CUDA. */
+ * MS_IMPLICIT, or farfield_dist != 0: this call sums every source directly;
+ * or cuda_stream is capturing: the tables are uploaded from host memory of
+ * the call), NONFINITE (a fraction became non-finite in this call's
+ * launches), CUDA. */
 int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid, const ms_heat_source* src,
                          float* x_as, float* x_am, float* aux, int64_t n_points,
                          int64_t step0, int64_t n_steps, double dt, void* cuda_stream);

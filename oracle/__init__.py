@@ -111,6 +111,7 @@ def _load():
             lib.orc_cn_step.argtypes, lib.orc_cn_step.restype = [P, d, d, d, P, P, P], ctypes.c_int
             lib.orc_n_substeps.argtypes, lib.orc_n_substeps.restype = [P, d], i64
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes, lib.orc_set_num_threads.restype = [ctypes.c_int], None
             lib.orc_param_count.restype = ctypes.c_int
             assert lib.orc_param_count() == len(PARAM_NAMES)
             _lib = lib
@@ -137,6 +138,11 @@ def _prm(p):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's point loops from now on (n > 0)."""
+    _load().orc_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- model pieces

@@ -544,4 +544,13 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the point loops (the timed CPU baseline also runs on one core). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 int orc_param_count(void) { return P_COUNT; }

@@ -62,7 +62,10 @@ int g_track_grid[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the static
 // array (its name in host code is only a host-side stand-in) and a cleared
-// tile map.  Not allocation: the array is part of the loaded module.
+// tile map.  Not allocation: the array is part of the loaded module.  The clear
+// goes to the legacy default stream, which does not order against streams
+// created non-blocking (torch's side streams, for one), so the set-up waits
+// for it before any work of the caller's stream can touch the array.
 int setup_device(int dev, Scratch** out, int* grid_per_device) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
@@ -70,7 +73,7 @@ int setup_device(int dev, Scratch** out, int* grid_per_device) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return ms::record_error(MS_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
-    if (cudaMemset(p, 0, sizeof(Scratch)) != cudaSuccess)
+    if (cudaMemset(p, 0, sizeof(Scratch)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "clearing the no-alloc scratch failed");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -163,7 +166,17 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
   int grid_cap = 0;
   if ((rc = setup_device(dev, &sc, &grid_cap)) != MS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cudaMemcpyAsync(&sc->spec, &up, sizeof(Upload), cudaMemcpyHostToDevice, st) != cudaSuccess)
+  // The tables are copied from this call's stack frame: a captured copy would
+  // read that frame again on every replay, long after the call returned.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess)
+    return ms::record_error(MS_ERR_CUDA, "cannot query the stream's capture status");
+  if (cap != cudaStreamCaptureStatusNone)
+    return ms::record_error(MS_ERR_UNSUPPORTED,
+                            "ms_run_track_noalloc uploads its tables from host memory of the "
+                            "call and refuses a capturing stream");
+  if (cudaMemsetAsync(&sc->err, 0, sizeof(int32_t), st) != cudaSuccess ||
+      cudaMemcpyAsync(&sc->spec, &up, sizeof(Upload), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return ms::record_error(MS_ERR_CUDA, "uploading the source tables failed");
 
   const ms::ModelConstT<float> mc = ms::model_const<float>(*p);
@@ -207,5 +220,13 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
       return ms::record_error(MS_ERR_CUDA, "hot-kernel launch failed");
     done += steps;
   }
+  // The device error word of this call's launches: wait for them and report a
+  // non-finite fraction as ms_run_track's contexts do at their sync points.
+  int32_t err = 0;
+  if (cudaMemcpyAsync(&err, &sc->err, sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return ms::record_error(MS_ERR_CUDA, "reading the device error word failed");
+  if (err & ms::DEVERR_NONFINITE)
+    return ms::record_error(MS_ERR_NONFINITE, "a fraction became non-finite");
   return MS_OK;
 }

@@ -145,6 +145,30 @@ def test_small_block_all_points_ragged(ms):
     check_sum(g)
 
 
+@pytest.mark.parametrize("case", ["line_4096", "small_block", "two_layers"])
+def test_fp32_path_against_the_literal_appendix_a_exit(ms, case):
+    """App. A leaves the alpha_s -> beta initiation once X~_beta dt > 1e-15.
+    The library (and the default oracle) also wait for X~_beta >= 1e-3
+    (reading A5: below that an FP32 state cannot hold 0.9 - X~_beta).  Here
+    the FP32 path with its default exit rule runs against the oracle with the
+    literal rule (init_exit_floor = 0) on the line, a small block and two
+    layers with interlayer cooling, at the workloads' dt = 1e-5 s, every
+    point: the floor moves no result there (a heating point crosses the
+    alpha_s -> beta band in milliseconds, while X~_beta needs seconds to reach
+    1e-10)."""
+    if case == "line_4096":
+        w = wl.line_4096()
+    elif case == "small_block":
+        w = wl.block_256(dims=(40, 24, 10), n_tracks=4, n_steps=1500, T_thr=0.0)
+    else:
+        w = wl.part_512(dims=(24, 20, 8), n_layers=2, tracks_per_layer=4, t_layer=2e-3,
+                        hatch=5e-5)
+    _, g = gpu_workload(w)
+    o = oracle_workload(w, p=orc.params(init_exit_floor=0.0))
+    assert max_abs_diff(g, o) <= RUN_TOL
+    check_sum(g)
+
+
 def test_batched_specimens_with_offsets(ms):
     """Several specimens of uneven sizes and start offsets in one context."""
     w = wl.batch_64(n_specimens=5, n_lo=200, n_hi=3000, n_steps=1200, T_thr=0.0)

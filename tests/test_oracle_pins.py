@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
+import workloads as wl
 from workloads import Grid, HeatSource, NEVER
 
 P = orc.params()
@@ -196,6 +197,22 @@ def test_p2_exit_rule_literal_vs_floor_agree():
             out.append(s.xas[0])
         diffs.append(abs(out[0] - out[1]))
     assert diffs[1] < 0.35 * diffs[0] and diffs[1] < 1e-5, diffs
+
+
+def test_p2_exit_floor_leaves_the_workloads_unchanged():
+    """At the workloads' dt = 1e-5 s a point heats through the alpha_s -> beta
+    band in milliseconds, and X~_beta stays far below 1e-10 there (App. A's
+    closed form: X~_beta ~ D (D k_beta t / c_beta)^c_beta with c_beta = 11),
+    so the literal exit rule (floor 0) and reading A5's floor give the same
+    bits on the line, a small block and two layers with interlayer cooling."""
+    from tests._util import oracle_workload
+    for w in (wl.line_4096(),
+              wl.block_256(dims=(40, 24, 10), n_tracks=4, n_steps=1500, T_thr=0.0),
+              wl.part_512(dims=(24, 20, 8), n_layers=2, tracks_per_layer=4, t_layer=2e-3,
+                          hatch=5e-5)):
+        a = oracle_workload(w)
+        b = oracle_workload(w, p=orc.params(init_exit_floor=0.0))
+        assert np.array_equal(a, b), w.name
 
 
 # --------------------------------------------------- alpha_m -> alpha_s (r2)

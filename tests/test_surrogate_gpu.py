@@ -13,10 +13,12 @@ Tolerances.
 * Zero network: MLP windows reduce to the correction g along the window's
   temperatures, so the hybrid is held to the explicit path's run tolerance
   (1e-4) against the oracle's window form.
-* Trained network: no closed form; the bar is max|dX| <= 1e-2 against the
-  FP64 explicit oracle (100x the explicit FP32 path's bar), with the judge's
-  own per-window error and the zero network's error (correction g only, no
-  diffusion in MLP windows) reported beside it.  The held-out residual RMS
+* Trained network: no closed form; the bar is the hybrid path's target,
+  max|dX| <= 5e-3 against the FP64 explicit oracle (50x the explicit FP32
+  path's bar), with the judge's own per-window error reported beside it.
+  What the network buys is measured against the same windows with a zero
+  network (correction g only, no diffusion in MLP windows): the trained
+  hybrid must be at least 10x closer to the oracle than that.  The held-out residual RMS
   error must be below half the residuals' own RMS (the network explains at
   least 75 % of their variance).
 """
@@ -33,7 +35,8 @@ from tests._util import max_abs_diff, oracle_params
 pytestmark = pytest.mark.gpu
 
 RUN_TOL = 1e-4
-HYBRID_TOL = 1e-2
+HYBRID_TOL = 5e-3     # the hybrid path's max|dX| target
+GAIN_MIN = 10.0       # zero-network error / trained error
 
 
 @pytest.fixture(scope="module")
@@ -234,6 +237,8 @@ def test_trained_hybrid_against_oracle(ms, trained):
           f"judge {st.judge_samples} windows max {st.judge_max_err:.3e}")
     assert st.surrogate_windows > 0 and st.judge_samples > 0
     assert err <= HYBRID_TOL
+    # what the trained network gains over the method without it (g only)
+    assert err0 >= GAIN_MIN * err, (err, err0)
     zctx.close()
     zero.close()
     ctx.close()

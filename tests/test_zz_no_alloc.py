@@ -6,9 +6,11 @@ costly in their loop, or their GPU footprint must not grow.  For them the
 library offers a no-alloc entry point that keeps its scratch in a static
 device array and works on state arrays the caller already owns.  This test
 gives it state arrays from the caller's allocator (torch here), runs the
-same specimen as a context does, on two calls in a row, and checks that the
-fractions agree within the whole-run tolerance of the GPU parity tests.  It
-sits in a file of its own that pytest collects last.
+same specimen as a context does, on two calls in a row, the first of them on
+a torch side stream (non-blocking, so nothing orders it against the legacy
+default stream), and checks that the fractions are bit-identical: both paths
+launch the same kernels on the same tiles and steps per launch.  It sits in a
+file of its own that pytest collects last.
 """
 import math
 
@@ -18,8 +20,6 @@ import pytest
 import workloads as wl
 
 pytestmark = pytest.mark.gpu
-
-RUN_TOL = 1e-4   # whole-run tolerance of tests/test_gpu_parity.py
 
 
 def test_noalloc_matches_context_path_on_two_calls():
@@ -41,21 +41,60 @@ def test_noalloc_matches_context_path_on_two_calls():
     xas = torch.full((n_pad,), 0.9, dtype=torch.float32, device=dev)
     xam = torch.zeros(n_pad, dtype=torch.float32, device=dev)
     aux = torch.zeros(n_pad, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev).cuda_stream
+    side = torch.cuda.Stream(dev)        # created non-blocking by torch
     torch.cuda.synchronize()
 
-    for step0, k in ((0, 300), (300, 300)):
+    for step0, k, stream in ((0, 300, side), (300, 300, torch.cuda.current_stream(dev))):
         ctx.run_track([sp.source], k, w.dt)
         ref_as, ref_am = ctx.fractions(with_beta=False)
+        # the raw per-point initiation state, from the context's checkpoint
+        # (a 64-byte header, then X_as, X_am and aux in the padded layout)
+        ref_aux = np.frombuffer(ctx.checkpoint(), dtype=np.float32, offset=64 + 2 * 4 * n_pad,
+                                count=n)
+        # the call returns once its stream has finished the work
         B.run_track_noalloc(params, sp.grid, sp.source, xas.data_ptr(), xam.data_ptr(),
-                            aux.data_ptr(), n, step0, k, w.dt, stream)
-        torch.cuda.synchronize()
+                            aux.data_ptr(), n, step0, k, w.dt, stream.cuda_stream)
         got_as = xas[:n].double().cpu().numpy()
         got_am = xam[:n].double().cpu().numpy()
-        err = max(float(np.max(np.abs(got_as - ref_as))), float(np.max(np.abs(got_am - ref_am))))
-        assert err <= RUN_TOL, (step0, err)
+        got_aux = aux[:n].cpu().numpy()
+        assert np.array_equal(got_as, ref_as), (step0, float(np.max(np.abs(got_as - ref_as))))
+        assert np.array_equal(got_am, ref_am), (step0, float(np.max(np.abs(got_am - ref_am))))
+        assert np.array_equal(got_aux, ref_aux), step0
     # the run did work: alpha_s dissolved where the tracks melted the block
     assert float(np.min(xas[:n].cpu().numpy())) < 0.5
+    ctx.close()
+
+
+def test_noalloc_reports_a_nonfinite_fraction():
+    """A NaN planted on the host in the caller's state comes back as
+    MS_ERR_NONFINITE from the call that stepped it; the next call, on a
+    clean state, succeeds (each call clears the error word)."""
+    torch = pytest.importorskip("torch")
+    import paper_2402_17580_gb300 as ms
+    from paper_2402_17580_gb300 import _binding as B
+
+    w = wl.block_256(dims=(32, 8, 4), n_tracks=2, n_steps=40, T_thr=0.0)
+    sp = w.specimens[0]
+    n = w.n_points
+    n_pad = math.ceil(n / 128) * 128
+    host = np.full(n_pad, 0.9, dtype=np.float32)
+    host[77] = np.nan
+    xas = torch.from_numpy(host).cuda()
+    xam = torch.zeros(n_pad, dtype=torch.float32, device="cuda")
+    aux = torch.zeros(n_pad, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    p = ms.default_params(T_thr=0.0, steps_per_launch=16)
+    with pytest.raises(ms.MSError) as e:
+        B.run_track_noalloc(p, sp.grid, sp.source, xas.data_ptr(), xam.data_ptr(),
+                            aux.data_ptr(), n, 0, 20, w.dt)
+    assert e.value.code == -5
+    xas.fill_(0.9)
+    xam.zero_()
+    aux.zero_()
+    torch.cuda.synchronize()
+    B.run_track_noalloc(p, sp.grid, sp.source, xas.data_ptr(), xam.data_ptr(), aux.data_ptr(),
+                        n, 0, 20, w.dt)
+    assert bool(torch.isfinite(xas[:n]).all())
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
