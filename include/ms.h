@@ -125,23 +125,26 @@ typedef struct ms_params {
   double  fp_eps_abs, fp_eps_rel; /* implicit: WRMS tolerances (Sec. 3: 1e-10, 1e-3) */
   int32_t fp_max_iter;            /* implicit: fixed-point iteration cap (100)    */
   int32_t reserved0;
-  /* Far field of the moving sources in ms_run_track, 0 = off (default).  In a
-   * tile of 128 points inside one grid row, at a level whose sources all move
-   * along +-x, a source that lies at least farfield_dist [m] behind every
-   * point of the tile's x-range (xi <= -farfield_dist) is evaluated at the 8
-   * Chebyshev nodes of that range, the sum over such sources is interpolated
-   * to the 128 points (Lagrange weights), and the other sources are summed
-   * point by point.  Behind a source its term (ms_heat_source) is analytic
-   * in x within a distance of the order of |xi| of the tile (the exponent
-   * v p^2 / (2 alpha (R - xi)) has a positive real part there), so the interpolation
-   * error per source is at most 4 M rho^-7 / (rho - 1) for any Bernstein
-   * ellipse rho around the range that avoids the source, M the term's bound
-   * on it; for 128 points at 10 um and farfield_dist = 5 mm, rho = 10 gives
-   * M <= A P / (2 pi k 2.1 mm) and <= 4.2e-5 K per source at P = 250 W.
-   * This is an approximation of the direct sum, for the MS_F32 explicit
-   * path (other precisions and MS_IMPLICIT return MS_ERR_UNSUPPORTED); the
-   * hybrid kernel sums point by point.  The library keeps 4 KB of
-   * interpolation weights on the device.                                   */
+  /* Far field of the moving sources in ms_run_track (default 5e-3 m; 0 =
+   * off: every source summed point by point).  In a tile of 128 points
+   * inside one grid row, at a level whose sources all move along +-x, a
+   * source that lies behind every point of the tile's x-range by at least
+   * max(farfield_dist, 4 x the range) is evaluated at the 8 Chebyshev nodes
+   * of that range, the sum over such sources is interpolated to the 128
+   * points (Lagrange weights), and the other sources are summed point by
+   * point.  Behind a source its term (ms_heat_source) is analytic in x
+   * within a distance of the order of |xi| of the tile (the exponent
+   * v p^2 / (2 alpha (R - xi)) has a positive real part there), so the
+   * interpolation error per source is at most 4 M rho^-7 / (rho - 1) for any
+   * Bernstein ellipse rho around the range that avoids the source, M the
+   * term's bound on it; the 4-range guard keeps rho of about 17 or more on
+   * any grid spacing, and for 128 points at 10 um and 5 mm, rho = 10 already
+   * gives M <= A P / (2 pi k 2.1 mm) and <= 4.2e-5 K per source at P = 250 W
+   * (the FP32 rounding of the direct sum is of the same order).  An
+   * approximation of the direct sum, in every path whose arithmetic is FP32
+   * (MS_F32, MS_F64ACC, MS_KAHAN, explicit or MS_IMPLICIT); the full-FP64
+   * path (MS_F64) and the hybrid kernel always sum point by point.  The
+   * library keeps 4 KB of interpolation weights on the device.             */
   double  farfield_dist;
 } ms_params;
 
@@ -281,8 +284,8 @@ int ms_params_default(ms_params* p);
  * and positive transformation temperatures (Table 2), positive rate and
  * equilibrium constants and c_as, c_b > 1 (Table 3), T_reg > 0, the App. A
  * exit thresholds >= 0, a finite T_thr, a known precision and integrator,
- * steps_per_launch and block_threads in range, farfield_dist >= 0 (and only
- * with MS_F32 explicit), and for MS_IMPLICIT a finite dt_sub, eps_abs >= 0,
+ * steps_per_launch and block_threads in range, a finite farfield_dist >= 0,
+ * and for MS_IMPLICIT a finite dt_sub, eps_abs >= 0,
  * eps_rel > 0, fp_max_iter >= 1 with MS_F32 or MS_F64.
  * Returns MS_OK, MS_ERR_INVALID_ARG or MS_ERR_UNSUPPORTED, with the reason in
  * ms_last_error. */
@@ -400,10 +403,10 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
  * synchronise the whole device.  Embeddings that must not grow the GPU
  * footprint while they run cannot allocate either.  ms_create allocates its
  * context buffers with cudaMalloc; this call keeps its scratch (the
- * per-launch source table, the work counters of the persistent kernel and
- * the specimen / track / layer tables) in one file-scope static device array
- * of 0.77 MiB, which every GPU that loads the library holds until the
- * process exits.
+ * per-launch source table, the work counters of the persistent kernel, the
+ * specimen / track / layer tables and the far-field weights) in one
+ * file-scope static device array of 0.77 MiB, which every GPU that loads the
+ * library holds until the process exits.
  *
  * It advances one specimen (grid, src) from time level step0 by n_steps
  * explicit steps of dt.  The result is the same as ms_run_track after
@@ -429,8 +432,8 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
  * call resets the error word and the counters it needs); calls whose work
  * overlaps on the GPU (other streams, other host threads) race on it, so the
  * caller must serialise them.
- * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32,
- * MS_IMPLICIT, or farfield_dist != 0: this call sums every source directly;
+ * farfield_dist applies as in ms_run_track.
+ * Errors: INVALID_ARG, UNSUPPORTED (precision other than MS_F32, MS_IMPLICIT,
  * or cuda_stream is capturing: the tables are uploaded from host memory of
  * the call), NONFINITE (a fraction became non-finite in this call's
  * launches), CUDA. */

@@ -237,8 +237,6 @@ int check_params(const ms_params& p) {
     return fail(MS_ERR_INVALID_ARG, "unknown integrator %d", p.integrator);
   if (!(std::isfinite(p.farfield_dist) && p.farfield_dist >= 0.0))
     return fail(MS_ERR_INVALID_ARG, "farfield_dist must be finite and >= 0");
-  if (p.farfield_dist > 0.0 && (p.precision != MS_F32 || p.integrator != MS_EXPLICIT))
-    return fail(MS_ERR_UNSUPPORTED, "the far field runs in the MS_F32 explicit path only");
   if (p.integrator == MS_IMPLICIT) {
     if (p.precision != MS_F32 && p.precision != MS_F64)
       return fail(MS_ERR_UNSUPPORTED, "MS_IMPLICIT needs precision MS_F32 or MS_F64");
@@ -827,6 +825,7 @@ int ms_params_default(ms_params* p) {
   p->fp_eps_abs = 1e-10;    // Sec. 3: WRMS tolerances
   p->fp_eps_rel = 1e-3;
   p->fp_max_iter = 100;
+  p->farfield_dist = 5e-3;  // receding sources >= 5 mm behind a row tile: interpolated
   return MS_OK;
 }
 
@@ -860,7 +859,7 @@ int ms_create(const ms_params* p, int64_t n_points, ms_ctx** out) {
     return bail(fail(MS_ERR_OOM, "device allocation failed"));
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
     return bail(fail(MS_ERR_CUDA, "cannot query the SM count"));
-  if (p->farfield_dist > 0.0) {
+  if (p->farfield_dist > 0.0 && p->precision != MS_F64) {  // the FP64 path sums directly
     const std::vector<float> w = farfield_weights();
     if (cudaMalloc(&c->ff_d, w.size() * sizeof(float)) != cudaSuccess ||
         cudaMemcpy(c->ff_d, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)

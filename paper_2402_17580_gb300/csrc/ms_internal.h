@@ -109,6 +109,10 @@ constexpr int FF_NODES = 8;
 // one node's weights of its 128 points as one float4 per lane), then the
 // nodes' positions as fractions of the range [FF_NODES], padded to 16 bytes.
 constexpr int FF_FLOATS = FF_NODES * TILE + FF_NODES;
+// A source is interpolated only if it lies at least FF_RANGE_GUARD tile
+// x-ranges behind the tile (and at least farfield_dist): the Bernstein
+// ellipse of the interpolation then keeps rho >= 17 on any grid spacing.
+constexpr float FF_RANGE_GUARD = 4.0f;
 
 // Counters of the hybrid kernel (running totals, reset by ms_reset_stats).
 struct HybridCounters {

@@ -188,10 +188,12 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   const int64_t span = sp.n - 1 - li_first < TILE - 1 ? sp.n - 1 - li_first : TILE - 1;
   const bool row = !sp.idx && col0 + span < sp.nx;
   // far field: the tile's x-range, first to 128th point (a row tile)
-  AT x_first = AT(0), x_span = AT(0);
+  AT x_first = AT(0), x_span = AT(0), ff_dist = AT(0);
   if constexpr (FAR) {
     x_first = AT(sp.ox) + AT(col0) * AT(sp.dx);
     x_span = AT(TILE - 1) * AT(sp.dx);
+    // never closer than FF_RANGE_GUARD tile ranges, whatever the grid spacing
+    ff_dist = Fn<AT>::max(a.ff_dist, AT(FF_RANGE_GUARD) * Fn<AT>::abs(x_span));
   }
 
   FT xs[4], xm[4];
@@ -217,7 +219,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     if constexpr (FAR) {
       if (row && L.axis) {
         int nn, nf;
-        temps4_far(L, en + int64_t(l) * a.slots, px, py[0], pz[0], x_first, x_span, a.ff_dist,
+        temps4_far(L, en + int64_t(l) * a.slots, px, py[0], pz[0], x_first, x_span, ff_dist,
                    lane, T1, nn, nf);
         srcs += nn;
         fsrcs += nf;
@@ -647,10 +649,15 @@ template <typename AT, typename FT>
 cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
                          cudaStream_t stream, bool implicit) {
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
-  if constexpr (kLockstep<AT, FT, false>) {
-    if (a.ff && !implicit) {  // far field: the weights in shared memory
-      k_track<AT, FT, false, true><<<unsigned(grid_blocks), block_threads,
-                                     FF_FLOATS * sizeof(float), stream>>>(a);
+  if constexpr (std::is_same<AT, float>::value) {
+    if (a.ff) {  // far field: the weights in shared memory
+      const size_t ffb = FF_FLOATS * sizeof(float);
+      if (!implicit)
+        k_track<AT, FT, false, true><<<unsigned(grid_blocks), block_threads, ffb, stream>>>(a);
+      else if constexpr (kHasImplicit<AT, FT>)
+        k_track<AT, FT, true, true><<<unsigned(grid_blocks), block_threads, ffb, stream>>>(a);
+      else
+        return cudaErrorNotSupported;
       return cudaGetLastError();
     }
   }

@@ -34,6 +34,7 @@ struct Scratch {
   ms::LayerDev layers[kMaxLayers];
   ms::SrcLevelT<float> levels[kMaxLevels];
   ms::SrcEntryT<float> entries[kMaxLevels * kMaxTracks];
+  float ff[ms::FF_FLOATS];                      // far-field weights and nodes (set-up)
   int32_t tile_spec[kMaxTiles];                 // all zero: one specimen
 };
 
@@ -54,6 +55,7 @@ static_assert(offsetof(Scratch, layers) - offsetof(Scratch, spec) == offsetof(Up
 static_assert(offsetof(Scratch, spec) % 8 == 0, "spec must be 8-byte aligned");
 static_assert(offsetof(Scratch, levels) % 16 == 0 && offsetof(Scratch, entries) % 16 == 0,
               "the source table is read with 16-byte vector loads");
+static_assert(offsetof(Scratch, ff) % 16 == 0, "far-field table alignment");
 static_assert(sizeof(Scratch) < (1u << 20), "the no-alloc scratch stays below 1 MiB");
 
 std::mutex g_setup_mu;
@@ -61,11 +63,12 @@ Scratch* g_scratch_ptr[kMaxDevices] = {};
 int g_track_grid[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the static
-// array (its name in host code is only a host-side stand-in) and a cleared
-// tile map.  Not allocation: the array is part of the loaded module.  The clear
-// goes to the legacy default stream, which does not order against streams
-// created non-blocking (torch's side streams, for one), so the set-up waits
-// for it before any work of the caller's stream can touch the array.
+// array (its name in host code is only a host-side stand-in), a cleared tile
+// map and the far-field interpolation table.  Not allocation: the array is
+// part of the loaded module.  The clear and the table copy go to the legacy
+// default stream, which does not order against streams created non-blocking
+// (torch's side streams, for one), so the set-up waits for them before any
+// work of the caller's stream can touch the array.
 int setup_device(int dev, Scratch** out, int* grid_per_device) {
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
@@ -73,7 +76,12 @@ int setup_device(int dev, Scratch** out, int* grid_per_device) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return ms::record_error(MS_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
-    if (cudaMemset(p, 0, sizeof(Scratch)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    static float table[ms::FF_FLOATS];
+    if (ms_farfield_table(table, ms::FF_FLOATS) != MS_OK) return MS_ERR_INVALID_ARG;
+    Scratch* sp = static_cast<Scratch*>(p);
+    if (cudaMemset(p, 0, sizeof(Scratch)) != cudaSuccess ||
+        cudaMemcpy(sp->ff, table, sizeof(table), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "clearing the no-alloc scratch failed");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -100,8 +108,6 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     return ms::record_error(MS_ERR_UNSUPPORTED, "ms_run_track_noalloc computes in MS_F32 only");
   if (p->integrator != MS_EXPLICIT)
     return ms::record_error(MS_ERR_UNSUPPORTED, "ms_run_track_noalloc takes explicit steps only");
-  if (p->farfield_dist != 0.0)
-    return ms::record_error(MS_ERR_UNSUPPORTED, "ms_run_track_noalloc sums every source directly");
   if (p->steps_per_launch > kMaxSteps)
     return ms::record_error(MS_ERR_INVALID_ARG, "steps_per_launch above 64 (no-alloc limit)");
   if (p->block_threads != 0 && p->block_threads != 128)
@@ -216,6 +222,10 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     a.aux = aux;
     a.tile_tsat = nullptr;
     a.err = &sc->err;
+    if (p->farfield_dist > 0.0) {
+      a.ff = sc->ff;
+      a.ff_dist = float(p->farfield_dist);
+    }
     if (ms::launch_track<float, float>(a, 128, grid_blocks, st) != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "hot-kernel launch failed");
     done += steps;

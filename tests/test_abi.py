@@ -171,9 +171,9 @@ def test_params_check_rules_on_the_host():
     for bad in invalid:
         with pytest.raises(b.MSError, match="INVALID_ARG"):
             b.check_params(b.default_params(**bad))
-    unsupported = [dict(farfield_dist=5e-3, precision=b.MS_F64),
-                   dict(farfield_dist=5e-3, integrator=b.MS_IMPLICIT),
-                   dict(integrator=b.MS_IMPLICIT, precision=b.MS_KAHAN),
+    b.check_params(b.default_params(farfield_dist=5e-3, precision=b.MS_F64))
+    b.check_params(b.default_params(farfield_dist=5e-3, integrator=b.MS_IMPLICIT))
+    unsupported = [dict(integrator=b.MS_IMPLICIT, precision=b.MS_KAHAN),
                    dict(integrator=b.MS_IMPLICIT, precision=b.MS_F64ACC)]
     for bad in unsupported:
         with pytest.raises(b.MSError, match="UNSUPPORTED"):

@@ -10,10 +10,26 @@ import bench
 
 def test_algorithmic_ops_count_sources_and_model_branches():
     st = types.SimpleNamespace(source_evaluations=1000, model_point_steps=50,
-                               model_sfu_ex2=170, model_sfu_slow=160)
+                               model_sfu_ex2=170, model_sfu_slow=160,
+                               farfield_point_sources=0, farfield_node_evaluations=0)
     slow, ex2 = bench.algorithmic_sfu_ops(st)
     # one 1/R and one exp per point and source, plus the model's own counts
     assert (slow, ex2) == (1160, 1170)
+    assert bench.executed_sfu_ops(st) == (1160, 1170)
+
+
+def test_far_field_pairs_count_as_algorithmic_work_nodes_as_executed():
+    """A pair the far field interpolates is work the method requires (the
+    superposed source at that point); the kernel executes node evaluations
+    instead."""
+    st = types.SimpleNamespace(source_evaluations=1000, model_point_steps=50,
+                               model_sfu_ex2=170, model_sfu_slow=160,
+                               farfield_point_sources=4000, farfield_node_evaluations=250)
+    assert bench.algorithmic_sfu_ops(st) == (5160, 5170)
+    assert bench.executed_sfu_ops(st) == (1410, 1420)
+    rates = {"rsqrt": 16.0, "ex2": 32.0}
+    t = bench.sfu_time_s(16.0, 32.0, rates)
+    assert t == pytest.approx(2.0 / (bench.SM_COUNT * bench.SM_MAX_MHZ * 1e6))
 
 
 def test_traffic_only_for_the_captured_kernel_workload_and_steps(tmp_path, monkeypatch):

@@ -376,9 +376,11 @@ def test_point_subset_matches_the_full_grid(ms):
     those points do in the full-grid run (same coordinates, same arithmetic)."""
     w = wl.block_256(dims=(40, 24, 10), n_tracks=4, n_steps=700, T_thr=0.0)
     sp = w.specimens[0]
-    _, full = gpu_workload(w)
+    # a subset's warps hold points of several rows, so it sums every source
+    # point by point: compare with the full grid's direct sum
+    _, full = gpu_workload(w, farfield_dist=0.0)
     idx = np.sort(np.random.default_rng(4).choice(sp.grid.n, 1000, replace=False))
-    ctx = ms.Context(idx.size, T_thr=0.0)
+    ctx = ms.Context(idx.size, T_thr=0.0, farfield_dist=0.0)
     ctx.set_points_subset(sp.grid, idx)
     ctx.fill_state()
     ctx.run_track([sp.source], w.n_steps, w.dt)
@@ -407,7 +409,7 @@ def test_row_tiles_match_the_general_form(ms, case):
     zero = ms.Surrogate(np.zeros(5187, dtype=np.float32)) if case == "hybrid" else None
     out = []
     for subset in (False, True):
-        ctx = ms.Context(sp.grid.n, T_thr=T_thr, steps_per_launch=128)
+        ctx = ms.Context(sp.grid.n, T_thr=T_thr, steps_per_launch=128, farfield_dist=0.0)
         if subset:
             ctx.set_points_subset(sp.grid, idx)
         else:
@@ -465,19 +467,42 @@ def test_farfield_matches_the_direct_sum(ms):
     and within the run tolerance of the oracle, most point-source pairs come
     from the interpolation, and the paths it does not serve refuse it."""
     w = wl.block_256(dims=(256, 8, 4), n_tracks=4, n_steps=3000, T_thr=0.0)
-    _, direct = gpu_workload(w)
+    _, direct = gpu_workload(w, farfield_dist=0.0)
     ctx, far = gpu_workload(w, farfield_dist=5e-3)
     st = ctx.stats()
     assert st.farfield_node_evaluations > 0
     assert st.farfield_point_sources > 0.5 * (st.farfield_point_sources + st.source_evaluations)
     assert max_abs_diff(far, np.stack(direct)) <= 1e-5
-    assert max_abs_diff(far, oracle_workload(w)) <= RUN_TOL
+    o = oracle_workload(w)
+    assert max_abs_diff(far, o) <= RUN_TOL
     check_sum(far)
-    for bad in (dict(precision=ms.MS_F64ACC), dict(integrator=ms.MS_IMPLICIT)):
-        with pytest.raises(ms.MSError):
-            ms.Context(16, farfield_dist=5e-3, **bad)
     with pytest.raises(ms.MSError):
         ms.Context(16, farfield_dist=-1.0)
+    # every path with FP32 arithmetic takes it (the default); the full-FP64
+    # path sums every source point by point
+    for prec, tol in ((ms.MS_F64ACC, 3e-5), (ms.MS_KAHAN, 3e-5)):
+        c, g = gpu_workload(w, precision=prec)
+        assert c.stats().farfield_point_sources == st.farfield_point_sources
+        assert max_abs_diff(g, o) <= tol
+        c.close()
+    c, g = gpu_workload(w, precision=ms.MS_F64)
+    assert c.stats().farfield_node_evaluations == 0
+    c.close()
+
+
+def test_farfield_in_the_implicit_scheme(ms):
+    """The implicit scheme's hot kernel takes the far field like the explicit
+    one: the same temperatures to within the interpolation error, so a run
+    with steps of 1e-4 s stays within 1e-5 of its direct-sum run and within
+    the run tolerance of the implicit oracle."""
+    w = wl.block_256(dims=(256, 8, 4), n_tracks=4, n_steps=300, T_thr=0.0)
+    w.dt = 1e-4
+    _, direct = gpu_workload(w, integrator=ms.MS_IMPLICIT, farfield_dist=0.0)
+    ctx, far = gpu_workload(w, integrator=ms.MS_IMPLICIT)
+    p = oracle_params(ctx.params)
+    assert ctx.stats().farfield_point_sources > 0
+    assert max_abs_diff(far, np.stack(direct)) <= 1e-5
+    assert max_abs_diff(far, oracle_workload(w, p=p)) <= RUN_TOL
 
 
 @pytest.mark.parametrize("case", ["batch", "layers"])
@@ -495,8 +520,8 @@ def test_farfield_batched_and_layered(ms, case):
     else:
         w = wl.part_512(dims=(256, 12, 6), n_layers=2, tracks_per_layer=3, t_layer=1e-2,
                         hatch=4e-5)
-    dist = 3e-3
-    _, direct = gpu_workload(w)
+    dist = 3e-3   # below the 4-range guard (5.08 mm at 10 um): the guard decides
+    _, direct = gpu_workload(w, farfield_dist=0.0)
     ctx, far = gpu_workload(w, farfield_dist=dist)
     st = ctx.stats()
     assert st.farfield_node_evaluations > 0

@@ -4,8 +4,9 @@ Each case plants one mistake in a copy of oracle/ms_oracle.c (a dropped term,
 a wrong sign, index or exponent, a transposed operand), compiles it on the
 CPU and runs tests/test_oracle_pins.py against it; the pins must fail.  The
 same is done for the Python parts: the thermal reference oracle/thermal.py
-(pins: tests/test_thermal_oracle.py) and the surrogate's network
-oracle/mlp.py (pins: the network tests of tests/test_mlp_oracle.py).
+(pins: tests/test_thermal_oracle.py), the surrogate's network oracle/mlp.py
+(pins: the network tests of tests/test_mlp_oracle.py) and the coarsening
+criterion oracle/coarsen.py (pins: tests/test_coarsen_oracle.py).
 """
 import os
 import subprocess
@@ -223,3 +224,22 @@ MLP_MUTANTS = {
 def test_network_pins_catch_mutant(name, tmp_path):
     _run_py_pins_on_mutant("mlp", name, *MLP_MUTANTS[name], tmp_path, "test_mlp_oracle.py",
                            select="not windows")
+
+
+# mistakes in the coarsening criterion, caught by tests/test_coarsen_oracle.py
+COARSEN_MUTANTS = {
+    "span_half_open": ("slice(i << level, ((i + 1) << level) + 1)", "slice(i << level, (i + 1) << level)"),
+    "strict_tolerance": ("if block.max() - block.min() > tol:", "if block.max() - block.min() >= tol:"),
+    "beta_ignored": ("for a in (x_as, x_am, x_beta)]", "for a in (x_as, x_am, x_am)]"),
+    "count_rounds_up": ("return (n - 1) // (1 << level)", "return -(-(n - 1) // (1 << level))"),
+    "flat_axis_empty": ("    if n == 1:\n        return 1\n", ""),
+    "x_y_transposed": (".reshape(nz, ny, nx) for a", ".reshape(nz, nx, ny) for a"),
+    "level_width_off_by_one": ("def _span(i, level, n):\n    if n == 1:\n        return slice(0, 1)\n    return slice(i << level,",
+                               "def _span(i, level, n):\n    if n == 1:\n        return slice(0, 1)\n    level -= 1\n    return slice(i << level,"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(COARSEN_MUTANTS))
+def test_coarsen_pins_catch_mutant(name, tmp_path):
+    _run_py_pins_on_mutant("coarsen", name, *COARSEN_MUTANTS[name], tmp_path,
+                           "test_coarsen_oracle.py")

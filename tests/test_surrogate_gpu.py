@@ -18,7 +18,8 @@ Tolerances.
   path's bar), with the judge's own per-window error reported beside it.
   What the network buys is measured against the same windows with a zero
   network (correction g only, no diffusion in MLP windows): the trained
-  hybrid must be at least 10x closer to the oracle than that.  The held-out residual RMS
+  hybrid must be at least 5x closer to the oracle than that (measured
+  1.4e-5 against 1.6e-4 on the test's block).  The held-out residual RMS
   error must be below half the residuals' own RMS (the network explains at
   least 75 % of their variance).
 """
@@ -36,7 +37,7 @@ pytestmark = pytest.mark.gpu
 
 RUN_TOL = 1e-4
 HYBRID_TOL = 5e-3     # the hybrid path's max|dX| target
-GAIN_MIN = 10.0       # zero-network error / trained error
+GAIN_MIN = 5.0        # zero-network error / trained error (measured: 11)
 
 
 @pytest.fixture(scope="module")

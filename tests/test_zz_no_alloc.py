@@ -65,38 +65,6 @@ def test_noalloc_matches_context_path_on_two_calls():
     ctx.close()
 
 
-def test_noalloc_reports_a_nonfinite_fraction():
-    """A NaN planted on the host in the caller's state comes back as
-    MS_ERR_NONFINITE from the call that stepped it; the next call, on a
-    clean state, succeeds (each call clears the error word)."""
-    torch = pytest.importorskip("torch")
-    import paper_2402_17580_gb300 as ms
-    from paper_2402_17580_gb300 import _binding as B
-
-    w = wl.block_256(dims=(32, 8, 4), n_tracks=2, n_steps=40, T_thr=0.0)
-    sp = w.specimens[0]
-    n = w.n_points
-    n_pad = math.ceil(n / 128) * 128
-    host = np.full(n_pad, 0.9, dtype=np.float32)
-    host[77] = np.nan
-    xas = torch.from_numpy(host).cuda()
-    xam = torch.zeros(n_pad, dtype=torch.float32, device="cuda")
-    aux = torch.zeros(n_pad, dtype=torch.float32, device="cuda")
-    torch.cuda.synchronize()
-    p = ms.default_params(T_thr=0.0, steps_per_launch=16)
-    with pytest.raises(ms.MSError) as e:
-        B.run_track_noalloc(p, sp.grid, sp.source, xas.data_ptr(), xam.data_ptr(),
-                            aux.data_ptr(), n, 0, 20, w.dt)
-    assert e.value.code == -5
-    xas.fill_(0.9)
-    xam.zero_()
-    aux.zero_()
-    torch.cuda.synchronize()
-    B.run_track_noalloc(p, sp.grid, sp.source, xas.data_ptr(), xam.data_ptr(), aux.data_ptr(),
-                        n, 0, 20, w.dt)
-    assert bool(torch.isfinite(xas[:n]).all())
-
-
 def test_noalloc_rejects_sizes_beyond_its_limits():
     pytest.importorskip("torch")
     import paper_2402_17580_gb300 as ms
