@@ -15,8 +15,10 @@ pinned host buffers (state upload, run, download of the four fractions);
 ``roofline`` is the hot kernel's achieved SFU rate against the SFU peak;
 ``cpu_baseline`` is the FP64 oracle on a bounded sample of the same workload
 on the host cores.  ``--impl reference`` times the oracle alone (rank 0).
-Under torchrun (N > 1) every rank advances its own block (weak scaling; no
-data exchange), and the time is the max over ranks.
+Under torchrun (N > 1) every rank advances its own instance (weak scaling)
+or, with --scaling strong, its shard of one instance (z-slabs of the block,
+groups of the batch's specimens); there is no data exchange, and the time is
+the max over ranks.
 """
 from __future__ import annotations
 
@@ -71,9 +73,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--scaling", choices=("weak", "strong"), default="weak",
+                    help="N > 1: every rank its own instance (weak) or one instance "
+                         "partitioned across the ranks (strong)")
     ap.add_argument("--workload", default="block_256")
     ap.add_argument("--precision", choices=("f32", "f64acc", "kahan"), default="f32")
     ap.add_argument("--steps-per-launch", type=int, default=0)
+    ap.add_argument("--tile-order", type=int, default=0,
+                    help="0: active tiles heaviest first (default), 1: index order")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -86,6 +93,10 @@ def parse_args():
                     help="skip the direct-sum leg (far field off)")
     ap.add_argument("--no-precisions", dest="precisions", action="store_false",
                     help="skip the FP64-accumulation and compensated-FP32 passes")
+    ap.add_argument("--no-fma", dest="fma", action="store_false",
+                    help="skip the FMA-pipe exp2/log2 leg")
+    ap.add_argument("--no-coarsen", dest="coarsen", action="store_false",
+                    help="skip the coarsening-criterion leg")
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batched 64-specimen leg")
     ap.add_argument("--no-part", dest="part", action="store_false",
@@ -106,17 +117,36 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def make_workload(name, rank=0):
+def make_workload(name, rank=0, world=1, strong=False):
+    """The workload of this rank.  Weak scaling: every rank its own seeded
+    instance.  Strong scaling: one instance partitioned across the ranks
+    with no data exchange (z-slabs of a single grid, each a grid of its own
+    with the parent's coordinates; size-balanced groups of specimens of a
+    batch); meta["whole_point_updates"] is then the whole instance's work."""
     import workloads as wl
+    from paper_2402_17580_gb300 import shard
     if name == "block_256":
-        return wl.block_256(seed=wl.SEED_BASE + 2 + 1000 * rank)
-    if name == "line_4096":
-        return wl.line_4096()
-    if name == "batch_64":
-        return wl.batch_64(seed=wl.SEED_BASE + 3 + 1000 * rank)
-    if name == "part_512":
-        return wl.part_512()
-    raise SystemExit(f"unknown workload {name}")
+        w = wl.block_256(seed=wl.SEED_BASE + 2 + (0 if strong else 1000 * rank))
+    elif name == "line_4096":
+        w = wl.line_4096()
+    elif name == "batch_64":
+        w = wl.batch_64(seed=wl.SEED_BASE + 3 + (0 if strong else 1000 * rank))
+    elif name == "part_512":
+        w = wl.part_512()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if strong and world > 1:
+        w.meta["whole_point_updates"] = w.point_updates
+        if len(w.specimens) == 1:
+            sp = w.specimens[0]
+            k0, k1 = shard.shard_slabs(sp.grid.dims[2], world)[rank]
+            w.specimens = [wl.Specimen(shard.slab_grid(sp.grid, k0, k1), sp.source)]
+            w.meta["shard"] = f"z-planes {k0}..{k1 - 1} of {sp.grid.dims[2]}"
+        else:
+            part = shard.shard_specimens([s.grid.n for s in w.specimens], world)[rank]
+            w.specimens = [w.specimens[i] for i in part]
+            w.meta["shard"] = f"{len(part)} of the batch's specimens"
+    return w
 
 
 def workload_config(w):
@@ -242,17 +272,35 @@ def timed_passes(one, stream, flush, torch, n):
     return times
 
 
-def kernel_roofline(st, rates):
-    """The hot kernel's SFU fraction from a context's counters: algorithmic
-    ops (every point-source pair) and executed ops, each over the kernel's
-    own CUDA-event time."""
+def count_pass(ctx, w, srcs, ms):
+    """One untimed pass of the same work in a context that counts the
+    model's transcendentals per branch (MS_FLAG_COUNT_OPS; the timed
+    contexts leave the counting off because it costs instructions in the
+    kernel): the stats of that pass."""
+    p = type(ctx.params).from_buffer_copy(ctx.params)
+    p.flags = int(p.flags) | ms._binding.MS_FLAG_COUNT_OPS
+    c = ms.Context(w.n_points, p)
+    c.set_points([s.grid for s in w.specimens])
+    c.fill_state(w.init_xas, w.init_xam)
+    c.reset_stats()
+    c.run_track(srcs, w.n_steps, w.dt)
+    st = c.stats()
+    c.close()
+    return st
+
+
+def kernel_roofline(st, rates, cst, passes):
+    """The hot kernel's SFU fraction: the algorithmic ops (every
+    point-source pair) and the executed ops of one pass, from the counting
+    pass cst, times the timed passes, over the kernel's own CUDA-event time
+    in the timed context st."""
     kern_s = st.hot_kernel_ms * 1e-3
     if kern_s <= 0:
         return None, None
-    a_slow, a_ex2 = algorithmic_sfu_ops(st)
-    e_slow, e_ex2 = executed_sfu_ops(st)
-    return (round(sfu_time_s(a_slow, a_ex2, rates) / kern_s, 4),
-            round(sfu_time_s(e_slow, e_ex2, rates) / kern_s, 4))
+    a_slow, a_ex2 = algorithmic_sfu_ops(cst)
+    e_slow, e_ex2 = executed_sfu_ops(cst)
+    return (round(passes * sfu_time_s(a_slow, a_ex2, rates) / kern_s, 4),
+            round(passes * sfu_time_s(e_slow, e_ex2, rates) / kern_s, 4))
 
 
 def measured_sfu_rates():
@@ -452,7 +500,8 @@ def run_ours(args):
     import paper_2402_17580_gb300 as ms
     ms.load()
 
-    w = make_workload(args.workload, rank)
+    strong = args.scaling == "strong"
+    w = make_workload(args.workload, rank, world, strong)
     if args.time_steps:
         w.meta["full_time_steps"] = w.n_steps
         w.n_steps = min(w.n_steps, args.time_steps)
@@ -470,6 +519,7 @@ def run_ours(args):
                     flags=ms._binding.MS_FLAG_TIME_KERNELS | tuned.params["flags"])
     if args.steps_per_launch:
         over["steps_per_launch"] = args.steps_per_launch
+    over["tile_order"] = args.tile_order
     ctx = ms.Context(w.n_points, **over)
     ctx.set_points([s.grid for s in w.specimens])
     srcs = [s.source for s in w.specimens]
@@ -525,15 +575,22 @@ def run_ours(args):
         t = torch.tensor([t_mean], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
-    value = w.point_updates * world / (t_max * 1e-3)
+    whole = w.meta.get("whole_point_updates", w.point_updates * world)
+    value = whole / (t_max * 1e-3)
 
     # roofline of the hot kernel (k_track): SFU-bound (state is L2-resident).
     # The SFU peak is op-mix weighted: ex2 and the rsqrt class run at
     # different measured rates.
     rates = measured_sfu_rates()
-    slow_ops, ex2_ops = algorithmic_sfu_ops(st)     # totals over the timed passes
+    # the model's transcendentals come from one counting pass of the same
+    # work (MS_FLAG_COUNT_OPS; the timed passes leave the counting off)
+    cst = count_pass(ctx, w, srcs, ms)
+    same_work = (int(cst.source_evaluations) * args.steps == int(st.source_evaluations) and
+                 int(cst.farfield_point_sources) * args.steps == int(st.farfield_point_sources)
+                 and int(cst.model_point_steps) * args.steps == int(st.model_point_steps))
+    slow_ops, ex2_ops = (args.steps * v for v in algorithmic_sfu_ops(cst))  # timed passes
     alg_ops = slow_ops + ex2_ops
-    x_slow, x_ex2 = executed_sfu_ops(st)
+    x_slow, x_ex2 = (args.steps * v for v in executed_sfu_ops(cst))
     launches_per_pass = st.hot_kernel_launches / args.steps
     kernel_ms_per_pass = st.hot_kernel_ms / args.steps
     ops_per_launch = alg_ops / st.hot_kernel_launches
@@ -562,9 +619,11 @@ def run_ours(args):
                      1, int(st.farfield_point_sources) + int(st.source_evaluations)), 4),
                  "farfield_dist_m": float(ctx.params.farfield_dist),
                  "model_sfu_per_model_point_step": {
-                     "ex2": round(st.model_sfu_ex2 / max(1, st.model_point_steps), 3),
-                     "log2_rcp": round(st.model_sfu_slow / max(1, st.model_point_steps), 3)},
-                 "note": "counted by k_track; algorithmic SFU ops are derived from these"},
+                     "ex2": round(cst.model_sfu_ex2 / max(1, cst.model_point_steps), 3),
+                     "log2_rcp": round(cst.model_sfu_slow / max(1, cst.model_point_steps), 3)},
+                 "note": "counted by k_track (the model's transcendentals in one extra "
+                         "untimed pass with MS_FLAG_COUNT_OPS); algorithmic SFU ops are "
+                         "derived from these"},
         "peak_basis": (f"measured SFU rates {rates['rsqrt']:.2f} (rsqrt/rcp class) and "
                        f"{rates['ex2']:.2f} (ex2) per SM per clock, {SM_COUNT} SMs, "
                        f"{SM_MAX_MHZ:.0f} MHz max clock, weighted by the algorithmic op mix"),
@@ -572,6 +631,7 @@ def run_ours(args):
                                    if clocks.get("sm_mhz") else None),
         "frac_of_executed_ops": round(sfu_time_s(x_slow, x_ex2, rates) /
                                       (st.hot_kernel_ms * 1e-3), 4),
+        "counting_pass_repeats_timed_work": same_work,
         "ops_basis": ("algorithmic: one 1/R and one exp per point and started source at every "
                       "processed level (pairs served by the far-field interpolation included) "
                       "plus the model's transcendentals; frac_of_executed_ops counts the far "
@@ -583,11 +643,14 @@ def run_ours(args):
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
+        "scaling": "strong" if strong and world > 1 else "weak",
         "vs_baseline": None,
         "dtype": {ms.MS_F32: "f32", ms.MS_F64ACC: "f32+f64acc", ms.MS_KAHAN: "f32+f32x2"}[prec],
         "data": "synthetic (seeded Rosenthal-driven tracks, no dataset)",
-        "config": dict(workload_config(w), parallelism=f"{world} independent blocks",
+        "config": dict(workload_config(w),
+                       parallelism=(f"1 instance in {world} shards, no exchange" if strong and
+                                    world > 1 else f"{world} independent instances"),
                        steps_per_launch=int(ctx.params.steps_per_launch),
                        block_threads=int(ctx.params.block_threads) or 128,
                        graph=bool(ctx.params.flags & ms._binding.MS_FLAG_GRAPH),
@@ -623,6 +686,12 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.farfield and prec == ms.MS_F32:
         out["direct"] = direct_pass(ctx, w, srcs, args, ms, torch, stream, flush, value,
                                     sample, rates)
+    if rank == 0 and world == 1 and args.farfield:
+        out["tile_order_index"] = tile_order_pass(ctx, w, srcs, args, ms, torch, stream, flush,
+                                                  value)
+    if rank == 0 and world == 1 and args.fma and prec == ms.MS_F32:
+        out["fma_transcendentals"] = fma_pass(ctx, w, srcs, args, ms, torch, stream, flush,
+                                              value, sample)
     if rank == 0 and world == 1 and args.precisions and prec == ms.MS_F32:
         out["precisions"] = {
             name: precision_pass(ctx, w, srcs, args, ms, torch, stream, flush, sample, rates, pv)
@@ -637,6 +706,8 @@ def run_ours(args):
         out["part_512"] = part_segment_pass(ms, torch, stream, surrogate)
     if surrogate is not None:
         surrogate.close()
+    if rank == 0 and world == 1 and args.coarsen:
+        out["coarsen"] = coarsen_pass(ms, torch, stream)
     if rank == 0 and world == 1 and not args.no_d6:
         ctx.close()
         out["roofline_ms_step"] = d6_layouts(ms, torch)
@@ -732,7 +803,7 @@ def direct_pass(ctx, w, srcs, args, ms, torch, stream, flush, default_value, sam
     times = timed_passes(one, stream, flush, torch, args.steps)
     st = c.stats()
     t = sum(times) / len(times)
-    frac, _ = kernel_roofline(st, rates)
+    frac, _ = kernel_roofline(st, rates, count_pass(c, w, srcs, ms), args.steps)
     res = {"value": w.point_updates / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
            "vs_default": w.point_updates / (t * 1e-3) / default_value,
            "roofline_frac": frac, "farfield_dist_m": 0.0,
@@ -744,6 +815,80 @@ def direct_pass(ctx, w, srcs, args, ms, torch, stream, flush, default_value, sam
         res["max_abs_dX_vs_default_pass"] = float(np.max(np.abs(
             g[:, idx] - np.stack(ctx.fractions())[:, idx])))
     c.close()
+    return res
+
+
+def tile_order_pass(ctx, w, srcs, args, ms, torch, stream, flush, default_value):
+    """The default pass with the active tiles taken in index order
+    (tile_order = 1) instead of heaviest first: the same results, and the
+    throughput that the ordering buys."""
+    p = type(ctx.params).from_buffer_copy(ctx.params)
+    c = ms.Context(w.n_points, p, tile_order=1)
+    c.set_points([s.grid for s in w.specimens])
+    c.set_stream(stream.cuda_stream)
+    one = lambda: (c.fill_state(w.init_xas, w.init_xam), c.run_track(srcs, w.n_steps, w.dt))
+    one()
+    c.synchronize()
+    times = timed_passes(one, stream, flush, torch, min(args.steps, 3))
+    t = sum(times) / len(times)
+    same = bool((c.checkpoint() == ctx.checkpoint()))
+    c.close()
+    return {"value": w.point_updates / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+            "default_vs_index_order": default_value / (w.point_updates / (t * 1e-3)),
+            "state_bit_identical_to_default": same}
+
+
+def fma_pass(ctx, w, srcs, args, ms, torch, stream, flush, default_value, sample):
+    """exp2 and log2 as FMA-pipe polynomials (MS_FLAG_FMA_TRANSCENDENTALS) in
+    place of the SFU: the default pass of the workload, and the implicit
+    external-temperature step (the compute-bound scheme) on 2^24 random
+    states in runs of 10 equal branch choices, each against the SFU build on
+    the same inputs; max|dX| of the pass on the oracle sample."""
+    import numpy as np
+
+    import workloads as wl
+    from paper_2402_17580_gb300._binding import MS_FLAG_FMA_TRANSCENDENTALS, MS_FLAG_TIME_KERNELS
+    p = type(ctx.params).from_buffer_copy(ctx.params)
+    p.flags = int(p.flags) | MS_FLAG_FMA_TRANSCENDENTALS
+    c = ms.Context(w.n_points, p)
+    c.set_points([s.grid for s in w.specimens])
+    c.set_stream(stream.cuda_stream)
+    one = lambda: (c.fill_state(w.init_xas, w.init_xam), c.run_track(srcs, w.n_steps, w.dt))
+    one()
+    c.synchronize()
+    times = timed_passes(one, stream, flush, torch, min(args.steps, 3))
+    t = sum(times) / len(times)
+    res = {"pass": {"value": w.point_updates / (t * 1e-3), "unit": UNIT, "ms_per_step": t,
+                    "vs_sfu": w.point_updates / (t * 1e-3) / default_value}}
+    if sample is not None:
+        idx, ofr = sample
+        res["pass"]["max_abs_dX"] = float(np.max(np.abs(np.stack(c.fractions())[:, idx] - ofr)))
+    c.close()
+    n, steps = 1 << 24, 10
+    xas, xam, T0, T1 = wl.random_states(n, seed=2402175816, block=10)
+    t0 = torch.tensor(T0, dtype=torch.float32, device="cuda")
+    t1 = torch.tensor(T1, dtype=torch.float32, device="cuda")
+    rates = {}
+    for name, fl in (("sfu", 0), ("fma", MS_FLAG_FMA_TRANSCENDENTALS)):
+        cc = ms.Context(n, flags=MS_FLAG_TIME_KERNELS | fl, integrator=ms.MS_IMPLICIT)
+        cc.set_stream(stream.cuda_stream)
+        cc.set_state(xas, xam)
+        for _ in range(3):
+            cc.step_device(t0.data_ptr(), t1.data_ptr(), 1e-5)
+        cc.synchronize()
+        cc.reset_stats()
+        for _ in range(steps):
+            cc.step_device(t0.data_ptr(), t1.data_ptr(), 1e-5)
+        cc.synchronize()
+        st = cc.stats()
+        ms_l = st.hot_kernel_ms / st.hot_kernel_launches
+        rates[name] = {"point_updates_per_s": n / (ms_l * 1e-3), "ms_per_launch": round(ms_l, 4),
+                       "GB_per_s": round(32 * n / (ms_l * 1e-3) / 1e9, 1)}
+        cc.close()
+    rates["fma_vs_sfu"] = rates["fma"]["point_updates_per_s"] / rates["sfu"]["point_updates_per_s"]
+    res["implicit_step_block_10"] = rates
+    res["decision"] = ("kept off by default" if res["pass"]["vs_sfu"] < 1.0 and
+                       rates["fma_vs_sfu"] < 1.0 else "faster in at least one kernel")
     return res
 
 
@@ -765,7 +910,7 @@ def precision_pass(ctx, w, srcs, args, ms, torch, stream, flush, sample, rates, 
     times = timed_passes(one, stream, flush, torch, n)
     st = c.stats()
     t = sum(times) / len(times)
-    frac, frac_x = kernel_roofline(st, rates)
+    frac, frac_x = kernel_roofline(st, rates, count_pass(c, w, srcs, ms), n)
     res = {"value": w.point_updates / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "steps": n,
            "roofline_frac": frac, "roofline_frac_of_executed_ops": frac_x,
            "state_bytes_per_point": 20}
@@ -807,7 +952,7 @@ def batch_pass(args, ms, torch, stream, flush, rates, cpu_seconds=8.0):
     times = timed_passes(one, stream, flush, torch, n)
     st = c.stats()
     t = sum(times) / len(times)
-    frac, frac_x = kernel_roofline(st, rates)
+    frac, frac_x = kernel_roofline(st, rates, count_pass(c, w, srcs, ms), n)
     res = {"workload": "batch_64", "specimens": len(w.specimens), "points": w.n_points,
            "time_steps": w.n_steps, "value": w.point_updates / (t * 1e-3), "unit": UNIT,
            "ms_per_step": t, "steps": n, "graph": True,
@@ -884,6 +1029,58 @@ def part_segment_pass(ms, torch, stream, surrogate, seg_steps=20000, n_sub=10000
     out["hybrid_vs_plain"] = out["hybrid_kahan"]["value"] / out["fp32_plain"]["value"]
     ref.close()
     return out
+
+
+def coarsen_pass(ms, torch, stream, dims=(512, 512, 256), tol=1e-2, n_levels=6, reps=5):
+    """The phase-aware coarsening criterion (ms_coarsen_mask, device arrays)
+    on the part-scale grid (67.1M points; X_as, X_am, X_beta in FP64 = 1.6 GB,
+    far above L2): a transformed band under serpentine tracks with sharp
+    fronts and a martensite layer, built on the device.  Each call reads the
+    three fields and writes one byte per octant of levels 1 .. n_levels, with
+    the scratch of the per-octant ranges given by the caller; the time is the
+    whole call on the stream (CUDA events).  Algorithmic bytes: 24 per point
+    + the masks."""
+    from paper_2402_17580_gb300 import _binding as B
+    nx, ny, nz = dims
+    n = nx * ny * nz
+    dev = torch.device("cuda", 0)
+    with torch.cuda.stream(stream):
+        j = torch.arange(ny, device=dev, dtype=torch.float64).view(1, ny, 1)
+        k = torch.arange(nz, device=dev, dtype=torch.float64).view(nz, 1, 1)
+        band = torch.remainder(j, 40.0)           # one transformed band per 40 rows
+        s = torch.sigmoid((8.0 - (band - 20.0).abs()) / 0.5)
+        xas = (0.9 - 0.8 * s).expand(nz, ny, nx).contiguous().view(-1)
+        xam = (torch.where(k < nz // 2, 0.35, 0.0) * (0.9 - xas.view(nz, ny, nx)) / 0.9).view(-1)
+        xb = 1.0 - xas - xam
+        sizes, sbytes = B.coarsen_sizes(dims, n_levels, with_scratch=True)
+        total = sum(sizes)
+        mask = torch.empty(total, dtype=torch.uint8, device=dev)
+        scratch = torch.empty(sbytes, dtype=torch.uint8, device=dev)
+    stream.synchronize()
+    call = lambda: B.coarsen_mask_device(xas.data_ptr(), xam.data_ptr(), xb.data_ptr(), dims, tol,
+                                         n_levels, mask.data_ptr(), stream.cuda_stream,
+                                         scratch.data_ptr(), sbytes)
+    counts = call()
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    t = sum(times) / len(times)
+    byts = 24 * n + total
+    gbs = byts / (t * 1e-3) / 1e9
+    del xas, xam, xb, mask, scratch
+    return {"kernel": "k_coarsen_l1 + k_coarsen_up", "bound": "hbm", "grid": "x".join(map(str, dims)),
+            "points": n, "levels": n_levels, "tol": tol, "ms_per_call": round(t, 4),
+            "bytes_per_call": byts, "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,
+            "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),
+            "coarsenable_per_level": counts,
+            "note": "whole-call time (the counters' copy and the stream sync included); "
+                    "algorithmic bytes: the three FP64 fields once plus one byte per octant"}
 
 
 def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sample):

@@ -69,6 +69,21 @@ extern "C" {
                                    of S steps) into a CUDA graph on first use and
                                    replays it when called again with the same start
                                    step, step count and dt (e.g. after ms_fill_state) */
+#define MS_FLAG_FMA_TRANSCENDENTALS 8  /* MS_F32: the hot kernels (ms_run_track,
+                                   ms_step) evaluate exp2 and log2 as polynomials on
+                                   the FMA pipe (IEEE-754 range reduction, a fitted
+                                   polynomial by Estrin's scheme: the paper's fast
+                                   transcendentals, Sec. 3.3) instead of the SFU;
+                                   relative error about 1e-7, like the SFU's.  Off
+                                   by default: on GB300 the SFU path measured
+                                   faster (the kernels are bound by instruction
+                                   issue, which the polynomials add to) */
+#define MS_FLAG_COUNT_OPS    4  /* the explicit hot kernel counts the phase model's
+                                   transcendentals on the branch each point takes
+                                   (ms_stats model_sfu_ex2 / model_sfu_slow); off by
+                                   default: the counting costs instructions in the
+                                   kernel, so timed runs leave it off and the counts
+                                   come from a separate run of the same work       */
 
 /* time integration of the diffusive rates (ms_params.integrator), Sec. 3 */
 #define MS_EXPLICIT 0  /* forward Euler + correction g (eq:explicit_integration) */
@@ -124,7 +139,14 @@ typedef struct ms_params {
                                      <= 0: no subcycling)                        */
   double  fp_eps_abs, fp_eps_rel; /* implicit: WRMS tolerances (Sec. 3: 1e-10, 1e-3) */
   int32_t fp_max_iter;            /* implicit: fixed-point iteration cap (100)    */
-  int32_t reserved0;
+  int32_t tile_order;             /* ms_run_track with the active set: the order in
+                                     which the persistent warps take the active
+                                     tiles.  0 (default): heaviest first, by the
+                                     cycles per step the hot kernel last spent on
+                                     each tile (four classes against the previous
+                                     launch's mean), so the launch's tail is made of
+                                     cheap tiles; 1: tile index order.  Results do
+                                     not depend on it.                            */
   /* Far field of the moving sources in ms_run_track (default 5e-3 m; 0 =
    * off: every source summed point by point).  In a tile of 128 points
    * inside one grid row, at a level whose sources all move along +-x, a
@@ -142,20 +164,26 @@ typedef struct ms_params {
    * gives M <= A P / (2 pi k 2.1 mm) and <= 4.2e-5 K per source at P = 250 W
    * (the FP32 rounding of the direct sum is of the same order).  An
    * approximation of the direct sum, in every path whose arithmetic is FP32
-   * (MS_F32, MS_F64ACC, MS_KAHAN, explicit or MS_IMPLICIT); the full-FP64
-   * path (MS_F64) and the hybrid kernel always sum point by point.  The
+   * (MS_F32, MS_F64ACC, MS_KAHAN, explicit or MS_IMPLICIT, and the hybrid
+   * kernel); the full-FP64 path (MS_F64) always sums point by point.  The
    * library keeps 4 KB of interpolation weights on the device.             */
   double  farfield_dist;
 } ms_params;
 
 /* ------------------------------------------------------------ geometry */
 /* A regular grid of points: x = origin[0] + i*spacing[0], y likewise with j,
- * z likewise with k (spacing may be negative, e.g. z going down). */
+ * z = origin[2] + (k + k_offset)*spacing[2] (spacing may be negative, e.g. z
+ * going down).  k_offset (>= 0) makes the grid the z-planes k_offset ..
+ * k_offset + nz - 1 of a larger grid with the same origin and spacing, with
+ * the same coordinates to the bit: a z-slab shard of a block advances exactly
+ * as those planes do in the block (ms_run_track, when nx * ny * k_offset is a
+ * multiple of 128 so that the tiles coincide).  The thermal solver takes
+ * k_offset = 0 only. */
 typedef struct ms_grid {
   double origin[3];
   double spacing[3];
   int32_t dims[3];                /* nx, ny, nz (each >= 1)                     */
-  int32_t reserved;
+  int32_t k_offset;               /* first z-plane in the parent grid (>= 0)    */
 } ms_grid;
 
 /* ----------------------------------------------------- moving heat source */
@@ -236,7 +264,8 @@ typedef struct ms_stats_t {
    * phase model on the point-steps where it ran, counted on the branch each
    * point took (Sec. 2.2: exponentials of the equilibria and of k_as, the
    * powers x^p = 2^(p log2 x) of the rates, the reciprocal of k_as, and the
-   * App. A closed form): ex2 class, and the log2 / reciprocal class        */
+   * App. A closed form): ex2 class, and the log2 / reciprocal class; only
+   * with MS_FLAG_COUNT_OPS (0 otherwise)                                     */
   int64_t model_sfu_ex2;
   int64_t model_sfu_slow;
   /* far field (farfield_dist > 0): source evaluations at the interpolation
@@ -392,6 +421,73 @@ int ms_set_state_blob(ms_ctx* ctx, const void* blob, size_t bytes);
  * Allocates and frees its own small buffers and stream.
  * Errors: INVALID_ARG (op out of range, NULL ops_per_s), CUDA. */
 int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
+
+/* ------------------------------------------------ coarsening criterion */
+/* The phase-aware coarsening criterion of the paper's adaptive mesh (Sec. 3,
+ * the adaptive-mesh passage: an octant made of eight sibling cells of one
+ * refinement level may be coarsened only when, for every microstructure
+ * phase, all its values are close to each other).  On a grid of points
+ * (dims = nx, ny, nz; natural order, x fastest) the finest cells lie between
+ * neighbouring points, and octant i of level l >= 1 spans the points
+ * i 2^l .. (i + 1) 2^l along an axis of n > 1 points (floor((n - 1) / 2^l)
+ * octants per axis) and the single point of an axis with n = 1.  The octant
+ * may be coarsened when, for each of X_as, X_am and X_beta, its largest
+ * minus its smallest value over the octant's points is <= tol (one FP64
+ * subtraction: the decision is exact).  A coarsenable octant's children are
+ * coarsenable, so the masks nest.  This is the criterion the phases impose;
+ * a mesh also coarsens by its own rules (the consolidated fraction, the
+ * refinement kept near the active layer), which are not part of it.       */
+#define MS_COARSEN_MAX_LEVELS 30
+
+/* Octant counts of levels 1 .. n_levels for grid dims (host only, no CUDA
+ * call): counts[l - 1] = octants of level l (0 once an axis runs out), and
+ * (scratch_bytes may be NULL) the device scratch ms_coarsen_mask needs: the
+ * per-octant minima and maxima of two levels (6 doubles per level-2 and per
+ * level-3 octant) and its counters.
+ * Errors: INVALID_ARG (dims < 1, n_levels outside [1, MS_COARSEN_MAX_LEVELS],
+ * NULL counts). */
+int ms_coarsen_sizes(const int32_t* dims, int32_t n_levels, int64_t* counts,
+                     size_t* scratch_bytes);
+
+/* The masks of levels 1 .. n_levels for the phase fields x_as, x_am, x_beta
+ * (nx ny nz doubles each, natural order).  mask receives the levels in turn,
+ * each x fastest, one byte per octant (1 = may be coarsened), sum of
+ * ms_coarsen_sizes' counts bytes in all; n_coarse (may be NULL) receives the
+ * coarsenable octants per level.  flags MS_PTR_DEVICE: the three fields and
+ * mask are device pointers, and scratch (may be NULL) is a device buffer of
+ * at least the scratch_bytes ms_coarsen_sizes gives, 16-byte aligned, that
+ * the call uses instead of allocating; without MS_PTR_DEVICE they are host
+ * pointers, copied through device buffers the call allocates (scratch must
+ * be NULL).  stream is a cudaStream_t (NULL = legacy default stream); the
+ * call returns when the result is in place.  One kernel reduces levels 1
+ * and 2 from the fields (a thread per level-2 slot), the next levels reduce
+ * the per-octant ranges of the level below.
+ * Errors: INVALID_ARG (NULL field or mask, dims < 1, n_levels out of range,
+ * tol negative or not finite, scratch without MS_PTR_DEVICE, too small or
+ * misaligned), OOM, CUDA. */
+int ms_coarsen_mask(const double* x_as, const double* x_am, const double* x_beta,
+                    const int32_t* dims, double tol, int32_t n_levels, uint8_t* mask,
+                    int64_t* n_coarse, void* scratch, size_t scratch_bytes, int32_t flags,
+                    void* stream);
+
+/* The same criterion on a context's current state: X_as, X_am and X_beta =
+ * 1 - X_liq - X_as - X_am at the temperature of its current time level, as
+ * ms_get_fractions returns them.  The context must hold one full grid
+ * (ms_set_points with one specimen); mask and n_coarse (may be NULL) are
+ * host arrays as in ms_coarsen_mask.  Synchronises the context's stream.
+ * Errors: INVALID_ARG (NULL mask, n_levels out of range, tol negative or not
+ * finite), STATE (no single full grid, or no temperature known yet), OOM,
+ * CUDA, NONFINITE (the sticky device error word). */
+int ms_coarsen_ctx(ms_ctx* ctx, double tol, int32_t n_levels, uint8_t* mask, int64_t* n_coarse);
+
+/* The device's exp2 and log2 on host arrays, for checking them against the
+ * mathematics: which = 0 the FMA-pipe polynomial exp2, 1 the FMA-pipe log2
+ * (MS_FLAG_FMA_TRANSCENDENTALS; the paper's fast transcendentals, Sec. 3.3),
+ * 2 the SFU's ex2.approx.ftz.f32, 3 the SFU's lg2.approx.ftz.f32, element
+ * by element from x to y (n floats each).  Allocates and frees its own
+ * device buffers; synchronous.
+ * Errors: INVALID_ARG (which outside 0..3, NULL x or y, n < 0), OOM, CUDA. */
+int ms_eval_transcendental(int which, const float* x, float* y, int64_t n);
 
 /* ms_run_track_noalloc -- the ms_run_track hot path without allocating.
  * The paper has no counterpart; this is an integration entry point.

@@ -55,13 +55,26 @@ def _span(i, level, n):
     return slice(i << level, ((i + 1) << level) + 1)
 
 
+def phase_fields(x_as, x_am, x_beta, dims):
+    """The three phases as (nz, ny, nx) arrays (natural grid order, x fastest)."""
+    nx, ny, nz = (int(d) for d in dims)
+    return [np.asarray(a, dtype=np.float64).reshape(nz, ny, nx) for a in (x_as, x_am, x_beta)]
+
+
+def octant_ranges(fields, level, i, j, k):
+    """max - min of each phase over octant (i, j, k) of `level`; the octant
+    may be coarsened when all three are <= tol."""
+    nz, ny, nx = fields[0].shape
+    sk, sj, si = _span(k, level, nz), _span(j, level, ny), _span(i, level, nx)
+    return [float(f[sk, sj, si].max() - f[sk, sj, si].min()) for f in fields]
+
+
 def coarsen_masks(x_as, x_am, x_beta, dims, tol, n_levels):
     """The masks of levels 1 .. n_levels as a list of uint8 arrays of shape
     (nz_l, ny_l, nx_l): octant (i, j, k) of level l is 1 when every phase's
     max - min over its points is <= tol.  The phase arrays are in natural
     grid order (x fastest)."""
-    nx, ny, nz = (int(d) for d in dims)
-    fields = [np.asarray(a, dtype=np.float64).reshape(nz, ny, nx) for a in (x_as, x_am, x_beta)]
+    fields = phase_fields(x_as, x_am, x_beta, dims)
     out = []
     for level in range(1, n_levels + 1):
         cx, cy, cz = level_shape(dims, level)
@@ -69,13 +82,7 @@ def coarsen_masks(x_as, x_am, x_beta, dims, tol, n_levels):
         for k in range(cz):
             for j in range(cy):
                 for i in range(cx):
-                    sk, sj, si = _span(k, level, nz), _span(j, level, ny), _span(i, level, nx)
-                    ok = True
-                    for f in fields:
-                        block = f[sk, sj, si]
-                        if block.max() - block.min() > tol:
-                            ok = False
-                            break
-                    m[k, j, i] = 1 if ok else 0
+                    ranges = octant_ranges(fields, level, i, j, k)
+                    m[k, j, i] = 1 if all(r <= tol for r in ranges) else 0
         out.append(m)
     return out

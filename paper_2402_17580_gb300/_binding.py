@@ -23,6 +23,8 @@ MS_EXPLICIT, MS_IMPLICIT = 0, 1
 MS_PTR_DEVICE = 1
 MS_FLAG_TIME_KERNELS = 1
 MS_FLAG_GRAPH = 2
+MS_FLAG_COUNT_OPS = 4
+MS_FLAG_FMA_TRANSCENDENTALS = 8
 MS_MLP_IN, MS_MLP_OUT, MS_MLP_PARAMS, MS_MLP_WINDOW = 12, 3, 5187, 8
 
 d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
@@ -35,11 +37,11 @@ class Params(ctypes.Structure):
         (n, i32) for n in ("martensite_literal", "init_ba_steps", "precision", "steps_per_launch",
                            "rebuild_steps", "block_threads", "flags", "integrator")] + [
         ("dt_sub", d), ("fp_eps_abs", d), ("fp_eps_rel", d), ("fp_max_iter", i32),
-        ("reserved0", i32), ("farfield_dist", d)]
+        ("tile_order", i32), ("farfield_dist", d)]
 
 
 class Grid(ctypes.Structure):
-    _fields_ = [("origin", d * 3), ("spacing", d * 3), ("dims", i32 * 3), ("reserved", i32)]
+    _fields_ = [("origin", d * 3), ("spacing", d * 3), ("dims", i32 * 3), ("k_offset", i32)]
 
 
 class Track(ctypes.Structure):
@@ -156,12 +158,25 @@ def load(build_if_missing: bool = True):
     lib.ms_thermal_get.argtypes = [P, P, P]
     lib.ms_thermal_stats.argtypes = [P, ctypes.POINTER(d), ctypes.POINTER(i64), ctypes.POINTER(d)]
     lib.ms_thermal_run_coupled.argtypes = [P, P, i64, d]
+    lib.ms_coarsen_sizes.argtypes = [ctypes.POINTER(i32), i32, ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_size_t)]
+    lib.ms_coarsen_mask.argtypes = [P, P, P, ctypes.POINTER(i32), d, i32, P,
+                                    ctypes.POINTER(i64), P, ctypes.c_size_t, i32, P]
+    lib.ms_coarsen_ctx.argtypes = [P, d, i32, P, ctypes.POINTER(i64)]
+    lib.ms_eval_transcendental.argtypes = [ctypes.c_int, P, P, i64]
     for i, s in enumerate(STRUCTS):
         if lib.ms_struct_size(i) != ctypes.sizeof(s):
             raise RuntimeError(f"ABI mismatch for {s.__name__}: C {lib.ms_struct_size(i)} "
                                f"vs ctypes {ctypes.sizeof(s)}")
     _lib = lib
     return lib
+
+
+def _grid(g) -> Grid:
+    """ms_grid of a workloads.Grid-like object (origin, spacing, dims, and
+    optionally k_offset)."""
+    return Grid((d * 3)(*g.origin), (d * 3)(*g.spacing), (i32 * 3)(*g.dims),
+                int(getattr(g, "k_offset", 0)))
 
 
 def _check(rc, where):
@@ -173,7 +188,7 @@ def run_track_noalloc(params, grid, source, xas_ptr, xam_ptr, aux_ptr, n_points,
                       dt, stream_handle=0):
     """ms_run_track_noalloc: advance one specimen whose state lives in the
     caller's device arrays (raw pointers), without any allocation."""
-    g = Grid((d * 3)(*grid.origin), (d * 3)(*grid.spacing), (i32 * 3)(*grid.dims), 0)
+    g = _grid(grid)
     h, keep = make_heat_source(source)
     _check(load().ms_run_track_noalloc(ctypes.byref(params), ctypes.byref(g), ctypes.byref(h),
                                        ctypes.c_void_p(xas_ptr), ctypes.c_void_p(xam_ptr),
@@ -181,6 +196,72 @@ def run_track_noalloc(params, grid, source, xas_ptr, xam_ptr, aux_ptr, n_points,
                                        int(n_steps), float(dt), ctypes.c_void_p(stream_handle or 0)),
            "ms_run_track_noalloc")
     del keep
+
+
+COARSEN_MAX_LEVELS = 30   # MS_COARSEN_MAX_LEVELS
+
+
+def coarsen_sizes(dims, n_levels, with_scratch=False):
+    """ms_coarsen_sizes: octants of levels 1 .. n_levels of a grid (host
+    only); with_scratch also returns the device scratch bytes."""
+    out = (i64 * int(n_levels))()
+    sb = ctypes.c_size_t(0)
+    _check(load().ms_coarsen_sizes((i32 * 3)(*dims), int(n_levels), out, ctypes.byref(sb)),
+           "ms_coarsen_sizes")
+    counts = [int(v) for v in out]
+    return (counts, int(sb.value)) if with_scratch else counts
+
+
+def _split_masks(flat, dims, n_levels):
+    out, off = [], 0
+    for l in range(1, n_levels + 1):
+        shp = tuple(1 if n == 1 else (n - 1) >> l for n in dims)
+        c = int(np.prod(shp))
+        out.append(flat[off:off + c].reshape(shp[::-1]))
+        off += c
+    return out
+
+
+def coarsen_mask(x_as, x_am, x_beta, dims, tol, n_levels):
+    """ms_coarsen_mask on host arrays: the masks of levels 1 .. n_levels as
+    uint8 arrays of shape (nz_l, ny_l, nx_l), and the coarsenable octants
+    per level."""
+    a, m, b = (np.ascontiguousarray(v, dtype=np.float64) for v in (x_as, x_am, x_beta))
+    n = int(np.prod(dims))
+    assert a.size == n and m.size == n and b.size == n
+    flat = np.empty(sum(coarsen_sizes(dims, n_levels)), dtype=np.uint8)
+    cnt = (i64 * int(n_levels))()
+    _check(load().ms_coarsen_mask(_ptr(a), _ptr(m), _ptr(b), (i32 * 3)(*dims), float(tol),
+                                  int(n_levels), _ptr(flat), cnt, None, 0, 0, None),
+           "ms_coarsen_mask")
+    return _split_masks(flat, dims, n_levels), [int(v) for v in cnt]
+
+
+def coarsen_mask_device(xas_ptr, xam_ptr, xbeta_ptr, dims, tol, n_levels, mask_ptr,
+                        stream_handle=0, scratch_ptr=0, scratch_bytes=0):
+    """ms_coarsen_mask on device arrays (raw pointers, and optionally the
+    caller's scratch); returns the coarsenable octants per level."""
+    cnt = (i64 * int(n_levels))()
+    _check(load().ms_coarsen_mask(ctypes.c_void_p(xas_ptr), ctypes.c_void_p(xam_ptr),
+                                  ctypes.c_void_p(xbeta_ptr), (i32 * 3)(*dims), float(tol),
+                                  int(n_levels), ctypes.c_void_p(mask_ptr), cnt,
+                                  ctypes.c_void_p(scratch_ptr or 0), int(scratch_bytes),
+                                  MS_PTR_DEVICE, ctypes.c_void_p(stream_handle or 0)),
+           "ms_coarsen_mask")
+    return [int(v) for v in cnt]
+
+
+TRANSCENDENTALS = ("fma_ex2", "fma_lg2", "sfu_ex2", "sfu_lg2")
+
+
+def eval_transcendental(which: str, x):
+    """ms_eval_transcendental: the device's exp2 / log2 (FMA-pipe polynomial
+    or SFU) of a float32 array."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    _check(load().ms_eval_transcendental(TRANSCENDENTALS.index(which), _ptr(x), _ptr(y), x.size),
+           "ms_eval_transcendental")
+    return y
 
 
 PROBE_OPS = ("ex2", "lg2", "rsqrt", "rcp", "ffma")
@@ -323,13 +404,13 @@ class Context:
     def set_points(self, grids):
         arr = (Grid * len(grids))()
         for i, g in enumerate(grids):
-            arr[i] = Grid((d * 3)(*g.origin), (d * 3)(*g.spacing), (i32 * 3)(*g.dims), 0)
+            arr[i] = _grid(g)
         _check(self._lib.ms_set_points(self._h, arr, len(grids)), "ms_set_points")
 
     def set_points_subset(self, grid, idx):
         """The context's points are grid points idx (natural grid indices)."""
         idx = np.ascontiguousarray(idx, dtype=np.int64)
-        g = Grid((d * 3)(*grid.origin), (d * 3)(*grid.spacing), (i32 * 3)(*grid.dims), 0)
+        g = _grid(grid)
         _check(self._lib.ms_set_points_subset(self._h, ctypes.byref(g),
                                               idx.ctypes.data_as(ctypes.POINTER(i64)), idx.size),
                "ms_set_points_subset")
@@ -383,6 +464,15 @@ class Context:
         assert len(outs) == 4 and all(o.dtype == np.float64 and o.size == self.n and
                                       o.flags["C_CONTIGUOUS"] for o in outs)
         _check(self._lib.ms_get_fractions(self._h, *[_ptr(o) for o in outs]), "ms_get_fractions")
+
+    def coarsen(self, tol, n_levels, dims):
+        """ms_coarsen_ctx: the coarsening masks of the context's grid (dims
+        as given to set_points) on its current state; (masks, counts)."""
+        flat = np.empty(sum(coarsen_sizes(dims, n_levels)), dtype=np.uint8)
+        cnt = (i64 * int(n_levels))()
+        _check(self._lib.ms_coarsen_ctx(self._h, float(tol), int(n_levels), _ptr(flat), cnt),
+               "ms_coarsen_ctx")
+        return _split_masks(flat, dims, n_levels), [int(v) for v in cnt]
 
     def aux(self):
         out = np.empty(self.n)
@@ -484,7 +574,7 @@ class Thermal:
         self._lib = load()
         p = params if params is not None else thermal_params(**overrides)
         self.params = p
-        g = Grid((d * 3)(*grid.origin), (d * 3)(*grid.spacing), (i32 * 3)(*grid.dims), 0)
+        g = _grid(grid)
         self.n = int(grid.dims[0]) * int(grid.dims[1]) * int(grid.dims[2])
         self._h = ctypes.c_void_p()
         _check(self._lib.ms_thermal_create(ctypes.byref(p), ctypes.byref(g), ctypes.byref(self._h)),

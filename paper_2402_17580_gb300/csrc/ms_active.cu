@@ -62,7 +62,8 @@ __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   }
   const double xa = sp.ox + double(ilo) * sp.dx, xb = sp.ox + double(ihi) * sp.dx;
   const double ya = sp.oy + double(jlo) * sp.dy, yb = sp.oy + double(jhi) * sp.dy;
-  const double za = sp.oz + double(k0) * sp.dz, zb = sp.oz + double(k1) * sp.dz;
+  const double za = sp.oz + double(k0 + sp.k_off) * sp.dz;
+  const double zb = sp.oz + double(k1 + sp.k_off) * sp.dz;
   const double bx0 = fmin(xa, xb), bx1 = fmax(xa, xb), by0 = fmin(ya, yb), by1 = fmax(ya, yb);
   const float bz1 = float(fmax(za, zb));
   // Per source the geometry runs in FP32 on coordinates relative to the
@@ -116,16 +117,39 @@ __device__ bool tile_is_active(const ActiveArgs& a, int t) {
   return false;
 }
 
+// Cost class of an active tile: its cycles per level in the launch that last
+// processed it against the previous launch's mean (0: >= 2x, 1: >= 1x, 2:
+// >= 1/2 x, 3: below, or not measured).
+__device__ __forceinline__ int cost_class(const ActiveArgs& a, int t, double mean) {
+  if (!a.tile_cost || !(mean > 0.0)) return COST_BUCKETS - 1;
+  const double c = double(a.tile_cost[t]);
+  return c >= 2.0 * mean ? 0 : (c >= mean ? 1 : (c >= 0.5 * mean ? 2 : 3));
+}
+
 __global__ void k_active(const ActiveArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int prev = a.prev_slot & 1;
+  const unsigned cnt = a.work->cost_cnt[prev];
+  const double mean = cnt ? double(a.work->cost_sum[prev]) / double(cnt) : 0.0;
+  if (t == 0) {  // this launch's slot, read by the next launch's active set
+    a.work->cost_cnt[prev ^ 1] = 0;
+    a.work->cost_sum[prev ^ 1] = 0;
+  }
   const bool act = t < a.n_tiles && tile_is_active(a, t);
-  const unsigned mask = __ballot_sync(0xffffffffu, act);
-  if (mask) {
-    const int lane = threadIdx.x & 31;
+  const int cls = act ? cost_class(a, t, mean) : -1;
+  const unsigned any = __ballot_sync(0xffffffffu, act);
+  if (!any) return;
+  if (lane == 0) atomicAdd(&a.work->n_active, __popc(any));
+#pragma unroll
+  for (int b = 0; b < COST_BUCKETS; ++b) {
+    const unsigned mask = __ballot_sync(0xffffffffu, cls == b);
+    if (!mask) continue;
     int base = 0;
-    if (lane == 0) base = atomicAdd(&a.work->n_active, __popc(mask));
+    if (lane == 0) base = atomicAdd(&a.work->n_bucket[b], __popc(mask));
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (act) a.tile_list[base + __popc(mask & ((1u << lane) - 1u))] = t;
+    if (cls == b)
+      a.tile_list[int64_t(b) * a.n_tiles + base + __popc(mask & ((1u << lane) - 1u))] = t;
   }
 }
 

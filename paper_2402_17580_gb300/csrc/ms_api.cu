@@ -84,7 +84,9 @@ struct ms_ctx {
   int* err_d = nullptr;
 
   // active set and work distribution of the persistent hot kernel
-  int32_t* tile_list_d = nullptr;
+  int32_t* tile_list_d = nullptr;  // COST_BUCKETS regions of n_tiles entries
+  uint32_t* tile_cost_d = nullptr; // per tile: cycles per level when last processed
+  int32_t cost_slot = 0;           // parity of the hot-kernel launches
   float* tile_tsat_d = nullptr;
   ms::WorkCounters* work_d = nullptr;
   int sm_count = 0;
@@ -235,6 +237,10 @@ int check_params(const ms_params& p) {
     return fail(MS_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
   if (p.integrator != MS_EXPLICIT && p.integrator != MS_IMPLICIT)
     return fail(MS_ERR_INVALID_ARG, "unknown integrator %d", p.integrator);
+  if (p.tile_order != 0 && p.tile_order != 1)
+    return fail(MS_ERR_INVALID_ARG, "tile_order must be 0 or 1");
+  if ((p.flags & MS_FLAG_FMA_TRANSCENDENTALS) && p.precision != MS_F32)
+    return fail(MS_ERR_UNSUPPORTED, "MS_FLAG_FMA_TRANSCENDENTALS needs precision MS_F32");
   if (!(std::isfinite(p.farfield_dist) && p.farfield_dist >= 0.0))
     return fail(MS_ERR_INVALID_ARG, "farfield_dist must be finite and >= 0");
   if (p.integrator == MS_IMPLICIT) {
@@ -277,6 +283,8 @@ void drop_graphs(ms_ctx* c) {
 void free_layout(ms_ctx* c) {
   cudaFree(c->tile_list_d);
   cudaFree(c->tile_tsat_d);
+  cudaFree(c->tile_cost_d);
+  c->tile_cost_d = nullptr;
   c->tile_list_d = nullptr;
   c->tile_tsat_d = nullptr;
   cudaFree(c->specs_d);
@@ -321,7 +329,9 @@ int build_layout(ms_ctx* c) {
   MS_CUDA(cudaMalloc(&c->xam_d, np * c->fbytes));
   MS_CUDA(cudaMalloc(&c->aux_d, np * sizeof(float)));
   MS_CUDA(cudaMalloc(&c->stage_d, size_t(c->n_points) * 4 * sizeof(double)));
-  MS_CUDA(cudaMalloc(&c->tile_list_d, size_t(tiles) * sizeof(int32_t)));
+  MS_CUDA(cudaMalloc(&c->tile_list_d, size_t(tiles) * ms::COST_BUCKETS * sizeof(int32_t)));
+  MS_CUDA(cudaMalloc(&c->tile_cost_d, size_t(tiles) * sizeof(uint32_t)));
+  MS_CUDA(cudaMemset(c->tile_cost_d, 0, size_t(tiles) * sizeof(uint32_t)));
   MS_CUDA(cudaMalloc(&c->tile_tsat_d, size_t(tiles) * sizeof(float)));
   MS_CUDA(ms::launch_fill_f32(c->tile_tsat_d, tiles, INFINITY, c->stream));
   {
@@ -555,6 +565,8 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
       aa.T_as_end = c->prm.T_as_end;
       aa.tile_list = c->tile_list_d;
       aa.work = c->work_d;
+      aa.tile_cost = c->prm.tile_order == 0 ? c->tile_cost_d : nullptr;
+      aa.prev_slot = c->cost_slot ^ 1;
       MS_CUDA(ms::launch_active(aa, c->stream));
       c->st.launches++;
     }
@@ -576,7 +588,12 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     a.tile_tsat = c->tile_tsat_d;
     a.err = c->err_d;
     a.ops = c->ops_d;
+    if (use_list && c->prm.tile_order == 0) {
+      a.tile_cost = c->tile_cost_d;
+      a.cost_slot = c->cost_slot;
+    }
     a.n_sub = n_substeps(c->prm, c->dt);
+    a.count_sfu = (c->prm.flags & MS_FLAG_COUNT_OPS) ? 1 : 0;
     if constexpr (std::is_same<AT, float>::value) {
       a.ff = c->ff_d;
       a.ff_dist = float(c->prm.farfield_dist);
@@ -596,11 +613,22 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
         hybrid = true;
       }
     }
-    if (!hybrid)
-      MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream,
+    if (!hybrid) {
+      bool fma = false;
+      if constexpr (std::is_same<AT, float>::value && std::is_same<FT, float>::value) {
+        if (c->prm.flags & MS_FLAG_FMA_TRANSCENDENTALS) {
+          MS_CUDA(ms::launch_track_fma(a, block_threads(c), c->track_grid, c->stream,
                                        c->prm.integrator == MS_IMPLICIT));
+          fma = true;
+        }
+      }
+      if (!fma)
+        MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream,
+                                         c->prm.integrator == MS_IMPLICIT));
+    }
     if ((rc = kernel_event(c, true)) != MS_OK) return rc;
     c->st.launches++;
+    c->cost_slot ^= 1;
     c->step_n += steps;
     c->st.steps += steps;
     c->st.point_updates += int64_t(steps) * c->n_points;
@@ -626,8 +654,17 @@ int step_impl(ms_ctx* c, const float* T0, const float* T1) {
   if ((rc = kernel_event(c, false)) != MS_OK) return rc;
   a.ops = c->ops_d;
   a.n_sub = n_substeps(c->prm, c->dt);
-  MS_CUDA(ms::launch_step_ext<AT, FT>(a, block_threads(c), c->stream,
+  bool fma = false;
+  if constexpr (std::is_same<AT, float>::value && std::is_same<FT, float>::value) {
+    if (c->prm.flags & MS_FLAG_FMA_TRANSCENDENTALS) {
+      MS_CUDA(ms::launch_step_ext_fma(a, block_threads(c), c->stream,
                                       c->prm.integrator == MS_IMPLICIT));
+      fma = true;
+    }
+  }
+  if (!fma)
+    MS_CUDA(ms::launch_step_ext<AT, FT>(a, block_threads(c), c->stream,
+                                        c->prm.integrator == MS_IMPLICIT));
   if ((rc = kernel_event(c, true)) != MS_OK) return rc;
   c->st.launches++;
   return MS_OK;
@@ -911,8 +948,8 @@ int ms_set_points(ms_ctx* c, const ms_grid* grids, int32_t n_specimens) {
   int64_t total = 0;
   for (int32_t s = 0; s < n_specimens; ++s) {
     const ms_grid& g = grids[s];
-    if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1)
-      return fail(MS_ERR_INVALID_ARG, "grid %d: dims must be >= 1", s);
+    if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1 || g.k_offset < 0)
+      return fail(MS_ERR_INVALID_ARG, "grid %d: dims must be >= 1 and k_offset >= 0", s);
     for (int a = 0; a < 3; ++a)
       if (!std::isfinite(g.origin[a]) || !std::isfinite(g.spacing[a]))
         return fail(MS_ERR_INVALID_ARG, "grid %d: non-finite origin or spacing", s);
@@ -926,6 +963,7 @@ int ms_set_points(ms_ctx* c, const ms_grid* grids, int32_t n_specimens) {
       d.dx = g.spacing[0]; d.dy = g.spacing[1]; d.dz = g.spacing[2];
     }
     d.nx = g.dims[0]; d.ny = g.dims[1]; d.nz = g.dims[2];
+    d.k_off = g.k_offset;
     d.n = int64_t(g.dims[0]) * g.dims[1] * g.dims[2];
     d.n_layers = 1;
     total += d.n;
@@ -952,8 +990,8 @@ int ms_set_points_subset(ms_ctx* c, const ms_grid* grid, const int64_t* idx, int
     return rc;
   }
   const int64_t total = int64_t(grid->dims[0]) * grid->dims[1] * grid->dims[2];
-  if (grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1)
-    return fail(MS_ERR_INVALID_ARG, "grid dims must be >= 1");
+  if (grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1 || grid->k_offset < 0)
+    return fail(MS_ERR_INVALID_ARG, "grid dims must be >= 1 and k_offset >= 0");
   for (int64_t i = 0; i < n; ++i)
     if (idx[i] < 0 || idx[i] >= total)
       return fail(MS_ERR_INVALID_ARG, "subset index %lld out of the grid", (long long)idx[i]);
@@ -972,6 +1010,7 @@ int ms_set_points_subset(ms_ctx* c, const ms_grid* grid, const int64_t* idx, int
     d.dx = grid->spacing[0]; d.dy = grid->spacing[1]; d.dz = grid->spacing[2];
   }
   d.nx = grid->dims[0]; d.ny = grid->dims[1]; d.nz = grid->dims[2];
+  d.k_off = grid->k_offset;
   d.n = n;
   d.n_layers = 1;
   d.idx = c->idx_d;
@@ -1303,6 +1342,41 @@ int ms_set_surrogate(ms_ctx* c, const ms_surrogate* s, double judge_frac) {
   c->mlp = ms::surrogate_weights(s);
   c->judge_thresh = uint64_t(std::llround(judge_frac * 4294967296.0));
   return MS_OK;
+}
+
+int ms_coarsen_ctx(ms_ctx* c, double tol, int32_t n_levels, uint8_t* mask, int64_t* n_coarse) {
+  if (!c || !mask) return fail(MS_ERR_INVALID_ARG, "NULL argument");
+  if (n_levels < 1 || n_levels > MS_COARSEN_MAX_LEVELS)
+    return fail(MS_ERR_INVALID_ARG, "n_levels must be in [1, MS_COARSEN_MAX_LEVELS]");
+  if (!(tol >= 0.0 && tol <= 1e300)) return fail(MS_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (!c->has_grid || c->specs_h.size() != 1 || c->specs_h[0].idx)
+    return fail(MS_ERR_STATE, "the coarsening criterion needs one full grid (ms_set_points)");
+  const SpecDev& sp = c->specs_h[0];
+  const int32_t dims[3] = {sp.nx, sp.ny, sp.nz};
+  int rc;
+  if ((rc = stage_fractions(c, true)) != MS_OK) return rc;
+  const int64_t n = c->n_points;
+  const int64_t total = ms::coarsen_counts(dims, n_levels, nullptr);
+  const size_t sb = ms::coarsen_scratch_bytes(dims);   // ranges, then the counters
+  char* buf = nullptr;
+  MS_CUDA(cudaMalloc(&buf, sb + size_t(total) + 64 * sizeof(unsigned long long)));
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(buf + sb);
+  uint8_t* dmask = reinterpret_cast<uint8_t*>(buf + sb + 64 * sizeof(unsigned long long));
+  const double* d = c->stage_d;
+  unsigned long long hc[64] = {};
+  cudaError_t e = ms::launch_coarsen(d, d + n, d + 2 * n, dims, tol, n_levels, dmask, buf, cnt,
+                                     c->stream);
+  if (e == cudaSuccess && total > 0)
+    e = cudaMemcpyAsync(mask, dmask, size_t(total), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hc, cnt, sizeof(unsigned long long) * size_t(n_levels),
+                        cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(MS_ERR_CUDA, "%s", cudaGetErrorString(e));
+  if (n_coarse)
+    for (int l = 0; l < n_levels; ++l) n_coarse[l] = int64_t(hc[l]);
+  return check_device_error(c);
 }
 
 int ms_stats(ms_ctx* c, ms_stats_t* out) {

@@ -113,12 +113,65 @@ __device__ __forceinline__ float sfu_rcp(float x) {
   return y;
 }
 
+// exp2 and log2 on the FMA pipe (the paper's polynomial transcendentals,
+// Sec. 3.3, for FP32): an IEEE-754 range reduction, a polynomial fitted by
+// weighted least squares on Chebyshev nodes (paper_2402_17580_gb300/
+// fit_poly.py prints the coefficients) evaluated with Estrin's scheme, and the
+// exponent written back into the bits.  No conversion instruction: integers
+// move through the 1.5 * 2^23 rounding constant.
+//   fma_ex2: x = n + f, n = round(x), |f| <= 1/2; 2^f by a degree-6 polynomial
+//            (relative error <= 1e-7 in FP32); 0 below 2^-126 like
+//            ex2.approx.ftz, 2^127.99 at most.
+//   fma_lg2: x = 2^e m, m in [sqrt(1/2), sqrt(2)), t = m - 1; log2(1 + t) =
+//            t q(t) with q of degree 8 (absolute error <= 6e-8 on t q);
+//            -inf for 0 and subnormals (ftz), NaN below 0, inf for inf.
+constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ float fma_ex2(float x) {
+  const float xc = fminf(x, 127.99f);
+  const float tn = xc + kRound;
+  const float n = tn - kRound;
+  const float f = xc - n;
+  const float f2 = f * f;
+  const float f4 = f2 * f2;
+  const float a = fmaf(6.931472056e-01f, f, 1.000000001e+00f);
+  const float b = fmaf(5.550328998e-02f, f, 2.402264661e-01f);
+  const float c = fmaf(1.339986036e-03f, f, 9.618519534e-03f);
+  const float d = fmaf(1.533757683e-04f, f2, c);
+  const float p = fmaf(f4, d, fmaf(f2, b, a));
+  const int ni = __float_as_int(tn) - 0x4B400000;
+  const float r = __int_as_float(__float_as_int(p) + (ni << 23));
+  return xc < -126.0f ? 0.0f : r;
+}
+__device__ __forceinline__ float fma_lg2(float x) {
+  const int i = __float_as_int(x);
+  const int e = (i - 0x3F3504F3) >> 23;
+  const float t = __int_as_float(i - (e << 23)) - 1.0f;
+  const float ef = __int_as_float(e + 0x4B400000) - kRound;
+  const float t2 = t * t;
+  const float t4 = t2 * t2;
+  const float q0 = fmaf(-7.213474818e-01f, t, 1.442695004e+00f);
+  const float q1 = fmaf(-3.606921079e-01f, t, 4.809107678e-01f);
+  const float q2 = fmaf(-2.391949061e-01f, t, 2.879017533e-01f);
+  const float q3 = fmaf(-2.057056070e-01f, t, 2.161191295e-01f);
+  const float q23 = fmaf(1.228052831e-01f, t4, fmaf(t2, q3, q2));
+  const float q = fmaf(t4, q23, fmaf(t2, q1, q0));
+  const float r = fmaf(t, q, ef);
+  return x >= 1.17549435e-38f ? (x < INFINITY ? r : x)
+                              : (x >= 0.0f ? -INFINITY : __int_as_float(0x7fffffff));
+}
+
 template <typename AT>
 struct Fn;
 template <>
 struct Fn<float> {
+#ifdef MS_FMA_TRANSCENDENTALS
+  // the translation unit of the FMA-pipe variant (MS_FLAG_FMA_TRANSCENDENTALS)
+  static __device__ __forceinline__ float ex2(float x) { return fma_ex2(x); }
+  static __device__ __forceinline__ float lg2(float x) { return fma_lg2(x); }
+#else
   static __device__ __forceinline__ float ex2(float x) { return sfu_ex2(x); }
   static __device__ __forceinline__ float lg2(float x) { return sfu_lg2(x); }
+#endif
   static __device__ __forceinline__ float rsqrt(float x) { return sfu_rsqrt(x); }
   static __device__ __forceinline__ float rcp(float x) { return sfu_rcp(x); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }

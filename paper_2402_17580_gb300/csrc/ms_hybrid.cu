@@ -111,9 +111,26 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   const float z_tol = sp.z_tol;
   const bool skipping = a.m.T_thr > 0.0f;
   const int n_steps = a.n_levels - 1;
+  // far field (as in k_track): the tile's x-range, first to 128th point
+  const int64_t col0 = __shfl_sync(full, col, 0);
+  const float x_first = float(sp.ox) + float(col0) * float(sp.dx);
+  const float x_span = float(TILE - 1) * float(sp.dx);
+  const float ff_dist = fmaxf(a.ff_dist, FF_RANGE_GUARD * fabsf(x_span));
+  const bool far = a.ff != nullptr && row;
+  // the temperatures of 4 points at level lvl, far field where it applies
+  auto temps = [&](int lvl, float* T) {
+    const SrcLevelT<float> L = lv[lvl];
+    if (far && L.axis) {
+      int nn, nf;
+      temps4_far(L, en + int64_t(lvl) * a.slots, px, py[0], pz[0], x_first, x_span, ff_dist,
+                 lane, T, nn, nf, a.ff);
+    } else {
+      temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, row, T);
+    }
+  };
 
   float T0[4];
-  temps4<float>(lv[0], en, px, py, pz, false, T0);  // once per tile: the general form (same bits)
+  temps(0, T0);
   for (int w0 = 0; w0 < n_steps; w0 += MLP_WINDOW) {
     const int K = min(MLP_WINDOW, n_steps - w0);
     bool band[4], all_act[4], any_act[4], noop[4], cool[4];
@@ -131,7 +148,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       const int lvl = w0 + 1 + l;
       const SrcLevelT<float> L = lv[lvl];
       float T1[4];
-      temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, row, T1);
+      temps(lvl, T1);
 #pragma unroll
       for (int q = 0; q < 4; ++q) sm.T[l][lane + 32 * q] = T1[q];
       const float zlim = L.z_surf + z_tol;
@@ -319,12 +336,16 @@ __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackA
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
   unsigned long long done = 0;
   HybCount cnt;
+  int nb[COST_BUCKETS];
+#pragma unroll
+  for (int b = 0; b < COST_BUCKETS; ++b) nb[b] = a.tile_list ? a.work->n_bucket[b] : 0;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    hybrid_tile<FT>(a, W, sm, a.tile_list ? a.tile_list[w] : w, lane, fdt, cnt);
+    hybrid_tile<FT>(a, W, sm, a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w, lane,
+                    fdt, cnt);
     ++done;
   }
 #pragma unroll

@@ -35,7 +35,7 @@ struct SpecDev {
   int32_t n_layers;
   float z_tol;
   float T0, T_max;
-  float pad0;
+  int32_t k_off;           // z-plane offset in the parent grid (ms_grid.k_offset)
   double A, k, alpha, t_offset;
 };
 
@@ -81,12 +81,35 @@ struct TableArgs {
   double t_a, t_b;
 };
 
+// Active tiles are handed out heaviest first: the active set sorts them into
+// COST_BUCKETS classes by the time k_track last spent on them per level
+// (>= 2x, >= 1x, >= 1/2 x the mean of the previous launch, the rest and
+// unmeasured tiles), one list region of n_tiles entries per class, and the
+// persistent warps pull the classes in order, so the launch's tail is made
+// of the cheapest tiles.  The order never changes a result (tiles are
+// independent).
+constexpr int COST_BUCKETS = 4;
+
 // Work counters of one launch of k_track (device memory, reset per launch).
 struct WorkCounters {
   int32_t n_active;            // tiles in the active list
   int32_t next;                // next list position handed to a warp
   unsigned long long tile_steps_active;  // running total of processed tile-steps
+  int32_t n_bucket[COST_BUCKETS];        // active tiles per cost class
+  uint32_t cost_cnt[2];                  // tiles timed by k_track, by launch parity
+  unsigned long long cost_sum[2];        // their cycles per level, summed
 };
+
+// Position w of the heaviest-first order -> tile index: the classes' list
+// regions (stride entries each) in turn.
+__device__ __forceinline__ int list_tile(const int32_t* list, int stride, const int* nb, int w) {
+#pragma unroll
+  for (int b = 0; b < COST_BUCKETS - 1; ++b) {
+    if (w < nb[b]) return list[int64_t(b) * stride + w];
+    w -= nb[b];
+  }
+  return list[int64_t(COST_BUCKETS - 1) * stride + w];
+}
 
 // Work done by the plain hot kernel (running totals, reset by
 // ms_reset_stats): point x source evaluations of the temperature, and point
@@ -144,6 +167,9 @@ struct TrackArgs {
   int32_t n_sub;               // implicit scheme: substeps per step
   const float* ff;             // far-field weights and nodes (FF_FLOATS), nullptr: off
   float ff_dist;               // far-field distance [m]
+  uint32_t* tile_cost;         // per tile: cycles per level when last processed (nullptr: not timed)
+  int32_t cost_slot;           // launch parity: WorkCounters::cost_sum slot this launch adds to
+  int32_t count_sfu;           // count the model's transcendentals per branch (MS_FLAG_COUNT_OPS)
   // hybrid kernel only
   const void* mlp;             // MlpDev of the attached surrogate
   HybridCounters* hyb;
@@ -163,8 +189,11 @@ struct ActiveArgs {
   int32_t pad;
   double T_thr;
   double T_as_end;             // fixed-point tiles are idle below it
-  int32_t* tile_list;
+  int32_t* tile_list;          // COST_BUCKETS regions of n_tiles entries
   WorkCounters* work;
+  const uint32_t* tile_cost;   // per tile: cycles per level when last processed (nullptr: one class)
+  int32_t prev_slot;           // the previous launch's cost slot (its mean sets the classes)
+  int32_t pad2;
 };
 
 // Arguments of the external-temperature step kernel.
@@ -204,6 +233,12 @@ cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid
                          cudaStream_t stream, bool implicit = false);
 template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads, bool implicit = false);
+// The same FP32 launches with exp2 / log2 on the FMA pipe (ms_kernels_fma.cu,
+// MS_FLAG_FMA_TRANSCENDENTALS).
+cudaError_t launch_track_fma(const TrackArgs<float, float>& a, int block_threads,
+                             int grid_blocks, cudaStream_t stream, bool implicit);
+cudaError_t launch_step_ext_fma(const StepArgs<float, float>& a, int block_threads,
+                                cudaStream_t stream, bool implicit);
 // Verification reductions (k_verify): out[0..2] device doubles.
 cudaError_t launch_verify(const double* a, int64_t na, const double* b, int64_t nb, int64_t n,
                           const int64_t* idx, double* out, cudaStream_t stream);
@@ -212,6 +247,17 @@ cudaError_t launch_verify(const double* a, int64_t na, const double* b, int64_t 
 // temperatures T[i][0 .. n_T - 1] in turn.
 cudaError_t launch_correct(const ModelConstT<double>& m, int64_t n, int n_T, const double* T,
                            double* xas, double* xam, cudaStream_t stream);
+
+// Phase-aware coarsening criterion (ms_coarsen.cu): octants of levels
+// 1 .. n_levels (<= MS_COARSEN_MAX_LEVELS) of a grid, their masks (x fastest,
+// levels in turn) and the number of coarsenable octants per level (device
+// counters).  coarsen_counts fills per_level (may be NULL) and returns the
+// total; the scratch holds the per-octant ranges of two levels.
+int64_t coarsen_counts(const int32_t dims[3], int n_levels, int64_t* per_level);
+size_t coarsen_scratch_bytes(const int32_t dims[3]);
+cudaError_t launch_coarsen(const double* xa, const double* xm, const double* xb,
+                           const int32_t dims[3], double tol, int n_levels, uint8_t* mask,
+                           void* scratch, unsigned long long* n_ok, cudaStream_t stream);
 
 // The stream and the number of points of a context (for the coupled runner).
 void* ctx_stream(ms_ctx* c);

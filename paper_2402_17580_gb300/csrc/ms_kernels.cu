@@ -137,6 +137,8 @@ __global__ void k_src_table(const TableArgs a, WorkCounters* work) {
   if (gt == 0 && work) {
     work->n_active = 0;
     work->next = 0;
+#pragma unroll
+    for (int b = 0; b < COST_BUCKETS; ++b) work->n_bucket[b] = 0;
   }
   const int warp = gt >> 5, lane = threadIdx.x & 31;
   const int n_table = a.n_specs * a.n_levels;
@@ -162,11 +164,13 @@ __global__ void k_fill_f32(float* p, int64_t n, float v) {
 template <typename AT, typename FT, bool IMPL>
 constexpr bool kLockstep = std::is_same<AT, float>::value && std::is_same<FT, float>::value && !IMPL;
 
-// One 128-point tile for the launch's S steps (4 points per lane).
-template <typename AT, typename FT, bool IMPL, bool FAR>
+// One 128-point tile for the launch's S steps (4 points per lane).  OC counts
+// the model's transcendentals per branch (SfuCount, MS_FLAG_COUNT_OPS) or
+// compiles the counting away (NoCount).
+template <typename AT, typename FT, bool IMPL, bool FAR, typename OC>
 __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane,
                                            unsigned long long& n_src, unsigned long long& n_model,
-                                           unsigned& fp_it, unsigned& fp_unconv, SfuCount& oc,
+                                           unsigned& fp_it, unsigned& fp_unconv, OC& oc,
                                            unsigned& n_ex2, unsigned& n_slow,
                                            unsigned long long& ff_nodes,
                                            unsigned long long& ff_pairs) {
@@ -212,6 +216,8 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   const unsigned long long nv = (unsigned long long)(rest < TILE ? rest : TILE);
   unsigned srcs = 0, models = 0, fsrcs = 0;  // per tile: <= 513 levels x slots
   AT T0[4];
+  float xeq[4];          // lockstep path: X_alpha^eq at T0, when have_xeq
+  bool have_xeq = false;
   for (int l = 0; l < a.n_levels; ++l) {  // level 0 only sets T0 (one inlined temps4)
     const SrcLevelT<AT> L = lv[l];
     AT T1[4];
@@ -220,7 +226,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
       if (row && L.axis) {
         int nn, nf;
         temps4_far(L, en + int64_t(l) * a.slots, px, py[0], pz[0], x_first, x_span, ff_dist,
-                   lane, T1, nn, nf);
+                   lane, T1, nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
         srcs += nn;
         fsrcs += nf;
         done_far = true;
@@ -243,13 +249,15 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
         noop = noop && (!valid[q] || !(pz[q] <= zlim) ||
                         step_is_noop<AT, FT>(a.m, T0[q], T1[q], xs[q], xm[q], ax[q]));
     }
-    if (!(skipping && __all_sync(0xffffffffu, noop))) {
+    if (skipping && __all_sync(0xffffffffu, noop)) {
+      have_xeq = false;
+    } else {
       ++models;
       if constexpr (kLockstep<AT, FT, IMPL>) {
         bool run[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) run[q] = valid[q] && pz[q] <= zlim;
-        point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, oc);
+        have_xeq = point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, oc, xeq, have_xeq);
       } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -269,9 +277,11 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   Vec4<FT>::store(a.xas + g0, xs);
   Vec4<FT>::store(a.xam + g0, xm);
   Vec4<float>::store(a.aux + g0, ax);
-  n_ex2 += oc.packed & 0xffffu;
-  n_slow += oc.packed >> 16;
-  oc.packed = 0;
+  if constexpr (std::is_same<OC, SfuCount>::value) {
+    n_ex2 += oc.packed & 0xffffu;
+    n_slow += oc.packed >> 16;
+    oc.packed = 0;
+  }
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
@@ -304,14 +314,14 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
 // Persistent hot kernel: every warp pulls tiles (from the active list, or all
 // tiles) through an atomic cursor until the work runs out, so the grid is
 // sized to the resident capacity and no launch tail is left idle.
-template <typename AT, typename FT, bool IMPL, bool FAR = false>
+template <typename AT, typename FT, bool IMPL, bool FAR = false, bool CNT = false>
 __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
     k_track(const TrackArgs<AT, FT> a) {
   const int lane = threadIdx.x & 31;
   const int n_work = a.tile_list ? a.work->n_active : a.n_tiles;
   unsigned long long done = 0, n_src = 0, n_model = 0;
   unsigned fp_it = 0, fp_unconv = 0;
-  SfuCount oc;
+  std::conditional_t<CNT, SfuCount, NoCount> oc;
   unsigned n_ex2 = 0, n_slow = 0;
   unsigned long long ff_nodes = 0, ff_pairs = 0;
   // far field: every block copies the interpolation weights to shared memory
@@ -320,16 +330,35 @@ __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
     for (int i = threadIdx.x; i < FF_FLOATS; i += blockDim.x) sm[i] = a.ff[i];
     __syncthreads();
   }
+  int nb[COST_BUCKETS];
+#pragma unroll
+  for (int b = 0; b < COST_BUCKETS; ++b) nb[b] = a.tile_list ? a.work->n_bucket[b] : 0;
+  unsigned long long cost_sum = 0;
+  unsigned cost_n = 0;
   for (;;) {
     int w = 0;
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    track_tile<AT, FT, IMPL, FAR>(a, a.tile_list ? a.tile_list[w] : w, lane, n_src, n_model, fp_it,
-                             fp_unconv, oc, n_ex2, n_slow, ff_nodes, ff_pairs);
+    const int tile = a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w;
+    const long long t0 = clock64();
+    track_tile<AT, FT, IMPL, FAR>(a, tile, lane, n_src, n_model, fp_it, fp_unconv, oc, n_ex2,
+                                  n_slow, ff_nodes, ff_pairs);
+    if (a.tile_cost && lane == 0) {  // cycles per level, the next launch's ordering hint
+      const long long dc = clock64() - t0;
+      const unsigned per = unsigned(min(dc / (a.n_levels - 1 > 0 ? a.n_levels - 1 : 1),
+                                        (long long)0x7fffffff));
+      a.tile_cost[tile] = per;
+      cost_sum += per;
+      ++cost_n;
+    }
     ++done;
   }
-  if (a.ops) {
+  if (a.tile_cost && lane == 0 && cost_n) {
+    atomicAdd(&a.work->cost_sum[a.cost_slot & 1], cost_sum);
+    atomicAdd(&a.work->cost_cnt[a.cost_slot & 1], cost_n);
+  }
+  if (CNT && a.ops) {
     unsigned long long e = n_ex2, sl = n_slow;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -399,7 +428,8 @@ __global__ void __launch_bounds__(256) k_step_ext(const StepArgs<AT, FT> a, int 
 #pragma unroll
     for (int q = 0; q < 4; ++q) run[q] = q < cnt;
     NoCount nc;
-    point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, nc);
+    float xeq[4];
+    point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, nc, xeq, false);
     if (cnt > 0) {
       Vec4<float>::store(a.xas + i0, xs);
       Vec4<float>::store(a.xam + i0, xm);
@@ -589,6 +619,80 @@ inline unsigned blocks_for(int64_t n, int threads) {
 
 }  // namespace
 
+// The Crank-Nicolson variants exist for (float, float) and (double, double).
+template <typename AT, typename FT>
+constexpr bool kHasImplicit =
+    (std::is_same<AT, float>::value && std::is_same<FT, float>::value) ||
+    (std::is_same<AT, double>::value && std::is_same<FT, double>::value);
+
+namespace {
+
+// The launches of the hot kernels, internal to this translation unit (the
+// FMA-transcendental variant compiles the same file into other kernels).
+template <typename AT, typename FT>
+cudaError_t track_launch(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
+                         cudaStream_t stream, bool implicit) {
+  if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
+  const unsigned g = unsigned(grid_blocks);
+  if constexpr (std::is_same<AT, float>::value) {
+    if (a.ff) {  // far field: the weights in shared memory
+      const size_t ffb = FF_FLOATS * sizeof(float);
+      if (!implicit) {
+        if (a.count_sfu)
+          k_track<AT, FT, false, true, true><<<g, block_threads, ffb, stream>>>(a);
+        else
+          k_track<AT, FT, false, true><<<g, block_threads, ffb, stream>>>(a);
+      } else if constexpr (kHasImplicit<AT, FT>) {
+        k_track<AT, FT, true, true><<<g, block_threads, ffb, stream>>>(a);
+      } else {
+        return cudaErrorNotSupported;
+      }
+      return cudaGetLastError();
+    }
+  }
+  if (implicit) {
+    if constexpr (kHasImplicit<AT, FT>)
+      k_track<AT, FT, true><<<g, block_threads, 0, stream>>>(a);
+    else
+      return cudaErrorNotSupported;
+  } else if (a.count_sfu) {
+    k_track<AT, FT, false, false, true><<<g, block_threads, 0, stream>>>(a);
+  } else {
+    k_track<AT, FT, false><<<g, block_threads, 0, stream>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename AT, typename FT>
+cudaError_t step_launch(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream,
+                        bool implicit) {
+  if (a.n <= 0) return cudaSuccess;
+  const int vec = ((reinterpret_cast<uintptr_t>(a.T0) | reinterpret_cast<uintptr_t>(a.T1)) & 15) == 0;
+  const unsigned blocks = blocks_for((a.n + 3) / 4, block_threads);
+  if (implicit) {
+    if constexpr (kHasImplicit<AT, FT>)
+      k_step_ext<AT, FT, true><<<blocks, block_threads, 0, stream>>>(a, vec);
+    else
+      return cudaErrorNotSupported;
+  } else {
+    k_step_ext<AT, FT, false><<<blocks, block_threads, 0, stream>>>(a, vec);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#ifdef MS_FMA_TRANSCENDENTALS
+// ----------------------------------- FMA-pipe exp2 / log2 (this file compiled again)
+cudaError_t launch_track_fma(const TrackArgs<float, float>& a, int block_threads,
+                             int grid_blocks, cudaStream_t stream, bool implicit) {
+  return track_launch<float, float>(a, block_threads, grid_blocks, stream, implicit);
+}
+cudaError_t launch_step_ext_fma(const StepArgs<float, float>& a, int block_threads,
+                                cudaStream_t stream, bool implicit) {
+  return step_launch<float, float>(a, block_threads, stream, implicit);
+}
+#else
 // ------------------------------------------------------------- launchers
 template <typename AT>
 cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_t stream) {
@@ -597,7 +701,6 @@ cudaError_t launch_src_table(const TableArgs& a, WorkCounters* work, cudaStream_
   k_src_table<AT><<<blocks_for(n, 128), 128, 0, stream>>>(a, work);
   return cudaGetLastError();
 }
-
 
 cudaError_t launch_fill_f32(float* p, int64_t n, float v, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
@@ -623,12 +726,6 @@ cudaError_t launch_correct(const ModelConstT<double>& m, int64_t n, int n_T, con
   return cudaGetLastError();
 }
 
-// The Crank-Nicolson variants exist for (float, float) and (double, double).
-template <typename AT, typename FT>
-constexpr bool kHasImplicit =
-    (std::is_same<AT, float>::value && std::is_same<FT, float>::value) ||
-    (std::is_same<AT, double>::value && std::is_same<FT, double>::value);
-
 template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads, bool implicit) {
   int nb = 0;
@@ -648,46 +745,13 @@ int track_blocks_per_sm(int block_threads, bool implicit) {
 template <typename AT, typename FT>
 cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
                          cudaStream_t stream, bool implicit) {
-  if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
-  if constexpr (std::is_same<AT, float>::value) {
-    if (a.ff) {  // far field: the weights in shared memory
-      const size_t ffb = FF_FLOATS * sizeof(float);
-      if (!implicit)
-        k_track<AT, FT, false, true><<<unsigned(grid_blocks), block_threads, ffb, stream>>>(a);
-      else if constexpr (kHasImplicit<AT, FT>)
-        k_track<AT, FT, true, true><<<unsigned(grid_blocks), block_threads, ffb, stream>>>(a);
-      else
-        return cudaErrorNotSupported;
-      return cudaGetLastError();
-    }
-  }
-  const size_t smem = 0;
-  if (implicit) {
-    if constexpr (kHasImplicit<AT, FT>)
-      k_track<AT, FT, true><<<unsigned(grid_blocks), block_threads, smem, stream>>>(a);
-    else
-      return cudaErrorNotSupported;
-  } else {
-    k_track<AT, FT, false><<<unsigned(grid_blocks), block_threads, smem, stream>>>(a);
-  }
-  return cudaGetLastError();
+  return track_launch<AT, FT>(a, block_threads, grid_blocks, stream, implicit);
 }
 
 template <typename AT, typename FT>
 cudaError_t launch_step_ext(const StepArgs<AT, FT>& a, int block_threads, cudaStream_t stream,
                             bool implicit) {
-  if (a.n <= 0) return cudaSuccess;
-  const int vec = ((reinterpret_cast<uintptr_t>(a.T0) | reinterpret_cast<uintptr_t>(a.T1)) & 15) == 0;
-  const unsigned blocks = blocks_for((a.n + 3) / 4, block_threads);
-  if (implicit) {
-    if constexpr (kHasImplicit<AT, FT>)
-      k_step_ext<AT, FT, true><<<blocks, block_threads, 0, stream>>>(a, vec);
-    else
-      return cudaErrorNotSupported;
-  } else {
-    k_step_ext<AT, FT, false><<<blocks, block_threads, 0, stream>>>(a, vec);
-  }
-  return cudaGetLastError();
+  return step_launch<AT, FT>(a, block_threads, stream, implicit);
 }
 
 template <typename FT>
@@ -749,5 +813,6 @@ MS_INSTANTIATE(float, float)
 MS_INSTANTIATE(float, double)
 MS_INSTANTIATE(float, KF)
 MS_INSTANTIATE(double, double)
+#endif  // MS_FMA_TRANSCENDENTALS
 
 }  // namespace ms

@@ -117,7 +117,7 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
   if (((reinterpret_cast<uintptr_t>(x_as) | reinterpret_cast<uintptr_t>(x_am) |
         reinterpret_cast<uintptr_t>(aux)) & 15) != 0)
     return ms::record_error(MS_ERR_INVALID_ARG, "state arrays must be 16-byte aligned");
-  if (grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1 ||
+  if (grid->dims[0] < 1 || grid->dims[1] < 1 || grid->dims[2] < 1 || grid->k_offset < 0 ||
       int64_t(grid->dims[0]) * grid->dims[1] * grid->dims[2] != n_points)
     return ms::record_error(MS_ERR_INVALID_ARG, "grid dims do not give n_points");
   const int64_t n_tiles = (n_points + ms::TILE - 1) / ms::TILE;
@@ -156,6 +156,7 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
   s.dx = double(float(grid->spacing[0])); s.dy = double(float(grid->spacing[1]));
   s.dz = double(float(grid->spacing[2]));
   s.nx = grid->dims[0]; s.ny = grid->dims[1]; s.nz = grid->dims[2];
+  s.k_off = grid->k_offset;
   s.n = n_points;
   s.n_tiles = int32_t(n_tiles);
   s.n_tracks = src->n_tracks;

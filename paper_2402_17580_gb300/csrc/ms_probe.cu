@@ -145,3 +145,35 @@ extern "C" int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz) {
   if (s) cudaStreamDestroy(s);
   return rc;
 }
+
+// ------------------------------------------------ transcendentals, evaluated
+namespace ms {
+namespace {
+
+__global__ void k_eval_transcendental(int which, const float* x, float* y, int64_t n) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = x[i];
+  y[i] = which == 0 ? fma_ex2(v) : which == 1 ? fma_lg2(v) : which == 2 ? sfu_ex2(v) : sfu_lg2(v);
+}
+
+}  // namespace
+}  // namespace ms
+
+extern "C" int ms_eval_transcendental(int which, const float* x, float* y, int64_t n) {
+  if (which < 0 || which > 3 || !x || !y || n < 0)
+    return ms::record_error(MS_ERR_INVALID_ARG, "which must be 0..3, x and y non-NULL, n >= 0");
+  if (n == 0) return MS_OK;
+  float* d = nullptr;
+  if (cudaMalloc(&d, size_t(n) * 2 * sizeof(float)) != cudaSuccess)
+    return ms::record_error(MS_ERR_OOM, "device allocation failed");
+  cudaError_t e = cudaMemcpy(d, x, size_t(n) * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    ms::k_eval_transcendental<<<unsigned((n + 255) / 256), 256>>>(which, d, d + n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(y, d + n, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return ms::record_error(MS_ERR_CUDA, cudaGetErrorString(e));
+  return MS_OK;
+}

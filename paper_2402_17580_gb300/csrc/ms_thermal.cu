@@ -264,6 +264,8 @@ int ms_thermal_create(const ms_thermal_params* p, const ms_grid* g, ms_thermal**
     if (g->dims[d] < 1 || !(std::isfinite(g->spacing[d]) && g->spacing[d] != 0.0) ||
         !std::isfinite(g->origin[d]))
       return ms::record_error(MS_ERR_INVALID_ARG, "invalid grid");
+  if (g->k_offset != 0)
+    return ms::record_error(MS_ERR_INVALID_ARG, "the thermal solver takes k_offset = 0 only");
   ms_thermal* th = new (std::nothrow) ms_thermal();
   if (!th) return ms::record_error(MS_ERR_OOM, "host allocation failed");
   auto bail = [&](int rc) { ms_thermal_destroy(th); return rc; };

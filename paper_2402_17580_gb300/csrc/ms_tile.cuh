@@ -25,7 +25,7 @@ __device__ __forceinline__ void point_coords(const SpecDev& sp, int64_t li, AT& 
   const int64_t j = r - k * sp.ny;
   x = AT(sp.ox) + AT(i) * AT(sp.dx);
   y = AT(sp.oy) + AT(j) * AT(sp.dy);
-  z = AT(sp.oz) + AT(k) * AT(sp.dz);
+  z = AT(sp.oz) + AT(k + sp.k_off) * AT(sp.dz);
 }
 
 // Coordinates of the four consecutive local points li0 .. li0 + 3 of a
@@ -69,7 +69,7 @@ __device__ __forceinline__ void point_coords4(const SpecDev& sp, int64_t li0, co
     const int64_t ii = valid[q] ? i : 0, jj = valid[q] ? j : 0, kk = valid[q] ? k : 0;
     x[q] = AT(sp.ox) + AT(ii) * AT(sp.dx);
     y[q] = AT(sp.oy) + AT(jj) * AT(sp.dy);
-    z[q] = AT(sp.oz) + AT(kk) * AT(sp.dz);
+    z[q] = AT(sp.oz) + AT(kk + sp.k_off) * AT(sp.dz);
   }
 }
 
@@ -197,16 +197,16 @@ extern __shared__ float4 ms_ff_smem[];
 // instead of at the 128 points: lane (k, g) = (lane & 7, lane >> 3) evaluates
 // node k (at x_first + x_span s_node) for every fourth far source, the four
 // groups' partial sums are added across the warp, and each lane interpolates
-// its four points with the Lagrange weights [k][point] that k_track keeps in
-// shared memory (ms_ff_smem, FF_FLOATS floats).
-// The other sources are summed point by point as in temps4.  n_near and
-// n_far return the level's two counts (warp-uniform).
+// its four points with the Lagrange weights [k][point] of the table ffw
+// (FF_FLOATS floats: k_track keeps it in shared memory, ms_ff_smem; the
+// hybrid kernel, whose shared memory holds the network, reads it through the
+// caches).  The other sources are summed point by point as in temps4.
+// n_near and n_far return the level's two counts (warp-uniform).
 __device__ __forceinline__ void temps4_far(const SrcLevelT<float>& L, const SrcEntryT<float>* en,
                                            const float* px, float py, float pz, float x_first,
                                            float x_span, float dist, int lane, float* T,
-                                           int& n_near, int& n_far) {
+                                           int& n_near, int& n_far, const float* ffw) {
   constexpr unsigned FULL = 0xffffffffu;
-  const float* ffw = reinterpret_cast<const float*>(ms_ff_smem);
   const float dz2 = depth2<float>(pz, L.z_surf);
   const int g = lane >> 3;
   const float xk = fmaf(x_span, ffw[FF_NODES * TILE + (lane & (FF_NODES - 1))], x_first);
@@ -304,10 +304,18 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
 // two give the same bits (a subset specimen, whose warps hold other points,
 // checks that).  run[q] marks the points to advance; every lane of the warp
 // must call this.
+//
+// xeq carries X_alpha^eq between consecutive steps: the correction of step n
+// evaluates it at T^{n+1}, and the rates of step n + 1 need it at the same
+// temperature, so with have_xeq (warp-uniform: the previous level took the
+// lockstep step) the step reads it instead of evaluating it again (the same
+// operation on the same operand, so the same bits).  Returns whether xeq
+// holds X_alpha^eq(T1) on return.
 template <typename OC>
-__device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const float* T0,
+__device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const float* T0,
                                             const float* T1, float dt, const bool* run,
-                                            float* xs, float* xm, float* ax, OC& oc) {
+                                            float* xs, float* xm, float* ax, OC& oc, float* xeq,
+                                            bool have_xeq) {
   constexpr unsigned FULL = 0xffffffffu;
   using F = Fn<float>;
   float xa[4], xeq0[4];
@@ -319,7 +327,10 @@ __device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const f
     any = any || (run[q] && mid0[q]);
   }
   // X_alpha^eq(T^n) (eq:equilibrium_phase_as)
-  if (__any_sync(FULL, any)) {
+  if (have_xeq) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xeq0[q] = xeq[q];
+  } else if (__any_sync(FULL, any)) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float e = 1.0f - F::ex2(m.kaeq_l2 * (T0[q] - m.T_as_start));
@@ -342,7 +353,7 @@ __device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const f
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (run[q]) point_step<float, float>(m, T0[q], T1[q], dt, xs[q], xm[q], ax[q], oc);
-    return;
+    return false;
   }
 
   // eq:explicit_integration with the rates at T^n; r1 and r3 exclude each
@@ -465,11 +476,14 @@ __device__ __forceinline__ void point_step4(const ModelConstT<float>& m, const f
     }
   }
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < 4; ++q) {
     if (run[q]) {
       xs[q] = nas[q];
       xm[q] = nam[q];
     }
+    xeq[q] = xeq1[q];
+  }
+  return true;
 }
 
 // ---------------------------------------------------------- state access

@@ -8,7 +8,11 @@ only collectives are a barrier and a max of the timings.
 * ``shard_specimens``: size-balanced greedy assignment of whole specimens
   (largest first, to the least-loaded rank); deterministic.
 * ``shard_slabs``: contiguous ranges of z-slabs of one grid (natural order has
-  k slowest, so a slab range is a contiguous range of points).
+  k slowest, so a slab range is a contiguous range of points); ``slab_grid``
+  makes a slab a grid of its own with the parent's coordinates (its
+  ``k_offset``), so that a sharded run is bit-identical to the whole one
+  when the slab boundaries fall on tile boundaries (nx * ny * k0 a multiple
+  of 128 points).
 """
 from __future__ import annotations
 
@@ -37,6 +41,23 @@ def shard_slabs(nz: int, world: int):
         out.append((k, k + n))
         k += n
     return out
+
+
+def slab_grid(grid, k0: int, k1: int):
+    """The z-planes k0 .. k1 - 1 of a grid as a grid of their own (same origin
+    and spacing, k_offset = k0 in the parent's frame), so that its points get
+    the parent's coordinates to the bit."""
+    from dataclasses import replace
+    nx, ny, nz = grid.dims
+    if not 0 <= k0 < k1 <= nz:
+        raise ValueError("slab outside the grid")
+    return replace(grid, dims=(nx, ny, k1 - k0), k_offset=int(getattr(grid, "k_offset", 0)) + k0)
+
+
+def slab_range(grid, k0: int, k1: int):
+    """Natural-order point range [start, stop) of the z-planes k0 .. k1 - 1."""
+    nx, ny, _ = grid.dims
+    return k0 * nx * ny, k1 * nx * ny
 
 
 def imbalance(sizes, parts) -> float:

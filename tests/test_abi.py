@@ -164,6 +164,7 @@ def test_params_check_rules_on_the_host():
                dict(T_thr=inf), dict(precision=7), dict(steps_per_launch=0),
                dict(steps_per_launch=100000), dict(block_threads=48), dict(block_threads=512),
                dict(integrator=2), dict(farfield_dist=-1.0), dict(farfield_dist=nan),
+               dict(tile_order=2), dict(tile_order=-1),
                dict(integrator=b.MS_IMPLICIT, fp_eps_rel=0.0),
                dict(integrator=b.MS_IMPLICIT, fp_eps_abs=-1.0),
                dict(integrator=b.MS_IMPLICIT, fp_max_iter=0),

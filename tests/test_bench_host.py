@@ -104,3 +104,29 @@ def test_profile_summaries_name_their_commands():
         assert "_work/" not in text, f
         if "ncu " in text:
             assert "--clock-control none" in text, f
+
+
+@pytest.mark.parametrize("world", [2, 3, 8])
+def test_strong_scaling_shards_cover_the_instance_once(world):
+    """bench.py --scaling strong: the ranks' shards hold every point of the
+    one instance exactly once, with the instance's coordinates (a slab is a
+    grid of its own whose k_offset keeps the parent's z; the batch's
+    specimens are dealt out whole), and the line divides the whole
+    instance's work by the time."""
+    import numpy as np
+    whole = bench.make_workload("block_256", 0, 1, False)
+    g = whole.specimens[0].grid
+    zs = []
+    for r in range(world):
+        w = bench.make_workload("block_256", r, world, True)
+        assert w.meta["whole_point_updates"] == whole.point_updates
+        sg = w.specimens[0].grid
+        assert sg.dims[:2] == g.dims[:2]
+        zs.append(sg.coords(np.arange(0, sg.n, sg.dims[0] * sg.dims[1]))[2])
+    np.testing.assert_array_equal(np.concatenate(zs),
+                                  g.coords(np.arange(0, g.n, g.dims[0] * g.dims[1]))[2])
+    batch = bench.make_workload("batch_64", 0, 1, False)
+    key = lambda sp: (sp.grid.dims, float(sp.source.t_offset), float(sp.source.tracks[0, 5]))
+    got = sorted(key(sp) for r in range(world)
+                 for sp in bench.make_workload("batch_64", r, world, True).specimens)
+    assert got == sorted(key(sp) for sp in batch.specimens)

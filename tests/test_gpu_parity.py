@@ -322,6 +322,23 @@ def test_active_set_full_block_against_dense_run(ms):
     ctx.close()
 
 
+def test_tile_order_does_not_change_results(ms):
+    """The persistent warps take the active tiles heaviest first (by the
+    cycles the previous launch spent on them) or in index order
+    (ms_params.tile_order); tiles are independent, so the two give the same
+    bits, over several launches whose active sets and classes change."""
+    w = wl.block_256(dims=(128, 48, 12), n_tracks=4, n_steps=2400)
+    out = []
+    for order in (0, 1):
+        ctx, g = gpu_workload(w, steps_per_launch=64, tile_order=order)
+        st = ctx.stats()
+        assert st.tile_steps_active < st.tile_steps_total
+        out.append((np.stack(g), ctx.aux()))
+        ctx.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
 def test_fixed_point_tiles_skip_exactly(ms):
     """A tile whose points all sit on the alpha_s plateau's fixed point
     (X_as = 0.9, X_am = 0, the untouched room-temperature state) stays out of
@@ -447,7 +464,7 @@ def test_model_transcendental_counts(ms, T, xas, xam, ex2, slow):
     grid = wl.Grid((0.0, 0.0, 0.0), (1e-5, 1e-5, -1e-5), (n, 1, 1))
     tracks = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 1.0, 0]], dtype=np.float64)
     src = wl.HeatSource(tracks, np.array([[0.0, 0.0, 1e9, 1e9]]), T0=T)
-    ctx = ms.Context(n, T_thr=0.0)
+    ctx = ms.Context(n, T_thr=0.0, flags=ms._binding.MS_FLAG_COUNT_OPS)
     ctx.set_points([grid])
     ctx.set_state(np.full(n, xas), np.full(n, xam))
     ctx.reset_stats()
@@ -457,6 +474,14 @@ def test_model_transcendental_counts(ms, T, xas, xam, ex2, slow):
     assert st.model_point_steps == n * steps
     assert st.model_sfu_ex2 == ex2 * n * steps
     assert st.model_sfu_slow == slow * n * steps
+    # without MS_FLAG_COUNT_OPS the kernel counts nothing and runs the same steps
+    plain = ms.Context(n, T_thr=0.0)
+    plain.set_points([grid])
+    plain.set_state(np.full(n, xas), np.full(n, xam))
+    plain.run_track([src], steps, 1e-5)
+    assert plain.stats().model_sfu_ex2 == 0
+    np.testing.assert_array_equal(np.stack(plain.fractions()), np.stack(ctx.fractions()))
+    plain.close()
 
 
 def test_farfield_matches_the_direct_sum(ms):

@@ -229,11 +229,13 @@ def test_network_pins_catch_mutant(name, tmp_path):
 # mistakes in the coarsening criterion, caught by tests/test_coarsen_oracle.py
 COARSEN_MUTANTS = {
     "span_half_open": ("slice(i << level, ((i + 1) << level) + 1)", "slice(i << level, (i + 1) << level)"),
-    "strict_tolerance": ("if block.max() - block.min() > tol:", "if block.max() - block.min() >= tol:"),
+    "strict_tolerance": ("1 if all(r <= tol for r in ranges)", "1 if all(r < tol for r in ranges)"),
     "beta_ignored": ("for a in (x_as, x_am, x_beta)]", "for a in (x_as, x_am, x_am)]"),
     "count_rounds_up": ("return (n - 1) // (1 << level)", "return -(-(n - 1) // (1 << level))"),
     "flat_axis_empty": ("    if n == 1:\n        return 1\n", ""),
     "x_y_transposed": (".reshape(nz, ny, nx) for a", ".reshape(nz, nx, ny) for a"),
+    "min_over_one_phase": ("f[sk, sj, si].max() - f[sk, sj, si].min()) for f in fields]",
+                           "f[sk, sj, si].max() - fields[0][sk, sj, si].min()) for f in fields]"),
     "level_width_off_by_one": ("def _span(i, level, n):\n    if n == 1:\n        return slice(0, 1)\n    return slice(i << level,",
                                "def _span(i, level, n):\n    if n == 1:\n        return slice(0, 1)\n    level -= 1\n    return slice(i << level,"),
 }

@@ -48,10 +48,13 @@ NEVER = 1e30               # "no end" time
 
 @dataclass
 class Grid:
-    """Points x = ox + i*dx, y = oy + j*dy, z = oz + k*dz; i fastest."""
+    """Points x = ox + i*dx, y = oy + j*dy, z = oz + (k + k_offset)*dz; i
+    fastest.  k_offset > 0: the z-planes k_offset .. k_offset + nz - 1 of a
+    larger grid with the same origin and spacing (a z-slab shard)."""
     origin: tuple = (0.0, 0.0, 0.0)
     spacing: tuple = (1e-5, 1e-5, -1e-5)
     dims: tuple = (1, 1, 1)
+    k_offset: int = 0
 
     @property
     def n(self) -> int:
@@ -70,7 +73,7 @@ class Grid:
         i, j, k = self.ijk(idx)
         ox, oy, oz = self.origin
         dx, dy, dz = self.spacing
-        return ox + i * dx, oy + j * dy, oz + k * dz
+        return ox + i * dx, oy + j * dy, oz + (k + self.k_offset) * dz
 
 
 @dataclass
