@@ -163,6 +163,13 @@ __global__ void k_fill_f32(float* p, int64_t n, float v) {
 // (point_step4); the other paths call point_step point by point.
 template <typename AT, typename FT, bool IMPL>
 constexpr bool kLockstep = std::is_same<AT, float>::value && std::is_same<FT, float>::value && !IMPL;
+// The wide fraction types (MS_F64ACC, MS_KAHAN) take the same lockstep step on
+// their state rounded to FP32 and add its Euler increments to the wide state
+// (the FP32 arithmetic of the rates and the correction, the wide type only
+// for the accumulation); where g sets a fraction, its FP32 value is taken.
+template <typename AT, typename FT, bool IMPL>
+constexpr bool kLockstepWide = std::is_same<AT, float>::value && !IMPL &&
+                               (std::is_same<FT, double>::value || std::is_same<FT, KF>::value);
 
 // One 128-point tile for the launch's S steps (4 points per lane).  OC counts
 // the model's transcendentals per branch (SfuCount, MS_FLAG_COUNT_OPS) or
@@ -258,6 +265,30 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
 #pragma unroll
         for (int q = 0; q < 4; ++q) run[q] = valid[q] && pz[q] <= zlim;
         have_xeq = point_step4(a.m, T0, T1, a.dt, run, xs, xm, ax, oc, xeq, have_xeq);
+      } else if constexpr (kLockstepWide<AT, FT, IMPL>) {
+        bool run[4];
+        float fs[4], fm[4], du_s[4], du_m[4];
+        unsigned mod = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          run[q] = valid[q] && pz[q] <= zlim;
+          fs[q] = float(xs[q]);
+          fm[q] = float(xm[q]);
+        }
+        have_xeq = point_step4<decltype(oc), true>(a.m, T0, T1, a.dt, run, fs, fm, ax, oc, xeq,
+                                                   have_xeq, du_s, du_m, &mod);
+        if (have_xeq) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (run[q]) {
+              xs[q] = (mod >> (2 * q)) & 1u ? FT(fs[q]) : xs[q] + FT(du_s[q]);
+              xm[q] = (mod >> (2 * q)) & 2u ? FT(fm[q]) : xm[q] + FT(du_m[q]);
+            }
+        } else {  // an initiation in the warp: the per-point step on the wide state
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (run[q]) point_step<AT, FT>(a.m, T0[q], T1[q], a.dt, xs[q], xm[q], ax[q], oc);
+        }
       } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -301,6 +332,18 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   }
 }
 
+// The state of one tile (X_as, X_am, aux) into L2 with bulk prefetches: the
+// padded arrays hold whole tiles, 16-byte aligned.
+template <typename AT, typename FT>
+__device__ __forceinline__ void prefetch_tile_state(const TrackArgs<AT, FT>& a, int tile) {
+  const SpecDev& sp = a.specs[a.tile_spec[tile]];
+  const int64_t g0 = sp.pad_off + int64_t(tile - sp.tile0) * TILE;
+  const unsigned fb = unsigned(TILE * sizeof(FT)), ab = unsigned(TILE * sizeof(float));
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.xas + g0), "r"(fb) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.xam + g0), "r"(fb) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.aux + g0), "r"(ab) : "memory");
+}
+
 // Minimum resident 256-thread blocks per SM for k_track: 3 caps it at 85
 // registers (24 resident warps at 128 threads per block), measured fastest on
 // the 256x256x64 block against 1 (107 registers) and 4 (64, with spills).
@@ -335,24 +378,39 @@ __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
   for (int b = 0; b < COST_BUCKETS; ++b) nb[b] = a.tile_list ? a.work->n_bucket[b] : 0;
   unsigned long long cost_sum = 0;
   unsigned cost_n = 0;
+  // Work is taken in chunks of consecutive positions, so that a launch with
+  // many tiles per warp (one step per launch over a large grid) does not
+  // queue on the cursor's atomic; with about one tile per warp (the active
+  // set of a long launch) the chunk is one tile.  While a tile computes, the
+  // next tile of the chunk has its state prefetched into L2.
+  const int n_warps = int(gridDim.x) * int(blockDim.x >> 5);
+  const int chunk = max(1, min(16, n_work / (8 * n_warps)));
   for (;;) {
-    int w = 0;
-    if (lane == 0) w = atomicAdd(&a.work->next, 1);
-    w = __shfl_sync(0xffffffffu, w, 0);
-    if (w >= n_work) break;
-    const int tile = a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w;
-    const long long t0 = clock64();
-    track_tile<AT, FT, IMPL, FAR>(a, tile, lane, n_src, n_model, fp_it, fp_unconv, oc, n_ex2,
-                                  n_slow, ff_nodes, ff_pairs);
-    if (a.tile_cost && lane == 0) {  // cycles per level, the next launch's ordering hint
-      const long long dc = clock64() - t0;
-      const unsigned per = unsigned(min(dc / (a.n_levels - 1 > 0 ? a.n_levels - 1 : 1),
-                                        (long long)0x7fffffff));
-      a.tile_cost[tile] = per;
-      cost_sum += per;
-      ++cost_n;
+    int w0 = 0;
+    if (lane == 0) w0 = atomicAdd(&a.work->next, chunk);
+    w0 = __shfl_sync(0xffffffffu, w0, 0);
+    if (w0 >= n_work) break;
+    const int w1 = min(w0 + chunk, n_work);
+    int tile = a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w0) : w0;
+    for (int w = w0; w < w1; ++w) {
+      const int next = w + 1 < w1 ? (a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w + 1)
+                                                  : w + 1)
+                                  : -1;
+      if (next >= 0 && lane == 0) prefetch_tile_state(a, next);
+      const long long t0 = clock64();
+      track_tile<AT, FT, IMPL, FAR>(a, tile, lane, n_src, n_model, fp_it, fp_unconv, oc, n_ex2,
+                                    n_slow, ff_nodes, ff_pairs);
+      if (a.tile_cost && lane == 0) {  // cycles per level, the next launch's ordering hint
+        const long long dc = clock64() - t0;
+        const unsigned per = unsigned(min(dc / (a.n_levels - 1 > 0 ? a.n_levels - 1 : 1),
+                                          (long long)0x7fffffff));
+        a.tile_cost[tile] = per;
+        cost_sum += per;
+        ++cost_n;
+      }
+      ++done;
+      tile = next;
     }
-    ++done;
   }
   if (a.tile_cost && lane == 0 && cost_n) {
     atomicAdd(&a.work->cost_sum[a.cost_slot & 1], cost_sum);

@@ -311,11 +311,21 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
 // lockstep step) the step reads it instead of evaluating it again (the same
 // operation on the same operand, so the same bits).  Returns whether xeq
 // holds X_alpha^eq(T1) on return.
-template <typename OC>
+//
+// With INC (the wide fraction types, whose state the caller keeps in FP64 or
+// as a compensated pair and passes here rounded to FP32) the step also
+// returns the Euler increments dt * rate of both fractions (du) and, in mod,
+// which of them the correction g changed (bit 2q for X_as, 2q + 1 for X_am):
+// the caller adds an increment to its wide state, or takes g's FP32 value
+// where g set it.  If a point of the warp takes an initiation (the rare
+// branch), nothing is stepped and false is returned: the caller steps its
+// wide state point by point.
+template <typename OC, bool INC = false>
 __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const float* T0,
                                             const float* T1, float dt, const bool* run,
                                             float* xs, float* xm, float* ax, OC& oc, float* xeq,
-                                            bool have_xeq) {
+                                            bool have_xeq, float* du_as = nullptr,
+                                            float* du_am = nullptr, unsigned* mod = nullptr) {
   constexpr unsigned FULL = 0xffffffffu;
   using F = Fn<float>;
   float xa[4], xeq0[4];
@@ -350,9 +360,11 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
     rare = rare || (run[q] && (ax[q] != 0.0f || enter5 || enter6));
   }
   if (__any_sync(FULL, rare)) {
+    if constexpr (!INC) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (run[q]) point_step<float, float>(m, T0[q], T1[q], dt, xs[q], xm[q], ax[q], oc);
+      for (int q = 0; q < 4; ++q)
+        if (run[q]) point_step<float, float>(m, T0[q], T1[q], dt, xs[q], xm[q], ax[q], oc);
+    }
     return false;
   }
 
@@ -396,8 +408,15 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
       d_as += r2;
       d_am = -r2;
     }
-    nas[q] = xs[q] + float(dt * d_as);
-    nam[q] = xm[q] + float(dt * d_am);
+    if constexpr (INC) {  // rounded product, then rounded sum: the caller adds du exactly so
+      du_as[q] = __fmul_rn(dt, d_as);
+      du_am[q] = __fmul_rn(dt, d_am);
+      nas[q] = __fadd_rn(xs[q], du_as[q]);
+      nam[q] = __fadd_rn(xm[q], du_am[q]);
+    } else {
+      nas[q] = xs[q] + float(dt * d_as);
+      nam[q] = xm[q] + float(dt * d_am);
+    }
     if (run[q]) {
       if (mid0[q]) oc.add(1, 0);
       oc.add(1, 1);                                      // k_as
@@ -474,6 +493,15 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
         if (run[q] && ex) oc.add(1, 0);
       }
     }
+  }
+  if constexpr (INC) {
+    unsigned mk = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (nas[q] != __fadd_rn(xs[q], du_as[q])) mk |= 1u << (2 * q);
+      if (nam[q] != __fadd_rn(xm[q], du_am[q])) mk |= 2u << (2 * q);
+    }
+    *mod = mk;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
