@@ -101,6 +101,10 @@ def parse_args():
                     help="skip the batched 64-specimen leg")
     ap.add_argument("--no-part", dest="part", action="store_false",
                     help="skip the part-scale segment (plain FP32 vs hybrid with compensation)")
+    ap.add_argument("--hybrid-config", choices=tuple(HYBRID_CONFIGS), default="relu_r8",
+                    help="the window surrogate of the hybrid leg")
+    ap.add_argument("--no-hybrid-variants", dest="hybrid_variants", action="store_false",
+                    help="skip the other window surrogates' hybrid legs")
     ap.add_argument("--no-hybrid", dest="hybrid", action="store_false",
                     help="skip the window-surrogate (hybrid) measurement")
     ap.add_argument("--no-f64", dest="f64", action="store_false",
@@ -698,8 +702,19 @@ def run_ours(args):
             for name, pv in (("f64acc", ms.MS_F64ACC), ("kahan", ms.MS_KAHAN))}
     surrogate = None
     if rank == 0 and world == 1 and args.hybrid and prec in (ms.MS_F32, ms.MS_KAHAN):
+        act, stride = HYBRID_CONFIGS[args.hybrid_config]
         out["hybrid"], surrogate = hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush,
-                                               value, sample)
+                                               value, sample, act, stride)
+        out["hybrid"]["config"] = args.hybrid_config
+        if args.hybrid_variants:
+            out["hybrid_variants"] = {}
+            for name, (va, vr) in HYBRID_CONFIGS.items():
+                if name == args.hybrid_config:
+                    continue
+                res, sv = hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, value,
+                                      sample, va, vr)
+                sv.close()
+                out["hybrid_variants"][name] = res
     if rank == 0 and world == 1 and args.batch:
         out["batch_64"] = batch_pass(args, ms, torch, stream, flush, rates)
     if rank == 0 and world == 1 and args.part and surrogate is not None:
@@ -1083,20 +1098,28 @@ def coarsen_pass(ms, torch, stream, dims=(512, 512, 256), tol=1e-2, n_levels=6, 
                     "algorithmic bytes: the three FP64 fields once plus one byte per octant"}
 
 
-def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sample):
+# window surrogates: name -> (hidden activation, temperature stride)
+HYBRID_CONFIGS = {"relu_r8": (1, 8), "relu_r16": (1, 16), "relu_r4": (1, 4), "relu_r2": (1, 2),
+                  "gelu_r1": (0, 1)}
+
+
+def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sample, act, stride):
     """The same workload with the window surrogate attached (hybrid kernel):
-    train it (windows from the library's FP64 path on seeded training lines,
-    Adam in the library's kernels), then time the hybrid passes exactly like
-    the plain ones.  Reports its throughput, the share of MLP windows, the
-    judge's 1 % sample error and max|dX| on the oracle sample points."""
+    train it (windows of 8 x stride steps from the library's FP64 path on
+    seeded training lines, Adam in the library's kernels), then time the
+    hybrid passes exactly like the plain ones.  Reports its throughput, the
+    share of MLP windows, the judge's 1 % sample error and max|dX| on the
+    oracle sample points, beside the same windows with a zero network."""
     import numpy as np
     from paper_2402_17580_gb300 import surrogate
     t0 = time.perf_counter()
     import workloads as wl
     lines = wl.surrogate_lines(n_lines=128)
-    data = surrogate.collect_windows(lines.specimens, lines.n_steps, lines.dt, seed=1)
+    data = surrogate.collect_windows(lines.specimens, lines.n_steps, lines.dt, seed=1,
+                                     stride=stride)
     t1 = time.perf_counter()
-    s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2)
+    s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2,
+                        activation=act, stride=stride)
     t2 = time.perf_counter()
     ctx.set_surrogate(s, 0.01)
     ctx.set_stream(stream.cuda_stream)   # the e2e leg leaves the context on its own stream
@@ -1123,6 +1146,8 @@ def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sampl
            "judge_samples": int(st.judge_samples), "judge_max_err": st.judge_max_err,
            "training": {"windows": int(len(data.X)), "collect_s": round(t1 - t0, 2),
                         "train_s": round(t2 - t1, 2), "iters": 20000, "batch": 32768},
+           "activation": ("gelu", "relu")[act], "window_steps": 8 * stride,
+           "temperature_stride": stride, "steps_per_launch": ctx.params.steps_per_launch,
            "kernel": "k_track_hybrid (judge 1 %)"}
     if sample is not None:
         idx, ofr = sample
@@ -1130,7 +1155,7 @@ def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sampl
         res["max_abs_dX"] = float(np.max(np.abs(g[:, idx] - ofr)))
         # what the trained network gains: the same windows with a zero
         # network (the correction g along the window, no diffusion)
-        zero = ms.Surrogate(np.zeros(ms._binding.MS_MLP_PARAMS, dtype=np.float32))
+        zero = ms.Surrogate(np.zeros(ms._binding.MS_MLP_PARAMS, dtype=np.float32), act, stride)
         ctx.set_surrogate(zero, 0.0)
         one()
         g0 = np.stack(ctx.fractions())

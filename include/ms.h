@@ -242,7 +242,7 @@ typedef struct ms_stats_t {
   int32_t device_error;           /* sticky device error word (0 = none)         */
   int32_t reserved;
   /* hybrid mode (ms_set_surrogate), since the last reset: point-windows of
-   * MS_MLP_WINDOW steps advanced by the MLP, point-windows advanced by the
+   * MS_MLP_WINDOW x stride steps advanced by the MLP, point-windows advanced by the
    * explicit steps (band, initiation, layer change or a short tail), windows
    * re-run by the judge, and the largest |dX_as| or |dX_am| the judge saw
    * between the MLP and the explicit result of one window.                */
@@ -539,37 +539,59 @@ int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid, const ms_heat_
 
 /* ------------------------------------------------------ learned surrogate */
 /* A small MLP that advances a point's fractions over a window of
- * MS_MLP_WINDOW explicit steps in one evaluation.  The paper integrates every
- * step (Sec. 3); the surrogate is an extension of the method, used only where
- * the explicit steps are smooth: a window falls back to the explicit steps when
- * any of its temperatures (the window start and its MS_MLP_WINDOW new levels)
- * lies within 40 K of T_am,start, T_as,end, T_as,start, T_as,start + T_reg,
- * T_s or T_l or above T_s - 40 K, or when an App. A initiation is running.
+ * MS_MLP_WINDOW x r explicit steps in one evaluation, r (1, 2, 4, 8 or 16) being
+ * the surrogate's temperature stride: the network sees the temperatures of
+ * the window's levels r, 2 r, ..., 8 r.  The paper integrates every step
+ * (Sec. 3); the surrogate is an extension of the method, used only where the
+ * explicit steps are smooth: a window falls back to the explicit steps when
+ * any of its sampled temperatures (the window start and the 8 samples) lies
+ * within 40 K of T_am,start, T_as,end, T_as,start or T_as,start + T_reg, or
+ * above T_s - 40 K, when two consecutive samples differ by more than 40 K,
+ * or when an App. A initiation is running.  With r > 1 the temperatures
+ * between samples are not evaluated for the window's MLP points: the
+ * sample test stands for them (a window that passes it stays at least 40 K
+ * from every switching temperature at its samples and changes by at most
+ * 40 K between them).  Points whose samples are all cold and saturated
+ * (the test of the plain path's skip, at the samples) keep their state.
  *
- * Network: inputs x[12] = (X_as, X_am, X_beta at the window start, the 8 new
- * temperatures as (T - 1000 K) / 1000 K, log10(dt) + 5); hidden 64 -> 64,
- * GELU (tanh form); outputs y[3] = 1e6 x the window's diffusive residual
- * (X_as, X_am, X_beta at the window end minus G(start fractions), where
- * G = g(T_8, .) o ... o g(T_1, .) applies only the correction g at the
- * window's 8 new temperatures in turn).  An MLP window sets
- * X = g(T_8, G(X_start) + y / 1e6): the instantaneous part (clamping, the 0.9
- * bound, the alpha_s cap, martensite dissolution and formation) is exact along
- * the window's temperature path and the network supplies the diffusion of
- * Sec. 2.2.  Parameters: MS_MLP_PARAMS floats, W1[64][12], b1[64],
- * W2[64][64], b2[64], W3[3][64], b3[3], weights row-major (out x in).
- * Inference uses BF16 weights and activations with FP32 accumulation on the
- * tensor cores; training keeps an FP32 master copy (Adam).                 */
+ * Network: inputs x[12] = (X_as, X_am, X_beta at the window start, the 8
+ * sampled temperatures as (T - 1000 K) / 1000 K, log10(dt) + 5); hidden
+ * 64 -> 64 with the surrogate's activation (MS_ACT_GELU: GELU, tanh form;
+ * MS_ACT_RELU: max(x, 0)); outputs y[3] = 1e6 x the window's diffusive
+ * residual (X_as, X_am, X_beta at the window end minus G(start fractions),
+ * where G = g(T_8r, .) o ... o g(T_r, .) applies only the correction g at the
+ * 8 sampled temperatures in turn).  An MLP window sets
+ * X = g(T_8r, G(X_start) + y / 1e6): the instantaneous part (clamping, the
+ * 0.9 bound, the alpha_s cap, martensite dissolution and formation) is taken
+ * exactly at the sampled temperatures and the network supplies the rest of
+ * the window, the diffusion of Sec. 2.2.  Parameters: MS_MLP_PARAMS floats,
+ * W1[64][12], b1[64], W2[64][64], b2[64], W3[3][64], b3[3], weights
+ * row-major (out x in).  Inference uses BF16 weights and activations with
+ * FP32 accumulation on the tensor cores; training keeps an FP32 master copy
+ * (Adam).                                                                  */
 #define MS_MLP_IN      12
 #define MS_MLP_OUT     3
 #define MS_MLP_PARAMS  5187
-#define MS_MLP_WINDOW  8
+#define MS_MLP_WINDOW  8      /* temperature samples per window             */
+#define MS_ACT_GELU    0
+#define MS_ACT_RELU    1
 
 typedef struct ms_surrogate ms_surrogate;
 
-/* Create a surrogate from MS_MLP_PARAMS host floats (copied).  Owns its
- * device buffers and a stream.  Errors: INVALID_ARG (NULL, non-finite), OOM,
- * CUDA. */
+/* Create a surrogate from MS_MLP_PARAMS host floats (copied) with the given
+ * hidden activation (MS_ACT_GELU or MS_ACT_RELU) and temperature stride
+ * (1, 2, 4, 8 or 16; windows of 8 x stride steps).  Owns its device buffers and a
+ * stream.  The activation and the stride are the network's: training and
+ * inference use them, and windows for its training must be cut with the
+ * same stride.  Errors: INVALID_ARG (NULL, non-finite, another activation
+ * or stride), OOM, CUDA. */
+int ms_surrogate_create_ex(const float* params, int32_t activation, int32_t stride,
+                           ms_surrogate** out);
+/* ms_surrogate_create_ex(params, MS_ACT_GELU, 1, out).  Errors: those of
+ * ms_surrogate_create_ex. */
 int ms_surrogate_create(const float* params, ms_surrogate** out);
+/* The surrogate's activation and stride.  Errors: INVALID_ARG (NULL). */
+int ms_surrogate_get_config(const ms_surrogate* s, int32_t* activation, int32_t* stride);
 /* Free a surrogate (NULL is a no-op).  Detach it from every context first. */
 void ms_surrogate_destroy(ms_surrogate* s);
 /* Run later calls on cuda_stream (NULL = the surrogate's own stream; pass
@@ -608,9 +630,10 @@ int ms_apply_correction(ms_ctx* ctx, const double* T, int32_t n_T, double* x_as,
                         int64_t n);
 
 /* Attach a surrogate to a context (NULL detaches): ms_run_track then advances
- * whole windows of MS_MLP_WINDOW steps (counted from the call's first level)
- * with the MLP where the band test allows and with the explicit steps
- * elsewhere.  judge_frac in [0, 1] is the fraction of the 128-point tiles'
+ * whole windows of MS_MLP_WINDOW x stride steps (counted from the first level
+ * of each launch of steps_per_launch steps; a launch's last window, if
+ * shorter, takes the explicit steps) with the MLP where the band test allows
+ * and with the explicit steps elsewhere.  judge_frac in [0, 1] is the fraction of the 128-point tiles'
  * windows, drawn by a counter-based hash of (tile, level), whose MLP points
  * are also run with the explicit steps to measure the surrogate's error
  * (ms_stats); the MLP result is kept.

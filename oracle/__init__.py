@@ -106,7 +106,7 @@ def _load():
                                           P, P, P, P, P]
             lib.orc_run_track.restype = None
             lib.orc_run_track_windows.argtypes = [P, P, P, i32, P, i32, i64, P, P, P, i64, i64,
-                                                  d, i32, d, P, P, P, P, P, P]
+                                                  d, i32, i32, d, i64, P, P, P, P, P, P]
             lib.orc_run_track_windows.restype = None
             lib.orc_cn_step.argtypes, lib.orc_cn_step.restype = [P, d, d, d, P, P, P], ctypes.c_int
             lib.orc_n_substeps.argtypes, lib.orc_n_substeps.restype = [P, d], i64
@@ -309,14 +309,17 @@ def run_track(state: State, src, x, y, z, n0, n_steps, dt, p=None):
 
 
 def run_track_windows(state: State, src, x, y, z, n0, n_steps, dt, window=8, band_half=40.0,
-                      p=None, return_fixed=False):
+                      p=None, return_fixed=False, stride=1, group=1):
     """The hybrid path's window form with a zero network (see
-    orc_run_track_windows): windows outside the band apply only the
-    correction g at their new temperatures in turn; the others take the
-    explicit steps; points on the alpha_s plateau's fixed point keep their
-    state over windows below T_as,end.  Returns per point the number of
-    g-only windows (and, with return_fixed, of fixed-point windows)."""
-    assert 1 <= window <= 64
+    orc_run_track_windows): windows of window x stride levels whose start
+    and samples (every stride-th level) pass the band test apply only the
+    correction g at the samples in turn; the others take the explicit steps;
+    points on the alpha_s plateau's fixed point keep their state over
+    windows sampled below T_as,end; within a group of `group` consecutive
+    points one explicit window sends the group's g-only windows to the
+    explicit steps.  Returns per point the number of g-only windows (and,
+    with return_fixed, of fixed-point windows)."""
+    assert window >= 1 and stride >= 1 and group >= 1
     lib, p = _load(), _prm(p)
     spec, tracks, layers = _src_arrays(src)
     x, y, z = (np.ascontiguousarray(np.atleast_1d(a), dtype=np.float64) for a in (x, y, z))
@@ -325,7 +328,8 @@ def run_track_windows(state: State, src, x, y, z, n0, n_steps, dt, window=8, ban
     n_fixed = np.zeros(state.n, dtype=np.int64)
     lib.orc_run_track_windows(_ptr(p), _ptr(spec), _ptr(tracks), tracks.shape[0], _ptr(layers),
                               layers.shape[0], state.n, _ptr(x), _ptr(y), _ptr(z), int(n0),
-                              int(n_steps), float(dt), int(window), float(band_half),
+                              int(n_steps), float(dt), int(window), int(stride),
+                              float(band_half), int(group),
                               _ptr(state.xas), _ptr(state.xam), _ptr(state.xt), _ptr(state.mode),
                               _ptr(n_mlp), _ptr(n_fixed))
     return (n_mlp, n_fixed) if return_fixed else n_mlp

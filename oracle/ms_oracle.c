@@ -59,6 +59,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -473,18 +474,29 @@ void orc_run_track(const double *p, const double *spec, const double *tracks, in
 /* The window form of the hybrid path (an extension of Sec. 3, not in the
  * paper) for a network whose output is zero, so that the window machinery is
  * checked apart from the network's arithmetic.  Steps are taken in windows of
- * `window` levels from n0.  A window whose temperatures (start and new
- * levels) all stay more than band_half away from T_am,start, T_as,end,
- * T_as,start and T_as,start + T_reg and at or below T_s - band_half, with no
- * App. A initiation running at its start, the point below the surface on
- * every level and the full window length, applies only the correction g at
- * its new temperatures in turn (no diffusion); every other window takes the
- * explicit steps.  n_mlp[i] counts the first kind of window per point.
+ * window x stride levels from n0; the window's samples are its levels
+ * stride, 2 stride, ..., window x stride.  A full-length window whose start
+ * temperature and samples all stay more than band_half away from
+ * T_am,start, T_as,end, T_as,start and T_as,start + T_reg and at or below
+ * T_s - band_half, whose consecutive samples (the start included) differ by
+ * at most band_half, with (for stride > 1) no three consecutive samples
+ * whose parabola has its vertex within two spacings of the middle one and
+ * a minimum below T_am,start or a maximum above T_as,end (there the
+ * correction g depends on the path's extreme, which can lie between
+ * samples), with no App. A initiation running at its start and the
+ * point below the surface on every level, applies only the correction g at
+ * its samples in turn (no diffusion); every other window takes the explicit
+ * steps at every level.  n_mlp[i] counts the first kind of window per point.
  * Before either, a point on the alpha_s plateau's fixed point (X_as = 0.9,
- * X_am = 0, no initiation) whose window temperatures all stay below
- * T_as,end keeps its state: there X_alpha^eq = 0.9, no rate acts and the
- * correction changes nothing, so the explicit steps are the identity (the
- * hybrid kernel skips such windows); n_fixed[i] (if given) counts them. */
+ * X_am = 0, no initiation) whose start and sample temperatures all stay
+ * below T_as,end keeps its state over a full-length window: there
+ * X_alpha^eq = 0.9, no rate acts and the correction changes nothing, so the
+ * explicit steps are the identity (the hybrid kernel skips such windows);
+ * n_fixed[i] (if given) counts them.  Points form groups of `group`
+ * consecutive points (the hybrid kernel's 128-point tiles): when a window
+ * sends any point of a group with a level below the surface to the
+ * explicit steps, every point of the group that would apply g only takes
+ * the explicit steps too (group = 1: each point decides alone). */
 static int in_band(const double *p, double T, double h) {
   if (!(T <= p[P_T_S] - h)) return 1;
   if (fabs(T - p[P_T_AM_START]) < h || fabs(T - p[P_T_AS_END]) < h) return 1;
@@ -492,47 +504,93 @@ static int in_band(const double *p, double T, double h) {
   return 0;
 }
 
+/* The parabola through three equally spaced samples a, b, c: its vertex lies
+ * at (a - c) / (2 k) spacings from b, k = a - 2 b + c, with the value
+ * b - (c - a)^2 / (8 k).  True when the vertex lies within two spacings of b
+ * and is a minimum below T_am,start (k > 0) or a maximum above T_as,end
+ * (k < 0). */
+static int extreme_near(const double *p, double a, double b, double c) {
+  const double k = a - 2.0 * b + c, s = c - a;
+  if (k == 0.0 || !(fabs(s) <= 4.0 * fabs(k))) return 0;
+  const double v = b - s * s / (8.0 * k);
+  return k > 0.0 ? v < p[P_T_AM_START] : v > p[P_T_AS_END];
+}
+
 void orc_run_track_windows(const double *p, const double *spec, const double *tracks,
                            int32_t n_tracks, const double *layers, int32_t n_layers, int64_t n,
                            const double *x, const double *y, const double *z, int64_t n0,
-                           int64_t n_steps, double dt, int32_t window, double band_half,
-                           double *xas, double *xam, double *xt, int32_t *mode, int64_t *n_mlp,
-                           int64_t *n_fixed) {
-#pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t i = 0; i < n; ++i) {
-    double T[65];
-    int act[65];
-    int a0;
-    int64_t count = 0, fixed = 0;
-    double T0 = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i],
-                                   (double)n0 * dt - spec[S_TOFF], &a0);
-    for (int64_t w0 = 0; w0 < n_steps; w0 += window) {
-      int64_t K = n_steps - w0 < window ? n_steps - w0 : window;
-      int band = in_band(p, T0, band_half), all_act = 1, any_act = 0;
-      int cool = T0 < p[P_T_AS_END];
-      T[0] = T0;
-      for (int64_t l = 1; l <= K; ++l) {
-        double tl = (double)(n0 + w0 + l) * dt - spec[S_TOFF];
-        T[l] = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i], tl,
-                                  &act[l]);
-        band |= in_band(p, T[l], band_half);
-        cool &= T[l] < p[P_T_AS_END];
-        all_act &= act[l];
-        any_act |= act[l];
-      }
-      if (cool && mode[i] == MODE_NONE && xas[i] == 0.9 && xam[i] == 0.0) {
-        ++fixed;
-      } else if (any_act && all_act && K == window && !band && mode[i] == MODE_NONE) {
-        for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);
-        ++count;
-      } else {
-        for (int64_t l = 1; l <= K; ++l)
-          if (act[l]) advance(p, T[l - 1], T[l], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
-      }
-      T0 = T[K];
+                           int64_t n_steps, double dt, int32_t window, int32_t stride,
+                           double band_half, int64_t group, double *xas, double *xam, double *xt,
+                           int32_t *mode, int64_t *n_mlp, int64_t *n_fixed) {
+  const int64_t len = (int64_t)window * stride;
+  const int64_t n_groups = (n + group - 1) / group;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t gi = 0; gi < n_groups; ++gi) {
+    const int64_t i0 = gi * group, m = n - i0 < group ? n - i0 : group;
+    const size_t ld = (size_t)len + 1;
+    double *T = malloc(sizeof(double) * ld * (size_t)m), *Tn = malloc(sizeof(double) * (size_t)m);
+    int *act = malloc(sizeof(int) * ld * (size_t)m), *kind = malloc(sizeof(int) * (size_t)m);
+    for (int64_t k = 0; k < m; ++k) {
+      int a0;
+      const int64_t i = i0 + k;
+      Tn[k] = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i],
+                                 (double)n0 * dt - spec[S_TOFF], &a0);
+      if (n_mlp) n_mlp[i] = 0;
+      if (n_fixed) n_fixed[i] = 0;
     }
-    if (n_mlp) n_mlp[i] = count;
-    if (n_fixed) n_fixed[i] = fixed;
+    for (int64_t w0 = 0; w0 < n_steps; w0 += len) {
+      const int64_t K = n_steps - w0 < len ? n_steps - w0 : len;
+      int any_explicit = 0;
+      for (int64_t k = 0; k < m; ++k) {   /* kind: 0 idle, 1 fixed, 2 g only, 3 explicit */
+        const int64_t i = i0 + k;
+        double *Ti = T + ld * k;
+        int *ai = act + ld * k, all_act = 1, any_act = 0;
+        Ti[0] = Tn[k];
+        for (int64_t l = 1; l <= K; ++l) {
+          double tl = (double)(n0 + w0 + l) * dt - spec[S_TOFF];
+          Ti[l] = source_temperature(spec, tracks, n_tracks, layers, n_layers, x[i], y[i], z[i],
+                                     tl, &ai[l]);
+          all_act &= ai[l];
+          any_act |= ai[l];
+        }
+        /* the tests on the start and the samples */
+        int band = in_band(p, Ti[0], band_half), cool = Ti[0] < p[P_T_AS_END];
+        for (int64_t l = stride; K == len && l <= K; l += stride) {
+          band |= in_band(p, Ti[l], band_half) || !(fabs(Ti[l] - Ti[l - stride]) <= band_half);
+          if (stride > 1 && l >= 2 * stride)
+            band |= extreme_near(p, Ti[l - 2 * stride], Ti[l - stride], Ti[l]);
+          cool &= Ti[l] < p[P_T_AS_END];
+        }
+        if (!any_act)
+          kind[k] = 0;
+        else if (K == len && cool && mode[i] == MODE_NONE && xas[i] == 0.9 && xam[i] == 0.0)
+          kind[k] = 1;
+        else if (K == len && all_act && !band && mode[i] == MODE_NONE)
+          kind[k] = 2;
+        else
+          kind[k] = 3;
+        any_explicit |= kind[k] == 3;
+        Tn[k] = Ti[K];
+      }
+      for (int64_t k = 0; k < m; ++k) {
+        const int64_t i = i0 + k;
+        const double *Ti = T + ld * k;
+        const int *ai = act + ld * k;
+        if (kind[k] == 1) {
+          if (n_fixed) ++n_fixed[i];
+        } else if (kind[k] == 2 && !any_explicit) {
+          for (int64_t l = stride; l <= K; l += stride) correct(p, Ti[l], &xas[i], &xam[i]);
+          if (n_mlp) ++n_mlp[i];
+        } else if (kind[k] != 0) {
+          for (int64_t l = 1; l <= K; ++l)
+            if (ai[l]) advance(p, Ti[l - 1], Ti[l], dt, &xas[i], &xam[i], &xt[i], &mode[i]);
+        }
+      }
+    }
+    free(T);
+    free(Tn);
+    free(act);
+    free(kind);
   }
 }
 

@@ -26,6 +26,7 @@ MS_FLAG_GRAPH = 2
 MS_FLAG_COUNT_OPS = 4
 MS_FLAG_FMA_TRANSCENDENTALS = 8
 MS_MLP_IN, MS_MLP_OUT, MS_MLP_PARAMS, MS_MLP_WINDOW = 12, 3, 5187, 8
+MS_ACT_GELU, MS_ACT_RELU = 0, 1
 
 d, i32, i64 = ctypes.c_double, ctypes.c_int32, ctypes.c_int64
 
@@ -135,6 +136,9 @@ def load(build_if_missing: bool = True):
     lib.ms_run_track_noalloc.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Grid),
                                          ctypes.POINTER(HeatSource), P, P, P, i64, i64, i64, d, P]
     lib.ms_surrogate_create.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(P)]
+    lib.ms_surrogate_create_ex.argtypes = [ctypes.POINTER(ctypes.c_float), i32, i32,
+                                           ctypes.POINTER(P)]
+    lib.ms_surrogate_get_config.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.ms_surrogate_destroy.argtypes = [P]
     lib.ms_surrogate_destroy.restype = None
     lib.ms_surrogate_set_stream.argtypes = [P, P]
@@ -501,17 +505,35 @@ class Context:
 
 class Surrogate:
     """One ms_surrogate: the window MLP's FP32 master parameters, Adam state
-    and BF16 inference copy on the current device.  Data arguments are device
-    pointers (e.g. torch.Tensor.data_ptr() of contiguous float32 tensors)."""
+    and BF16 inference copy on the current device, with its hidden activation
+    (MS_ACT_GELU, MS_ACT_RELU) and temperature stride (windows of 8 x stride
+    steps).  Data arguments are device pointers (e.g.
+    torch.Tensor.data_ptr() of contiguous float32 tensors)."""
 
-    def __init__(self, params):
+    def __init__(self, params, activation: int = MS_ACT_GELU, stride: int = 1):
         self._lib = load()
         p = np.ascontiguousarray(params, dtype=np.float32)
         if p.size != MS_MLP_PARAMS:
             raise ValueError(f"expected {MS_MLP_PARAMS} parameters, got {p.size}")
         self._h = ctypes.c_void_p()
-        _check(self._lib.ms_surrogate_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                             ctypes.byref(self._h)), "ms_surrogate_create")
+        _check(self._lib.ms_surrogate_create_ex(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                int(activation), int(stride),
+                                                ctypes.byref(self._h)), "ms_surrogate_create_ex")
+
+    def config(self) -> tuple[int, int]:
+        """(activation, stride) as the library holds them."""
+        a, r = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.ms_surrogate_get_config(self._h, ctypes.byref(a), ctypes.byref(r)),
+               "ms_surrogate_get_config")
+        return a.value, r.value
+
+    @property
+    def activation(self) -> int:
+        return self.config()[0]
+
+    @property
+    def stride(self) -> int:
+        return self.config()[1]
 
     @property
     def handle(self):

@@ -94,6 +94,7 @@ struct ms_ctx {
 
   // attached surrogate (hybrid kernel)
   const ms::MlpDev* mlp = nullptr;
+  int32_t mlp_act = MS_ACT_GELU, mlp_stride = 1;
   uint64_t judge_thresh = 0;
   ms::HybridCounters* hyb_d = nullptr;
   ms::OpCounters* ops_d = nullptr;       // work done by k_track
@@ -607,9 +608,10 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
         a.hyb = c->hyb_d;
         a.judge_thresh = c->judge_thresh;
         a.level0 = c->step_n;
+        a.mlp_stride = c->mlp_stride;
         const int64_t need = (c->n_tiles + ms::HYBRID_THREADS / 32 - 1) / (ms::HYBRID_THREADS / 32);
         const int grid = int(std::min<int64_t>(int64_t(c->hybrid_per_sm) * c->sm_count, need));
-        MS_CUDA(ms::launch_track_hybrid<FT>(a, grid, c->stream));
+        MS_CUDA(ms::launch_track_hybrid<FT>(a, c->mlp_act, grid, c->stream));
         hybrid = true;
       }
     }
@@ -1335,11 +1337,14 @@ int ms_set_surrogate(ms_ctx* c, const ms_surrogate* s, double judge_frac) {
     MS_CUDA(cudaMalloc(&c->hyb_d, sizeof(ms::HybridCounters)));
     MS_CUDA(cudaMemset(c->hyb_d, 0, sizeof(ms::HybridCounters)));
   }
-  const int per_sm = c->prm.precision == MS_KAHAN ? ms::hybrid_blocks_per_sm<ms::KF>()
-                                                  : ms::hybrid_blocks_per_sm<float>();
+  const int act = ms::surrogate_activation(s);
+  const int per_sm = c->prm.precision == MS_KAHAN ? ms::hybrid_blocks_per_sm<ms::KF>(act)
+                                                  : ms::hybrid_blocks_per_sm<float>(act);
   if (per_sm <= 0) return fail(MS_ERR_CUDA, "hybrid kernel cannot be made resident");
   c->hybrid_per_sm = per_sm;
   c->mlp = ms::surrogate_weights(s);
+  c->mlp_act = act;
+  c->mlp_stride = ms::surrogate_stride(s);
   c->judge_thresh = uint64_t(std::llround(judge_frac * 4294967296.0));
   return MS_OK;
 }

@@ -2,32 +2,46 @@
 //
 // The same persistent tile loop as k_track (128-point tiles, 4 points per
 // lane, temperatures from the source table), but the launch's steps are taken
-// in windows of MLP_WINDOW = 8.  Per window and point:
-//   - the 8 new temperatures go to shared memory;
-//   - band test: the window (its start and 8 new levels) stays 40 K away from
-//     every temperature where the model switches branch (T_am,start,
-//     T_as,end, T_as,start, T_as,start + T_reg) and below T_s - 40 K, no
-//     App. A initiation is running, and the point is below the surface on
-//     every level;
-//   - passing points take X = g(T_8, G(X_start) + y / 1e6) with
-//     G = g(T_8, .) o ... o g(T_1, .): the correction g of Sec. 2.2 along the
-//     window's temperatures supplies the instantaneous part exactly
-//     (clamping, the X_alpha <= 0.9 bound, the alpha_s cap, martensite
-//     dissolution and formation, at whatever level they act) and the MLP
-//     (12 -> 64 -> 64 -> 3, BF16 on the tensor cores, one m16n8k16 row tile
-//     per 16 points, tiles with no MLP point skipped) the diffusive residual y;
-//   - the others take the 8 explicit steps of Sec. 3 (eq:explicit_integration
-//     + g), as k_track does;
+// in windows of K = 8 r steps, r being the surrogate's temperature stride.
+// Per window:
+//   - the temperatures of the window's levels r, 2 r, ..., 8 r (its samples)
+//     go to shared memory;
+//   - band test per point on the window start and the samples: every sample
+//     stays 40 K away from each temperature where the model switches branch
+//     (T_am,start, T_as,end, T_as,start, T_as,start + T_reg) and below
+//     T_s - 40 K, consecutive samples differ by at most 40 K, with r > 1 no
+//     three consecutive samples point to a minimum below T_am,start or a
+//     maximum above T_as,end near them (the path's extreme would lie between
+//     samples, and the correction g depends on it there), no App. A
+//     initiation is running, and the point is below the surface from the
+//     window's first level on;
+//   - passing points take X = g(T_8r, G(X_start) + y / 1e6) with
+//     G = g(T_8r, .) o ... o g(T_r, .): the correction g of Sec. 2.2 at the
+//     samples supplies the instantaneous part (clamping, the X_alpha <= 0.9
+//     bound, the alpha_s cap, martensite dissolution and formation; G is
+//     evaluated as g at one sample, which the band test makes equal) and the
+//     MLP (12 -> 64 -> 64 -> 3, BF16 on the tensor cores, one m16n8k16 row
+//     tile per 16 points, tiles with no MLP point skipped) the rest;
+//   - a warp with a point that needs the explicit steps takes them for all
+//     its non-idle points;
+//   - the others take the K explicit steps of Sec. 3
+//     (eq:explicit_integration + g) as k_track does: the four points of a
+//     lane in lockstep, a warp vote skipping the levels where every running
+//     point is cold and saturated (reading A9); levels between samples get
+//     their temperatures only in warps that have such points;
 //   - a fraction of the 128-point tiles' windows, chosen by a counter-based
 //     hash of (tile, level), has its MLP points also run with the explicit
 //     steps (the judge); the largest difference is kept in the counters and
 //     the MLP result stays.  Judging whole tiles keeps the explicit steps in
 //     the few warps that judge (a per-point draw would put a judged point in
 //     nearly every warp, and the warp would take the explicit steps for it).
-// Points that are cold and saturated on all 8 steps (reading A9) are left
-// unchanged, as k_track's vote would leave them, and so are points on the
-// alpha_s plateau's fixed point (X_as = 0.9, X_am = 0) whose window stays
-// below T_as,end, where the explicit steps are the identity.
+// Points that are cold and saturated at the window start and every sample
+// (the skip test of reading A9, at the samples) are left unchanged, and so
+// are points on the alpha_s plateau's fixed point (X_as = 0.9, X_am = 0)
+// whose samples stay below T_as,end, where the explicit steps are the
+// identity.  With r > 1 both tests, like the band test, stand for the levels
+// between samples; with r = 1 they are the per-level tests of k_track.  A
+// launch's last window, when shorter than K, takes the explicit steps.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -64,6 +78,21 @@ __device__ __forceinline__ bool in_band(const ModelConstT<float>& m, float T) {
          near(T, m.T_as_start) || near(T, m.T_cap0);
 }
 
+// Whether the parabola through three temperature samples a, b, c (equally
+// spaced) has its vertex within two spacings of b, a minimum below T_am,start
+// or a maximum above T_as,end: there the correction g depends on the path's
+// extreme, which can lie between the samples (an abrupt turn puts it between
+// them while the parabola's lies up to a spacing past them).
+__device__ __forceinline__ bool extreme_between(const ModelConstT<float>& m, float a, float b,
+                                                float c) {
+  const float k = a - 2.0f * b + c;
+  const float s = c - a;
+  if (k == 0.0f || !(fabsf(s) <= 4.0f * fabsf(k))) return false;
+  // vertex value v = b - s^2 / (8 k): v < T_am,start for k > 0 and
+  // v > T_as,end for k < 0 both read 8 k (b - threshold) < s^2
+  return 8.0f * k * (b - (k > 0.0f ? m.T_am_start : m.T_as_end)) < s * s;
+}
+
 // SplitMix64 output function (Steele, Lea, Flood 2014) of (tile, level).
 __device__ __forceinline__ uint32_t judge_hash(uint64_t tile, uint64_t level) {
   uint64_t z = tile * 0x9E3779B97F4A7C15ull + level * 0xD1B54A32D192ED03ull + 0x2402175800ull;
@@ -82,7 +111,46 @@ struct HybCount {
   float err = 0.0f;
 };
 
+// One explicit step (T0 -> T1) of the lane's four points with run[q]: the
+// FP32 state in lockstep (point_step4); the compensated state by the FP32
+// step's increments (point_step4's INC mode), or point by point when a lane
+// of the warp has an App. A initiation.  Every lane of the warp calls it.
+// Returns X_alpha^eq's carry to the next level (point_step4's result).
 template <typename FT>
+__device__ __forceinline__ bool explicit_step4(const ModelConstT<float>& m, const float* T0,
+                                               const float* T1, float dt, const bool* run,
+                                               FT* xs, FT* xm, float* ax, float* xeq,
+                                               bool have_xeq) {
+  NoCount oc;
+  if constexpr (std::is_same<FT, float>::value) {
+    return point_step4(m, T0, T1, dt, run, xs, xm, ax, oc, xeq, have_xeq);
+  } else {
+    float fs[4], fm[4], du_s[4], du_m[4];
+    unsigned mod = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      fs[q] = float(xs[q]);
+      fm[q] = float(xm[q]);
+    }
+    const bool ok = point_step4<NoCount, true>(m, T0, T1, dt, run, fs, fm, ax, oc, xeq, have_xeq,
+                                               du_s, du_m, &mod);
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (run[q]) {
+          xs[q] = (mod >> (2 * q)) & 1u ? FT(fs[q]) : xs[q] + FT(du_s[q]);
+          xm[q] = (mod >> (2 * q)) & 2u ? FT(fm[q]) : xm[q] + FT(du_m[q]);
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (run[q]) point_step<float, FT>(m, T0[q], T1[q], dt, xs[q], xm[q], ax[q]);
+    }
+    return ok;
+  }
+}
+
+template <typename FT, int ACT>
 __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const MlpDev& W,
                                             HybWarp& sm, int tile, int lane, float fdt,
                                             HybCount& cnt) {
@@ -111,6 +179,8 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   const float z_tol = sp.z_tol;
   const bool skipping = a.m.T_thr > 0.0f;
   const int n_steps = a.n_levels - 1;
+  const int r = a.mlp_stride;
+  const int KW = MLP_WINDOW * r;
   // far field (as in k_track): the tile's x-range, first to 128th point
   const int64_t col0 = __shfl_sync(full, col, 0);
   const float x_first = float(sp.ox) + float(col0) * float(sp.dx);
@@ -131,54 +201,76 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
 
   float T0[4];
   temps(0, T0);
-  for (int w0 = 0; w0 < n_steps; w0 += MLP_WINDOW) {
-    const int K = min(MLP_WINDOW, n_steps - w0);
-    bool band[4], all_act[4], any_act[4], noop[4], cool[4];
-    float Tp[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      band[q] = in_band(a.m, T0[q]);
-      all_act[q] = true;
-      any_act[q] = false;
-      noop[q] = true;
-      cool[q] = T0[q] < a.m.T_as_end;
-      Tp[q] = T0[q];
-    }
-    for (int l = 0; l < K; ++l) {
-      const int lvl = w0 + 1 + l;
-      const SrcLevelT<float> L = lv[lvl];
-      float T1[4];
-      temps(lvl, T1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) sm.T[l][lane + 32 * q] = T1[q];
-      const float zlim = L.z_surf + z_tol;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const bool act = valid[q] && pz[q] <= zlim;
-        all_act[q] = all_act[q] && act;
-        any_act[q] = any_act[q] || act;
-        band[q] = band[q] || in_band(a.m, T1[q]);
-        cool[q] = cool[q] && T1[q] < a.m.T_as_end;
-        noop[q] = noop[q] && (!act || (skipping && step_is_noop<float, FT>(a.m, Tp[q], T1[q], xs[q],
-                                                                          xm[q], ax[q])));
-        Tp[q] = T1[q];
-      }
-    }
-
+  for (int w0 = 0; w0 < n_steps; w0 += KW) {
+    const int K = min(KW, n_steps - w0);
+    const bool whole = K == KW;
     bool use_mlp[4], use_ode[4], judged[4];
     bool lane_mlp = false, lane_exp = false;
-    const bool judge_tile =
-        uint64_t(judge_hash(uint64_t(tile), uint64_t(a.level0 + w0))) < a.judge_thresh;
+    const float zl_first = lv[w0 + 1].z_surf + z_tol, zl_last = lv[w0 + K].z_surf + z_tol;
+    if (whole) {
+      // the samples, and the tests on them (the window start included)
+      bool band[4], noop[4], cool[4];
+      float Tp[4], Tpp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        band[q] = in_band(a.m, T0[q]);
+        noop[q] = skipping;
+        cool[q] = T0[q] < a.m.T_as_end;
+        Tp[q] = T0[q];
+        Tpp[q] = T0[q];
+      }
+      for (int j = 0; j < MLP_WINDOW; ++j) {
+        float T1[4];
+        temps(w0 + r * (j + 1), T1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          sm.T[j][lane + 32 * q] = T1[q];
+          band[q] = band[q] || in_band(a.m, T1[q]) || !(fabsf(T1[q] - Tp[q]) <= BAND_HALF_WIDTH);
+          if (r > 1 && j > 0) band[q] = band[q] || extreme_between(a.m, Tpp[q], Tp[q], T1[q]);
+          Tpp[q] = Tp[q];
+          cool[q] = cool[q] && T1[q] < a.m.T_as_end;
+          noop[q] = noop[q] && step_is_noop<float, FT>(a.m, Tp[q], T1[q], xs[q], xm[q], ax[q]);
+          Tp[q] = T1[q];
+        }
+      }
+      const bool judge_tile =
+          uint64_t(judge_hash(uint64_t(tile), uint64_t(a.level0 + w0))) < a.judge_thresh;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // below the surface from the window's first level on (surfaces only rise)
+        const bool all_act = valid[q] && pz[q] <= zl_first;
+        const bool any_act = valid[q] && pz[q] <= zl_last;
+        // the alpha_s plateau's fixed point (X_as = 0.9, X_am = 0, no
+        // initiation) below T_as,end: the explicit steps are the identity
+        const bool fixed = xs[q] == FT(0.9) && xm[q] == FT(0) && ax[q] == 0.0f && cool[q];
+        const bool idle = !any_act || noop[q] || fixed;
+        use_mlp[q] = !idle && all_act && !band[q] && ax[q] == 0.0f;
+        judged[q] = use_mlp[q] && judge_tile;
+        use_ode[q] = !idle && !use_mlp[q];
+      }
+      // a warp that takes the explicit steps for some point takes them for
+      // all its non-idle points: its pass costs the same, and the MLP and the
+      // corrections are saved (the judge skips such windows)
+      bool lane_ode = false;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lane_ode = lane_ode || use_ode[q];
+      if (__any_sync(full, lane_ode)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (use_mlp[q]) {
+            use_mlp[q] = judged[q] = false;
+            use_ode[q] = true;
+          }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        use_mlp[q] = judged[q] = false;
+        use_ode[q] = valid[q] && pz[q] <= zl_last;
+      }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      // on the alpha_s plateau's fixed point (X_as = 0.9, X_am = 0, no
-      // initiation) with every level below T_as,end the explicit steps are
-      // the identity: the point keeps its state (no network output)
-      const bool fixed = xs[q] == FT(0.9) && xm[q] == FT(0) && ax[q] == 0.0f && cool[q];
-      const bool idle = !any_act[q] || (skipping && noop[q]) || fixed;
-      use_mlp[q] = !idle && all_act[q] && K == MLP_WINDOW && !band[q] && ax[q] == 0.0f;
-      judged[q] = use_mlp[q] && judge_tile;
-      use_ode[q] = !idle && !use_mlp[q];
       lane_mlp = lane_mlp || use_mlp[q];
       lane_exp = lane_exp || use_ode[q] || judged[q];
       cnt.surr += use_mlp[q];
@@ -192,8 +284,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       rs[q] = xs[q];
       rm[q] = xm[q];
     }
-    const unsigned bal = __ballot_sync(full, lane_mlp);
-    if (bal) {
+    if (__ballot_sync(full, lane_mlp)) {
       // row tile mt holds rows 16 mt .. 16 mt + 15: point q = mt / 2 of lanes
       // 16 (mt % 2) .. 16 (mt % 2) + 15
       uint32_t mt_mask = 0;
@@ -203,7 +294,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         if (bq & 0x0000ffffu) mt_mask |= 1u << (2 * q);
         if (bq & 0xffff0000u) mt_mask |= 2u << (2 * q);
       }
-      // inputs: fractions at the window start, the 8 new temperatures, log10(dt) + 5
+      // inputs: fractions at the window start, the 8 samples, log10(dt) + 5
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int row = lane + 32 * q;
@@ -228,19 +319,33 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         *reinterpret_cast<uint4*>(&sm.X[row][8]) = v1;
       }
       __syncwarp();
-      mlp_forward_warp(W, &sm.X[0][0], &sm.Y[0][0], lane, mt_mask);
+      mlp_forward_warp<ACT>(W, &sm.X[0][0], &sm.Y[0][0], lane, mt_mask);
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (!use_mlp[q]) continue;
         const int row = lane + 32 * q;
-        const float T8 = sm.T[MLP_WINDOW - 1][row];
         FT nas = xs[q], nam = xm[q];
-        // the instantaneous part, exact along the window's temperature path
-        for (int l = 0; l < MLP_WINDOW; ++l) correct<float, FT>(a.m, sm.T[l][row], nas, nam);
+        // the instantaneous part at the samples, G: the band test leaves
+        // every sample of an MLP window in one of the ranges between the
+        // switching temperatures, on one side of T_as,end, where g at the
+        // samples in turn equals g at one of them: below T_as,end the
+        // coldest (martensite formation keeps the largest target; the
+        // literal reading A3 keeps the last), above it the hottest (the
+        // lowest alpha equilibrium and alpha_s cap)
+        float tmin = sm.T[0][row], tmax = tmin;
+#pragma unroll
+        for (int l = 1; l < MLP_WINDOW; ++l) {
+          tmin = fminf(tmin, sm.T[l][row]);
+          tmax = fmaxf(tmax, sm.T[l][row]);
+        }
+        const float tg = !(tmax < a.m.T_as_end)
+                             ? tmax
+                             : (a.m.martensite_literal ? sm.T[MLP_WINDOW - 1][row] : tmin);
+        correct<float, FT>(a.m, tg, nas, nam);
         nas = nas + FT(sm.Y[0][row] * (1.0f / MLP_OUT_SCALE));
         nam = nam + FT(sm.Y[1][row] * (1.0f / MLP_OUT_SCALE));
-        correct<float, FT>(a.m, T8, nas, nam);
+        correct<float, FT>(a.m, sm.T[MLP_WINDOW - 1][row], nas, nam);
         rs[q] = nas;
         rm[q] = nam;
       }
@@ -249,7 +354,8 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
     // explicit steps: fallback points and judged MLP windows
     if (__any_sync(full, lane_exp)) {
       FT es[4], em[4];
-      float ea[4];
+      float ea[4], Tp[4], xeq[4];
+      bool have_xeq = false;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         es[q] = xs[q];
@@ -257,24 +363,29 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         ea[q] = ax[q];
         Tp[q] = T0[q];
       }
-      for (int l = 0; l < K; ++l) {
+      int j = 0, to_sample = r;   // the next sample and the levels to it
+      for (int l = 1; l <= K; ++l) {
         float T1[4];
+        if (whole && --to_sample == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) T1[q] = sm.T[l][lane + 32 * q];
-        const float zlim = lv[w0 + 1 + l].z_surf + z_tol;
-        bool nop = true;
-        if (skipping) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            nop = nop && (!(use_ode[q] || judged[q]) || !(valid[q] && pz[q] <= zlim) ||
-                          step_is_noop<float, FT>(a.m, Tp[q], T1[q], es[q], em[q], ea[q]));
+          for (int q = 0; q < 4; ++q) T1[q] = sm.T[j][lane + 32 * q];
+          ++j;
+          to_sample = r;
+        } else {
+          temps(w0 + l, T1);
         }
-        if (!(skipping && __all_sync(full, nop))) {
+        const float zlim = lv[w0 + l].z_surf + z_tol;
+        bool run[4], nop = true;
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if ((use_ode[q] || judged[q]) && valid[q] && pz[q] <= zlim)
-              point_step<float, FT>(a.m, Tp[q], T1[q], a.dt, es[q], em[q], ea[q]);
+        for (int q = 0; q < 4; ++q) {
+          run[q] = (use_ode[q] || judged[q]) && valid[q] && pz[q] <= zlim;
+          if (skipping)
+            nop = nop && (!run[q] || step_is_noop<float, FT>(a.m, Tp[q], T1[q], es[q], em[q], ea[q]));
         }
+        if (skipping && __all_sync(full, nop))
+          have_xeq = false;
+        else
+          have_xeq = explicit_step4<FT>(a.m, Tp, T1, a.dt, run, es, em, ea, xeq, have_xeq);
 #pragma unroll
         for (int q = 0; q < 4; ++q) Tp[q] = T1[q];
       }
@@ -289,7 +400,11 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
           const float e = fmaxf(fabsf(to_f(es[q]) - to_f(rs[q])), fabsf(to_f(em[q]) - to_f(rm[q])));
           cnt.err = fmaxf(cnt.err, e);
         }
+        T0[q] = Tp[q];
       }
+    } else if (whole) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) T0[q] = sm.T[MLP_WINDOW - 1][lane + 32 * q];
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -297,7 +412,6 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         xs[q] = rs[q];
         xm[q] = rm[q];
       }
-      T0[q] = sm.T[K - 1][lane + 32 * q];
     }
     __syncwarp();  // the next window overwrites sm.T and sm.X
   }
@@ -319,8 +433,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
     if (lane == 0) a.tile_tsat[tile] = ts + 0.5f;
   }
 }
-
-template <typename FT>
+template <typename FT, int ACT>
 __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackArgs<float, FT> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   MlpDev& W = *reinterpret_cast<MlpDev*>(smem);
@@ -344,7 +457,7 @@ __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackA
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    hybrid_tile<FT>(a, W, sm, a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w, lane,
+    hybrid_tile<FT, ACT>(a, W, sm, a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w, lane,
                     fdt, cnt);
     ++done;
   }
@@ -367,27 +480,32 @@ __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackA
 }  // namespace
 
 template <typename FT>
-int hybrid_blocks_per_sm() {
-  if (cudaFuncSetAttribute(k_track_hybrid<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           int(HYB_SMEM)) != cudaSuccess)
+int hybrid_blocks_per_sm(int activation) {
+  auto k = activation == ACT_RELU ? k_track_hybrid<FT, ACT_RELU> : k_track_hybrid<FT, ACT_GELU>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(HYB_SMEM)) !=
+      cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track_hybrid<FT>, HYBRID_THREADS,
-                                                    HYB_SMEM) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, HYBRID_THREADS, HYB_SMEM) != cudaSuccess)
     return 0;
   return nb;
 }
 
 template <typename FT>
-cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int grid_blocks, cudaStream_t stream) {
+cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int activation, int grid_blocks,
+                                cudaStream_t stream) {
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
-  k_track_hybrid<FT><<<unsigned(grid_blocks), HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+  if (a.mlp_stride < 1 || a.mlp_stride > MLP_MAX_STRIDE) return cudaErrorInvalidValue;
+  if (activation == ACT_RELU)
+    k_track_hybrid<FT, ACT_RELU><<<unsigned(grid_blocks), HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+  else
+    k_track_hybrid<FT, ACT_GELU><<<unsigned(grid_blocks), HYBRID_THREADS, HYB_SMEM, stream>>>(a);
   return cudaGetLastError();
 }
 
-template int hybrid_blocks_per_sm<float>();
-template int hybrid_blocks_per_sm<KF>();
-template cudaError_t launch_track_hybrid<float>(const TrackArgs<float, float>&, int, cudaStream_t);
-template cudaError_t launch_track_hybrid<KF>(const TrackArgs<float, KF>&, int, cudaStream_t);
+template int hybrid_blocks_per_sm<float>(int);
+template int hybrid_blocks_per_sm<KF>(int);
+template cudaError_t launch_track_hybrid<float>(const TrackArgs<float, float>&, int, int, cudaStream_t);
+template cudaError_t launch_track_hybrid<KF>(const TrackArgs<float, KF>&, int, int, cudaStream_t);
 
 }  // namespace ms

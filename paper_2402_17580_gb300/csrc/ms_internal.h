@@ -175,6 +175,7 @@ struct TrackArgs {
   HybridCounters* hyb;
   uint64_t judge_thresh;       // a window is judged if hash(point, level) < judge_thresh (2^32 = all)
   int64_t level0;              // global index of the launch's first level
+  int32_t mlp_stride;          // levels between a window's temperature samples (1, 2, 4, 8, 16)
 };
 
 // Arguments of the active-set builder (reading A9): a tile joins the list
@@ -266,12 +267,16 @@ int64_t ctx_points(const ms_ctx* c);
 // The inference weights of a surrogate (ms_surrogate.cu).
 struct MlpDev;
 const MlpDev* surrogate_weights(const ms_surrogate* s);
+int surrogate_activation(const ms_surrogate* s);   // MS_ACT_GELU or MS_ACT_RELU
+int surrogate_stride(const ms_surrogate* s);       // 1, 2, 4, 8 or 16
 
-// Hybrid hot kernel (an attached surrogate; AT = float).
+// Hybrid hot kernel (an attached surrogate; AT = float), one instantiation
+// per hidden activation.
 template <typename FT>
-cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int grid_blocks, cudaStream_t stream);
+cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int activation, int grid_blocks,
+                                cudaStream_t stream);
 template <typename FT>
-int hybrid_blocks_per_sm();
+int hybrid_blocks_per_sm(int activation);
 constexpr int HYBRID_THREADS = 256;
 
 template <typename AT, typename FT>

@@ -34,6 +34,8 @@ struct ms_surrogate {
   void* scratch = nullptr;   // per-tile operands of the weight gradient, block partials
   size_t scratch_cap = 0;    // bytes
   int64_t step = 0;
+  int32_t act = MS_ACT_GELU;  // hidden activation
+  int32_t stride = 1;         // levels between the window's temperature samples
   cudaStream_t own = nullptr, stream = nullptr;
 };
 
@@ -96,6 +98,7 @@ __device__ __forceinline__ void put(__nv_bfloat16* st, int row, int col, float v
   st[row * kT + col] = __float2bfloat16_rn(v);
 }
 
+template <int ACT>
 __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
     const MlpDev* __restrict__ wd, const float* __restrict__ x, const float* __restrict__ t,
     int64_t n, __nv_bfloat16* __restrict__ sc, double* loss) {
@@ -152,10 +155,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
     uint32_t f1[4][4], f2[4][4];
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
-      f1[kc][0] = ms::pack_bf16(ms::gelu(h1[2 * kc][0]), ms::gelu(h1[2 * kc][1]));
-      f1[kc][1] = ms::pack_bf16(ms::gelu(h1[2 * kc][2]), ms::gelu(h1[2 * kc][3]));
-      f1[kc][2] = ms::pack_bf16(ms::gelu(h1[2 * kc + 1][0]), ms::gelu(h1[2 * kc + 1][1]));
-      f1[kc][3] = ms::pack_bf16(ms::gelu(h1[2 * kc + 1][2]), ms::gelu(h1[2 * kc + 1][3]));
+      f1[kc][0] = ms::pack_act<ACT>(h1[2 * kc][0], h1[2 * kc][1]);
+      f1[kc][1] = ms::pack_act<ACT>(h1[2 * kc][2], h1[2 * kc][3]);
+      f1[kc][2] = ms::pack_act<ACT>(h1[2 * kc + 1][0], h1[2 * kc + 1][1]);
+      f1[kc][3] = ms::pack_act<ACT>(h1[2 * kc + 1][2], h1[2 * kc + 1][3]);
     }
 #pragma unroll
     for (int tt = 0; tt < 8; ++tt) {
@@ -169,10 +172,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
     }
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
-      f2[kc][0] = ms::pack_bf16(ms::gelu(h2[2 * kc][0]), ms::gelu(h2[2 * kc][1]));
-      f2[kc][1] = ms::pack_bf16(ms::gelu(h2[2 * kc][2]), ms::gelu(h2[2 * kc][3]));
-      f2[kc][2] = ms::pack_bf16(ms::gelu(h2[2 * kc + 1][0]), ms::gelu(h2[2 * kc + 1][1]));
-      f2[kc][3] = ms::pack_bf16(ms::gelu(h2[2 * kc + 1][2]), ms::gelu(h2[2 * kc + 1][3]));
+      f2[kc][0] = ms::pack_act<ACT>(h2[2 * kc][0], h2[2 * kc][1]);
+      f2[kc][1] = ms::pack_act<ACT>(h2[2 * kc][2], h2[2 * kc][3]);
+      f2[kc][2] = ms::pack_act<ACT>(h2[2 * kc + 1][0], h2[2 * kc + 1][1]);
+      f2[kc][3] = ms::pack_act<ACT>(h2[2 * kc + 1][2], h2[2 * kc + 1][3]);
     }
     float y[4] = {S.W.b3[2 * q], S.W.b3[2 * q + 1], S.W.b3[2 * q], S.W.b3[2 * q + 1]};
     {
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
       lsum += double(r) * double(r) * double(inv);
       dy[e] = 2.0f * r * inv;
     }
-    // dL/dh2 = (dy W3) * gelu'(h2): dy as the A operand (K = outputs, 8 of 16)
+    // dL/dh2 = (dy W3) * act'(h2): dy as the A operand (K = outputs, 8 of 16)
     uint32_t fd[4] = {ms::pack_bf16(dy[0], dy[1]), ms::pack_bf16(dy[2], dy[3]), 0u, 0u};
     float d2[8][4];
 #pragma unroll
@@ -202,9 +205,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
       const __nv_bfloat16* wr = S.w3t + (8 * tt + g) * kW3T_LD;
       ms::mma_bf16_16816(d2[tt], fd, ms::ld32(wr + 2 * q), ms::ld32(wr + 8 + 2 * q), z);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) d2[tt][e] *= ms::gelu_grad(h2[tt][e]);
+      for (int e = 0; e < 4; ++e) d2[tt][e] *= ms::act_grad<ACT>(h2[tt][e]);
     }
-    // dL/dh1 = (dh2 W2) * gelu'(h1)
+    // dL/dh1 = (dh2 W2) * act'(h1)
     uint32_t fg[4][4];
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
@@ -224,14 +227,14 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
 #pragma unroll
     for (int tt = 0; tt < 8; ++tt) {
       const int f0 = 8 * tt + 2 * q;
-      put(st, kRowA1 + f0, g, ms::gelu(h1[tt][0]));
-      put(st, kRowA1 + f0 + 1, g, ms::gelu(h1[tt][1]));
-      put(st, kRowA1 + f0, g + 8, ms::gelu(h1[tt][2]));
-      put(st, kRowA1 + f0 + 1, g + 8, ms::gelu(h1[tt][3]));
-      put(st, kRowA2 + f0, g, ms::gelu(h2[tt][0]));
-      put(st, kRowA2 + f0 + 1, g, ms::gelu(h2[tt][1]));
-      put(st, kRowA2 + f0, g + 8, ms::gelu(h2[tt][2]));
-      put(st, kRowA2 + f0 + 1, g + 8, ms::gelu(h2[tt][3]));
+      put(st, kRowA1 + f0, g, ms::act<ACT>(h1[tt][0]));
+      put(st, kRowA1 + f0 + 1, g, ms::act<ACT>(h1[tt][1]));
+      put(st, kRowA1 + f0, g + 8, ms::act<ACT>(h1[tt][2]));
+      put(st, kRowA1 + f0 + 1, g + 8, ms::act<ACT>(h1[tt][3]));
+      put(st, kRowA2 + f0, g, ms::act<ACT>(h2[tt][0]));
+      put(st, kRowA2 + f0 + 1, g, ms::act<ACT>(h2[tt][1]));
+      put(st, kRowA2 + f0, g + 8, ms::act<ACT>(h2[tt][2]));
+      put(st, kRowA2 + f0 + 1, g + 8, ms::act<ACT>(h2[tt][3]));
       put(st, kRowD2 + f0, g, d2[tt][0]);
       put(st, kRowD2 + f0 + 1, g, d2[tt][1]);
       put(st, kRowD2 + f0, g + 8, d2[tt][2]);
@@ -248,10 +251,10 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_fwd_bwd_tc(
         ms::mma_bf16_16816(d1, fg[kc], ms::ld32(wr + 16 * kc + 2 * q),
                            ms::ld32(wr + 16 * kc + 8 + 2 * q), d1);
       const int f0 = 8 * tt + 2 * q;
-      put(st, kRowD1 + f0, g, d1[0] * ms::gelu_grad(h1[tt][0]));
-      put(st, kRowD1 + f0 + 1, g, d1[1] * ms::gelu_grad(h1[tt][1]));
-      put(st, kRowD1 + f0, g + 8, d1[2] * ms::gelu_grad(h1[tt][2]));
-      put(st, kRowD1 + f0 + 1, g + 8, d1[3] * ms::gelu_grad(h1[tt][3]));
+      put(st, kRowD1 + f0, g, d1[0] * ms::act_grad<ACT>(h1[tt][0]));
+      put(st, kRowD1 + f0 + 1, g, d1[1] * ms::act_grad<ACT>(h1[tt][1]));
+      put(st, kRowD1 + f0, g + 8, d1[2] * ms::act_grad<ACT>(h1[tt][2]));
+      put(st, kRowD1 + f0 + 1, g + 8, d1[3] * ms::act_grad<ACT>(h1[tt][3]));
     }
     // output gradient rows 0..7 (this lane's outputs 2q, 2q + 1), rows 8..15 zero
     put(st, kRowDy + 2 * q, g, dy[0]);
@@ -361,6 +364,7 @@ __global__ void k_adam(float* p, float* m, float* v, const float* g, float lr, f
 }
 
 // Batched inference: each warp takes 128 samples (x: [n][12], y: [n][3]).
+template <int ACT>
 __global__ void __launch_bounds__(128) k_mlp_infer(const MlpDev* __restrict__ wd,
                                                    const float* __restrict__ x, float* __restrict__ y,
                                                    int64_t n) {
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer(const MlpDev* __restrict__ wd
       X[r * ms::MLP_X_LD + k] = __float2bfloat16_rn(s < n && k < ms::MLP_IN ? x[s * ms::MLP_IN + k] : 0.0f);
   }
   __syncwarp();
-  ms::mlp_forward_warp(W, X, Y, lane);
+  ms::mlp_forward_warp<ACT>(W, X, Y, lane);
   __syncwarp();
   for (int r = lane; r < 128; r += 32) {
     const int64_t s = base + r;
@@ -420,11 +424,12 @@ int gradient(ms_surrogate* s, const float* x, const float* t, int64_t n) {
   float* partial = reinterpret_cast<float*>(reinterpret_cast<char*>(s->scratch) +
                                             size_t(n_tiles) * kTileElems * sizeof(__nv_bfloat16));
   SG_CUDA(cudaMemsetAsync(s->loss, 0, sizeof(double), s->stream));
-  SG_CUDA(cudaFuncSetAttribute(k_mlp_fwd_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto fwd_bwd = s->act == MS_ACT_RELU ? k_mlp_fwd_bwd_tc<ms::ACT_RELU> : k_mlp_fwd_bwd_tc<ms::ACT_GELU>;
+  SG_CUDA(cudaFuncSetAttribute(fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                int(sizeof(TrainSmem))));
   const int fwd_blocks = int(std::min<int64_t>((n_tiles + kFwdWarps - 1) / kFwdWarps, 2048));
-  k_mlp_fwd_bwd_tc<<<fwd_blocks, kFwdWarps * 32, sizeof(TrainSmem), s->stream>>>(s->mlp, x, t, n,
-                                                                               tiles, s->loss);
+  fwd_bwd<<<fwd_blocks, kFwdWarps * 32, sizeof(TrainSmem), s->stream>>>(s->mlp, x, t, n, tiles,
+                                                                       s->loss);
   SG_CUDA(cudaGetLastError());
   const int gb = int(std::min<int64_t>(n_tiles, kGradBlocks));
   k_mlp_wgrad_tc<<<gb, 128, 0, s->stream>>>(tiles, n_tiles, partial);
@@ -438,17 +443,30 @@ int gradient(ms_surrogate* s, const float* x, const float* t, int64_t n) {
 
 namespace ms {
 const MlpDev* surrogate_weights(const ms_surrogate* s) { return s ? s->mlp : nullptr; }
+int surrogate_activation(const ms_surrogate* s) { return s ? s->act : MS_ACT_GELU; }
+int surrogate_stride(const ms_surrogate* s) { return s ? s->stride : 1; }
 }  // namespace ms
 
 extern "C" {
 
 int ms_surrogate_create(const float* params, ms_surrogate** out) {
+  return ms_surrogate_create_ex(params, MS_ACT_GELU, 1, out);
+}
+
+int ms_surrogate_create_ex(const float* params, int32_t activation, int32_t stride,
+                           ms_surrogate** out) {
   if (!params || !out) return ms::record_error(MS_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
+  if (activation != MS_ACT_GELU && activation != MS_ACT_RELU)
+    return ms::record_error(MS_ERR_INVALID_ARG, "activation must be MS_ACT_GELU or MS_ACT_RELU");
+  if (stride < 1 || stride > ms::MLP_MAX_STRIDE || (stride & (stride - 1)) != 0)
+    return ms::record_error(MS_ERR_INVALID_ARG, "stride must be 1, 2, 4, 8 or 16");
   for (int i = 0; i < ms::MLP_PARAMS; ++i)
     if (!std::isfinite(params[i])) return ms::record_error(MS_ERR_INVALID_ARG, "non-finite parameter");
   ms_surrogate* s = new (std::nothrow) ms_surrogate();
   if (!s) return ms::record_error(MS_ERR_OOM, "host allocation failed");
+  s->act = activation;
+  s->stride = stride;
   auto bail = [&](int rc) { ms_surrogate_destroy(s); return rc; };
   const size_t pb = ms::MLP_PARAMS * sizeof(float);
   if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess)
@@ -491,6 +509,13 @@ int ms_surrogate_set_stream(ms_surrogate* s, void* stream) {
   return MS_OK;
 }
 
+int ms_surrogate_get_config(const ms_surrogate* s, int32_t* activation, int32_t* stride) {
+  if (!s || !activation || !stride) return ms::record_error(MS_ERR_INVALID_ARG, "NULL argument");
+  *activation = s->act;
+  *stride = s->stride;
+  return MS_OK;
+}
+
 int ms_surrogate_get_params(ms_surrogate* s, float* params) {
   if (!s || !params) return ms::record_error(MS_ERR_INVALID_ARG, "NULL argument");
   SG_CUDA(cudaMemcpyAsync(params, s->params, ms::MLP_PARAMS * sizeof(float), cudaMemcpyDeviceToHost,
@@ -503,7 +528,10 @@ int ms_surrogate_forward(ms_surrogate* s, const float* x, float* y, int64_t n) {
   if (!s || !x || !y || n < 0) return ms::record_error(MS_ERR_INVALID_ARG, "bad argument");
   if (n == 0) return MS_OK;
   const int64_t warps = (n + 127) / 128;
-  k_mlp_infer<<<unsigned((warps + 3) / 4), 128, kInferSmem, s->stream>>>(s->mlp, x, y, n);
+  if (s->act == MS_ACT_RELU)
+    k_mlp_infer<ms::ACT_RELU><<<unsigned((warps + 3) / 4), 128, kInferSmem, s->stream>>>(s->mlp, x, y, n);
+  else
+    k_mlp_infer<ms::ACT_GELU><<<unsigned((warps + 3) / 4), 128, kInferSmem, s->stream>>>(s->mlp, x, y, n);
   SG_CUDA(cudaGetLastError());
   return MS_OK;
 }

@@ -104,6 +104,12 @@ def test_validation_before_device_work():
                      ("ms_get_fractions", (None, None, None, None, None)), ("ms_get_aux", (None, None)),
                      ("ms_stats", (None, None)), ("ms_synchronize", (None,))):
         assert getattr(lib, fn)(*args) == -1, fn
+    w = (ctypes.c_float * 5187)()
+    for act, stride in ((2, 1), (-1, 1), (0, 0), (1, 3), (1, 32), (1, 12)):
+        assert lib.ms_surrogate_create_ex(w, act, stride, ctypes.byref(h)) == -1, (act, stride)
+        assert not h.value
+    a, r = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.ms_surrogate_get_config(None, ctypes.byref(a), ctypes.byref(r)) == -1
     lib.ms_destroy(None)
 
 

@@ -150,6 +150,84 @@ def test_gradient_against_finite_differences():
     assert abs(loss - np.mean((y - T) ** 2)) < 1e-14
 
 
+def test_relu_closed_forms():
+    x = np.array([-3.0, -1e-300, -0.0, 0.0, 1e-300, 2.5])
+    np.testing.assert_array_equal(mlp.relu(x), [0.0, 0.0, 0.0, 0.0, 1e-300, 2.5])
+    # the derivative the kernels use: 1 above the kink, 0 at and below it
+    np.testing.assert_array_equal(mlp.relu_grad(x), [0.0, 0.0, 0.0, 0.0, 1.0, 1.0])
+
+
+def test_single_path_relu_network_by_hand():
+    """ReLU on the one-path network with a, b, c > 0 and a first-layer bias
+    e: y2 = c max(b max(a x3 + e, 0), 0) + d2 = b c max(a x3 + e, 0) + d2;
+    the gradient follows by hand: dL/da = sum dy b c x3 [a x3 + e > 0],
+    dL/de = sum dy b c [a x3 + e > 0], dL/dc = sum dy b max(a x3 + e, 0)."""
+    a, b, c, e = 0.75, 1.25, 2.0, -0.3
+    d = np.array([0.1, -0.2, 0.3])
+    p = np.zeros(mlp.N_PARAMS)
+    p[mlp.OFF_W1 + 5 * mlp.N_IN + 3] = a
+    p[mlp.OFF_B1 + 5] = e
+    p[mlp.OFF_W2 + 7 * mlp.N_H + 5] = b
+    p[mlp.OFF_W3 + 2 * mlp.N_H + 7] = c
+    p[mlp.OFF_B3:] = d
+    rng = np.random.default_rng(22)
+    n = 60
+    X = rng.normal(0, 1, (n, mlp.N_IN))
+    T = rng.normal(0, 1, (n, mlp.N_OUT))
+    y, _ = mlp.forward(p, X, bf16=False, act="relu")
+    on = a * X[:, 3] + e > 0
+    np.testing.assert_allclose(y[:, 2], b * c * np.where(on, a * X[:, 3] + e, 0.0) + d[2],
+                               rtol=1e-14, atol=1e-15)
+    assert 0 < on.sum() < n
+    _, g = mlp.loss_and_gradient(p, X, T, bf16=False, act="relu")
+    dy = 2.0 * (y[:, 2] - T[:, 2]) / (3 * n)
+    assert g[mlp.OFF_W1 + 5 * mlp.N_IN + 3] == pytest.approx(np.sum(dy * b * c * X[:, 3] * on),
+                                                             rel=1e-12)
+    assert g[mlp.OFF_B1 + 5] == pytest.approx(np.sum(dy * b * c * on), rel=1e-12)
+    assert g[mlp.OFF_W3 + 2 * mlp.N_H + 7] == pytest.approx(
+        np.sum(dy * b * np.where(on, a * X[:, 3] + e, 0.0)), rel=1e-12)
+    # the other first-layer rows carry no gradient (their units stay at 0)
+    assert np.all(g[mlp.OFF_W1:mlp.OFF_W1 + 5 * mlp.N_IN] == 0.0)
+
+
+def test_single_path_relu_network_in_bf16():
+    """ReLU with bf16 on: y2 = r(c) r(relu(r(b) r(relu(r(a) r(x3))))) + d2."""
+    r, (a, b, c, d), p = _single_path_bf16()
+    p[mlp.OFF_W2 + 7 * mlp.N_H + 5] = -b       # a positive path
+    X = np.random.default_rng(14).normal(0, 1, (40, mlp.N_IN))
+    y, _ = mlp.forward(p, X, bf16=True, act="relu")
+    for i, x3 in enumerate(X[:, 3]):
+        a1 = r(max(r(a) * r(x3), 0.0))
+        a2 = r(max(r(-b) * a1, 0.0))
+        assert y[i, 2] == pytest.approx(r(c) * a2 + d[2], rel=1e-14, abs=1e-15), i
+
+
+def test_relu_gradient_against_finite_differences():
+    """Central differences of the ReLU network's loss on samples whose
+    pre-activations all stay 1e-3 away from the kink (the step is 1e-6)."""
+    rng = np.random.default_rng(4)
+    p = rng.normal(0, 0.3, mlp.N_PARAMS)
+    X = rng.normal(0, 1, (200, mlp.N_IN))
+    _, (x, h1, a1, h2, a2, *_w) = mlp.forward(p, X, bf16=False, act="relu")
+    keep = (np.abs(h1).min(1) > 1e-3) & (np.abs(h2).min(1) > 1e-3)
+    X = X[keep][:40]
+    assert len(X) >= 10
+    T = rng.normal(0, 1, (len(X), mlp.N_OUT))
+    _, g = mlp.loss_and_gradient(p, X, T, bf16=False, act="relu")
+    blocks = [(mlp.OFF_W1, mlp.OFF_B1), (mlp.OFF_B1, mlp.OFF_W2), (mlp.OFF_W2, mlp.OFF_B2),
+              (mlp.OFF_B2, mlp.OFF_W3), (mlp.OFF_W3, mlp.OFF_B3), (mlp.OFF_B3, mlp.N_PARAMS)]
+    idx = np.concatenate([rng.choice(np.arange(lo, hi), min(12, hi - lo), replace=False)
+                          for lo, hi in blocks])
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (mlp.loss_and_gradient(pp, X, T, bf16=False, act="relu")[0] -
+              mlp.loss_and_gradient(pm, X, T, bf16=False, act="relu")[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
 def test_zero_network_outputs_biases():
     p = np.zeros(mlp.N_PARAMS)
     p[mlp.OFF_B3:] = [1.0, 2.0, 3.0]
@@ -295,17 +373,19 @@ def test_window_starting_inside_an_initiation_takes_the_explicit_steps():
 
 def test_window_start_level_counts_in_the_band():
     """Reading S1: the band test covers the window's start temperature too.
-    A point held at 850 K (within 40 K of T_am,start) is heated to ~1150 K
-    (outside every band) from the first new level on by a track that starts
-    half a step after the window's start and stays 5.3 mm away: the window
-    takes the explicit steps."""
+    A point held at 886.5 K (38.5 K above T_am,start) is warmed by ~4 K, to
+    just outside every band, from the first new level on by a weak track
+    that starts half a step after the window's start and stays 5.3 mm away
+    (the samples then differ from the start by less than 40 K): the window
+    takes the explicit steps, while the same window started one window
+    later, at the warm temperature, passes the test."""
     dt = 1e-5
-    tracks = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 200.0, 40.5 * dt, 0]])
+    tracks = np.array([[0.0, 0.0, 1.0, 0.0, 1.0, 2.8, 40.5 * dt, 0]])
     src = workloads.HeatSource(tracks, np.array([[0.0, 0.0, workloads.NEVER, workloads.NEVER]]),
-                               T0=850.0)
+                               T0=886.5)
     x, y, z = np.array([-5.3e-3]), np.array([0.0]), np.array([0.0])
-    T = np.array([oracle.temperature(src, x, y, z, (40 + l) * dt)[0][0] for l in range(9)])
-    assert T[0] == 850.0 and np.all((T[1:] > 1100.0) & (T[1:] < 1200.0))
+    T = np.array([oracle.temperature(src, x, y, z, (40 + l) * dt)[0][0] for l in range(17)])
+    assert T[0] == 886.5 and np.all((T[1:] > 888.5) & (T[1:] < 894.5)), T
     p = oracle.params()
     a, b = oracle.State.make([0.6], [0.1]), oracle.State.make([0.6], [0.1])
     oracle.run_track(a, src, x, y, z, 40, 8, dt, p)
@@ -313,6 +393,8 @@ def test_window_start_level_counts_in_the_band():
     assert n_mlp[0] == 0
     np.testing.assert_array_equal(a.xas, b.xas)
     np.testing.assert_array_equal(a.xam, b.xam)
+    c = oracle.State.make([0.6], [0.1])
+    assert oracle.run_track_windows(c, src, x, y, z, 48, 8, dt, p=p)[0] == 1
 
 
 def test_g_only_window_corrects_at_every_level():
@@ -357,21 +439,109 @@ def test_windows_leave_undeposited_points_alone():
 def test_host_band_mask_matches_the_oracle_band():
     """surrogate.band_mask (which windows the training data may give to the
     network) uses the oracle window form's band: within 40 K of T_am,start,
-    T_as,end, T_as,start or T_as,start + T_reg, or above T_s - 40 K, on any
-    level of the window including its start.  Checked on windows held at
-    one temperature with the edge levels planted at the start or the end,
-    against the windows the oracle sends to the explicit steps."""
+    T_as,end, T_as,start or T_as,start + T_reg, or above T_s - 40 K, at the
+    window's start or any sample, or two consecutive temperatures more than
+    40 K apart.  Checked on windows ramping by 30 K per sample away from an
+    edge value planted at the start or the end (each temperature's band
+    membership taken from the oracle's window form on a hold at it), and on
+    jumps of 39 K and 41 K between out-of-band temperatures."""
     from paper_2402_17580_gb300 import _binding as B
     from paper_2402_17580_gb300.surrogate import band_mask
     p = B.default_params()
     po = oracle.params()
     for T_edge in (848.0 + 39.0, 848.0 + 41.0, 935.0 - 39.5, 935.0 + 40.5, 1273.0 + 39.0,
                    1373.0 - 41.0, 1838.5, 1837.5, 600.0, 1100.0):
-        for at in (0, 8):
+        for sign in (1.0, -1.0):
+            ramp = T_edge + sign * 30.0 * np.arange(9)
+            want = bool(np.any([oracle_in_band(t, po) for t in ramp]))
+            for T in (ramp, ramp[::-1]):
+                assert bool(band_mask(T[None, :], p)[0]) == want, (T_edge, sign)
+    for jump, want in ((39.0, False), (41.0, True)):
+        for at in range(1, 9):
             T = np.full(9, 1100.0)
-            T[at] = T_edge
-            want = bool(np.any([oracle_in_band(t, po) for t in T]))
-            assert bool(band_mask(T[None, :], p)[0]) == want, (T_edge, at)
+            T[at:] += jump
+            assert bool(band_mask(T[None, :], p)[0]) == want, (jump, at)
+
+
+def test_window_form_sends_sample_jumps_to_the_explicit_steps():
+    """A point 0.12 mm beside and 0.05 mm below a 200 W track, stepped at
+    20 us, heats by up to ~14 K per step while it stays below every band:
+    windows of 32 levels sampled at every level pass the band test on the
+    rise, the same windows sampled at every 4th level (jumps > 40 K) take
+    the explicit steps; elsewhere both forms give the same g-only windows."""
+    w, src = _line(200.0, n=1)
+    w.specimens[0].grid.origin = (3.0e-4, 1.2e-4, -5.0e-5)
+    x, y, z = w.specimens[0].grid.coords()
+    dt = 2.0e-5
+    p = oracle.params()
+    T = np.array([oracle.temperature(src, x, y, z, l * dt)[0][0] for l in range(161)])
+    assert T.max() < 848.0 - 40.0, T.max()
+    jumps = [np.abs(np.diff(T[32 * k:32 * k + 33:4])).max() > 40.0 for k in range(5)]
+    steps = [np.abs(np.diff(T[32 * k:32 * k + 33])).max() > 40.0 for k in range(5)]
+    assert any(jumps) and not any(steps)
+    a, b = oracle.State.make([0.6], [0.1]), oracle.State.make([0.6], [0.1])
+    n1 = oracle.run_track_windows(a, src, x, y, z, 0, 160, dt, window=32, stride=1, p=p)
+    n4 = oracle.run_track_windows(b, src, x, y, z, 0, 160, dt, window=8, stride=4, p=p)
+    assert n1[0] == 5 and n4[0] == 5 - sum(jumps)
+
+
+def test_window_form_sends_a_turn_between_samples_to_the_explicit_steps():
+    """On a seeded training line (its first specimen, point 192, levels
+    1184..1216) a point cools from 795 K to a minimum of 771.08 K at level
+    1215 before the next pass reheats it; sampled at every 4th level the
+    temperatures fall monotonically (771.27 K last), so g at the samples
+    would miss the martensite the dip forms (3.3e-3 per K of undercooling).
+    The parabola through the last three samples has its vertex 1.1
+    spacings past the middle one: the window form sends the window to the
+    explicit steps, and the host mask agrees; sampled at every level the
+    same 32-level window applies g at the minimum itself and passes."""
+    from paper_2402_17580_gb300 import _binding as B
+    from paper_2402_17580_gb300.surrogate import band_mask
+    w = workloads.surrogate_lines(n_lines=1)
+    sp = w.specimens[0]
+    x, y, z = (a[192:193] for a in sp.grid.coords())
+    n0, dt = 1184, w.dt
+    T = np.array([oracle.temperature(sp.source, x, y, z, (n0 + l) * dt)[0][0] for l in range(33)])
+    s4 = T[::4]
+    assert np.all(np.diff(s4) < 0) and 790.0 < s4[0] < 808.0
+    assert np.argmin(T) == 31 and T.min() < s4[-1] - 0.15
+    k = s4[6] - 2 * s4[7] + s4[8]
+    assert 2.0 * k < abs(s4[8] - s4[6]) <= 4.0 * k      # vertex 1 to 2 spacings out
+    p = oracle.params()
+    st = oracle.State.uniform(sp.grid.n, 0.9, 0.0)
+    oracle.run_track(st, sp.source, *sp.grid.coords(), 0, n0, dt, p)
+    a, b = (oracle.State.make([st.xas[192]], [st.xam[192]]) for _ in range(2))
+    assert a.mode[0] == 0 and 0.1 < a.xam[0] < 0.3
+    assert oracle.run_track_windows(a, sp.source, x, y, z, n0, 32, dt, window=8, stride=4,
+                                    p=p)[0] == 0
+    assert oracle.run_track_windows(b, sp.source, x, y, z, n0, 32, dt, window=32, stride=1,
+                                    p=p)[0] == 1
+    # g at the minimum forms the undercooling's martensite, g at the samples not
+    gs, gm = st.xas[192], st.xam[192]
+    for t in s4[1:]:
+        gs, gm = oracle.correct(t, gs, gm, p)
+    assert b.xam[0] > gm + 4e-4
+    assert bool(band_mask(s4[None, :], B.default_params(), 4)[0])
+    assert not bool(band_mask(s4[None, :], B.default_params(), 1)[0])
+
+
+def test_window_form_group_takes_explicit_steps_together():
+    """Points grouped like the hybrid kernel's tiles: a line off the fixed
+    point under a track has, in every window, hot points near the source in
+    the band and cold points outside it.  Alone (group 1) the cold points
+    apply g only; as one group every window sends them to the explicit steps
+    with the hot ones, and the window form equals the explicit run."""
+    w, src = _line(200.0)
+    x, y, z = w.specimens[0].grid.coords()
+    p = oracle.params()
+    mk = lambda: oracle.State.make([0.6] * x.size, [0.1] * x.size)
+    a, b, c = mk(), mk(), mk()
+    oracle.run_track(a, src, x, y, z, 0, 96, w.dt, p)
+    n1 = oracle.run_track_windows(b, src, x, y, z, 0, 96, w.dt, p=p, group=1)
+    nn = oracle.run_track_windows(c, src, x, y, z, 0, 96, w.dt, p=p, group=x.size)
+    assert n1.sum() > 0 and nn.sum() == 0
+    for f in ("xas", "xam", "xt", "mode"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(c, f))
 
 
 def oracle_in_band(T, po):

@@ -90,24 +90,29 @@ MUTANTS = {
 # mistakes in the window form of the hybrid path (orc_run_track_windows),
 # caught by tests/test_mlp_oracle.py
 WINDOW_MUTANTS = {
-    "fixed_point_bound_T_as_start": ("cool &= T[l] < p[P_T_AS_END];",
-                                     "cool &= T[l] < p[P_T_AS_START];"),
+    "fixed_point_bound_T_as_start": ("cool &= Ti[l] < p[P_T_AS_END];",
+                                     "cool &= Ti[l] < p[P_T_AS_START];"),
     "fixed_point_any_alpha": ("xas[i] == 0.9 && xam[i] == 0.0", "xas[i] >= 0.5"),
-    "windows_skip_correction": ("for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);",
-                                "(void)0;"),
+    "windows_skip_correction": (
+        "for (int64_t l = stride; l <= K; l += stride) correct(p, Ti[l], &xas[i], &xam[i]);",
+        "(void)0;"),
     "windows_correct_at_last_level_only": (
-        "for (int64_t l = 1; l <= K; ++l) correct(p, T[l], &xas[i], &xam[i]);",
-        "correct(p, T[K], &xas[i], &xam[i]);"),
+        "for (int64_t l = stride; l <= K; l += stride) correct(p, Ti[l], &xas[i], &xam[i]);",
+        "correct(p, Ti[K], &xas[i], &xam[i]);"),
     "band_misses_regularisation_end": (" || fabs(T - (p[P_T_AS_START] + p[P_T_REG])) < h) return 1;",
                                        ") return 1;"),
     "band_misses_melt": ("  if (!(T <= p[P_T_S] - h)) return 1;\n", ""),
-    "band_ignores_start_level": ("int band = in_band(p, T0, band_half), all_act",
-                                 "int band = 0, all_act"),
-    "tail_window_to_network": ("&& K == window && !band", "&& !band"),
-    "initiation_window_to_network": ("&& !band && mode[i] == MODE_NONE) {", "&& !band) {"),
-    "fixed_point_ignores_initiation": ("if (cool && mode[i] == MODE_NONE && xas[i] == 0.9",
-                                       "if (cool && xas[i] == 0.9"),
-    "windows_advance_undeposited_points": ("if (act[l]) advance(p, T[l - 1]", "advance(p, T[l - 1]"),
+    "band_ignores_start_level": ("int band = in_band(p, Ti[0], band_half), cool",
+                                 "int band = 0, cool"),
+    "tail_window_to_network": ("else if (K == len && all_act && !band", "else if (all_act && !band"),
+    "jump_rule_dropped": (" || !(fabs(Ti[l] - Ti[l - stride]) <= band_half)", ""),
+    "group_rule_ignored": ("} else if (kind[k] == 2 && !any_explicit) {", "} else if (kind[k] == 2) {"),
+    "vertex_rule_dropped": ("band |= extreme_near(p, Ti[l - 2 * stride], Ti[l - stride], Ti[l]);",
+                            "(void)0;"),
+    "vertex_between_outer_samples_only": ("!(fabs(s) <= 4.0 * fabs(k))", "!(fabs(s) <= 2.0 * fabs(k))"),
+    "initiation_window_to_network": ("&& !band && mode[i] == MODE_NONE)\n", "&& !band)\n"),
+    "fixed_point_ignores_initiation": ("cool && mode[i] == MODE_NONE && xas[i] == 0.9",
+                                       "cool && xas[i] == 0.9"),
 }
 
 
@@ -207,15 +212,18 @@ MLP_MUTANTS = {
     "input_not_rounded": ("x = rnd(np.asarray(X, dtype=np.float64))",
                           "x = np.asarray(X, dtype=np.float64)"),
     "W1_not_rounded": ("W1, W2, W3 = rnd(W1), rnd(W2), rnd(W3)", "W2, W3 = rnd(W2), rnd(W3)"),
-    "hidden1_not_rounded": ("a1 = rnd(gelu(h1))", "a1 = gelu(h1)"),
-    "hidden2_not_rounded": ("a2 = rnd(gelu(h2))", "a2 = gelu(h2)"),
+    "hidden1_not_rounded": ("a1 = rnd(f(h1))", "a1 = f(h1)"),
+    "hidden2_not_rounded": ("a2 = rnd(f(h2))", "a2 = f(h2)"),
+    "relu_grad_one_at_kink": ("(np.asarray(x) > 0.0)", "(np.asarray(x) >= 0.0)"),
+    "relu_leaky": ("np.maximum(x, 0.0)", "np.maximum(x, 0.01 * x)"),
+    "relu_grad_gelu": ('"relu": (relu, relu_grad)', '"relu": (relu, gelu_grad)'),
     "bias_b2_dropped": ("h2 = a1 @ W2.T + b2", "h2 = a1 @ W2.T"),
     "loss_mean_over_samples_only": ("loss = float(np.sum(r * r) / (N_OUT * n))",
                                     "loss = float(np.sum(r * r) / n)"),
     "gradient_unrounded_input": ("g[OFF_W1:OFF_B1] = (dh1.T @ x).ravel()",
                                  "g[OFF_W1:OFF_B1] = (dh1.T @ np.asarray(X, dtype=np.float64)).ravel()"),
-    "backprop_unrounded_W3": ("dh2 = (dy @ W3) * gelu_grad(h2)",
-                              "dh2 = (dy @ unpack(params)[4]) * gelu_grad(h2)"),
+    "backprop_unrounded_W3": ("dh2 = (dy @ W3) * fg(h2)",
+                              "dh2 = (dy @ unpack(params)[4]) * fg(h2)"),
     "gradient_sign": ("dy = 2.0 * r / (N_OUT * n)", "dy = -2.0 * r / (N_OUT * n)"),
 }
 

@@ -4,24 +4,39 @@ oracle's window form, and a trained surrogate against the explicit oracle.
 
 Tolerances.
 * Network: inference and training round weights, inputs and hidden
-  activations to BF16 like the reference, but evaluate tanh with
-  tanh.approx.f32 (relative error about 2^-11) and sum in FP32.  A hidden
+  activations to BF16 like the reference, but evaluate GELU's tanh with
+  tanh.approx.f32 (relative error about 2^-11) and sum in FP32 (ReLU is
+  exact; its outputs differ from the reference by the FP32 sums, which can
+  still move an activation across a BF16 rounding boundary).  A hidden
   activation can then land on the neighbouring BF16 value (2^-8 relative),
   which moves an output by about |w| 2^-8 |a| ~ 1e-3 for the weight scales
   used; outputs are held to 2e-2 x max(1, |y|) element-wise and 2e-3 on
   average, gradients to 2e-2 of their norm.
-* Zero network: MLP windows reduce to the correction g along the window's
-  temperatures, so the hybrid is held to the explicit path's run tolerance
-  (1e-4) against the oracle's window form.
+* Zero network: MLP windows reduce to the correction g at the window's
+  samples, so the hybrid is held to the explicit path's run tolerance
+  (1e-4) against the oracle's window form, for windows sampled at every
+  level and at every 4th, 8th and 16th.
 * Trained network: no closed form; the bar is the hybrid path's target,
   max|dX| <= 5e-3 against the FP64 explicit oracle (50x the explicit FP32
   path's bar), with the judge's own per-window error reported beside it.
   What the network buys is measured against the same windows with a zero
   network (correction g only, no diffusion in MLP windows): the trained
-  hybrid must be at least 5x closer to the oracle than that (measured
-  1.4e-5 against 1.6e-4 on the test's block).  The held-out residual RMS
-  error must be below half the residuals' own RMS (the network explains at
-  least 75 % of their variance).
+  hybrid must be at least 5x closer to the oracle than that.  Three network
+  designs are trained and held to these bars: GELU with windows of 8 steps
+  sampled at every level, and ReLU with windows of 32 and 64 steps sampled
+  at every 4th and 8th level.  On held-out windows whose residuals stay
+  within 1e-4 (at least 99.9 % of them) the mean absolute error must be
+  below half the residuals' own mean absolute value with every level
+  sampled (measured 0.32), below 0.7 of it with r > 1 (measured 0.16 at
+  r = 4, 0.60 at r = 8), and with every level sampled the RMS error over
+  all windows below half their RMS (the network explains at least 75 % of
+  their variance).  With r > 1 the samples do not determine the path
+  between them, on which the diffusion depends: part of each residual is
+  beyond any function of the network's inputs, and the few larger
+  residuals come from temperature extremes between the samples that the
+  band test does not catch.  The block test is the bar that counts: at
+  r = 8 the trained hybrid sits 30x closer to the oracle than the zero
+  network.
 """
 import math
 
@@ -78,19 +93,24 @@ def _params(seed):
     return p
 
 
-def test_forward_matches_reference_network(ms, torch):
+ACTS = [(0, "gelu"), (1, "relu")]   # MS_ACT_GELU, MS_ACT_RELU
+
+
+@pytest.mark.parametrize("act,name", ACTS)
+def test_forward_matches_reference_network(ms, torch, act, name):
     n = 128 * 37 + 45  # several warps and CTAs and a ragged tail
     x = np.concatenate([_inputs(n - 200, 1), np.random.default_rng(2).normal(0, 1, (200, 12))
                         .astype(np.float32)])
     p = _params(3)
-    s = ms.Surrogate(p)
+    s = ms.Surrogate(p, act)
+    assert s.config() == (act, 1)
     # the surrogate's own stream; the results are read after a device-wide sync
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     s.forward(xd.data_ptr(), yd.data_ptr(), n)
     torch.cuda.synchronize()
     y = yd.cpu().numpy().astype(np.float64)
-    ref, _ = omlp.forward(p.astype(np.float64), x.astype(np.float64), bf16=True)
+    ref, _ = omlp.forward(p.astype(np.float64), x.astype(np.float64), bf16=True, act=name)
     err = np.abs(y - ref)
     assert np.all(err <= 2e-2 * np.maximum(1.0, np.abs(ref))), err.max()
     assert err.mean() <= 2e-3
@@ -98,25 +118,27 @@ def test_forward_matches_reference_network(ms, torch):
     s.close()
 
 
-def test_gradient_matches_reference_network(ms, torch):
+@pytest.mark.parametrize("act,name", ACTS)
+def test_gradient_matches_reference_network(ms, torch, act, name):
     n = 3000
     x = _inputs(n, 4)
     t = np.random.default_rng(5).normal(0, 0.5, (n, 3)).astype(np.float32)
     p = _params(6)
-    s = ms.Surrogate(p)
+    s = ms.Surrogate(p, act)
     # the surrogate's own stream; the results are read after a device-wide sync
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     gd = torch.empty(omlp.N_PARAMS, dtype=torch.float32, device="cuda")
     loss = s.gradient(xd.data_ptr(), td.data_ptr(), n, gd.data_ptr())
     g = gd.cpu().numpy().astype(np.float64)
     ref_loss, ref_g = omlp.loss_and_gradient(p.astype(np.float64), x.astype(np.float64),
-                                             t.astype(np.float64), bf16=True)
+                                             t.astype(np.float64), bf16=True, act=name)
     assert abs(loss - ref_loss) <= 1e-3 * ref_loss
     assert np.linalg.norm(g - ref_g) <= 2e-2 * np.linalg.norm(ref_g)
     s.close()
 
 
-def test_training_reduces_loss(ms, torch):
+@pytest.mark.parametrize("act", [0, 1])
+def test_training_reduces_loss(ms, torch, act):
     """Adam on a smooth synthetic target (numpy, seeded) lowers the loss by
     more than 5x in 400 steps."""
     n = 20000
@@ -124,7 +146,7 @@ def test_training_reduces_loss(ms, torch):
     A = np.random.default_rng(8).normal(0, 1, (12, 3))
     t = np.tanh(x.astype(np.float64) @ A).astype(np.float32)
     from paper_2402_17580_gb300 import surrogate
-    s = ms.Surrogate(surrogate.init_params(9))
+    s = ms.Surrogate(surrogate.init_params(9), act)
     # the surrogate's own stream; the results are read after a device-wide sync
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     first = s.gradient(xd.data_ptr(), td.data_ptr(), n)
@@ -147,14 +169,16 @@ def _run(ms, w, surrogate, judge=0.0, **kw):
     return ctx, ctx.fractions()
 
 
-@pytest.mark.parametrize("precision", [0, 2])
-def test_zero_network_hybrid_matches_window_oracle(ms, precision):
+@pytest.mark.parametrize("precision,stride,act", [(0, 1, 0), (2, 1, 0), (0, 4, 1), (2, 8, 1),
+                                                  (0, 16, 1)])
+def test_zero_network_hybrid_matches_window_oracle(ms, precision, stride, act):
     """A network with all parameters 0 outputs 0, so every MLP window only
-    applies g at its temperatures in turn: the hybrid
-    kernel must then follow orc_run_track_windows (band test, window
-    classification, fallback steps) on every point of the 4096-point line."""
+    applies g at its samples in turn: the hybrid kernel must then follow
+    orc_run_track_windows (band test, window classification, fallback
+    steps, the 128-point tiles taking the explicit steps together) on every
+    point of the 4096-point line."""
     w = wl.line_4096()
-    s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
+    s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32), act, stride)
     ctx, g = _run(ms, w, s, judge=1.0, precision=precision, steps_per_launch=128)
     st = ctx.stats()
     sp = w.specimens[0]
@@ -162,14 +186,15 @@ def test_zero_network_hybrid_matches_window_oracle(ms, precision):
     o = orc.State.uniform(w.n_points, w.init_xas, w.init_xam)
     p = oracle_params()
     n_mlp, n_fixed = orc.run_track_windows(o, sp.source, x, y, z, 0, w.n_steps, w.dt, p=p,
-                                           return_fixed=True)
+                                           return_fixed=True, stride=stride, group=128)
     T_last = orc.temperature(sp.source, x, y, z, w.n_steps * w.dt)[0]
     of = np.stack(orc.fractions(o, T_last, p))
     assert max_abs_diff(g, of) <= RUN_TOL
     # windows are g-only (MLP), explicit (ODE) or, on the alpha_s plateau's
     # fixed point below T_as,end, left alone (most of the line's windows:
     # the points ahead of the source and the cold tail)
-    total = w.n_points * w.n_steps // 8
+    L = 8 * stride
+    total = w.n_points * ((w.n_steps + L - 1) // L)
     n_m, n_f = int(n_mlp.sum()), int(n_fixed.sum())
     assert st.surrogate_windows > 0.1 * total and n_f > 0
     assert abs(st.surrogate_windows - n_m) <= 1e-3 * total
@@ -195,14 +220,17 @@ def test_hybrid_rejects_fp64_and_bad_fraction(ms):
     s.close()
 
 
-@pytest.fixture(scope="module")
-def trained(ms, torch):
+@pytest.fixture(scope="module", params=[(0, 1), (1, 4), (1, 8)],
+                ids=["gelu_r1", "relu_r4", "relu_r8"])
+def trained(ms, torch, request):
     from paper_2402_17580_gb300 import surrogate
+    act, stride = request.param
     w = wl.surrogate_lines(n_lines=64)
-    data = surrogate.collect_windows(w.specimens, w.n_steps, w.dt, seed=1)
-    s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2)
+    data = surrogate.collect_windows(w.specimens, w.n_steps, w.dt, seed=1, stride=stride)
+    s = surrogate.train(data.X, data.Y, iters=20000, batch=32768, lr=1e-3, seed=2,
+                        activation=act, stride=stride)
     held = wl.surrogate_lines(seed=wl.SEED_BASE + 40, n_lines=16)
-    hd = surrogate.collect_windows(held.specimens, held.n_steps, held.dt, seed=3)
+    hd = surrogate.collect_windows(held.specimens, held.n_steps, held.dt, seed=3, stride=stride)
     s.report = {"windows": len(data.X), "seen": data.windows_seen, "band": data.band_windows,
                 "held_out": surrogate.evaluate(s, hd.X, hd.Y)}
     yield s
@@ -211,10 +239,13 @@ def trained(ms, torch):
 
 def test_trained_surrogate_held_out_error(trained):
     r = trained.report
-    print("surrogate", r)
+    print("surrogate", trained.config(), r)
     assert r["windows"] > 10000
     h = r["held_out"]
-    assert h["rms"] < 0.5 * h["target_rms"]
+    assert h["core_share"] > 0.999
+    assert h["core_mae"] < (0.5 if trained.stride == 1 else 0.7) * h["core_target_mae"]
+    if trained.stride == 1:
+        assert h["rms"] < 0.5 * h["target_rms"]
 
 
 def test_trained_hybrid_against_oracle(ms, trained):
@@ -231,10 +262,11 @@ def test_trained_hybrid_against_oracle(ms, trained):
     o = oracle_workload(w, idx)
     err = max_abs_diff(g, o, idx)
     share = st.surrogate_windows / max(1, st.surrogate_windows + st.ode_windows)
-    zero = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
+    zero = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32), *trained.config())
     zctx, zg = _run(ms, w, zero)
     err0 = max_abs_diff(zg, o, idx)
-    print(f"hybrid max|dX| {err:.3e} (zero network {err0:.3e}), MLP share {share:.3f}, "
+    print(f"hybrid {trained.config()} max|dX| {err:.3e} (zero network {err0:.3e}), "
+          f"MLP share {share:.3f}, "
           f"judge {st.judge_samples} windows max {st.judge_max_err:.3e}")
     assert st.surrogate_windows > 0 and st.judge_samples > 0
     assert err <= HYBRID_TOL
