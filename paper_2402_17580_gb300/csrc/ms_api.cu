@@ -91,6 +91,7 @@ struct ms_ctx {
   ms::WorkCounters* work_d = nullptr;
   int sm_count = 0;
   int track_grid = 0;  // persistent grid size for the current layout
+  int dense_grid = 0;  // grid of the dense one-step launch (k_track_dense)
 
   // attached surrogate (hybrid kernel)
   const ms::MlpDev* mlp = nullptr;
@@ -343,6 +344,7 @@ int build_layout(ms_ctx* c) {
     });
     const int64_t need = (tiles + bt / 32 - 1) / (bt / 32);
     c->track_grid = int(std::min<int64_t>(int64_t(per_sm) * c->sm_count, need));
+    c->dense_grid = ms::track_dense_grid(tiles, ms::track_dense_blocks_per_sm(), c->sm_count);
   }
   MS_CUDA(cudaMemcpy(c->specs_d, c->specs_h.data(), c->specs_h.size() * sizeof(SpecDev),
                      cudaMemcpyHostToDevice));
@@ -530,6 +532,7 @@ int launch_table(ms_ctx* c, int64_t level0, int n_levels, bool with_window = fal
   ta.dt = c->dt;
   ta.levels = c->levels_d;
   ta.entries = c->entries_d;
+  ta.ff_dist = c->ff_d && c->prm.precision != MS_F64 ? c->prm.farfield_dist : 0.0;
   if (with_window && !c->tracks_h.empty()) {
     ta.win = c->win_d;
     ta.n_tracks = int32_t(c->tracks_h.size());
@@ -624,7 +627,16 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
           fma = true;
         }
       }
-      if (!fma)
+      bool dense = false;
+      if constexpr (std::is_same<AT, float>::value && std::is_same<FT, float>::value) {
+        // one explicit step over every tile: the streaming form of the same step
+        if (!fma && !use_list && steps == 1 && c->prm.integrator != MS_IMPLICIT &&
+            !a.count_sfu) {
+          MS_CUDA(ms::launch_track_dense(a, c->dense_grid, c->stream));
+          dense = true;
+        }
+      }
+      if (!fma && !dense)
         MS_CUDA(ms::launch_track<AT, FT>(a, block_threads(c), c->track_grid, c->stream,
                                          c->prm.integrator == MS_IMPLICIT));
     }

@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 namespace ms {
 
@@ -175,6 +176,7 @@ struct Fn<float> {
   static __device__ __forceinline__ float rsqrt(float x) { return sfu_rsqrt(x); }
   static __device__ __forceinline__ float rcp(float x) { return sfu_rcp(x); }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
   static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
   static __device__ __forceinline__ float min(float a, float b) { return fminf(a, b); }
   static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
@@ -186,6 +188,7 @@ struct Fn<double> {
   static __device__ __forceinline__ double rsqrt(double x) { return ::rsqrt(x); }
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
   static __device__ __forceinline__ double max(double a, double b) { return ::fmax(a, b); }
   static __device__ __forceinline__ double min(double a, double b) { return ::fmin(a, b); }
   static __device__ __forceinline__ double abs(double a) { return ::fabs(a); }
@@ -280,7 +283,7 @@ __device__ __forceinline__ AT logistic_step_log2(AT lX, AT D, AT k, AT c, AT inv
     u = Fn<AT>::ex2((lxi - Fn<AT>::lg2(AT(1) - xi)) * inv_c);
   }
   const AT w = Fn<AT>::fma(D * k * dt, inv_c, u);
-  return lD - softplus2<AT>(-c * Fn<AT>::lg2(w));
+  return lD - softplus2<AT>(Fn<AT>::mul_rn(-c, Fn<AT>::lg2(w)));
 }
 
 // ---------------------------------------------------------- correction g
@@ -320,7 +323,21 @@ __device__ __forceinline__ void correct(const ModelConstT<AT>& m, AT T, FT& xas,
 // rounds it the same way.  x = 0 or y = 0 give 2^-inf = 0 (reading A14).
 template <typename AT>
 __device__ __forceinline__ AT pow_rate(AT k, AT p, AT lx, AT q, AT y) {
-  return k * Fn<AT>::ex2(Fn<AT>::fma(q, Fn<AT>::lg2(y), p * lx));
+  return Fn<AT>::mul_rn(k, Fn<AT>::ex2(Fn<AT>::fma(q, Fn<AT>::lg2(y), p * lx)));
+}
+
+// The explicit Euler update x + dt d of a fraction: one FMA when the fraction
+// type is the arithmetic type, else the rounded increment added in the
+// fraction type.  It is written out, like the rounded product of pow_rate,
+// because whether the compiler fuses a multiply into an add depends on the
+// code around it: the per-point and the lockstep step would otherwise be free
+// to round the same update differently.
+template <typename AT, typename FT>
+__device__ __forceinline__ FT euler_add(FT x, AT dt, AT d) {
+  if constexpr (std::is_same<AT, FT>::value)
+    return Fn<AT>::fma(dt, d, x);
+  else
+    return x + FT(Fn<AT>::mul_rn(dt, d));
 }
 
 // aux encodes the App. A initiation: 0 none; < 0 alpha_s -> beta in progress
@@ -365,8 +382,8 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
     }
     const AT lX = logistic_step_log2<AT>(las, D, k, m.c_as, m.inv_c_as, dt, oc);
     oc.add(1, 0);
-    nas = FT(Fn<AT>::ex2(lX)) + FT(dt * r2);
-    nam = xam - FT(dt * r2);
+    nas = euler_add<AT, FT>(FT(Fn<AT>::ex2(lX)), dt, r2);
+    nam = euler_add<AT, FT>(xam, dt, -r2);
     if (m.init_ba_steps) a6 = true;
   } else {
     // eq:explicit_integration with the rates at T^n.  r1 and r3 exclude each
@@ -390,8 +407,8 @@ __device__ __forceinline__ void point_step(const ModelConstT<AT>& m, AT T0, AT T
       d_as += r2;
       d_am = -r2;
     }
-    nas = xas + FT(dt * d_as);
-    nam = xam + FT(dt * d_am);
+    nas = euler_add<AT, FT>(xas, dt, d_as);
+    nam = euler_add<AT, FT>(xam, dt, d_am);
   }
 
   const FT before = nas;
@@ -540,10 +557,17 @@ struct alignas(16) SrcEntryT {
 };
 using SrcEntry = SrcEntryT<float>;
 
+// SrcLevelT::axis: every source of the level moves along +-x (u_y == 0);
+// LEVEL_AXIS_NEAR also says that the far field can serve none of them in any
+// row tile (the source table's test against the specimen's whole x-range),
+// so the kernels sum them point by point without classifying them.
+constexpr int LEVEL_AXIS = 1;
+constexpr int LEVEL_AXIS_NEAR = 3;
+
 template <typename AT>
 struct alignas(16) SrcLevelT {
   int n;          // started sources of the current layer at this level
-  int axis;       // 1: every source of the level has u_y == 0 (moves along +-x)
+  int axis;       // 0, LEVEL_AXIS or LEVEL_AXIS_NEAR
   AT z_surf;      // current layer surface (all its sources sit on it)
   AT T0, T_max;
 };
@@ -562,21 +586,23 @@ using SrcLevel = SrcLevelT<float>;
 // its relative accuracy on both sides of the source with no reciprocal and no
 // branch.  The correction is folded into the exponent:
 //   cR d = cR d0 + hcR * (rinv f(d0)),  hcR = -cR / 2.
-// In FP32: 10 instructions, 2 on the SFU; the offsets add 1 per point in a
-// row tile (source_term_x) and 5 in the general form (source_term).
+// In FP32: 10 instructions, 2 on the SFU, the last an FMA that adds the term
+// to the caller's sum acc (written out, so that every path sums the sources
+// with the same roundings); the offsets add 1 per point in a row tile
+// (source_term_x) and 5 in the general form (source_term).
 //
 // The offsets are xi = px u_x + (py u_y - s_xi) and pp = px u_y + (py (-u_x)
 // - s_pp); the bracketed parts and, when u_y == 0, perp^2 do not depend on
 // px, so points that share py and pz may compute them once (source_offsets,
 // source_term_x) and get the same bits.
 template <typename AT>
-__device__ __forceinline__ AT source_term_x(const SrcEntryT<AT>& e, AT xi, AT perp2) {
+__device__ __forceinline__ AT source_term_x(const SrcEntryT<AT>& e, AT xi, AT perp2, AT acc) {
   const AT r2 = Fn<AT>::fma(xi, xi, perp2);
   const AT rinv = Fn<AT>::rsqrt(r2);
   const AT d = Fn<AT>::fma(r2, rinv, xi);                                  // R + xi, approximate
   const AT f = Fn<AT>::fma(d, Fn<AT>::fma(AT(-2), xi, d), -perp2);        // d (d - 2 xi) - perp^2
   const AT a = Fn<AT>::fma(e.hcR, rinv * f, Fn<AT>::fma(e.cR, d, e.lC));  // cR (R + xi) + lC
-  return rinv * Fn<AT>::ex2(a);
+  return Fn<AT>::fma(rinv, Fn<AT>::ex2(a), acc);
 }
 
 // The parts of xi and pp that do not depend on px.
@@ -587,12 +613,12 @@ __device__ __forceinline__ void source_offsets(const SrcEntryT<AT>& e, AT py, AT
 }
 
 template <typename AT>
-__device__ __forceinline__ AT source_term(const SrcEntryT<AT>& e, AT px, AT py, AT dz2) {
+__device__ __forceinline__ AT source_term(const SrcEntryT<AT>& e, AT px, AT py, AT dz2, AT acc) {
   AT c_xi, c_pp;
   source_offsets<AT>(e, py, c_xi, c_pp);
   const AT xi = Fn<AT>::fma(px, e.ux, c_xi);
   const AT pp = Fn<AT>::fma(px, e.uy, c_pp);
-  return source_term_x<AT>(e, xi, Fn<AT>::fma(pp, pp, dz2));
+  return source_term_x<AT>(e, xi, Fn<AT>::fma(pp, pp, dz2), acc);
 }
 
 }  // namespace ms

@@ -183,16 +183,18 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   const int KW = MLP_WINDOW * r;
   // far field (as in k_track): the tile's x-range, first to 128th point
   const int64_t col0 = __shfl_sync(full, col, 0);
-  const float x_first = float(sp.ox) + float(col0) * float(sp.dx);
+  const float x_first = grid_coord<float>(float(sp.ox), float(int32_t(col0)), float(sp.dx));
   const float x_span = float(TILE - 1) * float(sp.dx);
   const float ff_dist = fmaxf(a.ff_dist, FF_RANGE_GUARD * fabsf(x_span));
   const bool far = a.ff != nullptr && row;
+  const float py_row = __shfl_sync(full, py[0], 0);  // lane 0's first point is always valid
+  const float pz_row = __shfl_sync(full, pz[0], 0);
   // the temperatures of 4 points at level lvl, far field where it applies
   auto temps = [&](int lvl, float* T) {
     const SrcLevelT<float> L = lv[lvl];
-    if (far && L.axis) {
+    if (far && L.axis == LEVEL_AXIS) {
       int nn, nf;
-      temps4_far(L, en + int64_t(lvl) * a.slots, px, py[0], pz[0], x_first, x_span, ff_dist,
+      temps4_far(L, en + int64_t(lvl) * a.slots, px, py_row, pz_row, x_first, x_span, ff_dist,
                  lane, T, nn, nf, a.ff);
     } else {
       temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, row, T);

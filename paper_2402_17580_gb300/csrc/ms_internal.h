@@ -79,6 +79,7 @@ struct TableArgs {
   int32_t n_tracks;        // tracks of all specimens
   int32_t pad2;
   double t_a, t_b;
+  double ff_dist;          // far-field distance of the launches (0: far field off)
 };
 
 // Active tiles are handed out heaviest first: the active set sorts them into
@@ -234,6 +235,14 @@ cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid
                          cudaStream_t stream, bool implicit = false);
 template <typename AT, typename FT>
 int track_blocks_per_sm(int block_threads, bool implicit = false);
+// The dense launch of one step (no active list, S = 1, FP32 explicit):
+// k_track's arithmetic per tile, organised for streaming the state
+// (k_track_dense).  cudaErrorInvalidValue unless a.n_levels == 2 and there is
+// no tile list.
+cudaError_t launch_track_dense(const TrackArgs<float, float>& a, int grid_blocks,
+                               cudaStream_t stream);
+int track_dense_blocks_per_sm();
+int track_dense_grid(int64_t n_tiles, int blocks_per_sm, int sm_count);
 // The same FP32 launches with exp2 / log2 on the FMA pipe (ms_kernels_fma.cu,
 // MS_FLAG_FMA_TRANSCENDENTALS).
 cudaError_t launch_track_fma(const TrackArgs<float, float>& a, int block_threads,

@@ -65,7 +65,18 @@ __device__ __forceinline__ void table_level(const TableArgs& a, int id, int lane
   SrcEntryT<AT>* out =
       static_cast<SrcEntryT<AT>*>(a.entries) + (int64_t(s) * a.n_levels + lv) * a.slots;
   int n = 0;
-  bool axis = true;
+  bool axis = true, far = false;
+  // the far field's test (a source at least ff_dist behind every point of a
+  // row tile's x-range) against the whole x-range that row tiles can span:
+  // where no source passes it here, none passes it for any tile
+  double x_lo = 0.0, x_hi = 0.0, ffd = 0.0;
+  if (a.ff_dist > 0.0) {
+    const double ext = double(TILE - 1) * fabs(sp.dx);
+    const double xe = sp.ox + double(sp.nx - 1) * sp.dx;
+    x_lo = fmin(sp.ox, xe) - ext;
+    x_hi = fmax(sp.ox, xe) + ext;
+    ffd = fmax(a.ff_dist, double(FF_RANGE_GUARD) * ext) - 1e-6;  // margin over FP32 rounding
+  }
   for (int j0 = 0; j0 < sp.n_tracks && n < a.slots; j0 += 32) {
     const int j = j0 + lane;
     TrackDev tr{};
@@ -91,14 +102,19 @@ __device__ __forceinline__ void table_level(const TableArgs& a, int id, int lane
       e.pad1 = AT(0);
       out[slot] = e;
       axis = axis && e.uy == AT(0);
+      if (a.ff_dist > 0.0) {
+        const double sxi = sx * tr.ux + sy * tr.uy;
+        far = far || fmin(x_lo * tr.ux - sxi, x_hi * tr.ux - sxi) <= -ffd;
+      }
     }
     axis = __all_sync(0xffffffffu, axis);
     n += __popc(m);
   }
+  far = __any_sync(0xffffffffu, far);
   if (lane == 0) {
     SrcLevelT<AT> r;
     r.n = n < a.slots ? n : a.slots;
-    r.axis = axis ? 1 : 0;
+    r.axis = axis ? (a.ff_dist > 0.0 && !far ? LEVEL_AXIS_NEAR : LEVEL_AXIS) : 0;
     r.z_surf = AT(L.z);
     r.T0 = AT(sp.T0);
     r.T_max = AT(sp.T_max);
@@ -199,12 +215,14 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   const int64_t span = sp.n - 1 - li_first < TILE - 1 ? sp.n - 1 - li_first : TILE - 1;
   const bool row = !sp.idx && col0 + span < sp.nx;
   // far field: the tile's x-range, first to 128th point (a row tile)
-  AT x_first = AT(0), x_span = AT(0), ff_dist = AT(0);
+  AT x_first = AT(0), x_span = AT(0), ff_dist = AT(0), py_row = AT(0), pz_row = AT(0);
   if constexpr (FAR) {
-    x_first = AT(sp.ox) + AT(col0) * AT(sp.dx);
+    x_first = grid_coord<AT>(AT(sp.ox), AT(int32_t(col0)), AT(sp.dx));  // col0 < nx: 32-bit
     x_span = AT(TILE - 1) * AT(sp.dx);
     // never closer than FF_RANGE_GUARD tile ranges, whatever the grid spacing
     ff_dist = Fn<AT>::max(a.ff_dist, AT(FF_RANGE_GUARD) * Fn<AT>::abs(x_span));
+    py_row = __shfl_sync(0xffffffffu, py[0], 0);  // lane 0's first point is always valid
+    pz_row = __shfl_sync(0xffffffffu, pz[0], 0);
   }
 
   FT xs[4], xm[4];
@@ -230,9 +248,9 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     AT T1[4];
     bool done_far = false;
     if constexpr (FAR) {
-      if (row && L.axis) {
+      if (row && L.axis == LEVEL_AXIS) {
         int nn, nf;
-        temps4_far(L, en + int64_t(l) * a.slots, px, py[0], pz[0], x_first, x_span, ff_dist,
+        temps4_far(L, en + int64_t(l) * a.slots, px, py_row, pz_row, x_first, x_span, ff_dist,
                    lane, T1, nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
         srcs += nn;
         fsrcs += nf;
@@ -442,6 +460,233 @@ __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
   }
   if (lane == 0 && done) {
     atomicAdd(&a.work->tile_steps_active, done * (unsigned long long)(a.n_levels - 1));
+    if (a.ops) {
+      atomicAdd(&a.ops->source_evaluations, n_src);
+      atomicAdd(&a.ops->model_point_steps, n_model);
+      if (ff_nodes) {
+        atomicAdd(&a.ops->farfield_node_evaluations, ff_nodes);
+        atomicAdd(&a.ops->farfield_point_sources, ff_pairs);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------- dense one-step launches
+// Exact division of a 32-bit unsigned by a runtime divisor d >= 1 through a
+// multiply-high and two shifts (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Fig. 4.1): with
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+//   t = mulhi(m, n),  n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct UDiv {
+  uint32_t m;
+  uint32_t s1, s2;
+  __device__ __forceinline__ void init(uint32_t d) {
+    uint32_t l = 0;
+    while (l < 32 && (uint64_t(1) << l) < d) ++l;
+    m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - d)) / d + 1);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+// The dense launch of one step: no active list (T_thr = 0), S = 1, the FP32
+// explicit path.  Per tile it is k_track's arithmetic, in the same order and
+// through the same helpers (temps4 / temps4_far at both levels, point_step4),
+// so the two give the same bits; what differs is the organisation around it,
+// for a launch that streams every tile's state from HBM once:
+//  * tiles are dealt to warps in fixed chunks of DENSE_CHUNK consecutive
+//    tiles, round robin, with no work cursor; the padded state arrays hold
+//    the specimens' tiles in tile order (a specimen's pad_off is its first
+//    tile times TILE), so tile t's state starts at t * TILE whatever its
+//    specimen, and the warp bulk-prefetches its next chunk's state into L2
+//    (three copies of DENSE_CHUNK tiles) when it starts a chunk;
+//  * a warp keeps its specimen's grid data, the division constants of its
+//    grid dimensions and the coordinate origin and spacing in FP32 in shared
+//    memory while the specimen does not change, and a tile's first grid point
+//    comes from two multiply-high divisions instead of two integer divisions;
+//  * a row tile's points take x from the tile's first column plus the lane's
+//    offset and the row's y and z (point_coords4 is used only for tiles that
+//    cross a row and for subset specimens);
+//  * the model step skips the rate constants and the martensite equilibrium
+//    of warps at rest (point_step4's IDLE form: the same values);
+//  * the non-finite check sums the eight fractions (bounded by 1 when
+//    finite) and tests the sum.
+constexpr int DENSE_CHUNK = 4;
+constexpr int DENSE_THREADS = 128;
+// Minimum resident 128-thread blocks per SM: 5 (102 registers, 20 warps)
+// measured fastest on the 512 x 512 x 64 and x 256 grids against 4, 6, 7, 8.
+#ifndef MS_DENSE_MINB
+#define MS_DENSE_MINB 5
+#endif
+
+// The state of tiles t0 .. t1 - 1 (consecutive, t0 < t1) into L2.
+__device__ __forceinline__ void prefetch_dense(const TrackArgs<float, float>& a, int t0, int t1) {
+  const int64_t g0 = int64_t(t0) * TILE;
+  const unsigned bytes = unsigned(t1 - t0) * unsigned(TILE * sizeof(float));
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.xas + g0), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.xam + g0), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.aux + g0), "r"(bytes) : "memory");
+}
+
+// A warp's specimen in shared memory (written by lane 0 when the specimen
+// changes), so that the grid data does not hold registers across the tile.
+struct DenseSpec {
+  int64_t n;
+  int32_t tile0, nx, ny, k_off, sub, small;
+  float z_tol, ox, oy, oz, dx, dy, dz;
+  UDiv dvx, dvy;
+};
+
+template <bool FAR>
+__global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(const TrackArgs<float, float> a) {
+  __shared__ DenseSpec spw[DENSE_THREADS / 32];
+  const int lane = threadIdx.x & 31;
+  const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int n_warps = int(gridDim.x * (blockDim.x >> 5));
+  DenseSpec& ds = spw[threadIdx.x >> 5];
+  if constexpr (FAR) {
+    float* sm = reinterpret_cast<float*>(ms_ff_smem);
+    for (int i = threadIdx.x; i < FF_FLOATS; i += blockDim.x) sm[i] = a.ff[i];
+    __syncthreads();
+  }
+  NoCount oc;
+  unsigned long long done = 0, n_src = 0, n_model = 0, ff_nodes = 0, ff_pairs = 0;
+  int s_cur = -1;  // the warp's specimen (warp-uniform)
+  if (lane == 0 && warp * DENSE_CHUNK < a.n_tiles)
+    prefetch_dense(a, warp * DENSE_CHUNK, min((warp + 1) * DENSE_CHUNK, a.n_tiles));
+  for (int c = warp; c * DENSE_CHUNK < a.n_tiles; c += n_warps) {
+    const int c1 = c + n_warps;
+    if (lane == 0 && c1 * DENSE_CHUNK < a.n_tiles)
+      prefetch_dense(a, c1 * DENSE_CHUNK, min((c1 + 1) * DENSE_CHUNK, a.n_tiles));
+    const int t_end = min((c + 1) * DENSE_CHUNK, a.n_tiles);
+    for (int tile = c * DENSE_CHUNK; tile < t_end; ++tile) {
+      const int s = a.tile_spec[tile];
+      if (s != s_cur) {
+        s_cur = s;
+        if (lane == 0) {
+          const SpecDev& sp = a.specs[s];
+          ds.n = sp.n;
+          ds.tile0 = int32_t(sp.tile0);
+          ds.nx = sp.nx;
+          ds.ny = sp.ny;
+          ds.k_off = sp.k_off;
+          ds.sub = sp.idx != nullptr;
+          ds.small = sp.idx == nullptr && sp.n + 4 < (int64_t(1) << 31) &&
+                     sp.nz + sp.k_off < (1 << 30);
+          ds.z_tol = sp.z_tol;
+          ds.ox = float(sp.ox); ds.oy = float(sp.oy); ds.oz = float(sp.oz);
+          ds.dx = float(sp.dx); ds.dy = float(sp.dy); ds.dz = float(sp.dz);
+          ds.dvx.init(uint32_t(sp.nx));
+          ds.dvy.init(uint32_t(sp.ny));
+        }
+        __syncwarp();
+      }
+      const int64_t li_first = int64_t(tile - ds.tile0) * TILE;
+      const int64_t left = ds.n - li_first;
+      const int rem = left < TILE ? int(left) : TILE;  // points of the tile, 1 .. 128
+      const int64_t g0 = int64_t(tile) * TILE + lane * 4;
+      bool valid[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) valid[q] = lane * 4 + q < rem;
+
+      float xs[4], xm[4], ax[4];
+      Vec4<float>::load(a.xas + g0, xs);
+      Vec4<float>::load(a.xam + g0, xm);
+      Vec4<float>::load(a.aux + g0, ax);
+
+      // the tile's first grid point; a row tile keeps one (j, k)
+      const bool sub = ds.sub != 0;
+      float px[4], py[4], pz[4];
+      bool row = false;
+      int32_t col0 = 0;
+      if (ds.small) {  // 32-bit indices (the conversions stay off the FP64 pipe)
+        const uint32_t l = uint32_t(li_first);
+        const uint32_t r = ds.dvx.div(l);
+        const int32_t i0 = int32_t(l - r * uint32_t(ds.nx));
+        const int32_t k0 = int32_t(ds.dvy.div(r));
+        const int32_t j0 = int32_t(r) - k0 * ds.ny;
+        col0 = i0;
+        row = i0 + rem - 1 < ds.nx;
+        if (row) {
+          // the points past the specimen's end (a ragged last tile) take the
+          // row's coordinates too; their results are never stored
+          const float ox = ds.ox, dx = ds.dx;
+          const float y0 = grid_coord<float>(ds.oy, float(j0), ds.dy);
+          const float z0 = grid_coord<float>(ds.oz, float(k0 + ds.k_off), ds.dz);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            px[q] = grid_coord<float>(ox, float(i0 + lane * 4 + q), dx);
+            py[q] = y0;
+            pz[q] = z0;
+          }
+        }
+      }
+      if (!row) {
+        int64_t col;
+        point_coords4<float>(a.specs[s], li_first + lane * 4, valid, px, py, pz, col);
+        const int64_t c0 = __shfl_sync(0xffffffffu, col, 0);
+        if (!sub) {
+          row = c0 + rem - 1 < ds.nx;
+          col0 = int32_t(c0);
+        }
+      }
+      float x_first = 0.f, x_span = 0.f, ff_dist = 0.f, py_row = 0.f, pz_row = 0.f;
+      if constexpr (FAR) {
+        x_first = grid_coord<float>(ds.ox, float(col0), ds.dx);
+        x_span = float(TILE - 1) * ds.dx;
+        ff_dist = fmaxf(a.ff_dist, float(FF_RANGE_GUARD) * fabsf(x_span));
+        py_row = __shfl_sync(0xffffffffu, py[0], 0);
+        pz_row = __shfl_sync(0xffffffffu, pz[0], 0);
+      }
+
+      const SrcLevelT<float>* lv = a.levels + int64_t(s) * 2;
+      const SrcEntryT<float>* en = a.entries + int64_t(s) * 2 * a.slots;
+      float T[2][4];
+      unsigned srcs = 0, fsrcs = 0;
+#pragma unroll
+      for (int l = 0; l < 2; ++l) {
+        const SrcLevelT<float> L = lv[l];
+        bool done_far = false;
+        if constexpr (FAR) {
+          if (row && L.axis == LEVEL_AXIS) {
+            int nn, nf;
+            temps4_far(L, en + int64_t(l) * a.slots, px, py_row, pz_row, x_first, x_span, ff_dist,
+                       lane, T[l], nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
+            srcs += nn;
+            fsrcs += nf;
+            done_far = true;
+          }
+        }
+        if (!done_far) {
+          temps4<float>(L, en + int64_t(l) * a.slots, px, py, pz, row, T[l]);
+          srcs += L.n;
+        }
+      }
+      const float zlim = lv[1].z_surf + ds.z_tol;
+      bool run[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) run[q] = valid[q] && pz[q] <= zlim;
+      float xeq[4];
+      point_step4<NoCount, false, true>(a.m, T[0], T[1], a.dt, run, xs, xm, ax, oc, xeq, false);
+
+      Vec4<float>::store(a.xas + g0, xs);
+      Vec4<float>::store(a.xam + g0, xm);
+      Vec4<float>::store(a.aux + g0, ax);
+      const float sum = ((xs[0] + xs[1]) + (xs[2] + xs[3])) + ((xm[0] + xm[1]) + (xm[2] + xm[3]));
+      if (!::isfinite(sum)) atomicOr(a.err, DEVERR_NONFINITE);
+      n_src += srcs * unsigned(rem);
+      n_model += unsigned(rem);
+      ff_nodes += fsrcs * unsigned(FF_NODES);
+      ff_pairs += fsrcs * unsigned(rem);
+      ++done;
+    }
+  }
+  if (lane == 0 && done) {
+    atomicAdd(&a.work->tile_steps_active, done);
     if (a.ops) {
       atomicAdd(&a.ops->source_evaluations, n_src);
       atomicAdd(&a.ops->model_point_steps, n_model);
@@ -804,6 +1049,32 @@ template <typename AT, typename FT>
 cudaError_t launch_track(const TrackArgs<AT, FT>& a, int block_threads, int grid_blocks,
                          cudaStream_t stream, bool implicit) {
   return track_launch<AT, FT>(a, block_threads, grid_blocks, stream, implicit);
+}
+
+int track_dense_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_track_dense<true>, DENSE_THREADS,
+                                                    FF_FLOATS * sizeof(float)) != cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+int track_dense_grid(int64_t n_tiles, int blocks_per_sm, int sm_count) {
+  const int64_t chunks = (n_tiles + DENSE_CHUNK - 1) / DENSE_CHUNK;
+  const int64_t need = (chunks + DENSE_THREADS / 32 - 1) / (DENSE_THREADS / 32);
+  return int(std::max<int64_t>(1, std::min<int64_t>(int64_t(blocks_per_sm) * sm_count, need)));
+}
+
+cudaError_t launch_track_dense(const TrackArgs<float, float>& a, int grid_blocks,
+                               cudaStream_t stream) {
+  if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
+  if (a.n_levels != 2 || a.tile_list) return cudaErrorInvalidValue;
+  const unsigned g = unsigned(grid_blocks);
+  if (a.ff)
+    k_track_dense<true><<<g, DENSE_THREADS, FF_FLOATS * sizeof(float), stream>>>(a);
+  else
+    k_track_dense<false><<<g, DENSE_THREADS, 0, stream>>>(a);
+  return cudaGetLastError();
 }
 
 template <typename AT, typename FT>

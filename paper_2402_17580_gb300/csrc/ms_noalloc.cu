@@ -204,6 +204,7 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     ta.dt = dt;
     ta.levels = sc->levels;
     ta.entries = sc->entries;
+    ta.ff_dist = p->farfield_dist > 0.0 ? p->farfield_dist : 0.0;
     if (ms::launch_src_table<float>(ta, &sc->work, st) != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "source-table launch failed");
     ms::TrackArgs<float, float> a{};

@@ -14,6 +14,15 @@
 
 namespace ms {
 
+// A grid coordinate o + i d as one explicit FMA, so that every kernel and
+// every index path (32- or 64-bit, grid or subset) rounds it the same way
+// (a multiply and an add may be fused or not, depending on the code around
+// them).
+template <typename AT>
+__device__ __forceinline__ AT grid_coord(AT o, AT i, AT d) {
+  return Fn<AT>::fma(i, d, o);
+}
+
 // Coordinates of local point li of a specimen (a grid point, or the grid
 // point idx[li] for a subset specimen).
 template <typename AT>
@@ -23,17 +32,19 @@ __device__ __forceinline__ void point_coords(const SpecDev& sp, int64_t li, AT& 
   const int64_t i = ii - r * sp.nx;
   const int64_t k = r / sp.ny;
   const int64_t j = r - k * sp.ny;
-  x = AT(sp.ox) + AT(i) * AT(sp.dx);
-  y = AT(sp.oy) + AT(j) * AT(sp.dy);
-  z = AT(sp.oz) + AT(k + sp.k_off) * AT(sp.dz);
+  x = grid_coord<AT>(AT(sp.ox), AT(i), AT(sp.dx));
+  y = grid_coord<AT>(AT(sp.oy), AT(j), AT(sp.dy));
+  z = grid_coord<AT>(AT(sp.oz), AT(k + sp.k_off), AT(sp.dz));
 }
 
 // Coordinates of the four consecutive local points li0 .. li0 + 3 of a
 // specimen; points with valid[q] false take point 0's, as point_coords(sp, 0)
-// gives them.  One index decomposition per thread (32-bit when the specimen
-// allows it), then a carry per point instead of a division: the same integer
-// indices, so the same coordinates.  col returns the column of point li0
-// (0 for a subset specimen).
+// gives them.  One index decomposition per thread, then a carry per point
+// instead of a division: the same integer indices, so the same coordinates.
+// When the specimen's indices fit in 32 bits (every specimen below 2^31
+// points) the indices stay 32-bit integers: a conversion from a 64-bit
+// integer to floating point runs on the FP64 pipe.  col returns the column of
+// point li0 (0 for a subset specimen).
 template <typename AT>
 __device__ __forceinline__ void point_coords4(const SpecDev& sp, int64_t li0, const bool* valid,
                                               AT* x, AT* y, AT* z, int64_t& col) {
@@ -43,19 +54,36 @@ __device__ __forceinline__ void point_coords4(const SpecDev& sp, int64_t li0, co
     for (int q = 0; q < 4; ++q) point_coords<AT>(sp, valid[q] ? li0 + q : 0, x[q], y[q], z[q]);
     return;
   }
-  int64_t i, j, k;
-  if (sp.n + 4 < (int64_t(1) << 32)) {
-    const uint32_t l = uint32_t(li0), nx = uint32_t(sp.nx), ny = uint32_t(sp.ny);
-    const uint32_t r = l / nx;
-    i = l - r * nx;
-    k = r / ny;
-    j = r - uint32_t(k) * ny;
-  } else {
-    const int64_t r = li0 / sp.nx;
-    i = li0 - r * sp.nx;
-    k = r / sp.ny;
-    j = r - k * sp.ny;
+  const AT ox = AT(sp.ox), oy = AT(sp.oy), oz = AT(sp.oz);
+  const AT dx = AT(sp.dx), dy = AT(sp.dy), dz = AT(sp.dz);
+  if (sp.n + 4 < (int64_t(1) << 31) && sp.nz + sp.k_off < (1 << 30)) {
+    const int32_t nx = sp.nx, ny = sp.ny;
+    const uint32_t l = uint32_t(li0);
+    const uint32_t r = l / uint32_t(nx);
+    int32_t i = int32_t(l - r * uint32_t(nx));
+    int32_t k = int32_t(r / uint32_t(ny));
+    int32_t j = int32_t(r) - k * ny;
+    col = i;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q > 0 && ++i == nx) {
+        i = 0;
+        if (++j == ny) {
+          j = 0;
+          ++k;
+        }
+      }
+      const int32_t ii = valid[q] ? i : 0, jj = valid[q] ? j : 0, kk = valid[q] ? k : 0;
+      x[q] = grid_coord<AT>(ox, AT(ii), dx);
+      y[q] = grid_coord<AT>(oy, AT(jj), dy);
+      z[q] = grid_coord<AT>(oz, AT(kk + sp.k_off), dz);
+    }
+    return;
   }
+  const int64_t r = li0 / sp.nx;
+  int64_t i = li0 - r * sp.nx;
+  int64_t k = r / sp.ny;
+  int64_t j = r - k * sp.ny;
   col = i;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -67,9 +95,9 @@ __device__ __forceinline__ void point_coords4(const SpecDev& sp, int64_t li0, co
       }
     }
     const int64_t ii = valid[q] ? i : 0, jj = valid[q] ? j : 0, kk = valid[q] ? k : 0;
-    x[q] = AT(sp.ox) + AT(ii) * AT(sp.dx);
-    y[q] = AT(sp.oy) + AT(jj) * AT(sp.dy);
-    z[q] = AT(sp.oz) + AT(kk + sp.k_off) * AT(sp.dz);
+    x[q] = grid_coord<AT>(ox, AT(ii), dx);
+    y[q] = grid_coord<AT>(oy, AT(jj), dy);
+    z[q] = grid_coord<AT>(oz, AT(kk + sp.k_off), dz);
   }
 }
 
@@ -128,8 +156,8 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
       const AT q0 = Fn<AT>::fma(p0, p0, dz2), q1 = Fn<AT>::fma(p1, p1, dz2);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), q0);
-        acc[q] += source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), q1);
+        acc[q] = source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), q0, acc[q]);
+        acc[q] = source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), q1, acc[q]);
       }
     }
     if (j < L.n) {
@@ -138,7 +166,7 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
       source_offsets<AT>(e0, py[0], x0, p0);
       const AT q0 = Fn<AT>::fma(p0, p0, dz2);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), q0);
+      for (int q = 0; q < 4; ++q) acc[q] = source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), q0, acc[q]);
     }
   } else if (row) {
     const AT dz2 = depth2<AT>(pz[0], L.z_surf);
@@ -150,8 +178,8 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const AT pp0 = Fn<AT>::fma(px[q], e0.uy, p0), pp1 = Fn<AT>::fma(px[q], e1.uy, p1);
-        acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), Fn<AT>::fma(pp0, pp0, dz2));
-        acc[q] += source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), Fn<AT>::fma(pp1, pp1, dz2));
+        acc[q] = source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), Fn<AT>::fma(pp0, pp0, dz2), acc[q]);
+        acc[q] = source_term_x<AT>(e1, Fn<AT>::fma(px[q], e1.ux, x1), Fn<AT>::fma(pp1, pp1, dz2), acc[q]);
       }
     }
     if (j < L.n) {
@@ -161,7 +189,7 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const AT pp0 = Fn<AT>::fma(px[q], e0.uy, p0);
-        acc[q] += source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), Fn<AT>::fma(pp0, pp0, dz2));
+        acc[q] = source_term_x<AT>(e0, Fn<AT>::fma(px[q], e0.ux, x0), Fn<AT>::fma(pp0, pp0, dz2), acc[q]);
       }
     }
   } else {
@@ -172,14 +200,14 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
       const SrcEntryT<AT> e0 = load_entry(en + j), e1 = load_entry(en + j + 1);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
-        acc[q] += source_term<AT>(e1, px[q], py[q], dz2[q]);
+        acc[q] = source_term<AT>(e0, px[q], py[q], dz2[q], acc[q]);
+        acc[q] = source_term<AT>(e1, px[q], py[q], dz2[q], acc[q]);
       }
     }
     if (j < L.n) {
       const SrcEntryT<AT> e0 = load_entry(en + j);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += source_term<AT>(e0, px[q], py[q], dz2[q]);
+      for (int q = 0; q < 4; ++q) acc[q] = source_term<AT>(e0, px[q], py[q], dz2[q], acc[q]);
     }
   }
 #pragma unroll
@@ -201,7 +229,11 @@ extern __shared__ float4 ms_ff_smem[];
 // (FF_FLOATS floats: k_track keeps it in shared memory, ms_ff_smem; the
 // hybrid kernel, whose shared memory holds the network, reads it through the
 // caches).  The other sources are summed point by point as in temps4.
-// n_near and n_far return the level's two counts (warp-uniform).
+// n_near and n_far return the level's two counts (warp-uniform).  py and pz
+// are the row's y and z in every lane (lane 0's first point, broadcast): a
+// lane whose four points all lie past the specimen's end (a ragged last
+// tile) holds point 0's coordinates, and the node sums of all lanes are added
+// across the warp.
 __device__ __forceinline__ void temps4_far(const SrcLevelT<float>& L, const SrcEntryT<float>* en,
                                            const float* px, float py, float pz, float x_first,
                                            float x_span, float dist, int lane, float* T,
@@ -232,14 +264,14 @@ __device__ __forceinline__ void temps4_far(const SrcLevelT<float>& L, const SrcE
       source_offsets<float>(e0, py, x0, p0);
       const float q0 = fmaf(p0, p0, dz2);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += source_term_x<float>(e0, fmaf(px[q], e0.ux, x0), q0);
+      for (int q = 0; q < 4; ++q) acc[q] = source_term_x<float>(e0, fmaf(px[q], e0.ux, x0), q0, acc[q]);
     }
     for (int j = g; j < cnt; j += 4)
       if ((fm >> j) & 1u) {
         const SrcEntryT<float> e0 = load_entry(en + j0 + j);
         float x0, p0;
         source_offsets<float>(e0, py, x0, p0);
-        fk += source_term_x<float>(e0, fmaf(xk, e0.ux, x0), fmaf(p0, p0, dz2));
+        fk = source_term_x<float>(e0, fmaf(xk, e0.ux, x0), fmaf(p0, p0, dz2), fk);
       }
   }
   if (nf > 0) {
@@ -267,7 +299,7 @@ __device__ __forceinline__ AT temp1(const SrcLevelT<AT>& L, const SrcEntryT<AT>*
                                     AT pz) {
   AT acc = AT(0);
   const AT dz2 = depth2<AT>(pz, L.z_surf);
-  for (int j = 0; j < L.n; ++j) acc += source_term<AT>(load_entry(en + j), px, py, dz2);
+  for (int j = 0; j < L.n; ++j) acc = source_term<AT>(load_entry(en + j), px, py, dz2, acc);
   return Fn<AT>::min(L.T0 + acc, L.T_max);
 }
 
@@ -312,6 +344,13 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
 // operation on the same operand, so the same bits).  Returns whether xeq
 // holds X_alpha^eq(T1) on return.
 //
+// With IDLE (the dense one-step launch, where most warps hold points at rest)
+// a warp whose points have X_alpha = X_alpha^eq and no martensite skips the
+// rate constants, and one whose forming points all have X_as = 0.9 skips
+// X_am^eq: both give exactly what the full evaluation gives (no rate acts;
+// formation adds X_am^eq (0.9 - X_as) / 0.9 = 0), at two more votes per step,
+// which the other launches, whose warps are mostly busy, do not pay.
+//
 // With INC (the wide fraction types, whose state the caller keeps in FP64 or
 // as a compensated pair and passes here rounded to FP32) the step also
 // returns the Euler increments dt * rate of both fractions (du) and, in mod,
@@ -320,7 +359,7 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
 // where g set it.  If a point of the warp takes an initiation (the rare
 // branch), nothing is stepped and false is returned: the caller steps its
 // wide state point by point.
-template <typename OC, bool INC = false>
+template <typename OC, bool INC = false, bool IDLE = false>
 __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const float* T0,
                                             const float* T1, float dt, const bool* run,
                                             float* xs, float* xm, float* ax, OC& oc, float* xeq,
@@ -369,8 +408,38 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
   }
 
   // eq:explicit_integration with the rates at T^n; r1 and r3 exclude each
-  // other and share one lg2 / lg2 / ex2 triple
-  float k[4], las[4], lg[4], nas[4], nam[4];
+  // other and share one lg2 / lg2 / ex2 triple.  r1 and r3 carry a power of
+  // |X_alpha^eq - X_alpha| and r2 one of X_am, so where every point of the
+  // warp has X_alpha = X_alpha^eq and no martensite no rate acts: with IDLE
+  // the warp then skips the rate constants and takes d = 0, as the rates give.
+  float nas[4], nam[4];
+  bool any_rate = !IDLE;
+  if constexpr (IDLE) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      any_rate = any_rate || (run[q] && (xa[q] != xeq0[q] || xm[q] > 0.0f));
+    any_rate = __any_sync(FULL, any_rate);
+  }
+  if (!any_rate) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float d0 = 0.0f;
+      if constexpr (INC) {
+        du_as[q] = __fmul_rn(dt, d0);
+        du_am[q] = __fmul_rn(dt, d0);
+        nas[q] = __fadd_rn(xs[q], du_as[q]);
+        nam[q] = __fadd_rn(xm[q], du_am[q]);
+      } else {
+        nas[q] = euler_add<float, float>(xs[q], dt, d0);
+        nam[q] = euler_add<float, float>(xm[q], dt, d0);
+      }
+      if (run[q]) {
+        if (mid0[q]) oc.add(1, 0);
+        oc.add(1, 1);  // k_as
+      }
+    }
+  } else {
+  float k[4], las[4], lg[4];
   bool any_hi = false, any_am = false;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -414,8 +483,8 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
       nas[q] = __fadd_rn(xs[q], du_as[q]);
       nam[q] = __fadd_rn(xm[q], du_am[q]);
     } else {
-      nas[q] = xs[q] + float(dt * d_as);
-      nam[q] = xm[q] + float(dt * d_am);
+      nas[q] = euler_add<float, float>(xs[q], dt, d_as);
+      nam[q] = euler_add<float, float>(xm[q], dt, d_am);
     }
     if (run[q]) {
       if (mid0[q]) oc.add(1, 0);
@@ -424,6 +493,7 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
       if (hi) oc.add(1, 0.9f - xa[q] > 0.0f ? 2 : 1);
       if (xm[q] > 0.0f) oc.add(1, lo ? 1 : 2);
     }
+  }
   }
 
   // eq:explicit_correction at T^{n+1}
@@ -478,7 +548,24 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
     }
     if (run[q] && mid1[q]) oc.add(1, 0);
   }
-  if (__any_sync(FULL, any_form)) {
+  // Formation adds X_am^eq(T) (0.9 - X_as) / 0.9: nothing where X_as = 0.9,
+  // whatever X_am^eq, so with IDLE a warp whose forming points all sit there
+  // skips it (reading A3's literal form still sets X_am to that 0).
+  bool any_room = !IDLE;
+  const bool vote_form = __any_sync(FULL, any_form);
+  if constexpr (IDLE) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) any_room = any_room || (run[q] && form[q] && nas[q] != 0.9f);
+    any_room = __any_sync(FULL, any_room);
+  }
+  if (vote_form && !any_room) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (form[q]) {
+        if (m.martensite_literal) nam[q] = 0.0f;
+        if (run[q] && !(T1[q] < m.T_inf) && T1[q] <= m.T_am_start) oc.add(1, 0);
+      }
+  } else if (vote_form) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const bool ex = !(T1[q] < m.T_inf) && T1[q] <= m.T_am_start;

@@ -484,6 +484,24 @@ def test_model_transcendental_counts(ms, T, xas, xam, ex2, slow):
     plain.close()
 
 
+@pytest.mark.parametrize("dims", [(200, 7, 3), (250, 8, 4), (300, 5, 3)])
+def test_farfield_on_a_ragged_row_tile(ms, dims):
+    """The last tile of these grids lies inside one row but holds fewer than
+    128 points, so some lanes hold no point of the specimen.  The far field
+    sums the receding sources at the nodes of the tile's range in every lane
+    and adds the lanes' sums across the warp, all at the row's y and z: the
+    run must stay within 1e-5 of the direct sum and within the run tolerance
+    of the oracle (1800 steps: the receding sources of the first tracks are
+    far by then)."""
+    w = wl.block_256(dims=dims, n_tracks=4, n_steps=1800, T_thr=0.0)
+    assert w.n_points % 128 != 0
+    _, direct = gpu_workload(w, farfield_dist=0.0)
+    ctx, far = gpu_workload(w, farfield_dist=5e-3)
+    assert ctx.stats().farfield_point_sources > 0
+    assert max_abs_diff(far, np.stack(direct)) <= 1e-5
+    assert max_abs_diff(far, oracle_workload(w)) <= RUN_TOL
+
+
 def test_farfield_matches_the_direct_sum(ms):
     """ms_params.farfield_dist: in row tiles, sources at least 5 mm behind
     every point are summed at 8 Chebyshev nodes of the tile's x-range and

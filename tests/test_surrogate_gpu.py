@@ -205,6 +205,24 @@ def test_zero_network_hybrid_matches_window_oracle(ms, precision, stride, act):
     s.close()
 
 
+def test_zero_network_hybrid_ragged_row_tile(ms):
+    """The hybrid kernel's far field on grids whose last row tile holds fewer
+    than 128 points (lanes past the specimen's end): the zero network must
+    still follow orc_run_track_windows on every point."""
+    w = wl.block_256(dims=(200, 7, 3), n_tracks=4, n_steps=1800, T_thr=0.0)
+    s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32), 1, 4)
+    ctx, g = _run(ms, w, s, judge=0.0, steps_per_launch=128)
+    sp = w.specimens[0]
+    x, y, z = sp.grid.coords()
+    o = orc.State.uniform(w.n_points, w.init_xas, w.init_xam)
+    p = oracle_params()
+    orc.run_track_windows(o, sp.source, x, y, z, 0, w.n_steps, w.dt, p=p, stride=4, group=128)
+    T_last = orc.temperature(sp.source, x, y, z, w.n_steps * w.dt)[0]
+    assert max_abs_diff(g, np.stack(orc.fractions(o, T_last, p))) <= RUN_TOL
+    ctx.close()
+    s.close()
+
+
 def test_hybrid_rejects_fp64_and_bad_fraction(ms):
     s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
     ctx = ms.Context(1000, precision=ms.MS_F64)
