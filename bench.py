@@ -450,17 +450,18 @@ def d6_layouts(ms, torch, n=1 << 24, blocks=(1, 10, 100), steps=10, warmup=3):
 
 
 def dense_s1(ms, torch, steps=40, warmup=4):
-    """The dense mode of the hot kernel against HBM: k_track with no
-    skipping (T_thr = 0) and one step per launch (S = 1) on the 512 x 512 x 256
-    part grid (67.1M points; 805 MB of FP32 state, far above the 129 MB L2),
-    over the first steps of its first layer (one source).  Every launch reads
-    and writes every point's state once: 24 B per point-update of algorithmic
-    traffic, against the measured HBM copy bandwidth.  With the temperature
-    computed in the kernel at both levels of the step, the per-tile set-up
-    (point coordinates, the saturation temperature) and one model step per
-    load, this launch is bound by instruction issue, not by HBM; the HBM-bound
-    form of the same step is ms_step with the temperatures in memory
-    (roofline_ms_step)."""
+    """The dense mode of the hot path against HBM: ms_run_track with no
+    skipping (T_thr = 0) and one step per launch (S = 1) on the 512 x 512 x
+    256 part grid (67.1M points; 805 MB of FP32 state, far above the 129 MB
+    L2), over the first steps of its first layer (one source).  Every launch
+    reads and writes every point's state once: 24 B per point-update of
+    algorithmic traffic, against the measured HBM copy bandwidth.  These
+    launches take k_track_dense, the streaming form of the same step (bit for
+    bit k_track's results).  Each launch also computes the temperature of
+    every point at both levels of its step and runs the model on every point;
+    the model's compares and selects keep the ALU pipe busy, so the launch is
+    bound by instruction issue a little above the HBM time (the launch
+    without the model, timed separately, streams at ~0.78 of HBM)."""
     import workloads as wl
     from paper_2402_17580_gb300._binding import MS_FLAG_TIME_KERNELS
     w = wl.part_512()
@@ -480,16 +481,18 @@ def dense_s1(ms, torch, steps=40, warmup=4):
     bytes_launch = 24 * w.n_points
     gbs = bytes_launch / (ms_launch * 1e-3) / 1e9
     ctx.close()
-    return {"kernel": "k_track", "bound": "hbm", "workload": "part_512 grid, first layer",
+    return {"kernel": "k_track_dense", "bound": "hbm", "workload": "part_512 grid, first layer",
             "points": w.n_points, "steps_per_launch": 1, "T_thr": 0.0,
             "point_updates_per_s_kernel": w.n_points / (ms_launch * 1e-3),
             "ms_per_launch": round(ms_launch, 4), "bytes_per_launch": bytes_launch,
             "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS, "unit": "GB/s",
             "frac": round(gbs / HBM_PEAK_GBS, 4),
+            "model_point_steps_per_launch": st.model_point_steps / max(1, st.hot_kernel_launches),
             "note": "24 B per point-update (X_as, X_am, aux read and written once per launch); "
-                    "state 805 MB > L2, so every launch streams it from HBM; at S = 1 the "
-                    "launch is issue-bound (two temperature levels, per-tile set-up and one "
-                    "model step per load), see roofline_ms_step for the HBM-bound step"}
+                    "state 805 MB > L2, so every launch streams it from HBM; the temperature "
+                    "of both levels and the model step of every point are computed in the "
+                    "launch, which is issue-bound on the model's ALU work a little above the "
+                    "HBM time"}
 
 
 # ------------------------------------------------------------------ our arm
@@ -1089,13 +1092,16 @@ def coarsen_pass(ms, torch, stream, dims=(512, 512, 256), tol=1e-2, n_levels=6, 
     byts = 24 * n + total
     gbs = byts / (t * 1e-3) / 1e9
     del xas, xam, xb, mask, scratch
-    return {"kernel": "k_coarsen_l1 + k_coarsen_up", "bound": "hbm", "grid": "x".join(map(str, dims)),
+    return {"kernel": "k_coarsen_l12 + k_coarsen_up", "bound": "hbm", "grid": "x".join(map(str, dims)),
             "points": n, "levels": n_levels, "tol": tol, "ms_per_call": round(t, 4),
             "bytes_per_call": byts, "achieved": round(gbs, 1), "peak": HBM_PEAK_GBS,
             "unit": "GB/s", "frac": round(gbs / HBM_PEAK_GBS, 4),
             "coarsenable_per_level": counts,
             "note": "whole-call time (the counters' copy and the stream sync included); "
-                    "algorithmic bytes: the three FP64 fields once plus one byte per octant"}
+                    "algorithmic bytes: the three FP64 fields once plus one byte per octant; "
+                    "the level-1/2 kernel stages bricks of points in shared memory with "
+                    "asynchronous copies and takes minima and maxima on integer keys of the "
+                    "doubles, bound by the ALU pipe (64-bit compares)"}
 
 
 # window surrogates: name -> (hidden activation, temperature stride)

@@ -433,7 +433,8 @@ int ms_probe_sfu(int op, double* ops_per_s, double* sm_mhz);
  * octants per axis) and the single point of an axis with n = 1.  The octant
  * may be coarsened when, for each of X_as, X_am and X_beta, its largest
  * minus its smallest value over the octant's points is <= tol (one FP64
- * subtraction: the decision is exact).  A coarsenable octant's children are
+ * subtraction: the decision is exact; a NaN among the points makes the range
+ * NaN and the decision false).  A coarsenable octant's children are
  * coarsenable, so the masks nest.  This is the criterion the phases impose;
  * a mesh also coarsens by its own rules (the consolidated fraction, the
  * refinement kept near the active layer), which are not part of it.       */

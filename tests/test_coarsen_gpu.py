@@ -77,6 +77,27 @@ def test_masks_match_the_oracle_bit_for_bit(ms, dims, n_levels, tol, dyadic):
         assert 0 < counts[0] < got[0].size
 
 
+def test_negative_zero_and_nan_values(ms):
+    """The kernels order the values through integer keys of the doubles:
+    -0 and +0 (range 0), negative values, and a NaN, which reaches the
+    ranges of the octants that hold it (range <= tol is false there, as in
+    the oracle), must all give the oracle's masks."""
+    from paper_2402_17580_gb300 import _binding as B
+    dims, n_levels, tol = (37, 19, 11), 4, 1e-2
+    xas, xam, xb = synthetic_phases(dims, seed=5)
+    xam = xam.copy()
+    xam[::7] = -0.0
+    xb = xb - 1.5                      # negative values
+    xas = xas.copy()
+    xas[int(np.prod(dims)) // 2 + 3] = np.nan
+    got, counts = B.coarsen_mask(xas, xam, xb, dims, tol, n_levels)
+    ref = oc.coarsen_masks(xas, xam, xb, dims, tol, n_levels)
+    for l, (g, r) in enumerate(zip(got, ref), start=1):
+        np.testing.assert_array_equal(g, r, err_msg=f"level {l}")
+        assert counts[l - 1] == int(r.sum())
+    assert int(got[0].size - got[0].sum()) > 0
+
+
 def test_device_pointers_on_a_torch_stream(ms):
     torch = pytest.importorskip("torch")
     from paper_2402_17580_gb300 import _binding as B
