@@ -515,7 +515,10 @@ struct UDiv {
 //    of warps at rest (point_step4's IDLE form: the same values);
 //  * the non-finite check sums the eight fractions (bounded by 1 when
 //    finite) and tests the sum.
-constexpr int DENSE_CHUNK = 4;
+#ifndef MS_DENSE_CHUNK
+#define MS_DENSE_CHUNK 4
+#endif
+constexpr int DENSE_CHUNK = MS_DENSE_CHUNK;
 constexpr int DENSE_THREADS = 128;
 // Minimum resident 128-thread blocks per SM: 5 (102 registers, 20 warps)
 // measured fastest on the 512 x 512 x 64 and x 256 grids against 4, 6, 7, 8.
@@ -536,6 +539,8 @@ __device__ __forceinline__ void prefetch_dense(const TrackArgs<float, float>& a,
 // changes), so that the grid data does not hold registers across the tile.
 struct DenseSpec {
   int64_t n;
+  const SrcLevelT<float>* lv;  // the specimen's two levels
+  const SrcEntryT<float>* en;  // and their sources
   int32_t tile0, nx, ny, k_off, sub, small;
   float z_tol, ox, oy, oz, dx, dy, dz;
   UDiv dvx, dvy;
@@ -554,7 +559,8 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
     __syncthreads();
   }
   NoCount oc;
-  unsigned long long done = 0, n_src = 0, n_model = 0, ff_nodes = 0, ff_pairs = 0;
+  unsigned long long n_src = 0, n_model = 0, ff_nodes = 0, ff_pairs = 0;
+  unsigned done = 0;
   int s_cur = -1;  // the warp's specimen (warp-uniform)
   if (lane == 0 && warp * DENSE_CHUNK < a.n_tiles)
     prefetch_dense(a, warp * DENSE_CHUNK, min((warp + 1) * DENSE_CHUNK, a.n_tiles));
@@ -563,13 +569,22 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
     if (lane == 0 && c1 * DENSE_CHUNK < a.n_tiles)
       prefetch_dense(a, c1 * DENSE_CHUNK, min((c1 + 1) * DENSE_CHUNK, a.n_tiles));
     const int t_end = min((c + 1) * DENSE_CHUNK, a.n_tiles);
+    // the chunk's counts, in 32 bits (a chunk's are far below 2^32)
+    unsigned src_c = 0, model_c = 0, fsrc_c = 0, fpair_c = 0;
+    // the grid indices of the previous tile's first point, where the next
+    // tile's follow by one carry (rows of at least TILE points)
+    int32_t ci = 0, cj = 0, ck = 0;
+    bool have_ijk = false;
     for (int tile = c * DENSE_CHUNK; tile < t_end; ++tile) {
       const int s = a.tile_spec[tile];
       if (s != s_cur) {
         s_cur = s;
+        have_ijk = false;
         if (lane == 0) {
           const SpecDev& sp = a.specs[s];
           ds.n = sp.n;
+          ds.lv = a.levels + int64_t(s) * 2;
+          ds.en = a.entries + int64_t(s) * 2 * a.slots;
           ds.tile0 = int32_t(sp.tile0);
           ds.nx = sp.nx;
           ds.ny = sp.ny;
@@ -585,9 +600,18 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
         }
         __syncwarp();
       }
-      const int64_t li_first = int64_t(tile - ds.tile0) * TILE;
-      const int64_t left = ds.n - li_first;
-      const int rem = left < TILE ? int(left) : TILE;  // points of the tile, 1 .. 128
+      const bool small = ds.small != 0;
+      int64_t li_first;
+      int rem;  // points of the tile, 1 .. 128
+      if (small) {
+        const int32_t l32 = (tile - ds.tile0) * TILE, left = int32_t(ds.n) - l32;
+        li_first = l32;
+        rem = left < TILE ? left : TILE;
+      } else {
+        li_first = int64_t(tile - ds.tile0) * TILE;
+        const int64_t left = ds.n - li_first;
+        rem = left < TILE ? int(left) : TILE;
+      }
       const int64_t g0 = int64_t(tile) * TILE + lane * 4;
       bool valid[4];
 #pragma unroll
@@ -599,16 +623,33 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
       Vec4<float>::load(a.aux + g0, ax);
 
       // the tile's first grid point; a row tile keeps one (j, k)
-      const bool sub = ds.sub != 0;
       float px[4], py[4], pz[4];
       bool row = false;
       int32_t col0 = 0;
-      if (ds.small) {  // 32-bit indices (the conversions stay off the FP64 pipe)
-        const uint32_t l = uint32_t(li_first);
-        const uint32_t r = ds.dvx.div(l);
-        const int32_t i0 = int32_t(l - r * uint32_t(ds.nx));
-        const int32_t k0 = int32_t(ds.dvy.div(r));
-        const int32_t j0 = int32_t(r) - k0 * ds.ny;
+      if (small) {  // 32-bit indices (the conversions stay off the FP64 pipe)
+        int32_t i0, j0, k0;
+        if (have_ijk) {
+          i0 = ci + TILE;
+          j0 = cj;
+          k0 = ck;
+          if (i0 >= ds.nx) {
+            i0 -= ds.nx;
+            if (++j0 == ds.ny) {
+              j0 = 0;
+              ++k0;
+            }
+          }
+        } else {
+          const uint32_t l = uint32_t(li_first);
+          const uint32_t r = ds.dvx.div(l);
+          i0 = int32_t(l - r * uint32_t(ds.nx));
+          k0 = int32_t(ds.dvy.div(r));
+          j0 = int32_t(r) - k0 * ds.ny;
+        }
+        ci = i0;
+        cj = j0;
+        ck = k0;
+        have_ijk = ds.nx >= TILE;
         col0 = i0;
         row = i0 + rem - 1 < ds.nx;
         if (row) {
@@ -629,44 +670,47 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
         int64_t col;
         point_coords4<float>(a.specs[s], li_first + lane * 4, valid, px, py, pz, col);
         const int64_t c0 = __shfl_sync(0xffffffffu, col, 0);
-        if (!sub) {
+        if (!ds.sub) {
           row = c0 + rem - 1 < ds.nx;
           col0 = int32_t(c0);
         }
       }
-      float x_first = 0.f, x_span = 0.f, ff_dist = 0.f, py_row = 0.f, pz_row = 0.f;
-      if constexpr (FAR) {
-        x_first = grid_coord<float>(ds.ox, float(col0), ds.dx);
-        x_span = float(TILE - 1) * ds.dx;
-        ff_dist = fmaxf(a.ff_dist, float(FF_RANGE_GUARD) * fabsf(x_span));
-        py_row = __shfl_sync(0xffffffffu, py[0], 0);
-        pz_row = __shfl_sync(0xffffffffu, pz[0], 0);
-      }
 
-      const SrcLevelT<float>* lv = a.levels + int64_t(s) * 2;
-      const SrcEntryT<float>* en = a.entries + int64_t(s) * 2 * a.slots;
+      const SrcLevelT<float>* lv = ds.lv;
+      const SrcEntryT<float>* en = ds.en;
+      const SrcLevelT<float> L0 = lv[0], L1 = lv[1];
       float T[2][4];
       unsigned srcs = 0, fsrcs = 0;
-#pragma unroll
-      for (int l = 0; l < 2; ++l) {
-        const SrcLevelT<float> L = lv[l];
-        bool done_far = false;
+      const bool far0 = FAR && row && L0.axis == LEVEL_AXIS;
+      const bool far1 = FAR && row && L1.axis == LEVEL_AXIS;
+      if (row && L0.axis && L1.axis && !far0 && !far1 && L0.n == L1.n) {
+        temps4_x2(L0, en, L1, en + a.slots, px, py[0], pz[0], T[0], T[1]);
+        srcs = 2u * unsigned(L0.n);
+      } else {
+        float x_first = 0.f, x_span = 0.f, ff_dist = 0.f, py_row = 0.f, pz_row = 0.f;
         if constexpr (FAR) {
-          if (row && L.axis == LEVEL_AXIS) {
+          x_first = grid_coord<float>(ds.ox, float(col0), ds.dx);
+          x_span = float(TILE - 1) * ds.dx;
+          ff_dist = fmaxf(a.ff_dist, float(FF_RANGE_GUARD) * fabsf(x_span));
+          py_row = __shfl_sync(0xffffffffu, py[0], 0);
+          pz_row = __shfl_sync(0xffffffffu, pz[0], 0);
+        }
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const SrcLevelT<float>& L = l == 0 ? L0 : L1;
+          if ((l == 0 ? far0 : far1)) {
             int nn, nf;
-            temps4_far(L, en + int64_t(l) * a.slots, px, py_row, pz_row, x_first, x_span, ff_dist,
-                       lane, T[l], nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
+            temps4_far(L, en + int64_t(l) * a.slots, px, py_row, pz_row, x_first, x_span,
+                       ff_dist, lane, T[l], nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
             srcs += nn;
             fsrcs += nf;
-            done_far = true;
+          } else {
+            temps4<float>(L, en + int64_t(l) * a.slots, px, py, pz, row, T[l]);
+            srcs += L.n;
           }
         }
-        if (!done_far) {
-          temps4<float>(L, en + int64_t(l) * a.slots, px, py, pz, row, T[l]);
-          srcs += L.n;
-        }
       }
-      const float zlim = lv[1].z_surf + ds.z_tol;
+      const float zlim = L1.z_surf + ds.z_tol;
       bool run[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) run[q] = valid[q] && pz[q] <= zlim;
@@ -678,15 +722,21 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
       Vec4<float>::store(a.aux + g0, ax);
       const float sum = ((xs[0] + xs[1]) + (xs[2] + xs[3])) + ((xm[0] + xm[1]) + (xm[2] + xm[3]));
       if (!::isfinite(sum)) atomicOr(a.err, DEVERR_NONFINITE);
-      n_src += srcs * unsigned(rem);
-      n_model += unsigned(rem);
-      ff_nodes += fsrcs * unsigned(FF_NODES);
-      ff_pairs += fsrcs * unsigned(rem);
+      src_c += srcs * unsigned(rem);
+      model_c += unsigned(rem);
+      if constexpr (FAR) {
+        fsrc_c += fsrcs;
+        fpair_c += fsrcs * unsigned(rem);
+      }
       ++done;
     }
+    n_src += src_c;
+    n_model += model_c;
+    ff_nodes += (unsigned long long)fsrc_c * FF_NODES;
+    ff_pairs += fpair_c;
   }
   if (lane == 0 && done) {
-    atomicAdd(&a.work->tile_steps_active, done);
+    atomicAdd(&a.work->tile_steps_active, (unsigned long long)done);
     if (a.ops) {
       atomicAdd(&a.ops->source_evaluations, n_src);
       atomicAdd(&a.ops->model_point_steps, n_model);

@@ -214,6 +214,35 @@ __device__ __forceinline__ void temps4(const SrcLevelT<AT>& L, const SrcEntryT<A
   for (int q = 0; q < 4; ++q) T[q] = Fn<AT>::min(L.T0 + acc[q], L.T_max);
 }
 
+// temps4 at two levels with the same number of sources, for a row tile
+// whose levels both move along +-x (temps4's first form): one loop over the
+// sources evaluates both levels, each level summing its sources in order as
+// temps4 does, so each level gets temps4's bits.
+__device__ __forceinline__ void temps4_x2(const SrcLevelT<float>& La, const SrcEntryT<float>* ea,
+                                          const SrcLevelT<float>& Lb, const SrcEntryT<float>* eb,
+                                          const float* px, float py, float pz, float* Ta,
+                                          float* Tb) {
+  float acc_a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, acc_b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const float dza = depth2<float>(pz, La.z_surf), dzb = depth2<float>(pz, Lb.z_surf);
+  for (int j = 0; j < La.n; ++j) {
+    const SrcEntryT<float> e0 = load_entry(ea + j), e1 = load_entry(eb + j);
+    float x0, p0, x1, p1;
+    source_offsets<float>(e0, py, x0, p0);
+    source_offsets<float>(e1, py, x1, p1);
+    const float q0 = fmaf(p0, p0, dza), q1 = fmaf(p1, p1, dzb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc_a[q] = source_term_x<float>(e0, fmaf(px[q], e0.ux, x0), q0, acc_a[q]);
+      acc_b[q] = source_term_x<float>(e1, fmaf(px[q], e1.ux, x1), q1, acc_b[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    Ta[q] = fminf(La.T0 + acc_a[q], La.T_max);
+    Tb[q] = fminf(Lb.T0 + acc_b[q], Lb.T_max);
+  }
+}
+
 // Dynamic shared memory of the far-field kernel: the interpolation weights
 // and node positions (FF_FLOATS floats, see ms_internal.h).
 extern __shared__ float4 ms_ff_smem[];
@@ -359,6 +388,166 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
 // where g set it.  If a point of the warp takes an initiation (the rare
 // branch), nothing is stepped and false is returned: the caller steps its
 // wide state point by point.
+// point_step4 for a warp whose points all lie in the cold regime
+// T^n < T_as,end and T_inf <= T^{n+1} < T_am,start (room temperature up to
+// the martensite start: most points of a part most of the time).  There
+// X_alpha^eq = 0.9 at both levels, App. A's alpha_s -> beta entry cannot
+// hold, the regularisation cap does not act and martensite formation takes
+// its middle branch; this is point_step4's common branch with those choices
+// made once for the warp instead of per point, so it gives the same bits.
+// Used by point_step4's IDLE form; returns as point_step4 does.
+template <typename OC>
+__device__ __forceinline__ bool point_step4_cold(const ModelConstT<float>& m, const float* T0,
+                                                 const float* T1, float dt, const bool* run,
+                                                 float* xs, float* xm, float* ax, OC& oc,
+                                                 float* xeq) {
+  constexpr unsigned FULL = 0xffffffffu;
+  using F = Fn<float>;
+  float xa[4];
+  // a warp whose points all have no initiation, X_alpha = 0.9 and no
+  // martensite has no initiation to start either (that needs X_alpha <
+  // 0.9): one vote tells both
+  bool busy = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    xa[q] = xs[q] + xm[q];
+    busy = busy || (run[q] && (ax[q] != 0.0f || xa[q] != 0.9f || xm[q] > 0.0f));
+  }
+  bool any_rate = __any_sync(FULL, busy);
+  if (any_rate) {
+    bool rare = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      rare = rare || (run[q] && (ax[q] != 0.0f || (xa[q] < 0.9f && xs[q] == 0.0f)));
+    if (__any_sync(FULL, rare)) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (run[q]) point_step<float, float>(m, T0[q], T1[q], dt, xs[q], xm[q], ax[q], oc);
+      return false;
+    }
+    any_rate = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      any_rate = any_rate || (run[q] && (xa[q] != 0.9f || xm[q] > 0.0f));
+    any_rate = __any_sync(FULL, any_rate);
+  }
+  float nas[4], nam[4];
+  if (!any_rate) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float d0 = 0.0f;
+      nas[q] = euler_add<float, float>(xs[q], dt, d0);
+      nam[q] = euler_add<float, float>(xm[q], dt, d0);
+      if (run[q]) oc.add(1, 1);  // k_as
+    }
+  } else {
+    float k[4], las[4], lg[4];
+    bool any_hi = false, any_am = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      k[q] = k_alpha_s<float>(m, T0[q]);
+      las[q] = F::lg2(xs[q]);
+      lg[q] = 0.0f;
+      any_hi = any_hi || (run[q] && xa[q] > 0.9f);
+      any_am = any_am || (run[q] && xm[q] > 0.0f);
+    }
+    any_hi = __any_sync(FULL, any_hi);
+    if (any_hi) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float gap = 0.9f - xa[q];
+        lg[q] = gap > 0.0f ? F::lg2(gap) : -INFINITY;
+      }
+    }
+    any_am = __any_sync(FULL, any_am);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool lo = xa[q] < 0.9f, hi = xa[q] > 0.9f;
+      float d_as;
+      if (any_hi) {
+        const float kb = m.f * k[q];
+        const float r = pow_rate<float>(lo ? k[q] : -kb, lo ? m.pa : m.pb, lo ? las[q] : lg[q],
+                                        lo ? m.qa : m.qb, lo ? 0.9f - xa[q] : xa[q] - 0.9f);
+        d_as = lo || hi ? r : 0.0f;
+      } else {
+        const float r = pow_rate<float>(k[q], m.pa, las[q], m.qa, 0.9f - xa[q]);
+        d_as = lo ? r : 0.0f;
+      }
+      float d_am = 0.0f;
+      if (any_am && xm[q] > 0.0f) {
+        const float r2 = pow_rate<float>(k[q], m.pa, las[q], m.qa, xm[q]);
+        d_as += r2;
+        d_am = -r2;
+      }
+      nas[q] = euler_add<float, float>(xs[q], dt, d_as);
+      nam[q] = euler_add<float, float>(xm[q], dt, d_am);
+      if (run[q]) {
+        oc.add(1, 1);  // k_as
+        if (lo) oc.add(1, 2);
+        if (hi) oc.add(1, 0.9f - xa[q] > 0.0f ? 2 : 1);
+        if (xm[q] > 0.0f) oc.add(1, lo ? 1 : 2);
+      }
+    }
+  }
+  // eq:explicit_correction at T^{n+1}: no cap, X_alpha^eq = 0.9
+  bool any_big = false, any_run = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    nas[q] = nas[q] > 0.0f ? nas[q] : 0.0f;
+    nam[q] = nam[q] > 0.0f ? nam[q] : 0.0f;
+    any_big = any_big || (run[q] && nas[q] + nam[q] > 0.9f);
+    any_run = any_run || run[q];
+  }
+  if (__any_sync(FULL, any_big)) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = nas[q] + nam[q];
+      if (x > 0.9f) {
+        const float sc = 0.9f / x;
+        nas[q] *= sc;
+        nam[q] *= sc;
+      }
+    }
+  }
+  bool any_room = false;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (nas[q] + nam[q] > 0.9f) {
+      const float v = 0.9f - nas[q];
+      nam[q] = v > 0.0f ? v : 0.0f;
+    }
+    any_room = any_room || (run[q] && nas[q] != 0.9f);
+  }
+  // martensite formation, middle branch (T_inf <= T^{n+1} <= T_am,start)
+  if (__any_sync(FULL, any_run)) {
+    if (!__any_sync(FULL, any_room)) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (m.martensite_literal) nam[q] = 0.0f;
+        if (run[q]) oc.add(1, 0);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x0 = F::min(1.0f - F::ex2(m.kam_l2 * (T1[q] - m.T_am_start)), 0.9f);
+        const float e = x0 * (0.9f - nas[q]) * float(1.0 / 0.9);
+        if (m.martensite_literal) nam[q] = e;
+        else if (e > nam[q]) nam[q] = e;
+        if (run[q]) oc.add(1, 0);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (run[q]) {
+      xs[q] = nas[q];
+      xm[q] = nam[q];
+    }
+    xeq[q] = 0.9f;
+  }
+  return true;
+}
+
 template <typename OC, bool INC = false, bool IDLE = false>
 __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const float* T0,
                                             const float* T1, float dt, const bool* run,
@@ -367,6 +556,15 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
                                             float* du_am = nullptr, unsigned* mod = nullptr) {
   constexpr unsigned FULL = 0xffffffffu;
   using F = Fn<float>;
+  if constexpr (IDLE) {
+    static_assert(!INC, "the IDLE form is for the FP32 state");
+    bool cold = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      cold = cold && T0[q] < m.T_as_end && T1[q] < m.T_am_start && !(T1[q] < m.T_inf);
+    if (__all_sync(FULL, cold) && m.T_am_start < m.T_as_end && m.T_am_start <= m.T_as_start)
+      return point_step4_cold(m, T0, T1, dt, run, xs, xm, ax, oc, xeq);
+  }
   float xa[4], xeq0[4];
   bool mid0[4], any = false;
 #pragma unroll
