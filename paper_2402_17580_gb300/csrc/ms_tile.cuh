@@ -378,7 +378,10 @@ __device__ __forceinline__ float point_tsat(const ModelConstT<AT>& m, FT xas, FT
 // rate constants, and one whose forming points all have X_as = 0.9 skips
 // X_am^eq: both give exactly what the full evaluation gives (no rate acts;
 // formation adds X_am^eq (0.9 - X_as) / 0.9 = 0), at two more votes per step,
-// which the other launches, whose warps are mostly busy, do not pay.
+// which the other launches, whose warps are mostly busy, do not pay.  With
+// COLD (on with IDLE) a warp whose points all lie in the cold regime takes
+// point_step4_cold (the same bits); k_track's busy warps measured 1 % slower
+// with it, so k_track leaves it off.
 //
 // With INC (the wide fraction types, whose state the caller keeps in FP64 or
 // as a compensated pair and passes here rounded to FP32) the step also
@@ -548,7 +551,7 @@ __device__ __forceinline__ bool point_step4_cold(const ModelConstT<float>& m, co
   return true;
 }
 
-template <typename OC, bool INC = false, bool IDLE = false>
+template <typename OC, bool INC = false, bool IDLE = false, bool COLD = IDLE>
 __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const float* T0,
                                             const float* T1, float dt, const bool* run,
                                             float* xs, float* xm, float* ax, OC& oc, float* xeq,
@@ -556,8 +559,8 @@ __device__ __forceinline__ bool point_step4(const ModelConstT<float>& m, const f
                                             float* du_am = nullptr, unsigned* mod = nullptr) {
   constexpr unsigned FULL = 0xffffffffu;
   using F = Fn<float>;
-  if constexpr (IDLE) {
-    static_assert(!INC, "the IDLE form is for the FP32 state");
+  if constexpr (COLD) {
+    static_assert(!INC, "the cold-regime form is for the FP32 state");
     bool cold = true;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
