@@ -1041,6 +1041,7 @@ def part_segment_pass(ms, torch, stream, surrogate, seg_steps=20000, n_sub=10000
             rec["mlp_window_share"] = st.surrogate_windows / max(
                 1, st.surrogate_windows + st.ode_windows)
             rec["judge_max_err"] = st.judge_max_err
+            rec["judge_rejected"] = int(st.judge_rejected)
         out[name] = rec
         c.set_surrogate(None)
         c.close()
@@ -1150,6 +1151,7 @@ def hybrid_pass(ctx, w, srcs, args, ms, torch, stream, flush, plain_value, sampl
            "vs_plain": w.point_updates / (t * 1e-3) / plain_value,
            "mlp_window_share": st.surrogate_windows / max(1, st.surrogate_windows + st.ode_windows),
            "judge_samples": int(st.judge_samples), "judge_max_err": st.judge_max_err,
+           "judge_rejected": int(st.judge_rejected), "judge_tol": 5e-4,
            "training": {"windows": int(len(data.X)), "collect_s": round(t1 - t0, 2),
                         "train_s": round(t2 - t1, 2), "iters": 20000, "batch": 32768},
            "activation": ("gelu", "relu")[act], "window_steps": 8 * stride,

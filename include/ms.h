@@ -274,6 +274,8 @@ typedef struct ms_stats_t {
    * counts the point-source pairs evaluated directly                       */
   int64_t farfield_node_evaluations;
   int64_t farfield_point_sources;
+  int64_t judge_rejected;         /* judged tile-windows the judge sent back to
+                                     the explicit steps (ms_set_judge_tol)       */
 } ms_stats_t;
 
 typedef struct ms_ctx ms_ctx;
@@ -637,10 +639,22 @@ int ms_apply_correction(ms_ctx* ctx, const double* T, int32_t n_T, double* x_as,
  * and with the explicit steps elsewhere.  judge_frac in [0, 1] is the fraction of the 128-point tiles'
  * windows, drawn by a counter-based hash of (tile, level), whose MLP points
  * are also run with the explicit steps to measure the surrogate's error
- * (ms_stats); the MLP result is kept.
+ * (ms_stats); the MLP result is kept unless the judge's tolerance
+ * (ms_set_judge_tol) sends the tile-window back to the explicit steps.
  * The surrogate must outlive its attachment.  Requires MS_F32 or MS_KAHAN.
  * Errors: INVALID_ARG, UNSUPPORTED (other precisions). */
 int ms_set_surrogate(ms_ctx* ctx, const ms_surrogate* s, double judge_frac);
+
+#define MS_JUDGE_TOL_DEFAULT 5e-4
+/* The judge's tolerance (the paper has no surrogate; this is the hybrid
+ * path's own safeguard).  A judged 128-point tile-window whose largest
+ * |dX_as| or |dX_am| between the network's result and the explicit steps'
+ * exceeds tol takes the explicit steps' result for all its network points
+ * (fractions and App. A state), and ms_stats counts it in judge_rejected;
+ * tol = +inf keeps the network's result everywhere (the judge only
+ * measures).  Default MS_JUDGE_TOL_DEFAULT; applies from the next
+ * ms_run_track.  Errors: INVALID_ARG (NULL context, tol NaN or negative). */
+int ms_set_judge_tol(ms_ctx* ctx, double tol);
 
 /* ------------------------------------------------- grid thermal solver */
 /* An explicit finite-volume solver of the heat equation of Sec. 2.1 on a

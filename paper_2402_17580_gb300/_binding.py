@@ -69,7 +69,7 @@ class Stats(ctypes.Structure):
         ("judge_max_err", d), ("source_evaluations", i64), ("model_point_steps", i64),
         ("fp_iterations", i64), ("fp_unconverged", i64), ("model_sfu_ex2", i64),
         ("model_sfu_slow", i64), ("farfield_node_evaluations", i64),
-        ("farfield_point_sources", i64)]
+        ("farfield_point_sources", i64), ("judge_rejected", i64)]
 
 
 class ThermalParams(ctypes.Structure):
@@ -147,6 +147,7 @@ def load(build_if_missing: bool = True):
     lib.ms_surrogate_gradient.argtypes = [P, P, P, i64, P, ctypes.POINTER(d)]
     lib.ms_surrogate_train_step.argtypes = [P, P, P, i64, d, ctypes.POINTER(d)]
     lib.ms_set_surrogate.argtypes = [P, P, d]
+    lib.ms_set_judge_tol.argtypes = [P, d]
     lib.ms_apply_correction.argtypes = [P, P, i32, P, P, i64]
     lib.ms_verify.argtypes = [P, P, P, i64, P]
     lib.ms_thermal_params_default.argtypes = [ctypes.POINTER(ThermalParams)]
@@ -377,6 +378,11 @@ class Context:
         _check(self._lib.ms_set_surrogate(self._h, surrogate.handle if surrogate else None,
                                           float(judge_frac)), "ms_set_surrogate")
         self._surrogate = surrogate
+
+    def set_judge_tol(self, tol: float):
+        """ms_set_judge_tol: judged tile-windows whose network result differs
+        from the explicit steps' by more than tol take the explicit result."""
+        _check(self._lib.ms_set_judge_tol(self._h, float(tol)), "ms_set_judge_tol")
 
     def verify(self, ref: "Context", idx=None, n=None):
         """Device-side verification against another context (ms_verify):

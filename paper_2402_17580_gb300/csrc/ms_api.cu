@@ -97,6 +97,7 @@ struct ms_ctx {
   const ms::MlpDev* mlp = nullptr;
   int32_t mlp_act = MS_ACT_GELU, mlp_stride = 1;
   uint64_t judge_thresh = 0;
+  double judge_tol = MS_JUDGE_TOL_DEFAULT;
   ms::HybridCounters* hyb_d = nullptr;
   ms::OpCounters* ops_d = nullptr;       // work done by k_track
   float* ff_d = nullptr;                 // far-field weights and nodes (farfield_dist > 0)
@@ -421,6 +422,7 @@ int check_device_error(ms_ctx* c) {
     float e = 0.f;
     std::memcpy(&e, &hc.judge_err_bits, sizeof(e));
     c->st.judge_max_err = double(e);
+    c->st.judge_rejected = int64_t(hc.judge_rejected);
   }
   if (c->timed) {
     float ms_ = 0.f;
@@ -610,6 +612,7 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
         a.mlp = c->mlp;
         a.hyb = c->hyb_d;
         a.judge_thresh = c->judge_thresh;
+        a.judge_tol = c->judge_tol < 3.0e38 ? float(c->judge_tol) : INFINITY;
         a.level0 = c->step_n;
         a.mlp_stride = c->mlp_stride;
         const int64_t need = (c->n_tiles + ms::HYBRID_THREADS / 32 - 1) / (ms::HYBRID_THREADS / 32);
@@ -1358,6 +1361,17 @@ int ms_set_surrogate(ms_ctx* c, const ms_surrogate* s, double judge_frac) {
   c->mlp_act = act;
   c->mlp_stride = ms::surrogate_stride(s);
   c->judge_thresh = uint64_t(std::llround(judge_frac * 4294967296.0));
+  return MS_OK;
+}
+
+int ms_set_judge_tol(ms_ctx* c, double tol) {
+  if (!c) return fail(MS_ERR_INVALID_ARG, "NULL context");
+  if (!(tol >= 0.0)) return fail(MS_ERR_INVALID_ARG, "judge tolerance must be >= 0");
+  if (tol != c->judge_tol) {
+    MS_CUDA(cudaStreamSynchronize(c->stream));
+    drop_graphs(c);  // captured launches hold the old value
+    c->judge_tol = tol;
+  }
   return MS_OK;
 }
 

@@ -31,8 +31,10 @@
 //     their temperatures only in warps that have such points;
 //   - a fraction of the 128-point tiles' windows, chosen by a counter-based
 //     hash of (tile, level), has its MLP points also run with the explicit
-//     steps (the judge); the largest difference is kept in the counters and
-//     the MLP result stays.  Judging whole tiles keeps the explicit steps in
+//     steps (the judge); the largest difference is kept in the counters, and
+//     the MLP result stays unless the tile-window's largest difference passes
+//     the judge's tolerance, which sends it back to the explicit steps'
+//     result (ms_set_judge_tol).  Judging whole tiles keeps the explicit steps in
 //     the few warps that judge (a per-point draw would put a judged point in
 //     nearly every warp, and the warp would take the explicit steps for it).
 // Points that are cold and saturated at the window start and every sample
@@ -108,6 +110,7 @@ __device__ __forceinline__ float to_f<KF>(KF v) { return v.hi + v.lo; }
 
 struct HybCount {
   unsigned long long surr = 0, ode = 0, judged = 0;
+  unsigned long long rejected = 0;  // lane 0's count of the warp's sent-back tile-windows
   float err = 0.0f;
 };
 
@@ -391,6 +394,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
 #pragma unroll
         for (int q = 0; q < 4; ++q) Tp[q] = T1[q];
       }
+      float werr = 0.0f;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if (use_ode[q]) {
@@ -401,8 +405,26 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
         if (judged[q]) {
           const float e = fmaxf(fabsf(to_f(es[q]) - to_f(rs[q])), fabsf(to_f(em[q]) - to_f(rm[q])));
           cnt.err = fmaxf(cnt.err, e);
+          werr = fmaxf(werr, e);
         }
         T0[q] = Tp[q];
+      }
+      // the judge sends the tile-window back to the explicit steps when the
+      // network's largest difference on it passes judge_tol (a NaN too)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float w2 = __shfl_xor_sync(full, werr, o);
+        werr = (w2 > werr || w2 != w2) ? w2 : werr;
+      }
+      if (!(werr <= a.judge_tol)) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (judged[q]) {
+            rs[q] = es[q];
+            rm[q] = em[q];
+            ax[q] = ea[q];
+          }
+        if (lane == 0) ++cnt.rejected;
       }
     } else if (whole) {
 #pragma unroll
@@ -476,6 +498,7 @@ __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackA
     if (cnt.ode) atomicAdd(&a.hyb->ode_windows, cnt.ode);
     if (cnt.judged) atomicAdd(&a.hyb->judge_samples, cnt.judged);
     if (cnt.err > 0.0f) atomicMax(&a.hyb->judge_err_bits, __float_as_uint(cnt.err));
+    if (cnt.rejected) atomicAdd(&a.hyb->judge_rejected, cnt.rejected);
   }
 }
 

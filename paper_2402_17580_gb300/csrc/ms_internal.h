@@ -143,6 +143,7 @@ struct HybridCounters {
   unsigned long long surrogate_windows, ode_windows, judge_samples;
   unsigned int judge_err_bits;  // bits of the largest judged |dX| (>= 0, so integer order = float order)
   unsigned int pad;
+  unsigned long long judge_rejected;  // judged tile-windows sent back to the explicit steps
 };
 
 // Arguments of the run-track kernel (persistent warps pull 128-point tiles).
@@ -175,6 +176,7 @@ struct TrackArgs {
   const void* mlp;             // MlpDev of the attached surrogate
   HybridCounters* hyb;
   uint64_t judge_thresh;       // a window is judged if hash(point, level) < judge_thresh (2^32 = all)
+  float judge_tol;             // a judged tile-window with a larger |dX| takes the explicit result
   int64_t level0;              // global index of the launch's first level
   int32_t mlp_stride;          // levels between a window's temperature samples (1, 2, 4, 8, 16)
 };

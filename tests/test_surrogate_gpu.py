@@ -223,6 +223,54 @@ def test_zero_network_hybrid_ragged_row_tile(ms):
     s.close()
 
 
+def test_judge_sends_windows_back(ms):
+    """ms_set_judge_tol.  A zero network (g only over each window: about
+    1.6e-4 from the explicit oracle on this block) with every tile-window
+    judged.  At tol = +inf the judge only measures: the result is the
+    unjudged run's, bit for bit.  At tol = 0 every judged tile-window where
+    the network's result differs from the explicit steps' takes theirs: the
+    run then agrees with the FP64 explicit oracle to the FP32 path's run
+    tolerance, and ms_stats counts the windows sent back."""
+    w = wl.block_256(dims=(96, 96, 16), n_tracks=6, n_steps=4000)
+    zero = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32), 1, 8)
+
+    def run(judge, tol):
+        ctx = ms.Context(w.n_points, T_thr=w.T_thr)
+        ctx.set_points([sp.grid for sp in w.specimens])
+        ctx.fill_state(w.init_xas, w.init_xam)
+        ctx.set_surrogate(zero, judge)
+        ctx.set_judge_tol(tol)
+        ctx.run_track([sp.source for sp in w.specimens], w.n_steps, w.dt)
+        out = (ctx.fractions(), ctx.aux(), ctx.stats())
+        ctx.close()
+        return out
+
+    g0, a0, s0 = run(0.0, float("inf"))
+    gi, ai, si = run(1.0, float("inf"))
+    gr, ar, sr = run(1.0, 0.0)
+    for x, y in zip(g0, gi):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a0, ai)
+    assert si.judge_samples > 0 and si.judge_rejected == 0 and s0.judge_rejected == 0
+    assert sr.judge_rejected > 0
+    idx = np.random.default_rng(10).choice(w.n_points, 256, replace=False)
+    idx = np.unique(np.concatenate([idx, np.arange(0, w.n_points, 9973)]))
+    from tests._util import oracle_workload
+    o = oracle_workload(w, idx)
+    err_g = max_abs_diff(g0, o, idx)
+    err_r = max_abs_diff(gr, o, idx)
+    print(f"zero network {err_g:.3e}, judge sending back {sr.judge_rejected} windows {err_r:.3e}")
+    assert err_r <= RUN_TOL
+    assert err_r < 0.5 * err_g
+    with pytest.raises(ms.MSError):
+        c = ms.Context(16)
+        try:
+            c.set_judge_tol(float("nan"))
+        finally:
+            c.close()
+    zero.close()
+
+
 def test_hybrid_rejects_fp64_and_bad_fraction(ms):
     s = ms.Surrogate(np.zeros(omlp.N_PARAMS, dtype=np.float32))
     ctx = ms.Context(1000, precision=ms.MS_F64)
