@@ -117,6 +117,8 @@ WINDOW_MUTANTS = {
 
 
 def _run_pins_on_mutant(name, old, new, tmp_path, pins):
+    """The C oracle: compile the mutant and run the pins against it; returns
+    (caught, message)."""
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     mut = tmp_path / "mutant.c"
@@ -128,20 +130,9 @@ def _run_pins_on_mutant(name, old, new, tmp_path, pins):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+    return r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
-    _run_pins_on_mutant(name, *MUTANTS[name], tmp_path, "test_oracle_pins.py")
-
-
-@pytest.mark.parametrize("name", sorted(WINDOW_MUTANTS))
-def test_window_pins_catch_mutant(name, tmp_path):
-    _run_pins_on_mutant(name, *WINDOW_MUTANTS[name], tmp_path, "test_mlp_oracle.py")
-
-
-# mistakes in the thermal reference, caught by tests/test_thermal_oracle.py
 THERMAL_MUTANTS = {
     "face_mean_arithmetic": ("2.0 * a * b / np.where(s > 0.0, s, 1.0)", "0.5 * s"),
     "radiation_ambient_dropped": ("(Tt ** 4 - p.T_inf ** 4)", "Tt ** 4"),
@@ -176,7 +167,7 @@ def _run_py_pins_on_mutant(module, name, old, new, tmp_path, pins, select=None):
     """A Python part of the oracle: the mutant goes into a package ``oracle``
     of its own beside a copy of the pins, so that the pins import it and not
     the real one (a conftest checks that); the repository stays on the path
-    for the workload generators."""
+    for the workload generators.  Returns (caught, message)."""
     src = open(os.path.join(ROOT, "oracle", module + ".py")).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     pkg = tmp_path / "oracle"
@@ -192,13 +183,7 @@ def _run_py_pins_on_mutant(module, name, old, new, tmp_path, pins, select=None):
         cmd += ["-k", select]
     r = subprocess.run(cmd, cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
     # 1: a pin failed (a conftest that rejects the import ends with another code)
-    assert r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
-
-
-@pytest.mark.parametrize("name", sorted(THERMAL_MUTANTS))
-def test_thermal_pins_catch_mutant(name, tmp_path):
-    _run_py_pins_on_mutant("thermal", name, *THERMAL_MUTANTS[name], tmp_path,
-                           "test_thermal_oracle.py")
+    return r.returncode == 1, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
 
 
 # mistakes in the surrogate's reference network, caught by the network pins
@@ -228,12 +213,6 @@ MLP_MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
-def test_network_pins_catch_mutant(name, tmp_path):
-    _run_py_pins_on_mutant("mlp", name, *MLP_MUTANTS[name], tmp_path, "test_mlp_oracle.py",
-                           select="not windows")
-
-
 # mistakes in the coarsening criterion, caught by tests/test_coarsen_oracle.py
 COARSEN_MUTANTS = {
     "span_half_open": ("slice(i << level, ((i + 1) << level) + 1)", "slice(i << level, (i + 1) << level)"),
@@ -249,7 +228,66 @@ COARSEN_MUTANTS = {
 }
 
 
+# Every mutant is a compile and a pytest run of its own; they run in parallel
+# threads (each waits on its subprocesses) once per module, and each test
+# reads its mutant's outcome.
+def _jobs():
+    jobs = {}
+    for name, (old, new) in MUTANTS.items():
+        jobs[("c", name)] = (_run_pins_on_mutant, (name, old, new), "test_oracle_pins.py", None)
+    for name, (old, new) in WINDOW_MUTANTS.items():
+        jobs[("window", name)] = (_run_pins_on_mutant, (name, old, new), "test_mlp_oracle.py", None)
+    for module, table, pins, select in (("thermal", THERMAL_MUTANTS, "test_thermal_oracle.py", None),
+                                        ("mlp", MLP_MUTANTS, "test_mlp_oracle.py", "not windows"),
+                                        ("coarsen", COARSEN_MUTANTS, "test_coarsen_oracle.py", None)):
+        for name, (old, new) in table.items():
+            jobs[(module, name)] = (_run_py_pins_on_mutant, (module, name, old, new), pins, select)
+    return jobs
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    from concurrent.futures import ThreadPoolExecutor
+    jobs = _jobs()
+    dirs = {key: tmp_path_factory.mktemp("mutant_" + "_".join(key)) for key in jobs}
+
+    def run(key):
+        fn, args, pins, select = jobs[key]
+        d = dirs[key]
+        if fn is _run_pins_on_mutant:
+            return fn(*args, d, pins)
+        return fn(*args, d, pins, select=select)
+
+    with ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+        futures = {key: ex.submit(run, key) for key in jobs}
+        return {key: f.result() for key, f in futures.items()}
+
+
+def _check(outcomes, key):
+    caught, message = outcomes[key]
+    assert caught, message
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, outcomes):
+    _check(outcomes, ("c", name))
+
+
+@pytest.mark.parametrize("name", sorted(WINDOW_MUTANTS))
+def test_window_pins_catch_mutant(name, outcomes):
+    _check(outcomes, ("window", name))
+
+
+@pytest.mark.parametrize("name", sorted(THERMAL_MUTANTS))
+def test_thermal_pins_catch_mutant(name, outcomes):
+    _check(outcomes, ("thermal", name))
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_network_pins_catch_mutant(name, outcomes):
+    _check(outcomes, ("mlp", name))
+
+
 @pytest.mark.parametrize("name", sorted(COARSEN_MUTANTS))
-def test_coarsen_pins_catch_mutant(name, tmp_path):
-    _run_py_pins_on_mutant("coarsen", name, *COARSEN_MUTANTS[name], tmp_path,
-                           "test_coarsen_oracle.py")
+def test_coarsen_pins_catch_mutant(name, outcomes):
+    _check(outcomes, ("coarsen", name))
