@@ -192,6 +192,16 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   const bool far = a.ff != nullptr && row;
   const float py_row = __shfl_sync(full, py[0], 0);  // lane 0's first point is always valid
   const float pz_row = __shfl_sync(full, pz[0], 0);
+  // a tile across two rows (as in k_track): the far field over both rows' ranges
+  const int64_t span = min(sp.n - 1 - int64_t(tile - sp.tile0) * TILE, int64_t(TILE - 1));
+  const bool far2 = a.ff != nullptr && !row && !sp.idx && col0 + span < 2 * int64_t(sp.nx);
+  int m_two = 0;
+  float x_first_b = 0.f, y_b = 0.f, z_b = 0.f;
+  if (far2) {
+    m_two = int(sp.nx - col0);
+    x_first_b = grid_coord<float>(float(sp.ox), float(-m_two), float(sp.dx));
+    second_row_yz(py, pz, m_two, y_b, z_b);
+  }
   // the temperatures of 4 points at level lvl, far field where it applies
   auto temps = [&](int lvl, float* T) {
     const SrcLevelT<float> L = lv[lvl];
@@ -199,6 +209,10 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       int nn, nf;
       temps4_far(L, en + int64_t(lvl) * a.slots, px, py_row, pz_row, x_first, x_span, ff_dist,
                  lane, T, nn, nf, a.ff);
+    } else if (far2 && L.axis == LEVEL_AXIS) {
+      int nn, nf;
+      temps4_far2(L, en + int64_t(lvl) * a.slots, px, py_row, pz_row, y_b, z_b, m_two, x_first,
+                  x_first_b, x_span, ff_dist, lane, T, nn, nf, a.ff);
     } else {
       temps4<float>(L, en + int64_t(lvl) * a.slots, px, py, pz, row, T);
     }

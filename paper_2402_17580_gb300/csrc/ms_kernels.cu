@@ -224,6 +224,18 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
     py_row = __shfl_sync(0xffffffffu, py[0], 0);  // lane 0's first point is always valid
     pz_row = __shfl_sync(0xffffffffu, pz[0], 0);
   }
+  // a tile across two rows: the far field over both rows' ranges
+  bool two = false;
+  int m_two = 0;
+  AT x_first_b = AT(0), y_b = AT(0), z_b = AT(0);
+  if constexpr (FAR) {
+    two = !sp.idx && !row && col0 + span < 2 * int64_t(sp.nx);
+    if (two) {
+      m_two = int(sp.nx - col0);
+      x_first_b = grid_coord<AT>(AT(sp.ox), AT(-m_two), AT(sp.dx));
+      second_row_yz(py, pz, m_two, y_b, z_b);
+    }
+  }
 
   FT xs[4], xm[4];
   float ax[4];
@@ -239,7 +251,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   // valid points of this tile (all lanes agree): the work counters count them
   const int64_t rest = sp.n - int64_t(tile - sp.tile0) * TILE;
   const unsigned long long nv = (unsigned long long)(rest < TILE ? rest : TILE);
-  unsigned srcs = 0, models = 0, fsrcs = 0;  // per tile: <= 513 levels x slots
+  unsigned srcs = 0, models = 0, fsrcs = 0, fsrcs2 = 0;  // per tile: <= 513 levels x slots
   AT T0[4];
   float xeq[4];          // lockstep path: X_alpha^eq at T0, when have_xeq
   bool have_xeq = false;
@@ -254,6 +266,15 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
                    lane, T1, nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
         srcs += nn;
         fsrcs += nf;
+        done_far = true;
+      } else if (two && L.axis == LEVEL_AXIS) {
+        int nn, nf;
+        temps4_far2(L, en + int64_t(l) * a.slots, px, py_row, pz_row, y_b, z_b, m_two, x_first,
+                    x_first_b, x_span, ff_dist, lane, T1, nn, nf,
+                    reinterpret_cast<const float*>(ms_ff_smem));
+        srcs += nn;
+        fsrcs += nf;
+        fsrcs2 += nf;
         done_far = true;
       }
     }
@@ -336,7 +357,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   for (int q = 0; q < 4; ++q) ok = ok && finite_pair(xs[q], xm[q]);
   n_src += (unsigned long long)srcs * nv;
   n_model += (unsigned long long)models * nv;
-  ff_nodes += (unsigned long long)fsrcs * FF_NODES;
+  ff_nodes += (unsigned long long)(fsrcs + fsrcs2) * FF_NODES;  // two rows: 2 x 8 nodes
   ff_pairs += (unsigned long long)fsrcs * nv;
   if (!ok) atomicOr(a.err, DEVERR_NONFINITE);
   if (a.tile_tsat && skipping) {  // read by the active set, which runs only with T_thr > 0
@@ -675,12 +696,24 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
           col0 = int32_t(c0);
         }
       }
+      // a tile across two rows: the far field over both rows' ranges
+      bool two = false;
+      int m_two = 0;
+      float x_first_b = 0.f, y_b = 0.f, z_b = 0.f;
+      if constexpr (FAR) {
+        two = !row && !ds.sub && col0 + rem - 1 < 2 * ds.nx;
+        if (two) {
+          m_two = ds.nx - col0;
+          x_first_b = grid_coord<float>(ds.ox, float(-m_two), ds.dx);
+          second_row_yz(py, pz, m_two, y_b, z_b);
+        }
+      }
 
       const SrcLevelT<float>* lv = ds.lv;
       const SrcEntryT<float>* en = ds.en;
       const SrcLevelT<float> L0 = lv[0], L1 = lv[1];
       float T[2][4];
-      unsigned srcs = 0, fsrcs = 0;
+      unsigned srcs = 0, fsrcs = 0, fsrcs2 = 0;
       const bool far0 = FAR && row && L0.axis == LEVEL_AXIS;
       const bool far1 = FAR && row && L1.axis == LEVEL_AXIS;
       if (row && L0.axis && L1.axis && !far0 && !far1 && L0.n == L1.n) {
@@ -704,6 +737,14 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
                        ff_dist, lane, T[l], nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
             srcs += nn;
             fsrcs += nf;
+          } else if (FAR && two && L.axis == LEVEL_AXIS) {
+            int nn, nf;
+            temps4_far2(L, en + int64_t(l) * a.slots, px, py_row, pz_row, y_b, z_b, m_two,
+                        x_first, x_first_b, x_span, ff_dist, lane, T[l], nn, nf,
+                        reinterpret_cast<const float*>(ms_ff_smem));
+            srcs += nn;
+            fsrcs += nf;
+            fsrcs2 += nf;
           } else {
             temps4<float>(L, en + int64_t(l) * a.slots, px, py, pz, row, T[l]);
             srcs += L.n;
@@ -725,7 +766,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
       src_c += srcs * unsigned(rem);
       model_c += unsigned(rem);
       if constexpr (FAR) {
-        fsrc_c += fsrcs;
+        fsrc_c += fsrcs + fsrcs2;  // node sets: two for a tile across two rows
         fpair_c += fsrcs * unsigned(rem);
       }
       ++done;

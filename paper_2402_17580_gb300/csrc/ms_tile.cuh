@@ -322,6 +322,98 @@ __device__ __forceinline__ void temps4_far(const SrcLevelT<float>& L, const SrcE
   n_far = nf;
 }
 
+// For a tile whose points lie in two consecutive grid rows, points 0 .. m - 1
+// in the first: the second row's y and z, point m's (every lane must call
+// this with the same m; point m is always a point of the specimen).
+__device__ __forceinline__ void second_row_yz(const float* py, const float* pz, int m, float& y_b,
+                                              float& z_b) {
+  const int q = m & 3;
+  const float y = q == 0 ? py[0] : (q == 1 ? py[1] : (q == 2 ? py[2] : py[3]));
+  const float z = q == 0 ? pz[0] : (q == 1 ? pz[1] : (q == 2 ? pz[2] : pz[3]));
+  y_b = __shfl_sync(0xffffffffu, y, m >> 2);
+  z_b = __shfl_sync(0xffffffffu, z, m >> 2);
+}
+
+// temps4_far for a tile whose points lie in two consecutive grid rows: the
+// first m points in row A (y_a, z_a) from x_first_a on, the others in row B
+// (y_b, z_b) from the grid's first column on.  Row B's points take the
+// range [x_first_b, x_first_b + x_span] with x_first_b = x_first_a of B's
+// first point minus m columns, so that point p of the tile sits at position
+// p / 127 of its own row's range and one table of weights serves both.  A
+// source is far when it is far from both ranges; its node sums are taken at
+// 8 nodes of each range (lane (k, r, g) = (lane & 7, lane >> 3 & 1, lane >>
+// 4): node k of range r for every second far source), and each point
+// interpolates from its own row's nodes.  The near sources are summed point
+// by point at each point's row (as temps4 sums them for such a tile: the same
+// bits where no source is far).  n_near, n_far: the level's counts
+// (warp-uniform); the node evaluations are 2 FF_NODES per far source.
+__device__ __forceinline__ void temps4_far2(const SrcLevelT<float>& L, const SrcEntryT<float>* en,
+                                            const float* px, float y_a, float z_a, float y_b,
+                                            float z_b, int m, float x_first_a, float x_first_b,
+                                            float x_span, float dist, int lane, float* T,
+                                            int& n_near, int& n_far, const float* ffw) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const float dza = depth2<float>(z_a, L.z_surf), dzb = depth2<float>(z_b, L.z_surf);
+  bool in_b[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) in_b[q] = lane * 4 + q >= m;
+  const int r = (lane >> 3) & 1, g = lane >> 4;
+  const float s_k = ffw[FF_NODES * TILE + (lane & (FF_NODES - 1))];
+  const float xk = fmaf(x_span, s_k, r ? x_first_b : x_first_a);
+  const float yk = r ? y_b : y_a, dzk = r ? dzb : dza;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float fk = 0.0f;
+  int nn = 0, nf = 0;
+  for (int j0 = 0; j0 < L.n; j0 += 32) {
+    const int cnt = L.n - j0 < 32 ? L.n - j0 : 32;
+    bool far = false;
+    if (lane < cnt) {
+      const SrcEntryT<float> e = load_entry(en + j0 + lane);
+      const float xa = fmaf(x_first_a, e.ux, -e.s_xi), xb = fmaf(x_first_a + x_span, e.ux, -e.s_xi);
+      const float xc = fmaf(x_first_b, e.ux, -e.s_xi), xd = fmaf(x_first_b + x_span, e.ux, -e.s_xi);
+      far = fmaxf(fmaxf(xa, xb), fmaxf(xc, xd)) <= -dist;
+    }
+    const unsigned fm = __ballot_sync(FULL, far);
+    const unsigned all = cnt == 32 ? FULL : (1u << cnt) - 1u;
+    nf += __popc(fm);
+    nn += cnt - __popc(fm);
+    for (unsigned mm = all & ~fm; mm; mm &= mm - 1) {
+      const SrcEntryT<float> e0 = load_entry(en + j0 + __ffs(mm) - 1);
+      float x0a, p0a, x0b, p0b;
+      source_offsets<float>(e0, y_a, x0a, p0a);
+      source_offsets<float>(e0, y_b, x0b, p0b);
+      const float qa = fmaf(p0a, p0a, dza), qb = fmaf(p0b, p0b, dzb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        acc[q] = source_term_x<float>(e0, fmaf(px[q], e0.ux, in_b[q] ? x0b : x0a),
+                                      in_b[q] ? qb : qa, acc[q]);
+    }
+    for (int j = g; j < cnt; j += 2)
+      if ((fm >> j) & 1u) {
+        const SrcEntryT<float> e0 = load_entry(en + j0 + j);
+        float x0, p0;
+        source_offsets<float>(e0, yk, x0, p0);
+        fk = source_term_x<float>(e0, fmaf(xk, e0.ux, x0), fmaf(p0, p0, dzk), fk);
+      }
+  }
+  if (nf > 0) {
+    fk += __shfl_xor_sync(FULL, fk, 16);
+#pragma unroll
+    for (int k = 0; k < FF_NODES; ++k) {
+      const float Fa = __shfl_sync(FULL, fk, k), Fb = __shfl_sync(FULL, fk, k + FF_NODES);
+      const float4 w = reinterpret_cast<const float4*>(ffw + k * TILE)[lane];
+      acc[0] = fmaf(w.x, in_b[0] ? Fb : Fa, acc[0]);
+      acc[1] = fmaf(w.y, in_b[1] ? Fb : Fa, acc[1]);
+      acc[2] = fmaf(w.z, in_b[2] ? Fb : Fa, acc[2]);
+      acc[3] = fmaf(w.w, in_b[3] ? Fb : Fa, acc[3]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) T[q] = fminf(L.T0 + acc[q], L.T_max);
+  n_near = nn;
+  n_far = nf;
+}
+
 // Temperature of one point; the same arithmetic and order as temps4.
 template <typename AT>
 __device__ __forceinline__ AT temp1(const SrcLevelT<AT>& L, const SrcEntryT<AT>* en, AT px, AT py,

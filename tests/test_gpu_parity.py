@@ -502,6 +502,24 @@ def test_farfield_on_a_ragged_row_tile(ms, dims):
     assert max_abs_diff(far, oracle_workload(w)) <= RUN_TOL
 
 
+@pytest.mark.parametrize("dims", [(200, 9, 4), (100, 12, 3), (160, 7, 3)])
+def test_farfield_on_tiles_across_two_rows(ms, dims):
+    """Rows of fewer than 256 points, not a multiple of 128: most 128-point
+    tiles hold the end of one grid row and the start of the next.  The far
+    field serves them over both rows' x-ranges (8 nodes each, each point
+    interpolating from its own row's nodes); tiles across three rows sum
+    point by point.  The run must stay within 1e-5 of the direct sum and
+    within the run tolerance of the oracle, with the far field taking a
+    large share of the point-source pairs."""
+    w = wl.block_256(dims=dims, n_tracks=4, n_steps=3000, T_thr=0.0)
+    _, direct = gpu_workload(w, farfield_dist=0.0)
+    ctx, far = gpu_workload(w, farfield_dist=5e-3)
+    st = ctx.stats()
+    assert st.farfield_point_sources > 0.3 * (st.farfield_point_sources + st.source_evaluations)
+    assert max_abs_diff(far, np.stack(direct)) <= 1e-5
+    assert max_abs_diff(far, oracle_workload(w)) <= RUN_TOL
+
+
 def test_farfield_matches_the_direct_sum(ms):
     """ms_params.farfield_dist: in row tiles, sources at least 5 mm behind
     every point are summed at 8 Chebyshev nodes of the tile's x-range and
