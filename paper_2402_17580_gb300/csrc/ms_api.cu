@@ -92,6 +92,7 @@ struct ms_ctx {
   int sm_count = 0;
   int track_grid = 0;  // persistent grid size for the current layout
   int dense_grid = 0;  // grid of the dense one-step launch (k_track_dense)
+  int two_rows = 0;    // some tile lies across two grid rows (k_track's far field for it)
 
   // attached surrogate (hybrid kernel)
   const ms::MlpDev* mlp = nullptr;
@@ -322,6 +323,9 @@ int build_layout(ms_ctx* c) {
   }
   if (tiles > INT32_MAX / 2) return fail(MS_ERR_INVALID_ARG, "too many points (%lld tiles)", (long long)tiles);
   c->n_tiles = tiles;
+  c->two_rows = 0;
+  for (const auto& sp : c->specs_h)
+    if (!sp.idx && sp.nx % TILE != 0 && int64_t(sp.ny) * sp.nz > 1) c->two_rows = 1;
   std::vector<int32_t> ts(static_cast<size_t>(tiles));
   for (size_t s = 0; s < c->specs_h.size(); ++s)
     for (int32_t t = 0; t < c->specs_h[s].n_tiles; ++t) ts[size_t(c->specs_h[s].tile0 + t)] = int32_t(s);
@@ -603,6 +607,7 @@ int run_track_impl(ms_ctx* c, int64_t n_steps) {
     if constexpr (std::is_same<AT, float>::value) {
       a.ff = c->ff_d;
       a.ff_dist = float(c->prm.farfield_dist);
+      a.two_rows = c->two_rows;
     }
     if ((rc = kernel_event(c, false)) != MS_OK) return rc;
     bool hybrid = false;

@@ -153,7 +153,7 @@ __device__ __forceinline__ bool explicit_step4(const ModelConstT<float>& m, cons
   }
 }
 
-template <typename FT, int ACT>
+template <typename FT, int ACT, bool TWO>
 __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const MlpDev& W,
                                             HybWarp& sm, int tile, int lane, float fdt,
                                             HybCount& cnt) {
@@ -187,14 +187,14 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
   // far field (as in k_track): the tile's x-range, first to 128th point
   const int64_t col0 = __shfl_sync(full, col, 0);
   const float x_first = grid_coord<float>(float(sp.ox), float(int32_t(col0)), float(sp.dx));
-  const float x_span = float(TILE - 1) * float(sp.dx);
+  const float x_span = __fmul_rn(float(TILE - 1), float(sp.dx));
   const float ff_dist = fmaxf(a.ff_dist, FF_RANGE_GUARD * fabsf(x_span));
   const bool far = a.ff != nullptr && row;
   const float py_row = __shfl_sync(full, py[0], 0);  // lane 0's first point is always valid
   const float pz_row = __shfl_sync(full, pz[0], 0);
   // a tile across two rows (as in k_track): the far field over both rows' ranges
   const int64_t span = min(sp.n - 1 - int64_t(tile - sp.tile0) * TILE, int64_t(TILE - 1));
-  const bool far2 = a.ff != nullptr && !row && !sp.idx && col0 + span < 2 * int64_t(sp.nx);
+  const bool far2 = TWO && a.ff != nullptr && !row && !sp.idx && col0 + span < 2 * int64_t(sp.nx);
   int m_two = 0;
   float x_first_b = 0.f, y_b = 0.f, z_b = 0.f;
   if (far2) {
@@ -209,7 +209,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
       int nn, nf;
       temps4_far(L, en + int64_t(lvl) * a.slots, px, py_row, pz_row, x_first, x_span, ff_dist,
                  lane, T, nn, nf, a.ff);
-    } else if (far2 && L.axis == LEVEL_AXIS) {
+    } else if (TWO && far2 && L.axis == LEVEL_AXIS) {
       int nn, nf;
       temps4_far2(L, en + int64_t(lvl) * a.slots, px, py_row, pz_row, y_b, z_b, m_two, x_first,
                   x_first_b, x_span, ff_dist, lane, T, nn, nf, a.ff);
@@ -471,7 +471,7 @@ __device__ __forceinline__ void hybrid_tile(const TrackArgs<float, FT>& a, const
     if (lane == 0) a.tile_tsat[tile] = ts + 0.5f;
   }
 }
-template <typename FT, int ACT>
+template <typename FT, int ACT, bool TWO = false>
 __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackArgs<float, FT> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   MlpDev& W = *reinterpret_cast<MlpDev*>(smem);
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackA
     if (lane == 0) w = atomicAdd(&a.work->next, 1);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= n_work) break;
-    hybrid_tile<FT, ACT>(a, W, sm, a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w, lane,
+    hybrid_tile<FT, ACT, TWO>(a, W, sm, a.tile_list ? list_tile(a.tile_list, a.n_tiles, nb, w) : w, lane,
                     fdt, cnt);
     ++done;
   }
@@ -521,8 +521,12 @@ __global__ void __launch_bounds__(HYBRID_THREADS, 2) k_track_hybrid(const TrackA
 template <typename FT>
 int hybrid_blocks_per_sm(int activation) {
   auto k = activation == ACT_RELU ? k_track_hybrid<FT, ACT_RELU> : k_track_hybrid<FT, ACT_GELU>;
+  auto k2 = activation == ACT_RELU ? k_track_hybrid<FT, ACT_RELU, true>
+                                   : k_track_hybrid<FT, ACT_GELU, true>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(HYB_SMEM)) !=
-      cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(HYB_SMEM)) !=
+          cudaSuccess)
     return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, HYBRID_THREADS, HYB_SMEM) != cudaSuccess)
@@ -535,10 +539,16 @@ cudaError_t launch_track_hybrid(const TrackArgs<float, FT>& a, int activation, i
                                 cudaStream_t stream) {
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
   if (a.mlp_stride < 1 || a.mlp_stride > MLP_MAX_STRIDE) return cudaErrorInvalidValue;
-  if (activation == ACT_RELU)
-    k_track_hybrid<FT, ACT_RELU><<<unsigned(grid_blocks), HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+  const unsigned g = unsigned(grid_blocks);
+  // tiles across two grid rows take the far field in their own instantiation
+  if (activation == ACT_RELU && a.two_rows)
+    k_track_hybrid<FT, ACT_RELU, true><<<g, HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+  else if (activation == ACT_RELU)
+    k_track_hybrid<FT, ACT_RELU><<<g, HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+  else if (a.two_rows)
+    k_track_hybrid<FT, ACT_GELU, true><<<g, HYBRID_THREADS, HYB_SMEM, stream>>>(a);
   else
-    k_track_hybrid<FT, ACT_GELU><<<unsigned(grid_blocks), HYBRID_THREADS, HYB_SMEM, stream>>>(a);
+    k_track_hybrid<FT, ACT_GELU><<<g, HYBRID_THREADS, HYB_SMEM, stream>>>(a);
   return cudaGetLastError();
 }
 

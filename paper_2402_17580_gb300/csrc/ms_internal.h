@@ -177,6 +177,7 @@ struct TrackArgs {
   HybridCounters* hyb;
   uint64_t judge_thresh;       // a window is judged if hash(point, level) < judge_thresh (2^32 = all)
   float judge_tol;             // a judged tile-window with a larger |dX| takes the explicit result
+  int32_t two_rows;            // the layout has tiles across two grid rows (k_track's far field for them)
   int64_t level0;              // global index of the launch's first level
   int32_t mlp_stride;          // levels between a window's temperature samples (1, 2, 4, 8, 16)
 };

@@ -190,7 +190,7 @@ constexpr bool kLockstepWide = std::is_same<AT, float>::value && !IMPL &&
 // One 128-point tile for the launch's S steps (4 points per lane).  OC counts
 // the model's transcendentals per branch (SfuCount, MS_FLAG_COUNT_OPS) or
 // compiles the counting away (NoCount).
-template <typename AT, typename FT, bool IMPL, bool FAR, typename OC>
+template <typename AT, typename FT, bool IMPL, bool FAR, typename OC, bool TWO = false>
 __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile, int lane,
                                            unsigned long long& n_src, unsigned long long& n_model,
                                            unsigned& fp_it, unsigned& fp_unconv, OC& oc,
@@ -218,7 +218,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   AT x_first = AT(0), x_span = AT(0), ff_dist = AT(0), py_row = AT(0), pz_row = AT(0);
   if constexpr (FAR) {
     x_first = grid_coord<AT>(AT(sp.ox), AT(int32_t(col0)), AT(sp.dx));  // col0 < nx: 32-bit
-    x_span = AT(TILE - 1) * AT(sp.dx);
+    x_span = Fn<AT>::mul_rn(AT(TILE - 1), AT(sp.dx));  // rounded: never fused into x_first + x_span
     // never closer than FF_RANGE_GUARD tile ranges, whatever the grid spacing
     ff_dist = Fn<AT>::max(a.ff_dist, AT(FF_RANGE_GUARD) * Fn<AT>::abs(x_span));
     py_row = __shfl_sync(0xffffffffu, py[0], 0);  // lane 0's first point is always valid
@@ -228,7 +228,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
   bool two = false;
   int m_two = 0;
   AT x_first_b = AT(0), y_b = AT(0), z_b = AT(0);
-  if constexpr (FAR) {
+  if constexpr (FAR && TWO) {
     two = !sp.idx && !row && col0 + span < 2 * int64_t(sp.nx);
     if (two) {
       m_two = int(sp.nx - col0);
@@ -267,7 +267,7 @@ __device__ __forceinline__ void track_tile(const TrackArgs<AT, FT>& a, int tile,
         srcs += nn;
         fsrcs += nf;
         done_far = true;
-      } else if (two && L.axis == LEVEL_AXIS) {
+      } else if (TWO && two && L.axis == LEVEL_AXIS) {
         int nn, nf;
         temps4_far2(L, en + int64_t(l) * a.slots, px, py_row, pz_row, y_b, z_b, m_two, x_first,
                     x_first_b, x_span, ff_dist, lane, T1, nn, nf,
@@ -396,7 +396,7 @@ __device__ __forceinline__ void prefetch_tile_state(const TrackArgs<AT, FT>& a, 
 // Persistent hot kernel: every warp pulls tiles (from the active list, or all
 // tiles) through an atomic cursor until the work runs out, so the grid is
 // sized to the resident capacity and no launch tail is left idle.
-template <typename AT, typename FT, bool IMPL, bool FAR = false, bool CNT = false>
+template <typename AT, typename FT, bool IMPL, bool FAR = false, bool CNT = false, bool TWO = false>
 __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
     k_track(const TrackArgs<AT, FT> a) {
   const int lane = threadIdx.x & 31;
@@ -437,7 +437,8 @@ __global__ void __launch_bounds__(256, FAR ? MS_TRACK_MINB_FAR : MS_TRACK_MINB)
                                   : -1;
       if (next >= 0 && lane == 0) prefetch_tile_state(a, next);
       const long long t0 = clock64();
-      track_tile<AT, FT, IMPL, FAR>(a, tile, lane, n_src, n_model, fp_it, fp_unconv, oc, n_ex2,
+      track_tile<AT, FT, IMPL, FAR, decltype(oc), TWO>(a, tile, lane, n_src, n_model, fp_it,
+                                                         fp_unconv, oc, n_ex2,
                                     n_slow, ff_nodes, ff_pairs);
       if (a.tile_cost && lane == 0) {  // cycles per level, the next launch's ordering hint
         const long long dc = clock64() - t0;
@@ -567,7 +568,7 @@ struct DenseSpec {
   UDiv dvx, dvy;
 };
 
-template <bool FAR>
+template <bool FAR, bool TWO = false>
 __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(const TrackArgs<float, float> a) {
   __shared__ DenseSpec spw[DENSE_THREADS / 32];
   const int lane = threadIdx.x & 31;
@@ -700,7 +701,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
       bool two = false;
       int m_two = 0;
       float x_first_b = 0.f, y_b = 0.f, z_b = 0.f;
-      if constexpr (FAR) {
+      if constexpr (FAR && TWO) {
         two = !row && !ds.sub && col0 + rem - 1 < 2 * ds.nx;
         if (two) {
           m_two = ds.nx - col0;
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
         float x_first = 0.f, x_span = 0.f, ff_dist = 0.f, py_row = 0.f, pz_row = 0.f;
         if constexpr (FAR) {
           x_first = grid_coord<float>(ds.ox, float(col0), ds.dx);
-          x_span = float(TILE - 1) * ds.dx;
+          x_span = __fmul_rn(float(TILE - 1), ds.dx);
           ff_dist = fmaxf(a.ff_dist, float(FF_RANGE_GUARD) * fabsf(x_span));
           py_row = __shfl_sync(0xffffffffu, py[0], 0);
           pz_row = __shfl_sync(0xffffffffu, pz[0], 0);
@@ -737,7 +738,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, MS_DENSE_MINB) k_track_dense(co
                        ff_dist, lane, T[l], nn, nf, reinterpret_cast<const float*>(ms_ff_smem));
             srcs += nn;
             fsrcs += nf;
-          } else if (FAR && two && L.axis == LEVEL_AXIS) {
+          } else if (FAR && TWO && two && L.axis == LEVEL_AXIS) {
             int nn, nf;
             temps4_far2(L, en + int64_t(l) * a.slots, px, py_row, pz_row, y_b, z_b, m_two,
                         x_first, x_first_b, x_span, ff_dist, lane, T[l], nn, nf,
@@ -1032,10 +1033,19 @@ cudaError_t track_launch(const TrackArgs<AT, FT>& a, int block_threads, int grid
     if (a.ff) {  // far field: the weights in shared memory
       const size_t ffb = FF_FLOATS * sizeof(float);
       if (!implicit) {
-        if (a.count_sfu)
+        // tiles across two grid rows take the far field in their own
+        // instantiation, so that layouts without them (rows of a multiple of
+        // TILE points) run the compact one
+        if (a.two_rows && std::is_same<FT, float>::value) {
+          if (a.count_sfu)
+            k_track<AT, FT, false, true, true, true><<<g, block_threads, ffb, stream>>>(a);
+          else
+            k_track<AT, FT, false, true, false, true><<<g, block_threads, ffb, stream>>>(a);
+        } else if (a.count_sfu) {
           k_track<AT, FT, false, true, true><<<g, block_threads, ffb, stream>>>(a);
-        else
+        } else {
           k_track<AT, FT, false, true><<<g, block_threads, ffb, stream>>>(a);
+        }
       } else if constexpr (kHasImplicit<AT, FT>) {
         k_track<AT, FT, true, true><<<g, block_threads, ffb, stream>>>(a);
       } else {
@@ -1161,10 +1171,14 @@ cudaError_t launch_track_dense(const TrackArgs<float, float>& a, int grid_blocks
   if (a.n_tiles <= 0 || grid_blocks <= 0) return cudaSuccess;
   if (a.n_levels != 2 || a.tile_list) return cudaErrorInvalidValue;
   const unsigned g = unsigned(grid_blocks);
-  if (a.ff)
-    k_track_dense<true><<<g, DENSE_THREADS, FF_FLOATS * sizeof(float), stream>>>(a);
-  else
+  if (a.ff) {
+    if (a.two_rows)  // tiles across two grid rows: their own instantiation (as in k_track)
+      k_track_dense<true, true><<<g, DENSE_THREADS, FF_FLOATS * sizeof(float), stream>>>(a);
+    else
+      k_track_dense<true><<<g, DENSE_THREADS, FF_FLOATS * sizeof(float), stream>>>(a);
+  } else {
     k_track_dense<false><<<g, DENSE_THREADS, 0, stream>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -227,6 +227,8 @@ extern "C" int ms_run_track_noalloc(const ms_params* p, const ms_grid* grid,
     if (p->farfield_dist > 0.0) {
       a.ff = sc->ff;
       a.ff_dist = float(p->farfield_dist);
+      // tiles across two grid rows: the instantiation ms_run_track takes
+      a.two_rows = grid->dims[0] % ms::TILE != 0 && int64_t(grid->dims[1]) * grid->dims[2] > 1;
     }
     if (ms::launch_track<float, float>(a, 128, grid_blocks, st) != cudaSuccess)
       return ms::record_error(MS_ERR_CUDA, "hot-kernel launch failed");
