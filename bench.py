@@ -805,8 +805,9 @@ def coupled_pass(w, ms, torch, n_steps=2000, warmup=200):
 
 def direct_pass(ctx, w, srcs, args, ms, torch, stream, flush, default_value, sample, rates):
     """The same pass with the far field off (farfield_dist = 0): every
-    point-source pair summed point by point, the sum SURVEY-style configs
-    specify.  Timed like the default passes; reports throughput, the SFU
+    point-source pair summed point by point, the superposition of every
+    started source of the layer as the workloads define it.  Timed like the
+    default passes; reports throughput, the SFU
     fraction (algorithmic and executed ops coincide here), max|dX| on the
     oracle sample and against the default (far-field) pass."""
     import numpy as np
